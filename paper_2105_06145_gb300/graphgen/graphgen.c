@@ -1,0 +1,362 @@
+/*
+ * graphgen.c -- seeded synthetic graph generators (input side only).
+ *
+ * These build the CSR inputs that stand in for the paper's workloads: the
+ * power-law social/web graphs (RMAT), the road networks (a jittered,
+ * bond-percolated grid) and plain grids (Sec. 7 "Experimental setup": social
+ * and web weights uniform in [1, 2^18), road weights derived from geometry).
+ * No SSSP arithmetic lives here.  Every random choice is a pure function of
+ * (seed, index) through splitmix64 (Steele, Lea, Flood 2014), so results do
+ * not depend on thread count or platform.  Floating point (road geometry) is
+ * compiled with -ffp-contract=off so x86-64 and AArch64 agree bit for bit.
+ *
+ * Output CSR: off[n+1] (uint64), tgt[m] and w[m] (uint32); the out-edges of
+ * every vertex are sorted by target id; every graph produced here is
+ * symmetric (each undirected edge stored in both directions with one weight)
+ * and has no self-loops or duplicate edges.
+ */
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+
+static inline uint64_t gg_sm64(uint64_t seed, uint64_t k)
+{
+    uint64_t z = seed + (k + 1u) * 0x9E3779B97F4A7C15ULL;
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ULL;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBULL;
+    return z ^ (z >> 31);
+}
+
+static inline uint64_t gg_mulhi(uint64_t a, uint64_t b)
+{
+    return (uint64_t)(((unsigned __int128)a * (unsigned __int128)b) >> 64);
+}
+
+/* Weight of the undirected edge {u,v}: uniform in [1, wmax_excl) via the
+ * multiply-high reduction of a 64-bit hash of the ordered pair (min, max). */
+static inline uint32_t gg_pair_weight(uint64_t seed, uint32_t u, uint32_t v, uint32_t wmax_excl)
+{
+    uint32_t a = u < v ? u : v, b = u < v ? v : u;
+    uint64_t h = gg_sm64(seed, ((uint64_t)a << 32) | b);
+    return 1u + (uint32_t)gg_mulhi(h, (uint64_t)(wmax_excl - 1u));
+}
+
+void graphgen_free(void* p) { free(p); }
+
+/* ------------------------------------------------------------------------ */
+/* 4-neighbour R x C grid, id = r*C + c, both directions stored.            */
+/* ------------------------------------------------------------------------ */
+uint64_t graphgen_grid_edges(uint32_t R, uint32_t C)
+{
+    return 2ull * ((uint64_t)R * (C ? C - 1 : 0) + (uint64_t)C * (R ? R - 1 : 0));
+}
+
+/* Fills caller arrays (off: R*C+1, tgt/w: graphgen_grid_edges).  wmax_excl=0
+ * gives unit weights. */
+int graphgen_grid(uint32_t R, uint32_t C, uint64_t wseed, uint32_t wmax_excl,
+                  uint64_t* off, uint32_t* tgt, uint32_t* w)
+{
+    uint64_t e = 0;
+    for (uint32_t r = 0; r < R; ++r) {
+        for (uint32_t c = 0; c < C; ++c) {
+            uint32_t id = r * C + c;
+            off[id] = e;
+            uint32_t nb[4];
+            int k = 0;
+            if (r > 0) nb[k++] = id - C;
+            if (c > 0) nb[k++] = id - 1;
+            if (c + 1 < C) nb[k++] = id + 1;
+            if (r + 1 < R) nb[k++] = id + C;
+            for (int j = 0; j < k; ++j) {
+                tgt[e] = nb[j];
+                w[e] = wmax_excl ? gg_pair_weight(wseed, id, nb[j], wmax_excl) : 1u;
+                ++e;
+            }
+        }
+    }
+    off[(uint64_t)R * C] = e;
+    return 0;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Sorting helpers: LSD radix sort of 64-bit keys on their low `bits` bits. */
+/* ------------------------------------------------------------------------ */
+static int gg_radix_sort(uint64_t* keys, uint64_t count, int bits)
+{
+    uint64_t* tmp = (uint64_t*)malloc(sizeof(uint64_t) * (count ? count : 1));
+    if (!tmp) return -1;
+    const int D = 11;
+    uint64_t* src = keys;
+    uint64_t* dst = tmp;
+    for (int shift = 0; shift < bits; shift += D) {
+        uint64_t hist[1u << 11];
+        memset(hist, 0, sizeof hist);
+        for (uint64_t i = 0; i < count; ++i) hist[(src[i] >> shift) & 2047u]++;
+        uint64_t sum = 0;
+        for (int d = 0; d < 2048; ++d) { uint64_t t = hist[d]; hist[d] = sum; sum += t; }
+        for (uint64_t i = 0; i < count; ++i) dst[hist[(src[i] >> shift) & 2047u]++] = src[i];
+        uint64_t* t = src; src = dst; dst = t;
+    }
+    if (src != keys) memcpy(keys, src, sizeof(uint64_t) * count);
+    free(tmp);
+    return 0;
+}
+
+/* Turns a sorted, unique list of directed pairs key = (u << sh) | v into CSR
+ * with pair weights.  Allocates *off, *tgt, *w. */
+static int gg_keys_to_csr(const uint64_t* keys, uint64_t m, uint32_t n, int sh,
+                          uint64_t wseed, uint32_t wmax_excl,
+                          uint64_t** off_out, uint32_t** tgt_out, uint32_t** w_out)
+{
+    uint64_t* off = (uint64_t*)calloc((size_t)n + 1, sizeof(uint64_t));
+    uint32_t* tgt = (uint32_t*)malloc(sizeof(uint32_t) * (m ? m : 1));
+    uint32_t* w = (uint32_t*)malloc(sizeof(uint32_t) * (m ? m : 1));
+    if (!off || !tgt || !w) { free(off); free(tgt); free(w); return -1; }
+    uint64_t mask = (sh >= 64) ? ~0ull : ((1ull << sh) - 1u);
+    for (uint64_t i = 0; i < m; ++i) {
+        uint32_t u = (uint32_t)(keys[i] >> sh), v = (uint32_t)(keys[i] & mask);
+        off[u + 1]++;
+        tgt[i] = v;
+        w[i] = wmax_excl ? gg_pair_weight(wseed, u, v, wmax_excl) : 1u;
+    }
+    for (uint32_t u = 0; u < n; ++u) off[u + 1] += off[u];
+    *off_out = off; *tgt_out = tgt; *w_out = w;
+    return 0;
+}
+
+/* Symmetrise `cnt` pairs held as key=(u<<sh)|v in keys[0..cnt), keys having
+ * room for 2*cnt entries: drop self-loops, add reversed copies, sort, unique.
+ * Returns the final count. */
+static int64_t gg_symmetrise(uint64_t* keys, uint64_t cnt, int sh)
+{
+    uint64_t mask = (1ull << sh) - 1u;
+    uint64_t k = 0;
+    for (uint64_t i = 0; i < cnt; ++i) {
+        uint64_t u = keys[i] >> sh, v = keys[i] & mask;
+        if (u != v) keys[k++] = keys[i];
+    }
+    uint64_t half = k;
+    for (uint64_t i = 0; i < half; ++i) {
+        uint64_t u = keys[i] >> sh, v = keys[i] & mask;
+        keys[k++] = (v << sh) | u;
+    }
+    if (gg_radix_sort(keys, k, 2 * sh)) return -1;
+    uint64_t out = 0;
+    for (uint64_t i = 0; i < k; ++i)
+        if (out == 0 || keys[i] != keys[out - 1]) keys[out++] = keys[i];
+    return (int64_t)out;
+}
+
+/* ------------------------------------------------------------------------ */
+/* RMAT (Chakrabarti, Zhan, Faloutsos 2004), Graph500-style: ef * 2^scale   */
+/* edge draws, `scale` quadrant choices each with probabilities (a,b,c,d),  */
+/* no noise, then a seeded random relabelling of the vertices, then         */
+/* symmetrise, drop self-loops, sort, unique.                                */
+/* ------------------------------------------------------------------------ */
+int graphgen_rmat(uint32_t scale, uint32_t edgefactor, double a, double b, double c,
+                  uint64_t gen_seed, uint64_t wseed, uint32_t wmax_excl,
+                  uint32_t* n_out, uint64_t* m_out,
+                  uint64_t** off, uint32_t** tgt, uint32_t** w)
+{
+    if (scale < 1 || scale > 30) return -1;
+    uint32_t n = 1u << scale;
+    uint64_t E = (uint64_t)edgefactor << scale;
+    uint64_t* keys = (uint64_t*)malloc(sizeof(uint64_t) * (2 * E ? 2 * E : 1));
+    uint32_t* perm = (uint32_t*)malloc(sizeof(uint32_t) * (size_t)n);
+    if (!keys || !perm) { free(keys); free(perm); return -1; }
+    const uint64_t two32 = 4294967296ull;
+    uint64_t ta = (uint64_t)(a * (double)two32);
+    uint64_t tb = ta + (uint64_t)(b * (double)two32);
+    uint64_t tc = tb + (uint64_t)(c * (double)two32);
+    uint64_t per_edge = (scale + 1) / 2;
+    for (uint64_t e = 0; e < E; ++e) {
+        uint32_t u = 0, v = 0;
+        uint64_t h = 0;
+        for (uint32_t lvl = 0; lvl < scale; ++lvl) {
+            if ((lvl & 1u) == 0) h = gg_sm64(gen_seed, e * per_edge + lvl / 2);
+            uint64_t r = (lvl & 1u) ? (h >> 32) : (h & 0xFFFFFFFFull);
+            uint32_t bu, bv;
+            if (r < ta) { bu = 0; bv = 0; }
+            else if (r < tb) { bu = 0; bv = 1; }
+            else if (r < tc) { bu = 1; bv = 0; }
+            else { bu = 1; bv = 1; }
+            u = (u << 1) | bu;
+            v = (v << 1) | bv;
+        }
+        keys[e] = ((uint64_t)u << scale) | v;
+    }
+    /* random relabelling: Fisher-Yates driven by a second splitmix stream */
+    for (uint32_t i = 0; i < n; ++i) perm[i] = i;
+    uint64_t pseed = gen_seed ^ 0xA5A5A5A55A5A5A5AULL;
+    for (uint32_t i = n - 1; i > 0; --i) {
+        uint32_t j = (uint32_t)gg_mulhi(gg_sm64(pseed, i), (uint64_t)i + 1u);
+        uint32_t t = perm[i]; perm[i] = perm[j]; perm[j] = t;
+    }
+    uint64_t mask = ((uint64_t)1 << scale) - 1u;
+    for (uint64_t e = 0; e < E; ++e) {
+        uint32_t u = perm[keys[e] >> scale], v = perm[keys[e] & mask];
+        keys[e] = ((uint64_t)u << scale) | v;
+    }
+    free(perm);
+    int64_t m = gg_symmetrise(keys, E, (int)scale);
+    if (m < 0) { free(keys); return -1; }
+    int rc = gg_keys_to_csr(keys, (uint64_t)m, n, (int)scale, wseed, wmax_excl, off, tgt, w);
+    free(keys);
+    if (rc) return rc;
+    *n_out = n;
+    *m_out = (uint64_t)m;
+    return 0;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Road-like graph: side x side grid of points, each jittered uniformly      */
+/* within +-jitter of its cell centre; every right/down neighbour edge kept  */
+/* with probability keep_num/2^64 (one draw per undirected edge); weight =   */
+/* floor(scale * Euclidean length) + 1.                                     */
+/* ------------------------------------------------------------------------ */
+static inline double gg_unit(uint64_t h) { return (double)(h >> 11) * (1.0 / 9007199254740992.0); }
+
+int graphgen_road(uint32_t side, uint64_t keep_num, double jitter, double wscale,
+                  uint64_t seed, uint32_t* n_out, uint64_t* m_out,
+                  uint64_t** off_out, uint32_t** tgt_out, uint32_t** w_out)
+{
+    uint64_t n64 = (uint64_t)side * side;
+    if (side == 0 || n64 > 0xFFFFFFFFull) return -1;
+    uint32_t n = (uint32_t)n64;
+    double* px = (double*)malloc(sizeof(double) * n64);
+    double* py = (double*)malloc(sizeof(double) * n64);
+    uint8_t* keep = (uint8_t*)malloc(n64); /* bit0: right edge, bit1: down edge */
+    uint64_t* off = (uint64_t*)calloc(n64 + 1, sizeof(uint64_t));
+    if (!px || !py || !keep || !off) { free(px); free(py); free(keep); free(off); return -1; }
+    uint64_t pseed = seed, eseed = seed ^ 0x5DEECE66DULL;
+    for (uint32_t r = 0; r < side; ++r)
+        for (uint32_t c = 0; c < side; ++c) {
+            uint64_t id = (uint64_t)r * side + c;
+            double jx = -jitter + 2.0 * jitter * gg_unit(gg_sm64(pseed, 2 * id));
+            double jy = -jitter + 2.0 * jitter * gg_unit(gg_sm64(pseed, 2 * id + 1));
+            px[id] = (double)c + jx;
+            py[id] = (double)r + jy;
+            uint8_t k = 0;
+            if (c + 1 < side && gg_sm64(eseed, 2 * id) < keep_num) k |= 1;
+            if (r + 1 < side && gg_sm64(eseed, 2 * id + 1) < keep_num) k |= 2;
+            keep[id] = k;
+        }
+    /* degrees */
+    for (uint32_t r = 0; r < side; ++r)
+        for (uint32_t c = 0; c < side; ++c) {
+            uint64_t id = (uint64_t)r * side + c;
+            if (keep[id] & 1) { off[id + 1]++; off[id + 2]++; }
+            if (keep[id] & 2) { off[id + 1]++; off[id + side + 1]++; }
+        }
+    for (uint64_t i = 0; i < n64; ++i) off[i + 1] += off[i];
+    uint64_t m = off[n64];
+    uint32_t* tgt = (uint32_t*)malloc(sizeof(uint32_t) * (m ? m : 1));
+    uint32_t* w = (uint32_t*)malloc(sizeof(uint32_t) * (m ? m : 1));
+    if (!tgt || !w) { free(px); free(py); free(keep); free(off); free(tgt); free(w); return -1; }
+    for (uint32_t r = 0; r < side; ++r)
+        for (uint32_t c = 0; c < side; ++c) {
+            uint64_t id = (uint64_t)r * side + c;
+            uint64_t e = off[id];
+            uint64_t nb[4];
+            int k = 0;
+            if (r > 0 && (keep[id - side] & 2)) nb[k++] = id - side;
+            if (c > 0 && (keep[id - 1] & 1)) nb[k++] = id - 1;
+            if (keep[id] & 1) nb[k++] = id + 1;
+            if (keep[id] & 2) nb[k++] = id + side;
+            for (int j = 0; j < k; ++j) {
+                double dx = px[nb[j]] - px[id];
+                double dy = py[nb[j]] - py[id];
+                double len = sqrt(dx * dx + dy * dy);
+                tgt[e] = (uint32_t)nb[j];
+                w[e] = (uint32_t)floor(wscale * len) + 1u;
+                ++e;
+            }
+        }
+    free(px); free(py); free(keep);
+    *n_out = n; *m_out = m;
+    *off_out = off; *tgt_out = tgt; *w_out = w;
+    return 0;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Uniform random multigraph for tests: m directed edges (u,v) with u, v     */
+/* uniform, weights uniform in [wlo, whi] (inclusive); self-loops and       */
+/* duplicates are kept unless the flags drop them.  Not symmetric.           */
+/* ------------------------------------------------------------------------ */
+int graphgen_random(uint32_t n, uint64_t m, uint32_t wlo, uint32_t whi, uint64_t seed,
+                    int drop_self_loops, uint64_t* m_out,
+                    uint64_t** off_out, uint32_t** tgt_out, uint32_t** w_out)
+{
+    if (n == 0 || whi < wlo) return -1;
+    uint64_t* us = (uint64_t*)malloc(sizeof(uint64_t) * (m ? m : 1));
+    uint64_t* off = (uint64_t*)calloc((size_t)n + 1, sizeof(uint64_t));
+    uint32_t* tgt = (uint32_t*)malloc(sizeof(uint32_t) * (m ? m : 1));
+    uint32_t* w = (uint32_t*)malloc(sizeof(uint32_t) * (m ? m : 1));
+    if (!us || !off || !tgt || !w) { free(us); free(off); free(tgt); free(w); return -1; }
+    uint64_t k = 0;
+    for (uint64_t e = 0; e < m; ++e) {
+        uint32_t u = (uint32_t)gg_mulhi(gg_sm64(seed, 3 * e), n);
+        uint32_t v = (uint32_t)gg_mulhi(gg_sm64(seed, 3 * e + 1), n);
+        uint64_t span = (uint64_t)whi - wlo + 1u;
+        uint32_t ww = wlo + (uint32_t)gg_mulhi(gg_sm64(seed, 3 * e + 2), span);
+        if (drop_self_loops && u == v) continue;
+        us[k] = ((uint64_t)u << 32) | v;
+        tgt[k] = ww; /* weight parked in tgt for the bucket pass */
+        ++k;
+    }
+    /* bucket by source, stable */
+    for (uint64_t i = 0; i < k; ++i) off[(us[i] >> 32) + 1]++;
+    for (uint32_t u = 0; u < n; ++u) off[u + 1] += off[u];
+    uint64_t* pos = (uint64_t*)malloc(sizeof(uint64_t) * ((size_t)n + 1));
+    uint32_t* t2 = (uint32_t*)malloc(sizeof(uint32_t) * (k ? k : 1));
+    if (!pos || !t2) { free(us); free(off); free(tgt); free(w); free(pos); free(t2); return -1; }
+    memcpy(pos, off, sizeof(uint64_t) * ((size_t)n + 1));
+    for (uint64_t i = 0; i < k; ++i) {
+        uint64_t p = pos[us[i] >> 32]++;
+        t2[p] = (uint32_t)(us[i] & 0xFFFFFFFFu);
+        w[p] = tgt[i];
+    }
+    free(tgt); free(us); free(pos);
+    *m_out = k; *off_out = off; *tgt_out = t2; *w_out = w;
+    return 0;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Connected components of the undirected view (union-find), used to draw   */
+/* sources from the largest component.  label[v] = 1 for v in the largest   */
+/* component, else 0.  Returns the largest component's size.                */
+/* ------------------------------------------------------------------------ */
+static uint32_t gg_find(uint32_t* p, uint32_t x)
+{
+    while (p[x] != x) { p[x] = p[p[x]]; x = p[x]; }
+    return x;
+}
+
+int64_t graphgen_largest_cc(uint32_t n, const uint64_t* off, const uint32_t* tgt, uint8_t* label)
+{
+    uint32_t* p = (uint32_t*)malloc(sizeof(uint32_t) * (size_t)(n ? n : 1));
+    uint32_t* sz = (uint32_t*)calloc(n ? n : 1, sizeof(uint32_t));
+    if (!p || !sz) { free(p); free(sz); return -1; }
+    for (uint32_t v = 0; v < n; ++v) p[v] = v;
+    for (uint32_t u = 0; u < n; ++u)
+        for (uint64_t e = off[u]; e < off[u + 1]; ++e) {
+            uint32_t a = gg_find(p, u), b = gg_find(p, tgt[e]);
+            if (a != b) { if (a < b) p[b] = a; else p[a] = b; }
+        }
+    uint32_t best = 0, bestsz = 0;
+    for (uint32_t v = 0; v < n; ++v) sz[gg_find(p, v)]++;
+    for (uint32_t v = 0; v < n; ++v)
+        if (sz[v] > bestsz) { bestsz = sz[v]; best = v; }
+    for (uint32_t v = 0; v < n; ++v) label[v] = (gg_find(p, v) == best);
+    free(p); free(sz);
+    return (int64_t)bestsz;
+}
+
+/* The k-th vertex (0-based, in id order) among those with label[v] != 0. */
+int64_t graphgen_kth_labelled(uint32_t n, const uint8_t* label, uint64_t k)
+{
+    for (uint32_t v = 0; v < n; ++v)
+        if (label[v]) { if (k == 0) return v; --k; }
+    return -1;
+}

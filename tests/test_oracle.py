@@ -1,0 +1,332 @@
+"""Pins for the CPU oracle (no GPU).
+
+The oracle is checked against things other than itself: published generator
+vectors, a textbook worked example, brute force (Bellman-Ford and exhaustive
+simple-path enumeration), closed forms (Manhattan distance, prefix sums,
+star weights), the invariants that characterise d, and the step bounds of
+Lemma 5.1 and Theorems 5.3 / 5.5.  A planted mistake in any oracle function
+(a dropped term, a wrong sign or index) fails at least one of these.
+"""
+import itertools
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_2105_06145_gb300 import graphgen as gg
+from conftest import golden_path
+
+INF = (1 << 64) - 1
+
+
+def read_golden(name):
+    rows = []
+    with open(golden_path(name)) as f:
+        for line in f:
+            line = line.strip()
+            if line and not line.startswith("#"):
+                rows.append(line.split())
+    return rows
+
+
+# --------------------------------------------------------------------------
+# generator behind the rho sampler
+# --------------------------------------------------------------------------
+
+def test_splitmix64_published_vector():
+    for idx, val in read_golden("splitmix64_state0.txt"):
+        assert oracle.splitmix64(0, int(idx)) == int(val, 16)
+
+
+# --------------------------------------------------------------------------
+# Dijkstra: textbook example, brute force, closed forms
+# --------------------------------------------------------------------------
+
+def test_textbook_example():
+    rows = read_golden("clrs_dijkstra_example.txt")
+    edges = [tuple(map(int, r)) for r in rows if r[0] != "dist"]
+    expect = [int(x) for x in next(r for r in rows if r[0] == "dist")[1:]]
+    g = gg.from_edges(5, [e[0] for e in edges], [e[1] for e in edges], [e[2] for e in edges])
+    assert oracle.dijkstra(g, 0).tolist() == expect
+    assert oracle.bellman_ford(g, 0).tolist() == expect
+
+
+def _tiny_cases(count, seed0=0):
+    """Random tiny multigraphs: n <= 64, m <= 512, weights drawn from several
+    ranges including 0 and 2^32-1, self-loops and duplicates allowed."""
+    ranges = [(0, 0), (0, 3), (1, 10), (1, (1 << 18) - 1), (0xFFFFFFF0, 0xFFFFFFFF),
+              (0, 0xFFFFFFFF)]
+    rng = np.random.default_rng(seed0)
+    for k in range(count):
+        n = int(rng.integers(1, 65))
+        m = int(rng.integers(0, min(512, 8 * n) + 1))
+        lo, hi = ranges[k % len(ranges)]
+        g = gg.random_graph(n, m, lo, hi, seed=seed0 * 1000003 + k)
+        s = int(rng.integers(0, n))
+        yield g, s
+
+
+def test_dijkstra_matches_bellman_ford_10k_tiny_graphs():
+    checked = 0
+    for g, s in _tiny_cases(10000):
+        d = oracle.dijkstra(g, s)
+        b = oracle.bellman_ford(g, s)
+        assert np.array_equal(d, b), (g.n, g.m, s)
+        checked += 1
+    assert checked == 10000
+
+
+def _all_simple_paths_min(n, src, dst, w, s):
+    """Exhaustive enumeration of every simple path from s (tiny n only)."""
+    adj = [[] for _ in range(n)]
+    for u, v, ww in zip(src, dst, w):
+        adj[u].append((v, ww))
+    best = [INF] * n
+    best[s] = 0
+    stack = [(s, 0, 1 << s)]
+    while stack:
+        u, d, seen = stack.pop()
+        for v, ww in adj[u]:
+            if not (seen >> v) & 1:
+                nd = d + ww
+                if nd < best[v]:
+                    best[v] = nd
+                stack.append((v, nd, seen | (1 << v)))
+    return best
+
+
+def test_dijkstra_matches_exhaustive_paths():
+    rng = np.random.default_rng(7)
+    for k in range(400):
+        n = int(rng.integers(1, 8))
+        m = int(rng.integers(0, 14))
+        src = rng.integers(0, n, m).tolist()
+        dst = rng.integers(0, n, m).tolist()
+        hi = [5, 1 << 18, (1 << 32) - 1][k % 3]
+        w = rng.integers(0, hi, m, endpoint=True).tolist()
+        g = gg.from_edges(n, src, dst, w)
+        s = int(rng.integers(0, n))
+        assert oracle.dijkstra(g, s).tolist() == _all_simple_paths_min(n, src, dst, w, s)
+
+
+@pytest.mark.parametrize("R,C,sr,sc", [(1, 1, 0, 0), (1, 9, 0, 4), (37, 53, 0, 0), (37, 53, 18, 26),
+                                       (64, 64, 63, 0)])
+def test_unit_grid_is_manhattan(R, C, sr, sc):
+    g = gg.grid(R, C, wmax_excl=0)
+    d = oracle.dijkstra(g, sr * C + sc).reshape(R, C)
+    rr, cc = np.meshgrid(np.arange(R), np.arange(C), indexing="ij")
+    assert np.array_equal(d, (np.abs(rr - sr) + np.abs(cc - sc)).astype(np.uint64))
+
+
+def test_chain_is_prefix_sum_and_star_is_direct():
+    g = gg.chain(500, wseed=3, wlo=0, whi=(1 << 32) - 1)
+    d = oracle.dijkstra(g, 0)
+    assert d.tolist() == [0] + np.cumsum(g.w.astype(object)).tolist()
+    d7 = oracle.dijkstra(g, 7)
+    assert d7[:7].tolist() == [INF] * 7 and d7[7] == 0
+    st = gg.star(300, wseed=5)
+    ds = oracle.dijkstra(st, 0)
+    assert ds[0] == 0 and ds[1:].tolist() == st.w.tolist()
+    assert oracle.dijkstra(st, 5).tolist() == [INF] * 5 + [0] + [INF] * 294
+
+
+def test_grid256_invariants_and_symmetry():
+    g, s = gg.workload_grid256()
+    assert (g.n, g.m) == (65536, 261120)
+    d = oracle.dijkstra(g, s)
+    assert oracle.check(g, s, d) == (0, 0)
+    # undirected with symmetric weights: d(s, v) == d(v, s) for a few v
+    for v in (1, 255, 40000, 65535):
+        assert oracle.dijkstra(g, v)[s] == d[v]
+
+
+# --------------------------------------------------------------------------
+# invariant checker: accepts d, rejects planted mistakes
+# --------------------------------------------------------------------------
+
+def test_check_rejects_planted_mistakes():
+    g, s = gg.workload_grid256()
+    d = oracle.dijkstra(g, s)
+    assert oracle.check(g, s, d)[0] == 0
+    bad = d.copy(); bad[s] = 1
+    assert oracle.check(g, s, bad)[0] == 1
+    bad = d.copy(); bad[1234] -= np.uint64(1)
+    assert oracle.check(g, s, bad)[0] in (2, 3)
+    bad = d.copy(); bad[1234] += np.uint64(1)  # its tight in-edge is now violated
+    assert oracle.check(g, s, bad) == (2, 1234)
+    bad = d.copy(); bad[999] = oracle.INF
+    assert oracle.check(g, s, bad)[0] == 2
+    # an unreachable vertex given a finite value: graph with an isolated vertex
+    h = gg.from_edges(3, [0], [1], [4])
+    dh = oracle.dijkstra(h, 0)
+    assert dh.tolist() == [0, 4, INF] and oracle.check(h, 0, dh)[0] == 0
+    dh2 = dh.copy(); dh2[2] = 0
+    assert oracle.check(h, 0, dh2)[0] in (3, 4)
+
+
+# --------------------------------------------------------------------------
+# ExtDist pins
+# --------------------------------------------------------------------------
+
+def test_delta_extdist_closed_form():
+    # i starts at 1 and advances every step: theta = i * Delta
+    i = 1
+    for k in range(1, 6):
+        th, i = oracle.delta_extdist(i, 100, 0)
+        assert th == 100 * k and i == k + 1
+    # empty-bucket skip: qmin = 1234, Delta = 100 -> i jumps to ceil(12.34) = 13
+    th, i = oracle.delta_extdist(1, 100, 1234)
+    assert (th, i) == (1300, 14)
+    th, i = oracle.delta_extdist(1, 100, 1300)
+    assert (th, i) == (1300, 14)
+    # saturation: Delta = 2^64-1 is Bellman-Ford (theta = +inf)
+    assert oracle.delta_extdist(1, INF, 0)[0] == INF
+    assert oracle.delta_extdist(3, 1 << 63, 0)[0] == INF
+    # Delta = 1 with the skip is theta = min_Q delta (Dijkstra row of Table 2)
+    assert oracle.delta_extdist(1, 1, 777)[0] == 777
+
+
+def test_rho_extdist_special_cases():
+    n = 10 ** 6  # keeps 20*q <= n: no dense-step adjustment
+    dist = np.arange(100, dtype=np.uint64) * np.uint64(3)
+    q = np.arange(100, dtype=np.uint32)
+    # |Q| <= rho: every queued vertex is extracted (theta = +inf)
+    assert oracle.rho_extdist(q, dist, n, 100, 1, 1, 0) == INF
+    assert oracle.rho_extdist(q, dist, n, 1 << 40, 1, 1, 0) == INF
+    # all keys equal: theta is that key
+    same = np.full(100, 42, dtype=np.uint64)
+    assert oracle.rho_extdist(q, same, n, 10, 1, 1, 0) == 42
+    # theta is always the key of some queued vertex when sampling
+    th = oracle.rho_extdist(q, dist, n, 10, 9, 3, 0)
+    assert th in set(dist.tolist())
+
+
+def test_rho_extdist_rank_within_constant_factor():
+    """Appendix B: the sampled threshold ranks within a constant factor of rho
+    w.h.p.  Keys are a permutation of 0..q-1, so the rank of theta is theta+1."""
+    rng = np.random.default_rng(11)
+    good = total = 0
+    for trial in range(300):
+        q = int(rng.integers(1000, 200000))
+        rho = int(rng.integers(10, q // 2))
+        keys = rng.permutation(q).astype(np.uint64)
+        queue = rng.permutation(q).astype(np.uint32)
+        th = oracle.rho_extdist(queue, keys, 10 ** 9, rho, trial, 1 + trial % 5, 0)
+        rank = th + 1
+        total += 1
+        good += (rho / 2 <= rank <= 2 * rho)
+    assert good >= 0.97 * total, (good, total)
+
+
+def test_rho_extdist_dense_rule():
+    """The first two dense steps (20*|Q| > n) use rho/10 (Sec. 6)."""
+    q = 50000
+    keys = np.arange(q, dtype=np.uint64)
+    queue = np.arange(q, dtype=np.uint32)
+    n = 100000  # 20*q > n: dense
+    ranks_d = [oracle.rho_extdist(queue, keys, n, 5000, s, 1, 0) + 1 for s in range(40)]
+    ranks_3 = [oracle.rho_extdist(queue, keys, n, 5000, s, 1, 2) + 1 for s in range(40)]
+    assert 250 <= np.median(ranks_d) <= 1000
+    assert 2500 <= np.median(ranks_3) <= 10000
+    # a dense step with rho >= 10*q extracts everything even with the rule
+    assert oracle.rho_extdist(queue, keys, n, 10 * q, 0, 1, 0) == INF
+
+
+# --------------------------------------------------------------------------
+# Algorithm 1 run sequentially: exact distances and the paper's step bounds
+# --------------------------------------------------------------------------
+
+def _algo_cases():
+    return [(oracle.RHO, 1), (oracle.RHO, 2), (oracle.RHO, 31), (oracle.RHO, 1 << 10),
+            (oracle.RHO, (1 << 32) - 1), (oracle.DELTA_STAR, 1), (oracle.DELTA_STAR, 1 << 13),
+            (oracle.DELTA_STAR, INF), (oracle.BELLMAN_FORD, 0)]
+
+
+@pytest.mark.parametrize("algo,param", _algo_cases())
+def test_stepping_equals_dijkstra_tiny(algo, param):
+    for g, s in _tiny_cases(600, seed0=algo * 100 + (param % 97)):
+        d = oracle.dijkstra(g, s)
+        ds, st, _ = oracle.stepping(g, s, algo, param, seed=s)
+        assert np.array_equal(d, ds)
+
+
+def _bounded_graphs():
+    yield gg.grid(40, 40, wseed=9)
+    yield gg.rmat(12, 8, gen_seed=5, wseed=6)
+    yield gg.road(48, 0.75, seed=3)
+    yield gg.chain(300, wseed=1, wlo=1, whi=50, both=True)
+    yield gg.random_graph(3000, 20000, 1, 1000, seed=4, drop_self_loops=True)
+
+
+@pytest.mark.parametrize("algo,param", [(oracle.RHO, 1), (oracle.RHO, 64), (oracle.RHO, 1 << 12),
+                                        (oracle.DELTA_STAR, 1), (oracle.DELTA_STAR, 1 << 10),
+                                        (oracle.DELTA_STAR, 1 << 20), (oracle.BELLMAN_FORD, 0)])
+def test_stepping_bounds(algo, param):
+    """Lemma 5.1: every vertex is extracted at most h(v) times (fewest-hop
+    shortest-path length; weights >= 1).  Bellman-Ford: <= k_n + 1 steps.
+    Theorem 5.5: Delta* uses <= ceil(k_n L / Delta) + k_n + 1 steps.
+    Theorem 5.3's proof: rho-Stepping has <= k_n + 1 partial-extract steps."""
+    for g in _bounded_graphs():
+        s = int(np.flatnonzero(gg.largest_cc(g))[0])
+        d = oracle.dijkstra(g, s)
+        h, kn = oracle.hops(g, s)
+        ds, st, ext = oracle.stepping(g, s, algo, param, seed=1, want_ext=True)
+        assert np.array_equal(d, ds)
+        reach = d != oracle.INF
+        assert np.all(ext[~reach] == 0)
+        hv = h.astype(np.int64)
+        hv[s] = 1
+        assert np.all(ext[reach].astype(np.int64) <= hv[reach]), g.name
+        L = int(g.w.max())
+        if algo == oracle.BELLMAN_FORD:
+            assert st["steps"] <= kn + 1
+        elif algo == oracle.DELTA_STAR:
+            assert st["steps"] <= math.ceil(kn * L / param) + kn + 1
+        else:
+            assert st["partial_steps"] <= kn + 1
+
+
+def test_hops_pins():
+    # chain: h(v) = v; unit grid: h = Manhattan distance
+    g = gg.chain(50, wseed=2)
+    h, k = oracle.hops(g, 0)
+    assert h.tolist() == list(range(50)) and k == 49
+    gu = gg.grid(9, 11, wmax_excl=0)
+    hu, ku = oracle.hops(gu, 0)
+    rr, cc = np.meshgrid(np.arange(9), np.arange(11), indexing="ij")
+    assert np.array_equal(hu.reshape(9, 11), (rr + cc).astype(np.uint32)) and ku == 18
+    # fewest hops among equal-length paths: 0->1->2 (1+1) vs 0->2 (2)
+    t = gg.from_edges(3, [0, 1, 0], [1, 2, 2], [1, 1, 2])
+    assert oracle.hops(t, 0)[0].tolist() == [0, 1, 1]
+
+
+def test_bruteforce_hops_tiny():
+    """h(v) by exhaustive enumeration of simple paths on tiny graphs."""
+    rng = np.random.default_rng(5)
+    for _ in range(200):
+        n = int(rng.integers(1, 7))
+        m = int(rng.integers(0, 12))
+        src = rng.integers(0, n, m).tolist()
+        dst = rng.integers(0, n, m).tolist()
+        w = rng.integers(1, 4, m).tolist()
+        g = gg.from_edges(n, src, dst, w)
+        d = oracle.dijkstra(g, 0)
+        best = {}
+        adj = [[] for _ in range(n)]
+        for u, v, ww in zip(src, dst, w):
+            adj[u].append((v, ww))
+        stack = [(0, 0, 0, 1)]
+        while stack:
+            u, dd, hh, seen = stack.pop()
+            if dd == d[u]:
+                best[u] = min(best.get(u, 1 << 30), hh)
+            for v, ww in adj[u]:
+                if not (seen >> v) & 1:
+                    stack.append((v, dd + ww, hh + 1, seen | (1 << v)))
+        h, _ = oracle.hops(g, 0)
+        for v in range(n):
+            if d[v] == oracle.INF:
+                assert h[v] == 0xFFFFFFFF
+            else:
+                assert h[v] == best[v]

@@ -1,0 +1,176 @@
+/*
+ * sssp.h -- C ABI of the GB300 stepping-SSSP library (libsssp.so).
+ *
+ * The library computes exact single-source shortest-path distances on a
+ * directed graph with unsigned 32-bit integer weights by running the stepping
+ * framework of Dong, Gu, Sun, Zhang, "Efficient Stepping Algorithms and
+ * Implementations for Parallel Shortest Paths" (SPAA'21; Algorithm 1 and
+ * Table 2): each step picks a threshold theta (ExtDist), extracts every queued
+ * vertex whose tentative distance is <= theta (Extract of the LaB-PQ, Sec. 3.1),
+ * relaxes their out-edges with WriteMin and re-queues improved targets
+ * (Update, Sec. 3.1).  Three ExtDist rules are offered (Table 2): rho-Stepping,
+ * Delta*-Stepping and Bellman-Ford.  Every rule reaches the same, unique
+ * output d(s, v) (Sec. 1 problem statement): the sum of weights of a lightest
+ * s->v path, UINT64_MAX when v is unreachable.
+ *
+ * Conventions shared by every call:
+ *   - Return value: SSSP_OK (0) or a negative sssp_status.  The library never
+ *     aborts, traps or prints.
+ *   - Memory: "host" pointers are ordinary CPU memory; "device" pointers are
+ *     CUDA global memory of the current device (e.g. a torch CUDA tensor's
+ *     data_ptr()).  Graph storage and solver scratch are owned by the library;
+ *     distance outputs are owned by the caller.
+ *   - Streams: `stream` is a cudaStream_t passed as void* (NULL = legacy
+ *     default stream).  Device work is enqueued asynchronously on it.
+ *   - Threading: a graph handle may be read by many threads, but solves that
+ *     share one graph handle share its scratch, so they must be ordered (one
+ *     stream, or host synchronisation between them).
+ */
+#ifndef SSSP_H
+#define SSSP_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct sssp_graph sssp_graph; /* opaque; device copy of one CSR graph */
+
+/* ExtDist rule (Table 2). */
+typedef enum {
+    SSSP_RHO = 0,           /* theta = sampled rho-th smallest queued distance (Sec. 6, App. B) */
+    SSSP_DELTA_STAR = 1,    /* theta = i * Delta, i advancing every step (Table 2, Thm. 5.5)    */
+    SSSP_BELLMAN_FORD = 2   /* theta = +infinity (Table 2)                                       */
+} sssp_algo;
+
+typedef enum {
+    SSSP_OK = 0,
+    SSSP_ERR_INVALID_ARG = -1,   /* a pointer, size, id or parameter is out of range            */
+    SSSP_ERR_OUT_OF_MEMORY = -2, /* a device or host allocation failed                          */
+    SSSP_ERR_CUDA = -3,          /* a CUDA runtime call failed (no device, launch failure, ...) */
+    SSSP_ERR_TIMEOUT = -4,       /* a bounded device-wide wait ran out; outputs are undefined   */
+    SSSP_ERR_INTERNAL = -5       /* a device-side capacity or step guard fired                  */
+} sssp_status;
+
+/* Per-step record written when sssp_options.trace is set (device memory). */
+typedef struct {
+    uint64_t theta;     /* ExtDist threshold of the step (UINT64_MAX = extract all)        */
+    uint32_t queued;    /* |Q| at the start of the step                                    */
+    uint32_t extracted; /* |Extract(theta)|                                                */
+    uint64_t edges;     /* out-edges scanned by the extracted vertices                     */
+    uint64_t updates;   /* successful WriteMin calls in the step                           */
+} sssp_step_trace;
+
+/* Totals of the last solve (sssp_last_stats). */
+typedef struct {
+    uint64_t steps;     /* iterations of Algorithm 1's while loop                          */
+    uint64_t queued;    /* sum over steps of |Q|                                           */
+    uint64_t extracted; /* sum over steps of |Extract(theta)|                              */
+    uint64_t edges;     /* sum over steps of the out-edges scanned (relaxations attempted) */
+    uint64_t updates;   /* successful WriteMin calls                                       */
+    int32_t status;     /* device status of the solve (an sssp_status)                     */
+    uint32_t grid;      /* thread blocks of the persistent launch                          */
+} sssp_stats;
+
+/* Optional knobs of sssp_solve_ex.  Zero-initialise, then set what you need. */
+typedef struct {
+    uint64_t seed;           /* rho sampler seed; 0 derives it from the source            */
+    uint64_t timeout_ns;     /* bound on every device-wide wait; 0 = 2 s                  */
+    uint64_t max_steps;      /* 0 = no limit beyond the internal guard                    */
+    uint32_t* ext_count;     /* device uint32[n] or NULL: times each vertex was extracted */
+    sssp_step_trace* trace;  /* device array or NULL: one record per step                 */
+    uint32_t trace_cap;      /* records available in `trace`                              */
+    uint32_t grid_limit;     /* 0 = full device; else at most this many thread blocks     */
+    uint32_t test_exit_block;/* testing only: 1 + index of a block that leaves before the
+                                first device-wide wait (0 = none); the other blocks then
+                                time out and the solve reports SSSP_ERR_TIMEOUT           */
+    sssp_stats* stats_out;   /* device sssp_stats or NULL: the solve's totals are written
+                                here when it ends (grid is left 0), so a sequence of
+                                solves can be measured without host synchronisation       */
+    uint32_t reserved[2];
+} sssp_options;
+
+/*
+ * Copy a CSR graph (host arrays) to the device.
+ *   n        vertices, 1 <= n <= 2^32-1
+ *   m        directed edges, m < 2^40
+ *   offsets  host uint64[n+1]: offsets[0] = 0, non-decreasing, offsets[n] = m;
+ *            the out-edges of u are [offsets[u], offsets[u+1])
+ *   targets  host uint32[m], every entry < n (the graph notation of Sec. 2: N(u))
+ *   weights  host uint32[m], any value (0 allowed; the paper assumes >= 1)
+ *   out      receives the handle
+ * Self-loops and parallel edges are accepted.  The arrays are validated in
+ * O(n + m) and copied; the caller keeps ownership of them.  Errors:
+ * INVALID_ARG (bad sizes, non-monotone offsets, target >= n), OUT_OF_MEMORY,
+ * CUDA.  Synchronous.
+ */
+int sssp_graph_create(uint32_t n, uint64_t m, const uint64_t* offsets, const uint32_t* targets,
+                      const uint32_t* weights, sssp_graph** out);
+
+/* Release a graph and its scratch.  Synchronises the device first. */
+int sssp_graph_destroy(sssp_graph* g);
+
+/* Vertex and edge counts of a graph (host outputs; either may be NULL). */
+int sssp_graph_info(const sssp_graph* g, uint32_t* n, uint64_t* m);
+
+/*
+ * Distances from `source` (Algorithm 1 with the ExtDist of Table 2).
+ *   source    vertex id < n
+ *   algo      SSSP_RHO (param = rho >= 1), SSSP_DELTA_STAR (param = Delta >= 1),
+ *             SSSP_BELLMAN_FORD (param ignored)
+ *   dist_out  caller-owned DEVICE uint64[n]; receives d(source, v), UINT64_MAX if
+ *             unreachable.  It doubles as the tentative-distance array delta of
+ *             Algorithm 1 during the solve.
+ *   stream    cudaStream_t as void*
+ * Asynchronous: the return value covers argument checks and the launch only.
+ * Device-side failures (TIMEOUT, INTERNAL) are reported by sssp_last_status
+ * after the stream has completed the solve.  The whole solve is one
+ * persistent kernel launch: step count, theta and queue sizes stay on the
+ * device.
+ */
+int sssp_solve(const sssp_graph* g, uint32_t source, sssp_algo algo, uint64_t param,
+               uint64_t* dist_out, void* stream);
+
+/* sssp_solve with options (opt may be NULL = defaults). */
+int sssp_solve_ex(const sssp_graph* g, uint32_t source, sssp_algo algo, uint64_t param,
+                  uint64_t* dist_out, const sssp_options* opt, void* stream);
+
+/*
+ * End-to-end convenience: solve into library-owned device memory and copy the
+ * distances to HOST memory `host_dist_out` (uint64[n]; pinned memory copies
+ * fastest).  Synchronous; returns the device status of the solve.
+ */
+int sssp_solve_host(const sssp_graph* g, uint32_t source, sssp_algo algo, uint64_t param,
+                    uint64_t* host_dist_out, void* stream);
+
+/* Waits for `stream`, then returns the device status of the last solve on g. */
+int sssp_last_status(const sssp_graph* g, void* stream);
+
+/* Waits for `stream`, then copies the totals of the last solve on g to *out. */
+int sssp_last_stats(const sssp_graph* g, sssp_stats* out, void* stream);
+
+/*
+ * ExtDist of rho-Stepping alone, on the device (Sec. 6 "Threshold estimation",
+ * App. B; the same device code the solve runs).  Reads the queue queue[0..q)
+ * (device uint32 ids < n) and their keys dist[] (device uint64[n]); writes
+ * theta to *theta_out (device uint64).  n is the vertex count, step the
+ * 1-based step number, dense_before the number of earlier dense steps.
+ * The sample count s, its cap of 4096, the sample positions (splitmix64
+ * output step*2^32 + j from state `seed`, reduced by multiply-high), the
+ * rank floor(rho'*s/q) and the dense-step rule (rho' = max(1, rho/10) in the
+ * first two steps with 20*q > n) are those of the solve.  q <= rho' gives
+ * UINT64_MAX (extract every queued vertex).  Asynchronous on `stream`.
+ */
+int sssp_rho_threshold(const uint32_t* queue, uint32_t q, const uint64_t* dist, uint32_t n,
+                       uint64_t rho, uint64_t seed, uint64_t step, uint32_t dense_before,
+                       uint64_t* theta_out, void* stream);
+
+/* Static description of a status code (never NULL). */
+const char* sssp_status_string(int status);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* SSSP_H */

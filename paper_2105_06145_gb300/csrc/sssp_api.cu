@@ -1,0 +1,312 @@
+// sssp_api.cu -- host side of the C ABI declared in include/sssp.h.
+//
+// Owns the device copy of the graph and the solver scratch (queue bitmap,
+// queue lists, extraction lists, control block), validates arguments, and
+// launches the persistent cooperative solve kernel (sssp_kernels.cu).
+
+#include <cstdint>
+#include <cstdlib>
+#include <cstring>
+#include <mutex>
+#include <new>
+
+#include <cuda_runtime.h>
+
+#include "sssp_internal.h"
+
+using namespace sssp;
+
+struct sssp_graph {
+    uint32_t n = 0;
+    uint64_t m = 0;
+    int device = 0;
+    int num_sms = 0;
+    uint64_t* d_off = nullptr;
+    uint2* d_edges = nullptr;
+    // scratch
+    uint32_t* d_inq = nullptr;
+    uint32_t* d_qa = nullptr;
+    uint32_t* d_qb = nullptr;
+    uint32_t* d_fsmall = nullptr;
+    uint2* d_items = nullptr;
+    uint64_t item_cap = 0;
+    Ctrl* d_ctrl = nullptr;
+    uint64_t* d_dist_internal = nullptr;   // lazily allocated for sssp_solve_host
+    Ctrl* h_ctrl = nullptr;                // pinned readback
+    uint32_t last_grid = 0;
+    std::mutex mu;                         // guards lazy allocations / attributes
+};
+
+namespace {
+
+int cuda_fail(cudaError_t e)
+{
+    if (e == cudaErrorMemoryAllocation) return SSSP_ERR_OUT_OF_MEMORY;
+    return SSSP_ERR_CUDA;
+}
+
+template <typename T>
+cudaError_t dalloc(T** p, uint64_t count)
+{
+    return cudaMalloc(reinterpret_cast<void**>(p), (size_t)(count ? count : 1) * sizeof(T));
+}
+
+void free_graph(sssp_graph* g)
+{
+    if (!g) return;
+    cudaFree(g->d_off);
+    cudaFree(g->d_edges);
+    cudaFree(g->d_inq);
+    cudaFree(g->d_qa);
+    cudaFree(g->d_qb);
+    cudaFree(g->d_fsmall);
+    cudaFree(g->d_items);
+    cudaFree(g->d_ctrl);
+    cudaFree(g->d_dist_internal);
+    if (g->h_ctrl) cudaFreeHost(g->h_ctrl);
+    delete g;
+}
+
+// blocks per SM of the solve kernel for a given dynamic smem size
+int solve_blocks_per_sm(size_t dyn_smem, int* out)
+{
+    static std::mutex mu;
+    static size_t attr_smem = 0;
+    std::lock_guard<std::mutex> lk(mu);
+    const void* fn = solve_kernel_ptr();
+    if (dyn_smem > attr_smem) {
+        cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn_smem);
+        if (e != cudaSuccess) return cuda_fail(e);
+        attr_smem = dyn_smem;
+    }
+    int bps = 0;
+    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, fn, kBlock, dyn_smem);
+    if (e != cudaSuccess) return cuda_fail(e);
+    *out = bps;
+    return SSSP_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* sssp_status_string(int status)
+{
+    switch (status) {
+        case SSSP_OK: return "ok";
+        case SSSP_ERR_INVALID_ARG: return "invalid argument";
+        case SSSP_ERR_OUT_OF_MEMORY: return "out of memory";
+        case SSSP_ERR_CUDA: return "CUDA runtime error";
+        case SSSP_ERR_TIMEOUT: return "device-wide wait timed out";
+        case SSSP_ERR_INTERNAL: return "internal capacity or step guard";
+        default: return "unknown status";
+    }
+}
+
+int sssp_graph_create(uint32_t n, uint64_t m, const uint64_t* offsets, const uint32_t* targets,
+                      const uint32_t* weights, sssp_graph** out)
+{
+    if (!out) return SSSP_ERR_INVALID_ARG;
+    *out = nullptr;
+    if (n == 0 || !offsets || (m > 0 && (!targets || !weights))) return SSSP_ERR_INVALID_ARG;
+    if (m >= (1ull << 40)) return SSSP_ERR_INVALID_ARG;
+    if (offsets[0] != 0 || offsets[n] != m) return SSSP_ERR_INVALID_ARG;
+    for (uint32_t u = 0; u < n; ++u)
+        if (offsets[u + 1] < offsets[u]) return SSSP_ERR_INVALID_ARG;
+    for (uint64_t e = 0; e < m; ++e)
+        if (targets[e] >= n) return SSSP_ERR_INVALID_ARG;
+
+    sssp_graph* g = new (std::nothrow) sssp_graph();
+    if (!g) return SSSP_ERR_OUT_OF_MEMORY;
+    g->n = n;
+    g->m = m;
+    cudaError_t e = cudaGetDevice(&g->device);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&g->num_sms, cudaDevAttrMultiProcessorCount, g->device);
+    if (e != cudaSuccess) { free_graph(g); return cuda_fail(e); }
+
+    const uint64_t m_pad = (m + 1) & ~1ull;  // even, so 16-byte pair loads stay in bounds
+    const uint64_t m_alloc = m_pad < 2 ? 2 : m_pad;
+    uint32_t* d_tgt = nullptr;
+    uint32_t* d_w = nullptr;
+    g->item_cap = item_capacity(n, m);
+    if ((e = dalloc(&g->d_off, (uint64_t)n + 1)) != cudaSuccess ||
+        (e = dalloc(&g->d_edges, m_alloc)) != cudaSuccess ||
+        (e = dalloc(&g->d_inq, ((uint64_t)n + 31) / 32)) != cudaSuccess ||
+        (e = dalloc(&g->d_qa, n)) != cudaSuccess || (e = dalloc(&g->d_qb, n)) != cudaSuccess ||
+        (e = dalloc(&g->d_fsmall, n)) != cudaSuccess || (e = dalloc(&g->d_items, g->item_cap)) != cudaSuccess ||
+        (e = dalloc(&g->d_ctrl, 1)) != cudaSuccess ||
+        (e = cudaMallocHost(reinterpret_cast<void**>(&g->h_ctrl), sizeof(Ctrl))) != cudaSuccess ||
+        (e = dalloc(&d_tgt, m)) != cudaSuccess || (e = dalloc(&d_w, m)) != cudaSuccess) {
+        cudaFree(d_tgt);
+        cudaFree(d_w);
+        free_graph(g);
+        return cuda_fail(e);
+    }
+    memset(g->h_ctrl, 0, sizeof(Ctrl));
+    e = cudaMemcpy(g->d_off, offsets, sizeof(uint64_t) * ((size_t)n + 1), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess && m) e = cudaMemcpy(d_tgt, targets, sizeof(uint32_t) * m, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess && m) e = cudaMemcpy(d_w, weights, sizeof(uint32_t) * m, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = launch_pack_edges(d_tgt, d_w, g->d_edges, m, m_alloc, 0);
+    if (e == cudaSuccess) e = cudaMemset(g->d_ctrl, 0, sizeof(Ctrl));
+    if (e == cudaSuccess) e = cudaDeviceSynchronize();
+    cudaFree(d_tgt);
+    cudaFree(d_w);
+    if (e != cudaSuccess) { free_graph(g); return cuda_fail(e); }
+    *out = g;
+    return SSSP_OK;
+}
+
+int sssp_graph_destroy(sssp_graph* g)
+{
+    if (!g) return SSSP_ERR_INVALID_ARG;
+    cudaDeviceSynchronize();
+    free_graph(g);
+    return SSSP_OK;
+}
+
+int sssp_graph_info(const sssp_graph* g, uint32_t* n, uint64_t* m)
+{
+    if (!g) return SSSP_ERR_INVALID_ARG;
+    if (n) *n = g->n;
+    if (m) *m = g->m;
+    return SSSP_OK;
+}
+
+int sssp_solve_ex(const sssp_graph* gc, uint32_t source, sssp_algo algo, uint64_t param, uint64_t* dist_out,
+                  const sssp_options* opt, void* stream)
+{
+    sssp_graph* g = const_cast<sssp_graph*>(gc);
+    if (!g || !dist_out) return SSSP_ERR_INVALID_ARG;
+    if (source >= g->n) return SSSP_ERR_INVALID_ARG;
+    if (algo != SSSP_RHO && algo != SSSP_DELTA_STAR && algo != SSSP_BELLMAN_FORD) return SSSP_ERR_INVALID_ARG;
+    if (algo != SSSP_BELLMAN_FORD && param == 0) return SSSP_ERR_INVALID_ARG;
+    sssp_options o;
+    memset(&o, 0, sizeof o);
+    if (opt) o = *opt;
+    if (o.trace && o.trace_cap == 0) o.trace = nullptr;
+
+    SolveParams p;
+    memset(&p, 0, sizeof p);
+    p.off = g->d_off;
+    p.edges = g->d_edges;
+    p.n = g->n;
+    p.m = g->m;
+    p.dist = dist_out;
+    p.inq = g->d_inq;
+    p.qa = g->d_qa;
+    p.qb = g->d_qb;
+    p.fsmall = g->d_fsmall;
+    p.items = g->d_items;
+    p.item_cap = g->item_cap;
+    p.ctrl = g->d_ctrl;
+    p.source = source;
+    p.algo = (int)algo;
+    p.param = param;
+    p.seed = o.seed ? o.seed : (0x2105061450000000ull ^ (uint64_t)source);
+    p.timeout_ns = o.timeout_ns ? o.timeout_ns : 2000000000ull;
+    p.max_steps = o.max_steps;
+    p.ext_count = o.ext_count;
+    p.trace = o.trace;
+    p.trace_cap = o.trace_cap;
+    p.exit_block = o.test_exit_block;
+    p.stats_out = o.stats_out;
+    p.sample_cap = (algo == SSSP_RHO) ? rho_sample_bound(g->n, param) : 0;
+
+    const size_t dyn_smem = (size_t)p.sample_cap * sizeof(uint64_t);
+    int bps = 0;
+    int rc;
+    {
+        std::lock_guard<std::mutex> lk(g->mu);
+        cudaError_t e = cudaSetDevice(g->device);
+        if (e != cudaSuccess) return cuda_fail(e);
+        rc = solve_blocks_per_sm(dyn_smem, &bps);
+    }
+    if (rc != SSSP_OK) return rc;
+    if (bps < 1) return SSSP_ERR_CUDA;
+    uint32_t grid = (uint32_t)(bps * g->num_sms);
+    if (o.grid_limit && o.grid_limit < grid) grid = o.grid_limit;
+    if (p.exit_block > grid) return SSSP_ERR_INVALID_ARG;
+    g->last_grid = grid;
+
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    cudaError_t e = cudaMemsetAsync(g->d_ctrl, 0, sizeof(Ctrl), st);
+    if (e != cudaSuccess) return cuda_fail(e);
+    void* args[] = {&p};
+    e = cudaLaunchCooperativeKernel(solve_kernel_ptr(), dim3(grid), dim3(kBlock), args, dyn_smem, st);
+    if (e != cudaSuccess) return cuda_fail(e);
+    return SSSP_OK;
+}
+
+int sssp_solve(const sssp_graph* g, uint32_t source, sssp_algo algo, uint64_t param, uint64_t* dist_out,
+               void* stream)
+{
+    return sssp_solve_ex(g, source, algo, param, dist_out, nullptr, stream);
+}
+
+int sssp_last_stats(const sssp_graph* gc, sssp_stats* out, void* stream)
+{
+    sssp_graph* g = const_cast<sssp_graph*>(gc);
+    if (!g || !out) return SSSP_ERR_INVALID_ARG;
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    cudaError_t e = cudaMemcpyAsync(g->h_ctrl, g->d_ctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return cuda_fail(e);
+    const Ctrl& c = *g->h_ctrl;
+    out->steps = c.steps;
+    out->queued = c.queued;
+    out->extracted = c.extracted;
+    out->edges = c.edges;
+    out->updates = c.updates_total;
+    out->status = c.status;
+    out->grid = g->last_grid;
+    return SSSP_OK;
+}
+
+int sssp_last_status(const sssp_graph* g, void* stream)
+{
+    sssp_stats s;
+    int rc = sssp_last_stats(g, &s, stream);
+    if (rc != SSSP_OK) return rc;
+    return s.status;
+}
+
+int sssp_solve_host(const sssp_graph* gc, uint32_t source, sssp_algo algo, uint64_t param,
+                    uint64_t* host_dist_out, void* stream)
+{
+    sssp_graph* g = const_cast<sssp_graph*>(gc);
+    if (!g || !host_dist_out) return SSSP_ERR_INVALID_ARG;
+    {
+        std::lock_guard<std::mutex> lk(g->mu);
+        if (!g->d_dist_internal) {
+            cudaError_t e = dalloc(&g->d_dist_internal, g->n);
+            if (e != cudaSuccess) { g->d_dist_internal = nullptr; return cuda_fail(e); }
+        }
+    }
+    int rc = sssp_solve_ex(g, source, algo, param, g->d_dist_internal, nullptr, stream);
+    if (rc != SSSP_OK) return rc;
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    cudaError_t e = cudaMemcpyAsync(host_dist_out, g->d_dist_internal, sizeof(uint64_t) * (size_t)g->n,
+                                    cudaMemcpyDeviceToHost, st);
+    if (e != cudaSuccess) return cuda_fail(e);
+    return sssp_last_status(g, stream);
+}
+
+int sssp_rho_threshold(const uint32_t* queue, uint32_t q, const uint64_t* dist, uint32_t n, uint64_t rho,
+                       uint64_t seed, uint64_t step, uint32_t dense_before, uint64_t* theta_out, void* stream)
+{
+    if ((q > 0 && !queue) || !dist || !theta_out || n == 0 || rho == 0 || q > n) return SSSP_ERR_INVALID_ARG;
+    static uint32_t* d_err = nullptr;
+    static std::mutex mu;
+    {
+        std::lock_guard<std::mutex> lk(mu);
+        if (!d_err) {
+            cudaError_t e = dalloc(&d_err, 1);
+            if (e != cudaSuccess) { d_err = nullptr; return cuda_fail(e); }
+        }
+    }
+    cudaError_t e = launch_rho_threshold(queue, q, dist, n, rho, seed, step, dense_before, theta_out, d_err,
+                                         reinterpret_cast<cudaStream_t>(stream));
+    return e == cudaSuccess ? SSSP_OK : cuda_fail(e);
+}
+
+}  // extern "C"

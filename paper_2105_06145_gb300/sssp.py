@@ -1,0 +1,210 @@
+"""Python binding of libsssp.so (argument marshalling only).
+
+Every function here has the name of the C-ABI call it wraps (include/sssp.h)
+and does nothing but convert arguments: the solve itself runs in the CUDA
+kernels of libsssp.so.  Device buffers and streams come from PyTorch
+(``tensor.data_ptr()``, ``torch.cuda.current_stream().cuda_stream``); host
+graph arrays are numpy.  Importing this module fails loudly when the library
+has not been built: there is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libsssp.so")
+
+SSSP_RHO, SSSP_DELTA_STAR, SSSP_BELLMAN_FORD = 0, 1, 2
+ALGOS = {"rho": SSSP_RHO, "delta_star": SSSP_DELTA_STAR, "bellman_ford": SSSP_BELLMAN_FORD}
+SSSP_OK = 0
+SSSP_ERR_INVALID_ARG, SSSP_ERR_OUT_OF_MEMORY, SSSP_ERR_CUDA = -1, -2, -3
+SSSP_ERR_TIMEOUT, SSSP_ERR_INTERNAL = -4, -5
+INF = (1 << 64) - 1
+
+if not os.path.exists(LIB_PATH):
+    raise ImportError(f"libsssp.so is not built ({LIB_PATH}); run __graft_entry__.build() "
+                      "or python -m paper_2105_06145_gb300.build")
+
+_lib = ctypes.CDLL(LIB_PATH)
+
+
+class sssp_step_trace(ctypes.Structure):
+    _fields_ = [("theta", ctypes.c_uint64), ("queued", ctypes.c_uint32),
+                ("extracted", ctypes.c_uint32), ("edges", ctypes.c_uint64),
+                ("updates", ctypes.c_uint64)]
+
+
+class sssp_stats(ctypes.Structure):
+    _fields_ = [("steps", ctypes.c_uint64), ("queued", ctypes.c_uint64),
+                ("extracted", ctypes.c_uint64), ("edges", ctypes.c_uint64),
+                ("updates", ctypes.c_uint64), ("status", ctypes.c_int32),
+                ("grid", ctypes.c_uint32)]
+
+    def as_dict(self) -> dict:
+        return {k: int(getattr(self, k)) for k, _ in self._fields_}
+
+
+class sssp_options(ctypes.Structure):
+    _fields_ = [("seed", ctypes.c_uint64), ("timeout_ns", ctypes.c_uint64),
+                ("max_steps", ctypes.c_uint64), ("ext_count", ctypes.c_void_p),
+                ("trace", ctypes.c_void_p), ("trace_cap", ctypes.c_uint32),
+                ("grid_limit", ctypes.c_uint32), ("test_exit_block", ctypes.c_uint32),
+                ("stats_out", ctypes.c_void_p), ("reserved", ctypes.c_uint32 * 2)]
+
+
+TRACE_RECORD_BYTES = ctypes.sizeof(sssp_step_trace)
+STATS_BYTES = ctypes.sizeof(sssp_stats)
+
+_P, _u32, _u64, _i32 = ctypes.c_void_p, ctypes.c_uint32, ctypes.c_uint64, ctypes.c_int
+_lib.sssp_graph_create.argtypes = [_u32, _u64, _P, _P, _P, ctypes.POINTER(_P)]
+_lib.sssp_graph_create.restype = _i32
+_lib.sssp_graph_destroy.argtypes = [_P]
+_lib.sssp_graph_destroy.restype = _i32
+_lib.sssp_graph_info.argtypes = [_P, ctypes.POINTER(_u32), ctypes.POINTER(_u64)]
+_lib.sssp_graph_info.restype = _i32
+_lib.sssp_solve.argtypes = [_P, _u32, _i32, _u64, _P, _P]
+_lib.sssp_solve.restype = _i32
+_lib.sssp_solve_ex.argtypes = [_P, _u32, _i32, _u64, _P, ctypes.POINTER(sssp_options), _P]
+_lib.sssp_solve_ex.restype = _i32
+_lib.sssp_solve_host.argtypes = [_P, _u32, _i32, _u64, _P, _P]
+_lib.sssp_solve_host.restype = _i32
+_lib.sssp_last_status.argtypes = [_P, _P]
+_lib.sssp_last_status.restype = _i32
+_lib.sssp_last_stats.argtypes = [_P, ctypes.POINTER(sssp_stats), _P]
+_lib.sssp_last_stats.restype = _i32
+_lib.sssp_rho_threshold.argtypes = [_P, _u32, _P, _u32, _u64, _u64, _u64, _u32, _P, _P]
+_lib.sssp_rho_threshold.restype = _i32
+_lib.sssp_status_string.argtypes = [_i32]
+_lib.sssp_status_string.restype = ctypes.c_char_p
+
+EXPORTED = ["sssp_graph_create", "sssp_graph_destroy", "sssp_graph_info", "sssp_solve",
+            "sssp_solve_ex", "sssp_solve_host", "sssp_last_status", "sssp_last_stats",
+            "sssp_rho_threshold", "sssp_status_string"]
+
+
+class SSSPError(RuntimeError):
+    def __init__(self, code: int, what: str):
+        super().__init__(f"{what}: {sssp_status_string(code)} ({code})")
+        self.code = code
+
+
+def _check(code: int, what: str) -> int:
+    if code != SSSP_OK:
+        raise SSSPError(code, what)
+    return code
+
+
+def sssp_status_string(code: int) -> str:
+    return _lib.sssp_status_string(code).decode()
+
+
+def sssp_graph_create(n: int, m: int, offsets: np.ndarray, targets: np.ndarray,
+                      weights: np.ndarray) -> int:
+    offsets = np.ascontiguousarray(offsets, dtype=np.uint64)
+    targets = np.ascontiguousarray(targets, dtype=np.uint32)
+    weights = np.ascontiguousarray(weights, dtype=np.uint32)
+    h = _P()
+    _check(_lib.sssp_graph_create(n, m, offsets.ctypes.data, targets.ctypes.data if m else None,
+                                  weights.ctypes.data if m else None, ctypes.byref(h)),
+           "sssp_graph_create")
+    return h.value
+
+
+def sssp_graph_destroy(g: int) -> None:
+    _check(_lib.sssp_graph_destroy(g), "sssp_graph_destroy")
+
+
+def sssp_graph_info(g: int) -> tuple[int, int]:
+    n, m = _u32(), _u64()
+    _check(_lib.sssp_graph_info(g, ctypes.byref(n), ctypes.byref(m)), "sssp_graph_info")
+    return n.value, m.value
+
+
+def sssp_solve(g: int, source: int, algo: int, param: int, dist_out_ptr: int, stream: int = 0) -> int:
+    """Enqueue a solve; dist_out_ptr is a device pointer to uint64[n]."""
+    return _check(_lib.sssp_solve(g, source, algo, param, dist_out_ptr, stream or None), "sssp_solve")
+
+
+def make_options(seed: int = 0, timeout_ns: int = 0, max_steps: int = 0, ext_count_ptr: int = 0,
+                 trace_ptr: int = 0, trace_cap: int = 0, grid_limit: int = 0,
+                 test_exit_block: int = 0, stats_out_ptr: int = 0) -> sssp_options:
+    o = sssp_options()
+    o.seed, o.timeout_ns, o.max_steps = seed, timeout_ns, max_steps
+    o.ext_count = ext_count_ptr or None
+    o.trace = trace_ptr or None
+    o.trace_cap, o.grid_limit, o.test_exit_block = trace_cap, grid_limit, test_exit_block
+    o.stats_out = stats_out_ptr or None
+    return o
+
+
+def sssp_solve_ex(g: int, source: int, algo: int, param: int, dist_out_ptr: int,
+                  opts: sssp_options | None = None, stream: int = 0, check: bool = True) -> int:
+    rc = _lib.sssp_solve_ex(g, source, algo, param, dist_out_ptr,
+                            ctypes.byref(opts) if opts is not None else None, stream or None)
+    return _check(rc, "sssp_solve_ex") if check else rc
+
+
+def sssp_solve_host(g: int, source: int, algo: int, param: int, host_out: np.ndarray,
+                    stream: int = 0, check: bool = True) -> int:
+    assert host_out.dtype == np.uint64 and host_out.flags.c_contiguous
+    rc = _lib.sssp_solve_host(g, source, algo, param, host_out.ctypes.data, stream or None)
+    return _check(rc, "sssp_solve_host") if check else rc
+
+
+def sssp_solve_host_ptr(g: int, source: int, algo: int, param: int, host_ptr: int,
+                        stream: int = 0) -> int:
+    """sssp_solve_host with a raw host pointer (e.g. a pinned torch tensor)."""
+    return _lib.sssp_solve_host(g, source, algo, param, host_ptr, stream or None)
+
+
+def sssp_last_status(g: int, stream: int = 0) -> int:
+    return int(_lib.sssp_last_status(g, stream or None))
+
+
+def sssp_last_stats(g: int, stream: int = 0) -> dict:
+    s = sssp_stats()
+    _check(_lib.sssp_last_stats(g, ctypes.byref(s), stream or None), "sssp_last_stats")
+    return s.as_dict()
+
+
+def sssp_rho_threshold(queue_ptr: int, q: int, dist_ptr: int, n: int, rho: int, seed: int,
+                       step: int, dense_before: int, theta_out_ptr: int, stream: int = 0) -> int:
+    return _check(_lib.sssp_rho_threshold(queue_ptr or None, q, dist_ptr, n, rho, seed, step,
+                                          dense_before, theta_out_ptr, stream or None),
+                  "sssp_rho_threshold")
+
+
+class Graph:
+    """Owning wrapper of an sssp_graph handle built from a CSR (graphgen.CSR or
+    any object with n, off, tgt, w)."""
+
+    def __init__(self, csr):
+        self.n = int(csr.n)
+        self.m = int(csr.tgt.shape[0])
+        self.handle = sssp_graph_create(self.n, self.m, csr.off, csr.tgt, csr.w)
+
+    def close(self) -> None:
+        if self.handle:
+            sssp_graph_destroy(self.handle)
+            self.handle = 0
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def solve(self, source: int, algo: int, param: int, dist_out, stream: int = 0,
+              opts: sssp_options | None = None) -> None:
+        """dist_out: a CUDA tensor with n 8-byte elements (int64 or uint64)."""
+        assert dist_out.is_cuda and dist_out.numel() == self.n and dist_out.element_size() == 8
+        sssp_solve_ex(self.handle, source, algo, param, dist_out.data_ptr(), opts, stream)
+
+    def status(self, stream: int = 0) -> int:
+        return sssp_last_status(self.handle, stream)
+
+    def stats(self, stream: int = 0) -> dict:
+        return sssp_last_stats(self.handle, stream)

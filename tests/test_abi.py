@@ -1,0 +1,49 @@
+"""The C ABI library loads and exports every declared symbol (no GPU needed),
+and host-side argument validation rejects bad input before touching a device."""
+import ctypes
+import os
+import re
+
+import numpy as np
+import pytest
+
+from conftest import ROOT
+
+
+def _declared_functions():
+    src = open(os.path.join(ROOT, "include", "sssp.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"^\s*(?:const\s+)?\w+\*?\s+\*?(sssp_\w+)\s*\(", src, flags=re.M)))
+
+
+def test_header_declares_the_boundary():
+    names = _declared_functions()
+    for required in ("sssp_graph_create", "sssp_graph_destroy", "sssp_solve", "sssp_last_status"):
+        assert required in names
+
+
+def test_library_exports_every_declared_symbol():
+    from paper_2105_06145_gb300 import sssp
+    lib = ctypes.CDLL(sssp.LIB_PATH)
+    for name in _declared_functions():
+        assert hasattr(lib, name), name
+    assert set(_declared_functions()) <= set(sssp.EXPORTED) | {"sssp_solve_host_ptr"}
+
+
+def test_host_validation_without_gpu():
+    from paper_2105_06145_gb300 import sssp
+    off = np.array([0, 1, 2], dtype=np.uint64)
+    tgt = np.array([1, 5], dtype=np.uint32)  # 5 >= n
+    w = np.array([1, 1], dtype=np.uint32)
+    with pytest.raises(sssp.SSSPError) as e:
+        sssp.sssp_graph_create(2, 2, off, tgt, w)
+    assert e.value.code == sssp.SSSP_ERR_INVALID_ARG
+    bad_off = np.array([0, 2, 1], dtype=np.uint64)  # not monotone
+    with pytest.raises(sssp.SSSPError):
+        sssp.sssp_graph_create(2, 1, bad_off, tgt[:1], w[:1])
+    with pytest.raises(sssp.SSSPError):
+        sssp.sssp_graph_create(0, 0, np.zeros(1, np.uint64), tgt, w)
+    assert sssp._lib.sssp_solve(None, 0, 0, 1, None, None) == sssp.SSSP_ERR_INVALID_ARG
+    assert sssp._lib.sssp_rho_threshold(None, 4, None, 8, 1, 0, 1, 0, None, None) == \
+        sssp.SSSP_ERR_INVALID_ARG
+    assert sssp.sssp_status_string(sssp.SSSP_ERR_TIMEOUT) == "device-wide wait timed out"

@@ -1,0 +1,50 @@
+"""Full-size parity: the power-law (RMAT scale 22) and road-like (4096^2)
+workloads, in the launch configuration the benchmark times, compared element
+by element with the CPU oracle's Dijkstra (which finishes in seconds)."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2105_06145_gb300 import graphgen as gg
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def lib():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2105_06145_gb300 import sssp
+    return sssp
+
+
+def _run(lib, g, sources, cases):
+    G = lib.Graph(g)
+    dist = torch.empty(g.n, dtype=torch.int64, device="cuda")
+    stream = torch.cuda.current_stream().cuda_stream
+    for s in sources:
+        want = oracle.dijkstra(g, s)
+        assert oracle.check(g, s, want)[0] == 0
+        for algo, param in cases:
+            dist.fill_(0)
+            G.solve(s, algo, param, dist, stream)
+            st = G.stats(stream)
+            assert st["status"] == 0, (algo, param, st)
+            got = dist.cpu().numpy().view(np.uint64)
+            assert np.array_equal(got, want), (g.name, s, algo, param)
+    G.close()
+
+
+def test_rmat22_all_rules(lib):
+    g, s = gg.workload_rmat(22)
+    extra = gg.pick_sources(g, 3, 77)
+    cases = [(0, 1 << 18), (0, 1 << 20), (0, 1 << 22), (1, 1 << 13), (1, 1 << 15), (1, 1 << 17), (2, 0)]
+    _run(lib, g, [s], cases)
+    _run(lib, g, extra, [(0, 1 << 20)])
+
+
+def test_road4096(lib):
+    g, s = gg.workload_road(4096)
+    assert g.n == 4096 * 4096
+    _run(lib, g, [s], [(0, 1 << 20), (0, 1 << 14), (1, 1 << 13), (1, 1 << 15)])

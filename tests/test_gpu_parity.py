@@ -1,0 +1,239 @@
+"""Parity of the CUDA solve (through the C ABI) with the CPU oracle.
+
+Distances are unique, so every comparison is element-by-element equality of
+uint64 arrays.  Inputs come from the seeded generators; expected values come
+from the oracle only.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_2105_06145_gb300 import graphgen as gg
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+INF = (1 << 64) - 1
+
+
+@pytest.fixture(scope="module")
+def lib():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2105_06145_gb300 import sssp
+    return sssp
+
+
+def solve(lib, g, s, algo, param, opts=None, G=None):
+    own = G is None
+    if own:
+        G = lib.Graph(g)
+    dist = torch.full((g.n,), 7, dtype=torch.int64, device="cuda")
+    stream = torch.cuda.current_stream().cuda_stream
+    G.solve(s, algo, param, dist, stream, opts)
+    st = G.stats(stream)
+    out = dist.cpu().numpy().view(np.uint64).copy()
+    if own:
+        G.close()
+    return out, st
+
+
+ALGO_PARAMS = [(0, 1), (0, 2), (0, 31), (0, 1 << 10), (0, 65536), (0, (1 << 32) - 1),
+               (1, 1), (1, 1 << 13), (1, 1 << 17), (1, INF), (2, 0)]
+
+
+def test_grid256_all_rules(lib):
+    g, s = gg.workload_grid256()
+    want = oracle.dijkstra(g, s)
+    G = lib.Graph(g)
+    for algo, param in ALGO_PARAMS:
+        got, st = solve(lib, g, s, algo, param, G=G)
+        assert st["status"] == 0, (algo, param, st)
+        assert np.array_equal(got, want), (algo, param)
+    G.close()
+
+
+@pytest.mark.parametrize("algo,param", [(0, 1 << 12), (1, 1 << 15), (2, 0), (0, 3)])
+def test_rmat16_and_road(lib, algo, param):
+    for g in (gg.rmat(16, 16, gen_seed=11, wseed=12), gg.road(300, 0.75, seed=3)):
+        s = gg.pick_sources(g, 1, 5)[0]
+        want = oracle.dijkstra(g, s)
+        got, st = solve(lib, g, s, algo, param)
+        assert st["status"] == 0
+        assert np.array_equal(got, want), (g.name, algo, param)
+
+
+def test_edge_case_graphs(lib):
+    cases = [
+        (gg.from_edges(1, [], [], []), 0),                              # one vertex, no edges
+        (gg.from_edges(2, [0], [1], [0]), 0),                           # zero weight
+        (gg.from_edges(3, [0, 0, 1], [0, 1, 1], [5, 7, 3]), 0),         # self-loops
+        (gg.from_edges(3, [0, 0, 0], [1, 1, 2], [9, 4, 0xFFFFFFFF]), 0),  # multi-edge, max weight
+        (gg.chain(2000, wseed=1, wlo=0, whi=(1 << 32) - 1), 0),          # long chain, huge weights
+        (gg.chain(2000, wseed=1, both=True), 1000),
+        (gg.star(5000, wseed=2), 0),
+        (gg.star(5000, wseed=2), 17),                                    # isolated source
+        (gg.complete(90, wseed=4), 3),
+        (gg.random_graph(3000, 9000, 0, 3, seed=5), 1),                  # disconnected, w in [0,3]
+        (gg.random_graph(50, 2000, 0, 0xFFFFFFFF, seed=6), 0),
+        (gg.grid(1, 4099, wseed=3), 2049),                               # ragged 1-D grid
+    ]
+    for g, s in cases:
+        want = oracle.dijkstra(g, s)
+        for algo, param in ((0, 1), (0, 64), (0, INF), (1, 1), (1, 1000), (2, 0)):
+            got, st = solve(lib, g, s, algo, param)
+            assert st["status"] == 0, (g.name, algo, param)
+            assert np.array_equal(got, want), (g.name, s, algo, param)
+
+
+def test_tiny_random_graphs(lib):
+    rng = np.random.default_rng(3)
+    for k in range(150):
+        n = int(rng.integers(1, 200))
+        m = int(rng.integers(0, 6 * n + 1))
+        lo, hi = [(0, 0), (0, 5), (1, 1 << 18), (0, 0xFFFFFFFF)][k % 4]
+        g = gg.random_graph(n, m, lo, hi, seed=1000 + k)
+        s = int(rng.integers(0, n))
+        want = oracle.dijkstra(g, s)
+        algo, param = ALGO_PARAMS[k % len(ALGO_PARAMS)]
+        got, st = solve(lib, g, s, algo, param)
+        assert st["status"] == 0 and np.array_equal(got, want), (k, algo, param)
+
+
+def test_hub_vertices_use_chunked_relaxation(lib):
+    """Hubs with 2e5 out-edges (split into many chunk items) plus a sparse rest."""
+    n = 300000
+    rng = np.random.default_rng(9)
+    hubs = [0, 1, 2]
+    src, dst, w = [], [], []
+    for h in hubs:
+        t = rng.integers(0, n, 200000)
+        src.append(np.full(t.size, h)); dst.append(t); w.append(rng.integers(1, 1 << 18, t.size))
+    t = rng.integers(0, n, 3 * n)
+    src.append(rng.integers(0, n, t.size)); dst.append(t); w.append(rng.integers(1, 1 << 18, t.size))
+    src.append(np.array([5, 5, 5])); dst.append(np.array(hubs)); w.append(np.array([1, 2, 3]))
+    g = gg.from_edges(n, np.concatenate(src), np.concatenate(dst), np.concatenate(w))
+    want = oracle.dijkstra(g, 5)
+    for algo, param in ((0, 1 << 14), (1, 1 << 16), (2, 0)):
+        got, st = solve(lib, g, 5, algo, param)
+        assert st["status"] == 0 and np.array_equal(got, want), (algo, param)
+
+
+def test_repeated_solves_reuse_scratch(lib):
+    g = gg.rmat(14, 16, gen_seed=3, wseed=4)
+    G = lib.Graph(g)
+    srcs = gg.pick_sources(g, 6, 8)
+    for i, s in enumerate(srcs * 2):
+        algo, param = ALGO_PARAMS[i % len(ALGO_PARAMS)]
+        got, st = solve(lib, g, s, algo, param, G=G)
+        assert st["status"] == 0 and np.array_equal(got, oracle.dijkstra(g, s))
+    G.close()
+
+
+def test_solve_host_end_to_end(lib):
+    g = gg.rmat(15, 16, gen_seed=5, wseed=6)
+    s = gg.pick_sources(g, 1, 2)[0]
+    G = lib.Graph(g)
+    out = np.zeros(g.n, dtype=np.uint64)
+    assert lib.sssp_solve_host(G.handle, s, 0, 1 << 12, out) == 0
+    assert np.array_equal(out, oracle.dijkstra(g, s))
+    G.close()
+
+
+def test_step_bounds_and_counters(lib):
+    """Lemma 5.1 (each vertex extracted <= h(v) times, any interleaving, weights
+    >= 1), Bellman-Ford <= k_n + 1 steps, Theorem 5.5 for Delta*, and the
+    trace totals agree with the solve totals."""
+    for g in (gg.grid(80, 80, wseed=5), gg.rmat(13, 8, gen_seed=7, wseed=8), gg.road(120, 0.75, seed=9)):
+        s = gg.pick_sources(g, 1, 3)[0]
+        want = oracle.dijkstra(g, s)
+        h, kn = oracle.hops(g, s)
+        L = int(g.w.max())
+        G = lib.Graph(g)
+        for algo, param in ((0, 64), (0, 1 << 12), (1, 1 << 12), (1, 1 << 16), (2, 0)):
+            ext = torch.zeros(g.n, dtype=torch.int32, device="cuda")
+            cap = 100000
+            trace = torch.zeros(cap * lib.TRACE_RECORD_BYTES // 8, dtype=torch.int64, device="cuda")
+            opts = lib.make_options(ext_count_ptr=ext.data_ptr(), trace_ptr=trace.data_ptr(),
+                                    trace_cap=cap)
+            got, st = solve(lib, g, s, algo, param, opts=opts, G=G)
+            assert st["status"] == 0 and np.array_equal(got, want)
+            e = ext.cpu().numpy().astype(np.int64)
+            reach = want != np.uint64(INF)
+            assert np.all(e[~reach] == 0)
+            hv = h.astype(np.int64)
+            hv[s] = 1
+            assert np.all(e[reach] <= hv[reach]), (g.name, algo, param)
+            assert int(e.sum()) == st["extracted"]
+            if algo == 2:
+                assert st["steps"] <= kn + 1
+            elif algo == 1:
+                assert st["steps"] <= math.ceil(kn * L / param) + kn + 1
+            rec = np.frombuffer(trace.cpu().numpy().tobytes(), dtype=np.dtype(
+                [("theta", "<u8"), ("queued", "<u4"), ("extracted", "<u4"), ("edges", "<u8"),
+                 ("updates", "<u8")]))[: st["steps"]]
+            assert int(rec["extracted"].sum()) == st["extracted"]
+            assert int(rec["queued"].sum()) == st["queued"]
+            assert int(rec["edges"].sum()) == st["edges"]
+            assert int(rec["updates"].sum()) == st["updates"]
+            assert rec["queued"][0] == 1 and np.all(rec["extracted"] >= 1)
+            if algo == 2:
+                assert np.all(rec["theta"] == np.uint64(INF))
+            # edges scanned = sum of out-degrees of the extracted vertices
+            deg = g.degrees()
+            assert int((e * deg).sum()) == st["edges"]
+        G.close()
+
+
+def test_rho_threshold_matches_oracle(lib):
+    """ExtDist of rho-Stepping alone: the device rule equals the oracle's on the
+    same queue list, keys, seed and step (sampling, sort, rank, dense rule)."""
+    rng = np.random.default_rng(21)
+    out = torch.zeros(1, dtype=torch.int64, device="cuda")
+    stream = torch.cuda.current_stream().cuda_stream
+    for trial in range(200):
+        n = int(rng.integers(1, 300000))
+        q = int(rng.integers(0, n + 1))
+        dist = rng.integers(0, 1 << 40, n, dtype=np.uint64)
+        if trial % 7 == 0:
+            dist[:] = 5
+        queue = rng.permutation(n)[:q].astype(np.uint32)
+        rho = int([1, 2, 10, 1000, q // 3 + 1, q, 1 << 40][trial % 7])
+        seed = int(rng.integers(0, 1 << 62))
+        step = int(rng.integers(1, 1000))
+        dense_before = int(trial % 4)
+        want = oracle.rho_extdist(queue, dist, n, rho, seed, step, dense_before)
+        dq = torch.from_numpy(queue.view(np.int32).copy()).cuda() if q else torch.zeros(1, dtype=torch.int32, device="cuda")
+        dd = torch.from_numpy(dist.view(np.int64).copy()).cuda()
+        lib.sssp_rho_threshold(dq.data_ptr(), q, dd.data_ptr(), n, rho, seed, step, dense_before,
+                               out.data_ptr(), stream)
+        got = int(out.cpu().numpy().view(np.uint64)[0])
+        assert got == want, (trial, n, q, rho)
+
+
+def test_timeout_is_reported_not_hung(lib):
+    """A block that leaves before the first device-wide wait makes the others'
+    bounded waits run out: the solve returns SSSP_ERR_TIMEOUT and the context
+    stays usable for the next solve."""
+    g = gg.grid(64, 64, wseed=2)
+    G = lib.Graph(g)
+    dist = torch.empty(g.n, dtype=torch.int64, device="cuda")
+    stream = torch.cuda.current_stream().cuda_stream
+    opts = lib.make_options(timeout_ns=50_000_000, test_exit_block=2)
+    G.solve(0, 0, 64, dist, stream, opts)
+    assert G.status(stream) == lib.SSSP_ERR_TIMEOUT
+    got, st = solve(lib, g, 0, 0, 64, G=G)
+    assert st["status"] == 0 and np.array_equal(got, oracle.dijkstra(g, 0))
+    G.close()
+
+
+def test_invalid_arguments(lib):
+    g = gg.grid(8, 8)
+    G = lib.Graph(g)
+    dist = torch.empty(g.n, dtype=torch.int64, device="cuda")
+    for src, algo, param in ((64, 0, 1), (0, 0, 0), (0, 1, 0), (0, 7, 1)):
+        rc = lib.sssp_solve_ex(G.handle, src, algo, param, dist.data_ptr(), None, 0, check=False)
+        assert rc == lib.SSSP_ERR_INVALID_ARG
+    G.close()

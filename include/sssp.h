@@ -88,6 +88,7 @@ typedef struct {
     sssp_stats* stats_out;   /* device sssp_stats or NULL: the solve's totals are written
                                 here when it ends (grid is left 0), so a sequence of
                                 solves can be measured without host synchronisation       */
+    uint64_t solve_timeout_ns; /* bound on the whole solve; 0 = 60 s (SSSP_ERR_TIMEOUT)  */
     uint32_t reserved[2];
 } sssp_options;
 

@@ -204,6 +204,7 @@ int sssp_solve_ex(const sssp_graph* gc, uint32_t source, sssp_algo algo, uint64_
     p.param = param;
     p.seed = o.seed ? o.seed : (0x2105061450000000ull ^ (uint64_t)source);
     p.timeout_ns = o.timeout_ns ? o.timeout_ns : 2000000000ull;
+    p.solve_timeout_ns = o.solve_timeout_ns ? o.solve_timeout_ns : 60000000000ull;
     p.max_steps = o.max_steps;
     p.ext_count = o.ext_count;
     p.trace = o.trace;

@@ -54,7 +54,8 @@ struct SolveParams {
     int algo;
     uint64_t param;
     uint64_t seed;
-    uint64_t timeout_ns;
+    uint64_t timeout_ns;          // bound on each device-wide wait
+    uint64_t solve_timeout_ns;    // bound on the whole solve
     uint64_t max_steps;
     uint32_t* ext_count;          // optional [n]
     sssp_step_trace* trace;       // optional [trace_cap]

@@ -89,6 +89,9 @@ __device__ __noinline__ bool grid_sync(Ctrl* ctrl, unsigned long long& target, u
             }
         }
         __threadfence();
+        // an error recorded before the barrier (timeout, capacity, step or time
+        // guard) is visible to every block after it: all of them leave together
+        if (ok && *reinterpret_cast<volatile int*>(&ctrl->status) != 0) ok = 0;
         s_ok = ok;
     }
     __syncthreads();
@@ -288,6 +291,7 @@ __global__ void __launch_bounds__(kBlock, 2) solve_kernel(SolveParams p)
     const uint2* __restrict__ edges = p.edges;
 
     if (tid == 0) s_err = 0;
+    const unsigned long long t_start = global_timer_ns();
 
     // ---- init: delta <- inf, delta[s] <- 0, Q.Update(s) (Algorithm 1) ----
     for (uint64_t i = gtid; i < n; i += gthreads) dist[i] = (i == p.source) ? 0ull : kInf;
@@ -343,6 +347,10 @@ __global__ void __launch_bounds__(kBlock, 2) solve_kernel(SolveParams p)
             if (blockIdx.x == 0 && tid == 0) set_status(ctrl, SSSP_ERR_INTERNAL);
             break;
         }
+        // whole-solve time guard: block 0 records it; every block leaves at the
+        // next barrier
+        if (blockIdx.x == 0 && tid == 0 && global_timer_ns() - t_start > p.solve_timeout_ns)
+            set_status(ctrl, SSSP_ERR_TIMEOUT);
 
         // ---------------- ExtDist ----------------
         uint64_t theta;

@@ -52,7 +52,8 @@ class sssp_options(ctypes.Structure):
                 ("max_steps", ctypes.c_uint64), ("ext_count", ctypes.c_void_p),
                 ("trace", ctypes.c_void_p), ("trace_cap", ctypes.c_uint32),
                 ("grid_limit", ctypes.c_uint32), ("test_exit_block", ctypes.c_uint32),
-                ("stats_out", ctypes.c_void_p), ("reserved", ctypes.c_uint32 * 2)]
+                ("stats_out", ctypes.c_void_p), ("solve_timeout_ns", ctypes.c_uint64),
+                ("reserved", ctypes.c_uint32 * 2)]
 
 
 TRACE_RECORD_BYTES = ctypes.sizeof(sssp_step_trace)
@@ -130,13 +131,15 @@ def sssp_solve(g: int, source: int, algo: int, param: int, dist_out_ptr: int, st
 
 def make_options(seed: int = 0, timeout_ns: int = 0, max_steps: int = 0, ext_count_ptr: int = 0,
                  trace_ptr: int = 0, trace_cap: int = 0, grid_limit: int = 0,
-                 test_exit_block: int = 0, stats_out_ptr: int = 0) -> sssp_options:
+                 test_exit_block: int = 0, stats_out_ptr: int = 0,
+                 solve_timeout_ns: int = 0) -> sssp_options:
     o = sssp_options()
     o.seed, o.timeout_ns, o.max_steps = seed, timeout_ns, max_steps
     o.ext_count = ext_count_ptr or None
     o.trace = trace_ptr or None
     o.trace_cap, o.grid_limit, o.test_exit_block = trace_cap, grid_limit, test_exit_block
     o.stats_out = stats_out_ptr or None
+    o.solve_timeout_ns = solve_timeout_ns
     return o
 
 

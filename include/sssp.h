@@ -60,6 +60,7 @@ typedef struct {
     uint32_t extracted; /* |Extract(theta)|                                                */
     uint64_t edges;     /* out-edges scanned by the extracted vertices                     */
     uint64_t updates;   /* successful WriteMin calls in the step                           */
+    uint64_t t_ns;      /* device time from the start of the solve to the start of the step */
 } sssp_step_trace;
 
 /* Totals of the last solve (sssp_last_stats). */

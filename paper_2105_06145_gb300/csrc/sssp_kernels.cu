@@ -313,6 +313,7 @@ __global__ void __launch_bounds__(kBlock, 2) solve_kernel(SolveParams p)
     uint64_t delta_i = 1;          // Delta*-Stepping bucket index (Table 2)
     uint32_t dense_seen = 0;       // rho-Stepping: dense steps so far (Sec. 6)
     uint64_t prev_theta = 0;       // block 0: theta of the previous step, for the trace
+    uint64_t prev_t = 0;           // block 0: start time of the previous step, for the trace
     unsigned long long t_queued = 0, t_ext = 0, t_edges = 0, t_upd = 0;
 
     uint64_t k = 1;
@@ -335,10 +336,11 @@ __global__ void __launch_bounds__(kBlock, 2) solve_kernel(SolveParams p)
                 if (p.trace && k - 2 < p.trace_cap) {
                     sssp_step_trace rec;
                     rec.theta = prev_theta; rec.queued = qq; rec.extracted = ff;
-                    rec.edges = ee; rec.updates = uu;
+                    rec.edges = ee; rec.updates = uu; rec.t_ns = prev_t;
                     p.trace[k - 2] = rec;
                 }
             }
+            prev_t = global_timer_ns() - t_start;
             ctrl->qsize[pv] = 0; ctrl->fsmall[pv] = 0; ctrl->fchunk[pv] = 0; ctrl->fcount[pv] = 0;
             ctrl->fedges[pv] = 0; ctrl->updates[pv] = 0; ctrl->qmin[pv] = kInf;
         }

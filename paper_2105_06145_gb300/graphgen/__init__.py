@@ -140,10 +140,42 @@ def grid(R: int, C: int, wseed: int = 1, wmax_excl: int = WMAX_EXCL) -> CSR:
     return CSR(R * C, off, tgt, w, f"grid{R}x{C}", {"R": R, "C": C, "wseed": wseed})
 
 
+def _cached(key: str, make):
+    """When SSSP_GRAPH_CACHE names a directory, keep generated graphs there as
+    .npy files so that several processes of one run share one generation."""
+    d = os.environ.get("SSSP_GRAPH_CACHE")
+    if not d:
+        return make()
+    base = os.path.join(d, key)
+    try:
+        off = np.load(base + ".off.npy")
+        tgt = np.load(base + ".tgt.npy")
+        w = np.load(base + ".w.npy")
+        meta = {}
+        return CSR(off.shape[0] - 1, off, tgt, w, key, meta)
+    except (OSError, ValueError):
+        pass
+    g = make()
+    os.makedirs(d, exist_ok=True)
+    for nm, arr in (("off", g.off), ("tgt", g.tgt), ("w", g.w)):
+        tmp = f"{base}.{nm}.tmp{os.getpid()}.npy"
+        np.save(tmp, arr)
+        os.replace(tmp, f"{base}.{nm}.npy")
+    return g
+
+
 def rmat(scale: int, edgefactor: int = 16, a: float = 0.57, b: float = 0.19, c: float = 0.19,
          gen_seed: int = 2, wseed: int = 3, wmax_excl: int = WMAX_EXCL) -> CSR:
     """RMAT power-law graph, symmetrised, no self-loops or duplicates, vertices
     randomly relabelled; weights uniform in [1, wmax_excl)."""
+    key = f"rmat_s{scale}_ef{edgefactor}_{a}_{b}_{c}_g{gen_seed}_w{wseed}_{wmax_excl}"
+    g = _cached(key, lambda: _rmat(scale, edgefactor, a, b, c, gen_seed, wseed, wmax_excl))
+    g.name = f"rmat{scale}"
+    g.meta = {"scale": scale, "edgefactor": edgefactor, "gen_seed": gen_seed, "wseed": wseed}
+    return g
+
+
+def _rmat(scale, edgefactor, a, b, c, gen_seed, wseed, wmax_excl) -> CSR:
     lib = _L()
     n = ctypes.c_uint32()
     m = ctypes.c_uint64()
@@ -163,6 +195,14 @@ def road(side: int, keep: float = 0.75, seed: int = 5, jitter: float = 0.4,
          wscale: float = 1000.0) -> CSR:
     """Road-like graph: jittered side x side point grid, each 4-neighbour edge
     kept with probability `keep`, weight floor(wscale * length) + 1."""
+    key = f"road_{side}_{keep}_{seed}_{jitter}_{wscale}"
+    g = _cached(key, lambda: _road(side, keep, seed, jitter, wscale))
+    g.name = f"road{side}"
+    g.meta = {"side": side, "keep": keep, "seed": seed}
+    return g
+
+
+def _road(side, keep, seed, jitter, wscale) -> CSR:
     lib = _L()
     keep_num = min((1 << 64) - 1, int(round(keep * float(1 << 64))))
     n = ctypes.c_uint32()

@@ -34,7 +34,11 @@ _lib = ctypes.CDLL(LIB_PATH)
 class sssp_step_trace(ctypes.Structure):
     _fields_ = [("theta", ctypes.c_uint64), ("queued", ctypes.c_uint32),
                 ("extracted", ctypes.c_uint32), ("edges", ctypes.c_uint64),
-                ("updates", ctypes.c_uint64)]
+                ("updates", ctypes.c_uint64), ("t_ns", ctypes.c_uint64)]
+
+
+TRACE_DTYPE = [("theta", "<u8"), ("queued", "<u4"), ("extracted", "<u4"), ("edges", "<u8"),
+               ("updates", "<u8"), ("t_ns", "<u8")]
 
 
 class sssp_stats(ctypes.Structure):

@@ -171,9 +171,9 @@ def test_step_bounds_and_counters(lib):
                 assert st["steps"] <= kn + 1
             elif algo == 1:
                 assert st["steps"] <= math.ceil(kn * L / param) + kn + 1
-            rec = np.frombuffer(trace.cpu().numpy().tobytes(), dtype=np.dtype(
-                [("theta", "<u8"), ("queued", "<u4"), ("extracted", "<u4"), ("edges", "<u8"),
-                 ("updates", "<u8")]))[: st["steps"]]
+            rec = np.frombuffer(trace.cpu().numpy().tobytes(),
+                                dtype=np.dtype(lib.TRACE_DTYPE))[: st["steps"]]
+            assert np.all(np.diff(rec["t_ns"].astype(np.int64)) >= 0)
             assert int(rec["extracted"].sum()) == st["extracted"]
             assert int(rec["queued"].sum()) == st["queued"]
             assert int(rec["edges"].sum()) == st["edges"]

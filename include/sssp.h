@@ -168,6 +168,49 @@ int sssp_rho_threshold(const uint32_t* queue, uint32_t q, const uint64_t* dist, 
                        uint64_t rho, uint64_t seed, uint64_t step, uint32_t dense_before,
                        uint64_t* theta_out, void* stream);
 
+/* Largest graph sssp_solve_noalloc accepts. */
+#define SSSP_NOALLOC_MAX_VERTICES (1u << 18)   /* 262,144 vertices            */
+#define SSSP_NOALLOC_MAX_EDGES (1ull << 22)    /* 4,194,304 directed edges     */
+
+/*
+ * A solve that allocates nothing.  (The paper has no counterpart: this is a
+ * systems entry point of this library.)  It is meant for callers that cannot
+ * allocate device memory when they need a solve -- a plugin whose enqueue step
+ * runs inside a framework that owns all device memory, code running while a
+ * stream is captured into a CUDA graph, or a latency-critical loop that cannot
+ * take the implicit device synchronisation of cudaMalloc/cudaFree.  It calls
+ * no cudaMalloc, cudaFree or other allocating routine.
+ *
+ * The solver's working memory is a file-scope device array of about 7.5 MB,
+ * sized for SSSP_NOALLOC_MAX_VERTICES and SSSP_NOALLOC_MAX_EDGES; every GPU
+ * that loads it keeps it until the process exits.  All calls on a device
+ * share that array: calls that overlap on the GPU (different streams, or host
+ * threads without ordering) race and give undefined results; order them.
+ * The first call on a device looks up the array's device address (once per
+ * device, with that device current); make that first call before any stream
+ * capture begins.
+ *
+ *   n, m       vertex and edge counts; n in [1, SSSP_NOALLOC_MAX_VERTICES],
+ *              m <= SSSP_NOALLOC_MAX_EDGES, otherwise SSSP_ERR_INVALID_ARG
+ *   offsets    DEVICE uint64[n+1], a valid CSR (offsets[0] = 0, non-decreasing,
+ *              offsets[n] = m); not checked (it is in device memory)
+ *   edges      DEVICE uint32 array of (target, weight) pairs, pair e at
+ *              edges[2e], edges[2e+1]; 16-byte aligned; it must hold an even
+ *              number of pairs (when m is odd, the pair slot m is read and
+ *              ignored); every target < n (not checked)
+ *   source, algo, param   as for sssp_solve
+ *   dist_out   DEVICE uint64[n], receives the distances
+ *   stats_out  DEVICE sssp_stats or NULL: the solve's totals and device status
+ *              (SSSP_OK, SSSP_ERR_TIMEOUT, SSSP_ERR_INTERNAL) once the stream
+ *              has run the solve
+ *   stream     cudaStream_t as void*
+ * Asynchronous; the return value covers the argument checks and the launch.
+ * Results are identical to sssp_solve's.
+ */
+int sssp_solve_noalloc(uint32_t n, uint64_t m, const uint64_t* offsets, const uint32_t* edges,
+                       uint32_t source, sssp_algo algo, uint64_t param, uint64_t* dist_out,
+                       sssp_stats* stats_out, void* stream);
+
 /* Static description of a status code (never NULL). */
 const char* sssp_status_string(int status);
 

@@ -82,12 +82,17 @@ _lib.sssp_last_stats.argtypes = [_P, ctypes.POINTER(sssp_stats), _P]
 _lib.sssp_last_stats.restype = _i32
 _lib.sssp_rho_threshold.argtypes = [_P, _u32, _P, _u32, _u64, _u64, _u64, _u32, _P, _P]
 _lib.sssp_rho_threshold.restype = _i32
+_lib.sssp_solve_noalloc.argtypes = [_u32, _u64, _P, _P, _u32, _i32, _u64, _P, _P, _P]
+_lib.sssp_solve_noalloc.restype = _i32
 _lib.sssp_status_string.argtypes = [_i32]
 _lib.sssp_status_string.restype = ctypes.c_char_p
 
 EXPORTED = ["sssp_graph_create", "sssp_graph_destroy", "sssp_graph_info", "sssp_solve",
             "sssp_solve_ex", "sssp_solve_host", "sssp_last_status", "sssp_last_stats",
-            "sssp_rho_threshold", "sssp_status_string"]
+            "sssp_rho_threshold", "sssp_status_string", "sssp_solve_noalloc"]
+
+NOALLOC_MAX_VERTICES = 1 << 18
+NOALLOC_MAX_EDGES = 1 << 22
 
 
 class SSSPError(RuntimeError):
@@ -182,6 +187,15 @@ def sssp_rho_threshold(queue_ptr: int, q: int, dist_ptr: int, n: int, rho: int, 
     return _check(_lib.sssp_rho_threshold(queue_ptr or None, q, dist_ptr, n, rho, seed, step,
                                           dense_before, theta_out_ptr, stream or None),
                   "sssp_rho_threshold")
+
+
+def sssp_solve_noalloc(n: int, m: int, offsets_ptr: int, edges_ptr: int, source: int, algo: int,
+                       param: int, dist_out_ptr: int, stats_out_ptr: int = 0, stream: int = 0,
+                       check: bool = True) -> int:
+    """All pointers are device pointers; see include/sssp.h (no allocation)."""
+    rc = _lib.sssp_solve_noalloc(n, m, offsets_ptr or None, edges_ptr or None, source, algo, param,
+                                 dist_out_ptr or None, stats_out_ptr or None, stream or None)
+    return _check(rc, "sssp_solve_noalloc") if check else rc
 
 
 class Graph:

@@ -59,8 +59,12 @@ typedef struct {
     uint32_t queued;    /* |Q| at the start of the step                                    */
     uint32_t extracted; /* |Extract(theta)|                                                */
     uint64_t edges;     /* out-edges scanned by the extracted vertices                     */
-    uint64_t updates;   /* successful WriteMin calls in the step                           */
+    uint64_t updates;   /* WriteMin calls that passed the pre-check cand < delta[v]         */
     uint64_t t_ns;      /* device time from the start of the solve to the start of the step */
+    uint64_t t_relax_ns;/* device time from the start of the solve to the step's relaxation */
+    uint64_t t_extract_end_max; /* latest time a block finished its Extract work         */
+    uint64_t t_relax_end_min;   /* earliest time a block finished its relaxation work    */
+    uint64_t t_relax_end_max;   /* latest time a block finished its relaxation work      */
 } sssp_step_trace;
 
 /* Totals of the last solve (sssp_last_stats). */
@@ -69,7 +73,7 @@ typedef struct {
     uint64_t queued;    /* sum over steps of |Q|                                           */
     uint64_t extracted; /* sum over steps of |Extract(theta)|                              */
     uint64_t edges;     /* sum over steps of the out-edges scanned (relaxations attempted) */
-    uint64_t updates;   /* successful WriteMin calls                                       */
+    uint64_t updates;   /* WriteMin calls that passed the pre-check cand < delta[v]        */
     int32_t status;     /* device status of the solve (an sssp_status)                     */
     uint32_t grid;      /* thread blocks of the persistent launch                          */
 } sssp_stats;
@@ -181,7 +185,7 @@ int sssp_rho_threshold(const uint32_t* queue, uint32_t q, const uint64_t* dist, 
  * take the implicit device synchronisation of cudaMalloc/cudaFree.  It calls
  * no cudaMalloc, cudaFree or other allocating routine.
  *
- * The solver's working memory is a file-scope device array of about 7.5 MB,
+ * The solver's working memory is a file-scope device array of about 10.4 MB,
  * sized for SSSP_NOALLOC_MAX_VERTICES and SSSP_NOALLOC_MAX_EDGES; every GPU
  * that loads it keeps it until the process exits.  All calls on a device
  * share that array: calls that overlap on the GPU (different streams, or host

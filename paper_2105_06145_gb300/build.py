@@ -38,17 +38,22 @@ def _stale() -> bool:
     return any(os.path.getmtime(d) > t for d in deps)
 
 
-def build(force: bool = False, verbose: bool = False) -> str:
-    if not force and not _stale():
+def build(force: bool = False, verbose: bool = False, extra: list[str] | None = None,
+          out: str | None = None) -> str:
+    """Compile libsssp.so; `extra` adds nvcc flags (e.g. -D switches) and `out`
+    writes the library elsewhere (objects then go to a separate folder)."""
+    lib = out or LIB
+    if not force and out is None and not extra and not _stale():
         return LIB
-    os.makedirs(BUILD, exist_ok=True)
+    bdir = BUILD if out is None else os.path.join(os.path.dirname(os.path.abspath(out)), "_build_variant")
+    os.makedirs(bdir, exist_ok=True)
     cc = nvcc()
     procs = []
     objs = []
     for s in SOURCES:
-        obj = os.path.join(BUILD, s.replace(".cu", ".o"))
+        obj = os.path.join(bdir, s.replace(".cu", ".o"))
         log = obj + ".log"
-        cmd = [cc, *NVCC_FLAGS, "-c", os.path.join(CSRC, s), "-o", obj]
+        cmd = [cc, *NVCC_FLAGS, *(extra or []), "-c", os.path.join(CSRC, s), "-o", obj]
         procs.append((subprocess.Popen(cmd, stdout=open(log, "w"), stderr=subprocess.STDOUT), cmd, log))
         objs.append(obj)
     failed = False
@@ -60,10 +65,10 @@ def build(force: bool = False, verbose: bool = False) -> str:
             sys.stdout.write(open(log).read())
     if failed:
         raise RuntimeError("nvcc failed building libsssp")
-    tmp = LIB + f".tmp{os.getpid()}"
+    tmp = lib + f".tmp{os.getpid()}"
     subprocess.check_call([cc, *ARCH, "-shared", "-o", tmp, *objs, "-cudart", "static"])
-    os.replace(tmp, LIB)
-    return LIB
+    os.replace(tmp, lib)
+    return lib
 
 
 if __name__ == "__main__":

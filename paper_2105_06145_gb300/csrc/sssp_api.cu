@@ -27,8 +27,9 @@ struct sssp_graph {
     uint32_t* d_inq = nullptr;
     uint32_t* d_qa = nullptr;
     uint32_t* d_qb = nullptr;
-    uint32_t* d_fsmall = nullptr;
-    uint2* d_items = nullptr;
+    uint4* d_fsmall = nullptr;
+    uint64_t fsmall_cap = 0;
+    uint4* d_items = nullptr;
     uint64_t item_cap = 0;
     Ctrl* d_ctrl = nullptr;
     uint64_t* d_dist_internal = nullptr;   // lazily allocated for sssp_solve_host
@@ -67,20 +68,16 @@ void free_graph(sssp_graph* g)
     delete g;
 }
 
-// blocks per SM of the solve kernel for a given dynamic smem size
-int solve_blocks_per_sm(size_t dyn_smem, int* out)
+// blocks per SM of the solve kernel (its dynamic shared memory is fixed)
+int solve_blocks_per_sm(int* out)
 {
     static std::mutex mu;
-    static size_t attr_smem = 0;
     std::lock_guard<std::mutex> lk(mu);
     const void* fn = solve_kernel_ptr();
-    if (dyn_smem > attr_smem) {
-        cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn_smem);
-        if (e != cudaSuccess) return cuda_fail(e);
-        attr_smem = dyn_smem;
-    }
+    cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSolveDynSmem);
+    if (e != cudaSuccess) return cuda_fail(e);
     int bps = 0;
-    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, fn, kBlock, dyn_smem);
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, fn, kBlock, kSolveDynSmem);
     if (e != cudaSuccess) return cuda_fail(e);
     *out = bps;
     return SSSP_OK;
@@ -116,6 +113,16 @@ int sssp_graph_create(uint32_t n, uint64_t m, const uint64_t* offsets, const uin
     for (uint64_t e = 0; e < m; ++e)
         if (targets[e] >= n) return SSSP_ERR_INVALID_ARG;
 
+    // exact capacities of the relaxation records one Extract can produce:
+    // each vertex is queued at most once, so at most every vertex at once
+    uint64_t small_cap = 0, item_cap = 0;
+    for (uint32_t u = 0; u < n; ++u) {
+        const uint64_t deg = offsets[u + 1] - offsets[u];
+        if (deg == 0) continue;
+        if (deg <= kSmallDeg) ++small_cap;
+        else item_cap += chunk_count(offsets[u], offsets[u + 1]);
+    }
+
     sssp_graph* g = new (std::nothrow) sssp_graph();
     if (!g) return SSSP_ERR_OUT_OF_MEMORY;
     g->n = n;
@@ -128,12 +135,14 @@ int sssp_graph_create(uint32_t n, uint64_t m, const uint64_t* offsets, const uin
     const uint64_t m_alloc = m_pad < 2 ? 2 : m_pad;
     uint32_t* d_tgt = nullptr;
     uint32_t* d_w = nullptr;
-    g->item_cap = item_capacity(n, m);
+    g->fsmall_cap = small_cap + 1;
+    g->item_cap = item_cap + 1;
     if ((e = dalloc(&g->d_off, (uint64_t)n + 1)) != cudaSuccess ||
         (e = dalloc(&g->d_edges, m_alloc)) != cudaSuccess ||
         (e = dalloc(&g->d_inq, ((uint64_t)n + 31) / 32)) != cudaSuccess ||
         (e = dalloc(&g->d_qa, n)) != cudaSuccess || (e = dalloc(&g->d_qb, n)) != cudaSuccess ||
-        (e = dalloc(&g->d_fsmall, n)) != cudaSuccess || (e = dalloc(&g->d_items, g->item_cap)) != cudaSuccess ||
+        (e = dalloc(&g->d_fsmall, g->fsmall_cap)) != cudaSuccess ||
+        (e = dalloc(&g->d_items, g->item_cap)) != cudaSuccess ||
         (e = dalloc(&g->d_ctrl, 1)) != cudaSuccess ||
         (e = cudaMallocHost(reinterpret_cast<void**>(&g->h_ctrl), sizeof(Ctrl))) != cudaSuccess ||
         (e = dalloc(&d_tgt, m)) != cudaSuccess || (e = dalloc(&d_w, m)) != cudaSuccess) {
@@ -196,6 +205,7 @@ int sssp_solve_ex(const sssp_graph* gc, uint32_t source, sssp_algo algo, uint64_
     p.qa = g->d_qa;
     p.qb = g->d_qb;
     p.fsmall = g->d_fsmall;
+    p.fsmall_cap = g->fsmall_cap;
     p.items = g->d_items;
     p.item_cap = g->item_cap;
     p.ctrl = g->d_ctrl;
@@ -213,14 +223,14 @@ int sssp_solve_ex(const sssp_graph* gc, uint32_t source, sssp_algo algo, uint64_
     p.stats_out = o.stats_out;
     p.sample_cap = (algo == SSSP_RHO) ? rho_sample_bound(g->n, param) : 0;
 
-    const size_t dyn_smem = (size_t)p.sample_cap * sizeof(uint64_t);
+    const size_t dyn_smem = kSolveDynSmem;
     int bps = 0;
     int rc;
     {
         std::lock_guard<std::mutex> lk(g->mu);
         cudaError_t e = cudaSetDevice(g->device);
         if (e != cudaSuccess) return cuda_fail(e);
-        rc = solve_blocks_per_sm(dyn_smem, &bps);
+        rc = solve_blocks_per_sm(&bps);
     }
     if (rc != SSSP_OK) return rc;
     if (bps < 1) return SSSP_ERR_CUDA;

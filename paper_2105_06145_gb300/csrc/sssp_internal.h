@@ -9,14 +9,37 @@
 
 namespace sssp {
 
-constexpr int kBlock = 512;                 // threads per block of the persistent kernel
+#ifndef SSSP_BLOCK
+#define SSSP_BLOCK 1024
+#endif
+constexpr int kBlock = SSSP_BLOCK;                // threads per block of the persistent kernel (1 per SM)
 constexpr int kWarps = kBlock / 32;
-constexpr uint32_t kSmallDeg = 32;          // degree <= this: warp-flattened relaxation groups
+#ifndef SSSP_SMALL_DEG
+#define SSSP_SMALL_DEG 32
+#endif
+#ifndef SSSP_EXTRACT_ITEMS
+#define SSSP_EXTRACT_ITEMS 4
+#endif
+constexpr uint32_t kSmallDeg = SSSP_SMALL_DEG;  // degree <= this: warp-flattened relaxation groups
+constexpr int kSmallRounds = 4;             // 32-edge rounds per batch in the flattened path
 constexpr uint32_t kChunk = 256;            // edges per relaxation chunk item (even)
-constexpr int kExtractItems = 4;            // queue entries per thread per extract tile
+constexpr uint32_t kChunkPairs = kChunk / 2;  // 16-byte edge pairs per chunk
+constexpr int kExtractItems = SSSP_EXTRACT_ITEMS;  // queue entries per thread per extract tile
 constexpr int kStage = 512;                 // per-warp staging slots for re-queued ids
 constexpr uint32_t kMaxSamples = 4096;      // cap on the rho sampler's sample count
 constexpr uint64_t kInf = ~0ull;
+
+// Dynamic shared memory of the solve kernel: per warp kStage re-queue staging
+// slots; the rho sampler's keys reuse the same region at the start of a step
+// (the staging slots are empty between steps).  Kept small so that most of
+// the SM's unified L1/shared storage stays L1 cache.
+constexpr uint32_t kStageBytes = kWarps * (uint32_t)kStage * 4u;        // 64 KB
+constexpr uint32_t kSolveDynSmem = kStageBytes;
+static_assert(kMaxSamples * 8u <= kStageBytes, "sample keys must fit the staging region");
+
+// Relaxation record written by Extract and read by the relaxation: a run of
+// at most kChunk out-edges of one extracted vertex u.  x,y = first edge index
+// | (edge count << 40); z,w = delta[u] when u was extracted.
 
 // Device control block of one solve.  Zeroed by the host before each launch.
 // Per-step counters live in a ring of three slots indexed by step % 3: slot
@@ -46,8 +69,9 @@ struct SolveParams {
     uint32_t* inq;                // LaB-PQ membership bitmap [ceil(n/32)]
     uint32_t* qa;                 // queue lists (alternating) [n]
     uint32_t* qb;
-    uint32_t* fsmall;             // extracted ids with 1 <= degree <= kSmallDeg [n]
-    uint2* items;                 // (id, chunk) relaxation items of larger vertices
+    uint4* fsmall;                // records of extracted vertices with 1 <= degree <= kSmallDeg
+    uint64_t fsmall_cap;
+    uint4* items;                 // chunk records of extracted vertices with degree > kSmallDeg
     uint64_t item_cap;
     Ctrl* ctrl;
     uint32_t source;
@@ -61,13 +85,22 @@ struct SolveParams {
     sssp_step_trace* trace;       // optional [trace_cap]
     uint32_t trace_cap;
     uint32_t exit_block;          // testing: 1 + block that leaves before the first wait
-    uint32_t sample_cap;          // power of two >= the largest sample count, or 0
+    uint32_t sample_cap;          // power of two >= the largest sample count (<= kMaxSamples)
     sssp_stats* stats_out;        // optional device copy of the totals
 };
 
-// Upper bound on items produced by one Extract: each extracted vertex of
-// degree > kSmallDeg yields at most deg/kChunk + 2 chunk items.
-inline uint64_t item_capacity(uint32_t n, uint64_t m) { return m / kChunk + 2ull * n + 64; }
+// Chunk records of one vertex: its edge range [b, e) cut at multiples of kChunk.
+inline uint64_t chunk_count(uint64_t b, uint64_t e) { return e > b ? (e - 1) / kChunk - b / kChunk + 1 : 0; }
+
+// Upper bound on chunk records of one Extract when only n and m are known:
+// each vertex of degree > kSmallDeg yields at most deg/kChunk + 2 records and
+// there are at most m/(kSmallDeg+1) such vertices.
+inline uint64_t item_capacity_bound(uint64_t n, uint64_t m)
+{
+    uint64_t heavy = m / (kSmallDeg + 1);
+    if (heavy > n) heavy = n;
+    return m / kChunk + 2ull * heavy + 64;
+}
 
 // Launch helpers implemented in sssp_kernels.cu.
 cudaError_t launch_pack_edges(const uint32_t* tgt, const uint32_t* w, uint2* edges, uint64_t m,

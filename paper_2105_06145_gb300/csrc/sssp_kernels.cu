@@ -37,6 +37,19 @@ __device__ __forceinline__ uint64_t ldcg64(const uint64_t* p)
 }
 __device__ __forceinline__ uint32_t ldcg32(const uint32_t* p) { return __ldcg(p); }
 
+// Load of delta[v] for the relaxation pre-check.  Within a solve delta only
+// decreases after the init barrier, so a value served from a non-coherent L1
+// line can only be too high: the pre-check then lets an extra atomicMin
+// through, never skips a needed one.
+__device__ __forceinline__ uint64_t ld_precheck(const uint64_t* p)
+{
+#ifdef SSSP_PRECHECK_L1
+    return __ldca(reinterpret_cast<const unsigned long long*>(p));
+#else
+    return __ldcg(reinterpret_cast<const unsigned long long*>(p));
+#endif
+}
+
 __device__ __forceinline__ unsigned long long global_timer_ns()
 {
     unsigned long long t;
@@ -71,18 +84,19 @@ __device__ __forceinline__ uint64_t sat_mul(uint64_t a, uint64_t b)
 // ---------------------------------------------------------------------------
 // bounded grid barrier (all blocks are co-resident: cooperative launch)
 // ---------------------------------------------------------------------------
-__device__ __noinline__ bool grid_sync(Ctrl* ctrl, unsigned long long& target, uint64_t timeout_ns)
+__device__ __noinline__ bool grid_sync(Ctrl* ctrl, unsigned long long* target, uint64_t timeout_ns)
 {
     __shared__ int s_ok;
     __syncthreads();
     if (threadIdx.x == 0) {
-        target += gridDim.x;
+        const unsigned long long tgt = *target + gridDim.x;
+        *target = tgt;
         __threadfence();
         atomicAdd(&ctrl->bar, 1ull);
         int ok = 1;
         const unsigned long long t0 = global_timer_ns();
         unsigned int spins = 0;
-        while (ld_acquire_u64(&ctrl->bar) < target) {
+        while (ld_acquire_u64(&ctrl->bar) < tgt) {
             if ((++spins & 31u) == 0) {
                 if (*reinterpret_cast<volatile int*>(&ctrl->status) != 0) { ok = 0; break; }
                 if (global_timer_ns() - t0 > timeout_ns) { set_status(ctrl, SSSP_ERR_TIMEOUT); ok = 0; break; }
@@ -222,22 +236,23 @@ __device__ uint64_t rho_extdist_block(const uint32_t* Q, uint32_t q, const uint6
 // ---------------------------------------------------------------------------
 // Relaxation helpers
 // ---------------------------------------------------------------------------
-// WriteMin(delta[v], cand) (Sec. 2) after a plain pre-check; on success,
-// Update(v): test-and-set v's queue bit; returns true when v must be
-// appended to the next queue list (its bit was clear).
-__device__ __forceinline__ bool relax_edge(uint64_t* dist, uint32_t* inq, uint32_t v, uint64_t cand,
-                                           uint64_t dv, uint64_t& lmin, uint32_t& lupd)
+__device__ __forceinline__ uint4 make_rec(uint64_t start, uint64_t len, uint64_t du)
 {
-    if (cand >= dv) return false;
-    const uint64_t old = atomicMin(reinterpret_cast<unsigned long long*>(&dist[v]),
-                                   (unsigned long long)cand);
-    if (cand >= old) return false;
-    ++lupd;
-    lmin = cand < lmin ? cand : lmin;
-    const uint32_t bit = 1u << (v & 31u);
-    const uint32_t prev = atomicOr(&inq[v >> 5], bit);
-    return (prev & bit) == 0;
+    const uint64_t a = start | (len << 40);
+    return make_uint4((uint32_t)a, (uint32_t)(a >> 32), (uint32_t)du, (uint32_t)(du >> 32));
 }
+__device__ __forceinline__ uint64_t rec_start(uint4 r) { return ((uint64_t)r.x | ((uint64_t)(r.y & 0xFFu) << 32)); }
+__device__ __forceinline__ uint32_t rec_len(uint4 r) { return r.y >> 8; }
+__device__ __forceinline__ uint64_t rec_du(uint4 r) { return (uint64_t)r.z | ((uint64_t)r.w << 32); }
+
+__device__ __forceinline__ void cp_async16(void* smem, const void* gmem)
+{
+    const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(s), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
 
 // Warp-uniform: add the lanes' pushes to the warp's staging buffer.
 __device__ __forceinline__ void stage_push(bool push, uint32_t v, uint32_t* stage, uint32_t& stc,
@@ -246,6 +261,44 @@ __device__ __forceinline__ void stage_push(bool push, uint32_t v, uint32_t* stag
     const uint32_t b = __ballot_sync(FULL_MASK, push);
     if (push) stage[stc + __popc(b & ((1u << lane) - 1u))] = v;
     stc += __popc(b);
+}
+
+// Warp-uniform: one batch of (up to) 4 relaxations per lane.
+//   1. load delta[v] for the pre-check (4 gathers in flight),
+//   2. for every candidate with cand < delta[v]: WriteMin(delta[v], cand)
+//      (Sec. 2) as a fire-and-forget atomic minimum, then Update(v): the
+//      test-and-set of v's queue bit (all test-and-sets of the batch in flight),
+//   3. stage the ids whose bit was clear for the next queue list.
+// A candidate that passes the pre-check but loses the race to a smaller one
+// still marks v: the winner lowered delta[v] in this same phase and queues v
+// too, so the queued set is exactly the set whose distance dropped, and the
+// bit keeps each vertex at most once in the queue.
+__device__ __forceinline__ void relax_batch4(uint64_t* dist, uint32_t* inq, const uint32_t (&v)[4],
+                                             const uint64_t (&cand)[4], const bool (&ok)[4],
+                                             uint32_t* stage, uint32_t& stc, uint32_t lane,
+                                             uint64_t& lmin, uint32_t& lupd)
+{
+    uint64_t dv[4];
+#pragma unroll
+    for (int t = 0; t < 4; ++t) dv[t] = ok[t] ? ld_precheck(&dist[v[t]]) : 0ull;
+    uint32_t prev[4];
+    uint32_t pass = 0;
+#pragma unroll
+    for (int t = 0; t < 4; ++t) {
+        prev[t] = ~0u;
+        if (ok[t] && cand[t] < dv[t]) {
+            atomicMin(reinterpret_cast<unsigned long long*>(&dist[v[t]]), (unsigned long long)cand[t]);
+            ++lupd;
+            lmin = cand[t] < lmin ? cand[t] : lmin;
+            prev[t] = atomicOr(&inq[v[t] >> 5], 1u << (v[t] & 31u));
+            pass |= 1u << t;
+        }
+    }
+#pragma unroll
+    for (int t = 0; t < 4; ++t) {
+        const bool push = ((pass >> t) & 1u) && (prev[t] & (1u << (v[t] & 31u))) == 0;
+        stage_push(push, v[t], stage, stc, lane);
+    }
 }
 
 // Warp-uniform: move the staged ids to the next queue list (one atomic per flush).
@@ -266,15 +319,68 @@ __device__ __forceinline__ void stage_flush(uint32_t* stage, uint32_t& stc, uint
     stc = 0;
 }
 
+// Warp-uniform: relax the edges of one chunk record (<= kChunk edges of one
+// vertex, within one kChunk-aligned block of the edge array), read as 16-byte
+// pairs of packed edges.
+__device__ __forceinline__ void relax_chunk(uint4 rec, uint64_t du, const uint4* __restrict__ pairs,
+                                            uint64_t* dist, uint32_t* inq, uint32_t* stage, uint32_t& stc,
+                                            uint32_t lane, uint64_t& lmin, uint32_t& lupd)
+{
+    const uint64_t cs = rec_start(rec), ce = cs + rec_len(rec);
+    const uint64_t p0 = cs >> 1, p1 = (ce + 1) >> 1;
+#pragma unroll 1
+    for (uint32_t h = 0; h < kChunkPairs; h += 64) {
+        if (p0 + h >= p1) break;  // warp-uniform
+        uint32_t vv[4];
+        uint64_t cand[4];
+        bool ok[4];
+#pragma unroll
+        for (int t = 0; t < 2; ++t) {
+            const uint64_t P = p0 + h + 32u * t + lane;
+            const bool okp = P < p1;
+            const uint4 pr = okp ? __ldcs(&pairs[P]) : make_uint4(0, 0, 0, 0);
+            vv[2 * t] = pr.x; cand[2 * t] = du + pr.y; ok[2 * t] = okp && 2 * P >= cs;       // 2P < ce when P < p1
+            vv[2 * t + 1] = pr.z; cand[2 * t + 1] = du + pr.w; ok[2 * t + 1] = okp && 2 * P + 1 < ce;  // 2P+1 >= cs when P >= p0
+        }
+        relax_batch4(dist, inq, vv, cand, ok, stage, stc, lane, lmin, lupd);
+    }
+}
+
+// Block-wide reduction of two sums and a minimum; results valid in thread 0.
+__device__ __forceinline__ void block_reduce_2add_min(uint64_t& a, uint64_t& b, uint64_t& mn, uint64_t* s_tmp)
+{
+    const uint32_t lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        a += __shfl_xor_sync(FULL_MASK, a, o);
+        b += __shfl_xor_sync(FULL_MASK, b, o);
+        const uint64_t y = __shfl_xor_sync(FULL_MASK, mn, o);
+        mn = y < mn ? y : mn;
+    }
+    __syncthreads();
+    if (lane == 0) { s_tmp[wid] = a; s_tmp[kWarps + wid] = b; s_tmp[2 * kWarps + wid] = mn; }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        a = 0; b = 0; mn = kInf;
+        for (int i = 0; i < kWarps; ++i) {
+            a += s_tmp[i];
+            b += s_tmp[kWarps + i];
+            mn = s_tmp[2 * kWarps + i] < mn ? s_tmp[2 * kWarps + i] : mn;
+        }
+    }
+}
+
 // ---------------------------------------------------------------------------
 // The persistent solve kernel
 // ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(kBlock, 2) solve_kernel(SolveParams p)
+__global__ void __launch_bounds__(kBlock, 1) solve_kernel(SolveParams p)
 {
-    extern __shared__ uint64_t s_dyn[];                // rho sample keys [p.sample_cap]
-    __shared__ uint32_t s_stage[kWarps][kStage];       // per-warp re-queue staging
-    __shared__ uint64_t s_tmp[kWarps];
+    extern __shared__ __align__(16) unsigned char s_dyn[];
+    uint32_t* s_stage = reinterpret_cast<uint32_t*>(s_dyn);  // [kWarps][kStage]
+    uint64_t* s_keys = reinterpret_cast<uint64_t*>(s_dyn);   // rho samples (aliases the empty staging)
+    __shared__ uint64_t s_tmp[3 * kWarps];
     __shared__ uint32_t s_base[3];
+    __shared__ uint32_t s_wcnt[kWarps];
     __shared__ int s_err;
 
     const uint32_t tid = threadIdx.x, lane = tid & 31u, wid = tid >> 5;
@@ -286,12 +392,24 @@ __global__ void __launch_bounds__(kBlock, 2) solve_kernel(SolveParams p)
     Ctrl* ctrl = p.ctrl;
     uint64_t* dist = p.dist;
     uint32_t* inq = p.inq;
-    unsigned long long bar_target = 0;
+    __shared__ unsigned long long s_bar_target;   // thread 0: barrier arrivals expected so far
+    __shared__ unsigned long long s_t_start;      // solve start (globaltimer)
+    __shared__ unsigned long long s_prev_theta;   // block 0: theta of the previous step (trace)
+    __shared__ unsigned long long s_prev_t;       // block 0: start time of the previous step (trace)
+    __shared__ unsigned long long s_prev_tr;      // block 0: start of the previous step's relaxation
     const uint64_t* __restrict__ off = p.off;
     const uint2* __restrict__ edges = p.edges;
+    const uint4* __restrict__ pairs = reinterpret_cast<const uint4*>(p.edges);
+    uint32_t* stage = s_stage + wid * kStage;
 
-    if (tid == 0) s_err = 0;
-    const unsigned long long t_start = global_timer_ns();
+    if (tid == 0) {
+        s_err = 0;
+        s_bar_target = 0;
+        s_t_start = global_timer_ns();
+        s_prev_theta = 0;
+        s_prev_t = 0;
+        s_prev_tr = 0;
+    }
 
     // ---- init: delta <- inf, delta[s] <- 0, Q.Update(s) (Algorithm 1) ----
     for (uint64_t i = gtid; i < n; i += gthreads) dist[i] = (i == p.source) ? 0ull : kInf;
@@ -300,6 +418,12 @@ __global__ void __launch_bounds__(kBlock, 2) solve_kernel(SolveParams p)
         inq[i] = (i == (p.source >> 5)) ? (1u << (p.source & 31u)) : 0u;
     if (p.ext_count)
         for (uint64_t i = gtid; i < n; i += gthreads) p.ext_count[i] = 0;
+    if (p.trace)
+        for (uint64_t i = gtid; i < p.trace_cap; i += gthreads) {
+            p.trace[i].t_extract_end_max = 0;
+            p.trace[i].t_relax_end_min = kInf;
+            p.trace[i].t_relax_end_max = 0;
+        }
     if (blockIdx.x == 0 && tid == 0) {
         p.qa[0] = p.source;
         ctrl->qsize[1] = 1;
@@ -308,13 +432,10 @@ __global__ void __launch_bounds__(kBlock, 2) solve_kernel(SolveParams p)
         ctrl->qmin[2] = kInf;
     }
     if (p.exit_block != 0 && blockIdx.x == p.exit_block - 1) return;  // fault-injection test
-    if (!grid_sync(ctrl, bar_target, p.timeout_ns)) return;
+    if (!grid_sync(ctrl, &s_bar_target, p.timeout_ns)) return;
 
     uint64_t delta_i = 1;          // Delta*-Stepping bucket index (Table 2)
     uint32_t dense_seen = 0;       // rho-Stepping: dense steps so far (Sec. 6)
-    uint64_t prev_theta = 0;       // block 0: theta of the previous step, for the trace
-    uint64_t prev_t = 0;           // block 0: start time of the previous step, for the trace
-    unsigned long long t_queued = 0, t_ext = 0, t_edges = 0, t_upd = 0;
 
     uint64_t k = 1;
     for (;; ++k) {
@@ -332,15 +453,14 @@ __global__ void __launch_bounds__(kBlock, 2) solve_kernel(SolveParams p)
                 const uint32_t ff = ldcg32(&ctrl->fcount[pv]);
                 const uint64_t ee = ldcg64((const uint64_t*)&ctrl->fedges[pv]);
                 const uint64_t uu = ldcg64((const uint64_t*)&ctrl->updates[pv]);
-                t_queued += qq; t_ext += ff; t_edges += ee; t_upd += uu;
+                ctrl->queued += qq; ctrl->extracted += ff; ctrl->edges += ee; ctrl->updates_total += uu;
                 if (p.trace && k - 2 < p.trace_cap) {
-                    sssp_step_trace rec;
-                    rec.theta = prev_theta; rec.queued = qq; rec.extracted = ff;
-                    rec.edges = ee; rec.updates = uu; rec.t_ns = prev_t;
-                    p.trace[k - 2] = rec;
+                    sssp_step_trace* rec = &p.trace[k - 2];  // time extremes are filled by all blocks
+                    rec->theta = s_prev_theta; rec->queued = qq; rec->extracted = ff;
+                    rec->edges = ee; rec->updates = uu; rec->t_ns = s_prev_t; rec->t_relax_ns = s_prev_tr;
                 }
             }
-            prev_t = global_timer_ns() - t_start;
+            s_prev_t = global_timer_ns() - s_t_start;
             ctrl->qsize[pv] = 0; ctrl->fsmall[pv] = 0; ctrl->fchunk[pv] = 0; ctrl->fcount[pv] = 0;
             ctrl->fedges[pv] = 0; ctrl->updates[pv] = 0; ctrl->qmin[pv] = kInf;
         }
@@ -351,7 +471,7 @@ __global__ void __launch_bounds__(kBlock, 2) solve_kernel(SolveParams p)
         }
         // whole-solve time guard: block 0 records it; every block leaves at the
         // next barrier
-        if (blockIdx.x == 0 && tid == 0 && global_timer_ns() - t_start > p.solve_timeout_ns)
+        if (blockIdx.x == 0 && tid == 0 && global_timer_ns() - s_t_start > p.solve_timeout_ns)
             set_status(ctrl, SSSP_ERR_TIMEOUT);
 
         // ---------------- ExtDist ----------------
@@ -368,25 +488,26 @@ __global__ void __launch_bounds__(kBlock, 2) solve_kernel(SolveParams p)
             }
             delta_i = cur + 1;
         } else {
-            theta = rho_extdist_block(Qcur, q, dist, n, p.param, p.seed, k, dense_seen, s_dyn,
+            theta = rho_extdist_block(Qcur, q, dist, n, p.param, p.seed, k, dense_seen, s_keys,
                                       p.sample_cap, &s_err);
             if ((uint64_t)q * 20ull > (uint64_t)n) ++dense_seen;
             if (s_err) {
                 if (tid == 0) set_status(ctrl, SSSP_ERR_INTERNAL);
             }
         }
-        prev_theta = theta;
+        if (blockIdx.x == 0 && tid == 0) s_prev_theta = theta;
 
         // ---------------- Extract(theta) ----------------
+        // kept ids -> next queue list; extracted ids -> relaxation records
+        // (degree <= kSmallDeg: one record in fsmall; larger: one record per
+        // kChunk-aligned run of its edges in items).
         {
             uint64_t l_fcount = 0, l_fedges = 0, l_kmin = kInf;
             const uint64_t tile = (uint64_t)kBlock * kExtractItems;
             for (uint64_t base = (uint64_t)blockIdx.x * tile; base < q; base += (uint64_t)gridDim.x * tile) {
                 uint32_t v[kExtractItems];
                 uint64_t d[kExtractItems];
-                uint64_t beg[kExtractItems];
-                uint32_t nch[kExtractItems];
-                uint8_t kind[kExtractItems];  // 0 none, 1 keep, 2 small, 3 chunked, 4 extracted w/o edges
+                uint32_t kind[kExtractItems];  // 0 none, 1 keep, 2 small, 3 chunked, 4 extracted w/o edges
 #pragma unroll
                 for (int j = 0; j < kExtractItems; ++j) {
                     const uint64_t idx = base + (uint64_t)j * kBlock + tid;
@@ -401,14 +522,13 @@ __global__ void __launch_bounds__(kBlock, 2) solve_kernel(SolveParams p)
 #pragma unroll
                 for (int j = 0; j < kExtractItems; ++j) {
                     const uint64_t idx = base + (uint64_t)j * kBlock + tid;
-                    kind[j] = 0; nch[j] = 0; beg[j] = 0;
+                    kind[j] = 0;
                     if (idx < q) {
                         if (d[j] <= theta) {
                             atomicAnd(&inq[v[j] >> 5], ~(1u << (v[j] & 31u)));
                             const uint64_t b = __ldg(&off[v[j]]);
                             const uint64_t e = __ldg(&off[v[j] + 1]);
                             const uint64_t deg = e - b;
-                            beg[j] = b;
                             l_fcount += 1;
                             l_fedges += deg;
                             if (p.ext_count) p.ext_count[v[j]] += 1u;
@@ -418,8 +538,7 @@ __global__ void __launch_bounds__(kBlock, 2) solve_kernel(SolveParams p)
                                 kind[j] = 2; ++nsmall;
                             } else {
                                 kind[j] = 3;
-                                nch[j] = (uint32_t)((e - 1) / kChunk - b / kChunk + 1);
-                                nchunks += nch[j];
+                                nchunks += (uint32_t)((e - 1) / kChunk - b / kChunk + 1);
                             }
                         } else {
                             kind[j] = 1; ++nkeep;
@@ -437,71 +556,99 @@ __global__ void __launch_bounds__(kBlock, 2) solve_kernel(SolveParams p)
                     s_base[0] = tk ? atomicAdd(&ctrl->qsize[nx], tk) : 0u;
                     s_base[1] = ts ? atomicAdd(&ctrl->fsmall[c], ts) : 0u;
                     s_base[2] = tc ? atomicAdd(&ctrl->fchunk[c], tc) : 0u;
-                    if ((uint64_t)s_base[0] + tk > n || (uint64_t)s_base[1] + ts > n ||
+                    if ((uint64_t)s_base[0] + tk > n || (uint64_t)s_base[1] + ts > p.fsmall_cap ||
                         (uint64_t)s_base[2] + tc > p.item_cap)
                         set_status(ctrl, SSSP_ERR_INTERNAL);
                 }
                 __syncthreads();
                 uint32_t pk = s_base[0] + (uint32_t)(ex & 0xFFFFu);
-                uint32_t ps = s_base[1] + (uint32_t)((ex >> 16) & 0xFFFFu);
+                uint64_t ps = (uint64_t)s_base[1] + ((ex >> 16) & 0xFFFFu);
                 uint64_t pc = (uint64_t)s_base[2] + (ex >> 32);
 #pragma unroll
                 for (int j = 0; j < kExtractItems; ++j) {
+                    uint64_t bj = 0, ej = 0;  // edge range again (L1-resident since the classification)
+                    if (kind[j] >= 2) { bj = __ldg(&off[v[j]]); ej = __ldg(&off[v[j] + 1]); }
+                    const uint64_t nch = kind[j] == 3 ? (ej - 1) / kChunk - bj / kChunk + 1 : 0;
                     if (kind[j] == 1) {
                         if (pk < n) Qnext[pk] = v[j];
                         ++pk;
                     } else if (kind[j] == 2) {
-                        if (ps < n) p.fsmall[ps] = v[j];
+                        if (ps < p.fsmall_cap) p.fsmall[ps] = make_rec(bj, ej - bj, d[j]);
                         ++ps;
-                    } else if (kind[j] == 3) {
-                        const uint32_t c0 = (uint32_t)(beg[j] / kChunk);
-                        for (uint32_t t = 0; t < nch[j]; ++t, ++pc)
-                            if (pc < p.item_cap) p.items[pc] = make_uint2(v[j], c0 + t);
+                    } else if (kind[j] == 3 && nch <= 4) {
+                        for (uint64_t c0 = bj / kChunk * kChunk; c0 < ej; c0 += kChunk, ++pc) {
+                            const uint64_t cs = bj > c0 ? bj : c0;
+                            const uint64_t ce = ej < c0 + kChunk ? ej : c0 + kChunk;
+                            if (pc < p.item_cap) p.items[pc] = make_rec(cs, ce - cs, v[j]);
+                        }
                     }
+                    // vertices with many chunks: the whole warp writes their records
+                    uint32_t many = __ballot_sync(FULL_MASK, kind[j] == 3 && nch > 4);
+                    while (many) {
+                        const int src = __ffs(many) - 1;
+                        many &= many - 1;
+                        const uint64_t sb = __shfl_sync(FULL_MASK, bj, src);
+                        const uint64_t se = __shfl_sync(FULL_MASK, ej, src);
+                        const uint32_t sv = __shfl_sync(FULL_MASK, v[j], src);
+                        const uint64_t sp = __shfl_sync(FULL_MASK, pc, src);
+                        const uint64_t sn = (se - 1) / kChunk - sb / kChunk + 1;
+                        for (uint64_t t = lane; t < sn; t += 32) {
+                            const uint64_t c0 = (sb / kChunk + t) * kChunk;
+                            const uint64_t cs = sb > c0 ? sb : c0;
+                            const uint64_t ce = se < c0 + kChunk ? se : c0 + kChunk;
+                            if (sp + t < p.item_cap) p.items[sp + t] = make_rec(cs, ce - cs, sv);
+                        }
+                    }
+                    if (kind[j] == 3 && nch > 4) pc += nch;
                 }
                 __syncthreads();  // s_tmp / s_base reuse
             }
-            const uint64_t bf = block_reduce_add64(l_fcount, s_tmp);
-            if (tid == 0 && bf) atomicAdd(&ctrl->fcount[c], (unsigned int)bf);
-            const uint64_t be = block_reduce_add64(l_fedges, s_tmp);
-            if (tid == 0 && be) atomicAdd(&ctrl->fedges[c], (unsigned long long)be);
-            if (p.algo == SSSP_DELTA_STAR) {
-                const uint64_t bm = block_reduce_min64(l_kmin, s_tmp);
-                if (tid == 0 && bm != kInf) atomicMin(&ctrl->qmin[nx], (unsigned long long)bm);
+            uint64_t bf = l_fcount, be = l_fedges, bm = l_kmin;
+            block_reduce_2add_min(bf, be, bm, s_tmp);
+            if (tid == 0) {
+                if (bf) atomicAdd(&ctrl->fcount[c], (unsigned int)bf);
+                if (be) atomicAdd(&ctrl->fedges[c], (unsigned long long)be);
+                if (p.algo == SSSP_DELTA_STAR && bm != kInf) atomicMin(&ctrl->qmin[nx], (unsigned long long)bm);
             }
         }
-        if (!grid_sync(ctrl, bar_target, p.timeout_ns)) return;
+        if (p.trace && tid == 0 && k - 1 < p.trace_cap)
+            atomicMax((unsigned long long*)&p.trace[k - 1].t_extract_end_max, global_timer_ns() - s_t_start);
+        if (!grid_sync(ctrl, &s_bar_target, p.timeout_ns)) return;
 
         // ---------------- relax the out-edges of F ----------------
+        if (blockIdx.x == 0 && tid == 0) s_prev_tr = global_timer_ns() - s_t_start;
         {
-            uint32_t fs = ldcg32(&ctrl->fsmall[c]);
-            fs = fs < n ? fs : n;
+            uint64_t fs = ldcg32(&ctrl->fsmall[c]);
+            fs = fs < p.fsmall_cap ? fs : p.fsmall_cap;
             uint64_t fc = ldcg32(&ctrl->fchunk[c]);
             fc = fc < p.item_cap ? fc : p.item_cap;
-            uint32_t* stage = s_stage[wid];
             uint32_t stc = 0;
             uint64_t lmin = kInf;
             uint32_t lupd = 0;
 
-            // (a) low-degree vertices: 32 per warp, edges flattened across lanes
-            const uint32_t ngroups = (fs + 31u) >> 5;
-            for (uint32_t g = gwarp; g < ngroups; g += nwarps) {
-                const uint32_t idx = g * 32u + lane;
-                const bool valid = idx < fs;
-                const uint32_t u = valid ? ldcg32(&p.fsmall[idx]) : 0u;
-                const uint64_t b = valid ? __ldg(&off[u]) : 0ull;
-                const uint32_t deg = valid ? (uint32_t)(__ldg(&off[u + 1]) - b) : 0u;
-                const uint64_t du = valid ? ldcg64(&dist[u]) : 0ull;
+            // (a) low-degree vertices: 32 records per warp, edges flattened across lanes
+            const uint64_t ngroups = (fs + 31u) >> 5;
+            const uint32_t lmask = lane == 31 ? FULL_MASK : ((2u << lane) - 1u);
+            uint64_t g = gwarp;
+            uint4 rnext = make_uint4(0, 0, 0, 0);
+            if (g < ngroups && g * 32u + lane < fs) rnext = __ldcg(&p.fsmall[g * 32u + lane]);
+            for (; g < ngroups; g += nwarps) {
+                const uint4 rec = rnext;
+                const uint64_t gn = g + nwarps;  // prefetch the next group's records
+                rnext = (gn < ngroups && gn * 32u + lane < fs) ? __ldcg(&p.fsmall[gn * 32u + lane])
+                                                              : make_uint4(0, 0, 0, 0);
+                const uint64_t b = rec_start(rec);
+                const uint32_t deg = rec_len(rec);
+                const uint64_t du = rec_du(rec);
                 const uint32_t incl = (uint32_t)warp_incl_scan64(deg, lane);
                 const uint32_t excl = incl - deg;
                 const uint32_t total = __shfl_sync(FULL_MASK, incl, 31);
                 uint32_t started = 0;
-                const uint32_t lmask = lane == 31 ? FULL_MASK : ((2u << lane) - 1u);
-                for (uint32_t r0 = 0; r0 < total; r0 += 128) {
-                    uint64_t eidx[4], cdu[4];
-                    bool ok[4];
+                for (uint32_t r0 = 0; r0 < total; r0 += 32 * kSmallRounds) {
+                    uint64_t eidx[kSmallRounds], cdu[kSmallRounds];
+                    bool ok[kSmallRounds];
 #pragma unroll
-                    for (int t = 0; t < 4; ++t) {
+                    for (int t = 0; t < kSmallRounds; ++t) {
                         const uint32_t rb = r0 + 32u * t;
                         const uint32_t contrib =
                             (deg > 0 && excl >= rb && excl < rb + 32u) ? (1u << (excl - rb)) : 0u;
@@ -516,86 +663,74 @@ __global__ void __launch_bounds__(kBlock, 2) solve_kernel(SolveParams p)
                         cdu[t] = __shfl_sync(FULL_MASK, du, owner);
                         eidx[t] = ob + (e - oe);
                     }
-                    uint2 ed[4];
+                    uint32_t vv[kSmallRounds];
+                    uint64_t cand[kSmallRounds];
 #pragma unroll
-                    for (int t = 0; t < 4; ++t) ed[t] = ok[t] ? __ldcs(&edges[eidx[t]]) : make_uint2(0, 0);
-                    uint64_t dv[4];
-#pragma unroll
-                    for (int t = 0; t < 4; ++t) dv[t] = ok[t] ? ldcg64(&dist[ed[t].x]) : 0ull;
-#pragma unroll
-                    for (int t = 0; t < 4; ++t) {
-                        const bool push = ok[t] && relax_edge(dist, inq, ed[t].x, cdu[t] + ed[t].y, dv[t], lmin, lupd);
-                        stage_push(push, ed[t].x, stage, stc, lane);
+                    for (int t = 0; t < kSmallRounds; ++t) {
+                        const uint2 ed = ok[t] ? __ldcs(&edges[eidx[t]]) : make_uint2(0, 0);
+                        vv[t] = ed.x;
+                        cand[t] = cdu[t] + ed.y;
                     }
+                    relax_batch4(dist, inq, vv, cand, ok, stage, stc, lane, lmin, lupd);
                     if (stc > (uint32_t)(kStage - 256)) stage_flush(stage, stc, lane, ctrl, nx, Qnext, n);
                 }
             }
 
-            // (b) higher-degree vertices: one warp per chunk item of <= kChunk edges,
-            //     read as 16-byte pairs of packed edges
-            const uint4* pairs = reinterpret_cast<const uint4*>(edges);
-            for (uint64_t it = gwarp; it < fc; it += nwarps) {
-                const uint2 item = __ldcg(&p.items[it]);
-                const uint32_t u = item.x;
-                const uint64_t b = __ldg(&off[u]);
-                const uint64_t e = __ldg(&off[u + 1]);
-                const uint64_t c0 = (uint64_t)item.y * kChunk;
-                const uint64_t cs = b > c0 ? b : c0;
-                const uint64_t ce = e < c0 + kChunk ? e : c0 + kChunk;
-                const uint64_t du = ldcg64(&dist[u]);
-                const uint64_t p0 = cs >> 1, p1 = (ce + 1) >> 1;
-                // up to kChunk/2 = 128 pairs: two halves of 64, each with two
-                // 16-byte loads per lane in flight
-#pragma unroll 1
-                for (uint64_t h0 = p0; h0 < p1; h0 += 64) {
-                    uint4 pr[2];
-                    bool oka[2], okb[2];
-#pragma unroll
-                    for (int t = 0; t < 2; ++t) {
-                        const uint64_t P = h0 + 32u * t + lane;
-                        const bool okp = P < p1;
-                        pr[t] = okp ? __ldcs(&pairs[P]) : make_uint4(0, 0, 0, 0);
-                        oka[t] = okp && (2 * P >= cs) && (2 * P < ce);
-                        okb[t] = okp && (2 * P + 1 >= cs) && (2 * P + 1 < ce);
-                    }
-                    uint64_t dva[2], dvb[2];
-#pragma unroll
-                    for (int t = 0; t < 2; ++t) {
-                        dva[t] = oka[t] ? ldcg64(&dist[pr[t].x]) : 0ull;
-                        dvb[t] = okb[t] ? ldcg64(&dist[pr[t].z]) : 0ull;
-                    }
-#pragma unroll
-                    for (int t = 0; t < 2; ++t) {
-                        const bool pa = oka[t] && relax_edge(dist, inq, pr[t].x, du + pr[t].y, dva[t], lmin, lupd);
-                        stage_push(pa, pr[t].x, stage, stc, lane);
-                        const bool pb = okb[t] && relax_edge(dist, inq, pr[t].z, du + pr[t].w, dvb[t], lmin, lupd);
-                        stage_push(pb, pr[t].z, stage, stc, lane);
-                    }
+            // (b) higher-degree vertices: one warp per chunk record; the next
+            //     record is prefetched while the current chunk is relaxed, and
+            //     delta[u] is read when the chunk starts (Algorithm 1 reads it at
+            //     relaxation time; the freshest value wastes the fewest relaxations)
+            {
+                uint64_t it = gwarp;
+                uint4 rn = it < fc ? __ldcg(&p.items[it]) : make_uint4(0, 0, 0, 0);
+                for (; it < fc; it += nwarps) {
+                    const uint4 rc = rn;
+                    const uint64_t nit = it + nwarps;
+                    rn = nit < fc ? __ldcg(&p.items[nit]) : make_uint4(0, 0, 0, 0);
+                    const uint64_t du = ldcg64(&dist[rc.z]);
+                    relax_chunk(rc, du, pairs, dist, inq, stage, stc, lane, lmin, lupd);
+                    if (stc > (uint32_t)(kStage - 256)) stage_flush(stage, stc, lane, ctrl, nx, Qnext, n);
                 }
-                if (stc > (uint32_t)(kStage - 256)) stage_flush(stage, stc, lane, ctrl, nx, Qnext, n);
             }
-            stage_flush(stage, stc, lane, ctrl, nx, Qnext, n);
 
-            const uint64_t bu = block_reduce_add64(lupd, s_tmp);
-            if (tid == 0 && bu) atomicAdd(&ctrl->updates[c], (unsigned long long)bu);
-            if (p.algo == SSSP_DELTA_STAR) {
-                const uint64_t bm = block_reduce_min64(lmin, s_tmp);
-                if (tid == 0 && bm != kInf) atomicMin(&ctrl->qmin[nx], (unsigned long long)bm);
+            // (c) block-aggregated flush of what is left in the warps' staging
+            if (lane == 0) s_wcnt[wid] = stc;
+            __syncthreads();
+            if (tid == 0) {
+                uint32_t tot = 0;
+                for (int w = 0; w < kWarps; ++w) { const uint32_t cnt = s_wcnt[w]; s_wcnt[w] = tot; tot += cnt; }
+                uint32_t base = tot ? atomicAdd(&ctrl->qsize[nx], tot) : 0u;
+                if ((uint64_t)base + tot > (uint64_t)n) { set_status(ctrl, SSSP_ERR_INTERNAL); tot = 0; }
+                s_base[0] = base;
+                s_base[1] = tot;
+            }
+            __syncthreads();
+            if (s_base[1] != 0) {
+                const uint32_t wb = s_base[0] + s_wcnt[wid];
+                for (uint32_t i = lane; i < stc; i += 32) Qnext[wb + i] = stage[i];
+            }
+            uint64_t bu = lupd, unused = 0, bm = lmin;
+            block_reduce_2add_min(bu, unused, bm, s_tmp);
+            if (tid == 0) {
+                if (bu) atomicAdd(&ctrl->updates[c], (unsigned long long)bu);
+                if (p.algo == SSSP_DELTA_STAR && bm != kInf) atomicMin(&ctrl->qmin[nx], (unsigned long long)bm);
+                if (p.trace && k - 1 < p.trace_cap) {
+                    const unsigned long long now = global_timer_ns() - s_t_start;
+                    atomicMin((unsigned long long*)&p.trace[k - 1].t_relax_end_min, now);
+                    atomicMax((unsigned long long*)&p.trace[k - 1].t_relax_end_max, now);
+                }
             }
         }
-        if (!grid_sync(ctrl, bar_target, p.timeout_ns)) return;
+        if (!grid_sync(ctrl, &s_bar_target, p.timeout_ns)) return;
     }
 
     if (blockIdx.x == 0 && tid == 0) {
         ctrl->steps = k - 1;
-        ctrl->queued = t_queued;
-        ctrl->extracted = t_ext;
-        ctrl->edges = t_edges;
-        ctrl->updates_total = t_upd;
         if (p.stats_out) {
             sssp_stats so;
-            so.steps = k - 1; so.queued = t_queued; so.extracted = t_ext; so.edges = t_edges;
-            so.updates = t_upd; so.status = *reinterpret_cast<volatile int*>(&ctrl->status); so.grid = 0;
+            so.steps = k - 1; so.queued = ctrl->queued; so.extracted = ctrl->extracted;
+            so.edges = ctrl->edges; so.updates = ctrl->updates_total;
+            so.status = *reinterpret_cast<volatile int*>(&ctrl->status); so.grid = 0;
             *p.stats_out = so;
         }
     }

@@ -34,7 +34,8 @@ constexpr uint64_t align256(uint64_t x) { return (x + 255ull) & ~255ull; }
 
 constexpr uint64_t kNaVertices = SSSP_NOALLOC_MAX_VERTICES;
 constexpr uint64_t kNaEdges = SSSP_NOALLOC_MAX_EDGES;
-constexpr uint64_t kNaItems = kNaEdges / kChunk + 2ull * kNaVertices + 64ull;  // chunk-item bound
+constexpr uint64_t kNaHeavy = kNaEdges / (kSmallDeg + 1) < kNaVertices ? kNaEdges / (kSmallDeg + 1) : kNaVertices;
+constexpr uint64_t kNaItems = kNaEdges / kChunk + 2ull * kNaHeavy + 64ull;  // chunk-record bound
 
 // byte offsets of the regions inside the scratch array
 constexpr uint64_t kOffCtrl = 0;
@@ -42,8 +43,8 @@ constexpr uint64_t kOffInq = align256(kOffCtrl + sizeof(Ctrl));
 constexpr uint64_t kOffQa = align256(kOffInq + 4ull * ((kNaVertices + 31) / 32));
 constexpr uint64_t kOffQb = align256(kOffQa + 4ull * kNaVertices);
 constexpr uint64_t kOffFsmall = align256(kOffQb + 4ull * kNaVertices);
-constexpr uint64_t kOffItems = align256(kOffFsmall + 4ull * kNaVertices);
-constexpr uint64_t kScratchBytes = align256(kOffItems + 8ull * kNaItems);
+constexpr uint64_t kOffItems = align256(kOffFsmall + 16ull * kNaVertices);
+constexpr uint64_t kScratchBytes = align256(kOffItems + 16ull * kNaItems);
 
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kScratchBytes];
 
@@ -103,8 +104,9 @@ extern "C" int sssp_solve_noalloc(uint32_t n, uint64_t m, const uint64_t* offset
     p.inq = reinterpret_cast<uint32_t*>(base + kOffInq);
     p.qa = reinterpret_cast<uint32_t*>(base + kOffQa);
     p.qb = reinterpret_cast<uint32_t*>(base + kOffQb);
-    p.fsmall = reinterpret_cast<uint32_t*>(base + kOffFsmall);
-    p.items = reinterpret_cast<uint2*>(base + kOffItems);
+    p.fsmall = reinterpret_cast<uint4*>(base + kOffFsmall);
+    p.fsmall_cap = kNaVertices;
+    p.items = reinterpret_cast<uint4*>(base + kOffItems);
     p.item_cap = kNaItems;
     p.ctrl = reinterpret_cast<Ctrl*>(base + kOffCtrl);
     p.source = source;
@@ -116,12 +118,10 @@ extern "C" int sssp_solve_noalloc(uint32_t n, uint64_t m, const uint64_t* offset
     p.stats_out = stats_out;
     p.sample_cap = (algo == SSSP_RHO) ? rho_sample_bound(n, param) : 0;
 
-    // The largest dynamic shared memory any solve uses; never lowered here.
     const void* fn = solve_kernel_ptr();
-    cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)(kMaxSamples * sizeof(uint64_t)));
+    cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSolveDynSmem);
     if (e != cudaSuccess) return SSSP_ERR_CUDA;
-    const size_t dyn_smem = (size_t)p.sample_cap * sizeof(uint64_t);
+    const size_t dyn_smem = kSolveDynSmem;
     int bps = 0;
     e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, fn, kBlock, dyn_smem);
     if (e != cudaSuccess || bps < 1) return SSSP_ERR_CUDA;

@@ -15,7 +15,8 @@ import os
 import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(_HERE, "libsssp.so")
+# SSSP_LIB may name another build of the same library (e.g. a variant for A/B timing)
+LIB_PATH = os.environ.get("SSSP_LIB") or os.path.join(_HERE, "libsssp.so")
 
 SSSP_RHO, SSSP_DELTA_STAR, SSSP_BELLMAN_FORD = 0, 1, 2
 ALGOS = {"rho": SSSP_RHO, "delta_star": SSSP_DELTA_STAR, "bellman_ford": SSSP_BELLMAN_FORD}
@@ -34,11 +35,14 @@ _lib = ctypes.CDLL(LIB_PATH)
 class sssp_step_trace(ctypes.Structure):
     _fields_ = [("theta", ctypes.c_uint64), ("queued", ctypes.c_uint32),
                 ("extracted", ctypes.c_uint32), ("edges", ctypes.c_uint64),
-                ("updates", ctypes.c_uint64), ("t_ns", ctypes.c_uint64)]
+                ("updates", ctypes.c_uint64), ("t_ns", ctypes.c_uint64),
+                ("t_relax_ns", ctypes.c_uint64), ("t_extract_end_max", ctypes.c_uint64),
+                ("t_relax_end_min", ctypes.c_uint64), ("t_relax_end_max", ctypes.c_uint64)]
 
 
 TRACE_DTYPE = [("theta", "<u8"), ("queued", "<u4"), ("extracted", "<u4"), ("edges", "<u8"),
-               ("updates", "<u8"), ("t_ns", "<u8")]
+               ("updates", "<u8"), ("t_ns", "<u8"), ("t_relax_ns", "<u8"),
+               ("t_extract_end_max", "<u8"), ("t_relax_end_min", "<u8"), ("t_relax_end_max", "<u8")]
 
 
 class sssp_stats(ctypes.Structure):

@@ -47,6 +47,30 @@ def algorithmic_bytes(st: dict) -> int:
             BYTES_PER_EDGE * st["edges"] + BYTES_PER_UPDATE * st["updates"])
 
 
+def kernel_hash() -> str:
+    import hashlib
+    h = hashlib.sha256()
+    for f in ("paper_2105_06145_gb300/csrc/sssp_kernels.cu", "paper_2105_06145_gb300/csrc/sssp_internal.h"):
+        with open(os.path.join(ROOT, f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def captured_traffic():
+    """(bytes, edges) of the committed ncu DRAM capture of solve_kernel, if it
+    was taken on the current kernel source; else None."""
+    path = os.path.join(ROOT, "profiles", "solve_kernel_rmat22_rho2e18_dram.md")
+    try:
+        for line in open(path):
+            if line.startswith("traffic:"):
+                kv = dict(x.split("=") for x in line.split()[1:])
+                if kv.get("kernel_sha256_16") == kernel_hash():
+                    return int(kv["bytes"]), int(kv["edges"])
+    except OSError:
+        pass
+    return None
+
+
 def load_peaks() -> tuple[float, str]:
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     try:
@@ -198,7 +222,7 @@ def main():
         dist.init_process_group("nccl")
         pg = dist
     algo = sssp.ALGOS[args.algo]
-    param = args.param or {"rho": 1 << 20, "delta_star": 1 << 15, "bellman_ford": 0}[args.algo]
+    param = args.param or {"rho": 1 << 18, "delta_star": 1 << 15, "bellman_ford": 0}[args.algo]
     if args.workload == "road" and not args.param and args.algo == "delta_star":
         param = 1 << 13
 
@@ -252,7 +276,32 @@ def main():
     abytes = [algorithmic_bytes(s) for s in stats]
     ach_gbs = float(np.mean([b / (t * 1e-3) / 1e9 for b, t in zip(abytes, per_ms)]))
     floor_bytes = 8 * g.m + 28 * g.n
+    cap = captured_traffic() if args.workload == "rmat" and args.scale == 22 else None
+    traffic = None
+    if cap is not None:  # scale the captured launch's DRAM bytes by edges scanned
+        traffic = cap[0] / cap[1] * float(np.mean([s_["edges"] for s_ in stats]))
     floor_gbs = floor_bytes / (np.mean(per_ms) * 1e-3) / 1e9
+
+    # Calibration: a stream + random-gather ceiling on this GPU, measured with a
+    # library routine (torch.index_select of the graph's m edge targets into the
+    # n-entry distance array: 8 B streamed index + one random 8-byte gather per
+    # edge, the relaxation's memory pattern without its atomics).
+    gather = None
+    if rank == 0:
+        idx = torch.from_numpy(g.tgt.astype(np.int64))
+        idx = idx.to("cuda", non_blocking=False)
+        outg = torch.empty(g.m, dtype=torch.int64, device="cuda")
+        for _ in range(2):
+            torch.index_select(dist_out, 0, idx, out=outg)
+        ge0, ge1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        ge0.record()
+        for _ in range(3):
+            torch.index_select(dist_out, 0, idx, out=outg)
+        ge1.record()
+        torch.cuda.synchronize()
+        gms = ge0.elapsed_time(ge1) / 3
+        gather = {"gathers_per_s": g.m / (gms * 1e-3), "kernel": "torch.index_select (int64 index)"}
+        del idx, outg
 
     # end-to-end through the C ABI with a host output buffer (pinned)
     e2e = None
@@ -295,11 +344,13 @@ def main():
                        "l2": "inputs larger than L2 (packed edges %.2f GB > 129 MB L2)" % (8 * g.m / 1e9),
                        "per_solve_mean": mean_stats},
             "roofline": {"bound": "hbm", "achieved": ach_gbs, "peak": peak, "unit": "GB/s",
-                         "frac": ach_gbs / peak, "traffic": None,
+                         "frac": ach_gbs / peak, "traffic": traffic,
                          "peak_kind": peak_kind + " (burst copy)",
                          "kernel": "sssp::solve_kernel (persistent, one launch per solve)",
                          "algorithmic_bytes_per_launch": float(np.mean(abytes)),
-                         "floor_frac": floor_gbs / peak},
+                         "floor_frac": floor_gbs / peak,
+                         "edge_scan_rate": float(np.mean([s_["edges"] for s_ in stats]) / (np.mean(per_ms) * 1e-3)),
+                         "gather_ceiling": gather},
             "cpu_baseline": cpu,
             "e2e": e2e,
             "gpu_launches": K,

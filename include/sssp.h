@@ -172,6 +172,48 @@ int sssp_rho_threshold(const uint32_t* queue, uint32_t q, const uint64_t* dist, 
                        uint64_t rho, uint64_t seed, uint64_t step, uint32_t dense_before,
                        uint64_t* theta_out, void* stream);
 
+/* ------------------------------------------------------------------------ */
+/* Batched solves: many independent instances of the stepping loop (each its */
+/* own source, parameter, LaB-PQ and threshold; Algorithm 1 / Table 2) in   */
+/* one persistent launch.  The results equal k separate sssp_solve calls.    */
+/* ------------------------------------------------------------------------ */
+
+#define SSSP_MAX_BATCH 2048   /* instances per batched call */
+
+/*
+ * k sources on one graph.
+ *   sources   HOST uint32[k], each < n (repeats allowed)
+ *   params    HOST uint64[k] per-instance rho / Delta (as for sssp_solve), or
+ *             NULL: rho = max(64, n/16), Delta = max(1, mean weight / 4)
+ *   dist_out  DEVICE uint64[k * n], instance-major: instance i's distances at
+ *             dist_out[i*n .. i*n + n)
+ * Asynchronous on `stream`.  Working memory (per instance: queue bitmap, two
+ * queue lists, extraction records) is a library-owned per-device workspace
+ * grown to the largest batch seen; batched calls on one device share it, so
+ * they must be ordered (one stream, or host synchronisation).  Errors:
+ * INVALID_ARG (k = 0 or > SSSP_MAX_BATCH, bad source or parameter, graphs on
+ * different devices), OUT_OF_MEMORY, CUDA; device-side status via
+ * sssp_batch_last_stats.
+ */
+int sssp_solve_sources(const sssp_graph* g, const uint32_t* sources, uint32_t k, sssp_algo algo,
+                       const uint64_t* params, uint64_t* dist_out, void* stream);
+
+/*
+ * k independent graphs, one source each (instance i solves gs[i] from
+ * sources[i] into dist_outs[i], a DEVICE uint64[n_i]).  gs and dist_outs are
+ * HOST arrays of k entries; graphs may repeat.  Otherwise as
+ * sssp_solve_sources.
+ */
+int sssp_solve_multi(const sssp_graph* const* gs, const uint32_t* sources, uint32_t k, sssp_algo algo,
+                     const uint64_t* params, uint64_t* const* dist_outs, void* stream);
+
+/*
+ * Waits for `stream`, then copies the per-instance totals of the last batched
+ * call on the current device to HOST out[0..k) (k <= that call's k) and
+ * returns its device status (SSSP_OK, SSSP_ERR_TIMEOUT, SSSP_ERR_INTERNAL).
+ */
+int sssp_batch_last_stats(sssp_stats* out, uint32_t k, void* stream);
+
 /* Largest graph sssp_solve_noalloc accepts. */
 #define SSSP_NOALLOC_MAX_VERTICES (1u << 18)   /* 262,144 vertices            */
 #define SSSP_NOALLOC_MAX_EDGES (1ull << 22)    /* 4,194,304 directed edges     */

@@ -15,8 +15,8 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libsssp.so")
-SOURCES = ["sssp_kernels.cu", "sssp_api.cu", "sssp_noalloc.cu"]
-HEADERS = ["sssp_internal.h", os.path.join("..", "..", "include", "sssp.h")]
+SOURCES = ["sssp_kernels.cu", "sssp_api.cu", "sssp_noalloc.cu", "sssp_batch.cu"]
+HEADERS = ["sssp_internal.h", "sssp_device.cuh", os.path.join("..", "..", "include", "sssp.h")]
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr",

@@ -7,7 +7,6 @@
 #include <cstdint>
 #include <cstdlib>
 #include <cstring>
-#include <mutex>
 #include <new>
 
 #include <cuda_runtime.h>
@@ -16,27 +15,8 @@
 
 using namespace sssp;
 
-struct sssp_graph {
-    uint32_t n = 0;
-    uint64_t m = 0;
-    int device = 0;
-    int num_sms = 0;
-    uint64_t* d_off = nullptr;
-    uint2* d_edges = nullptr;
-    // scratch
-    uint32_t* d_inq = nullptr;
-    uint32_t* d_qa = nullptr;
-    uint32_t* d_qb = nullptr;
-    uint4* d_fsmall = nullptr;
-    uint64_t fsmall_cap = 0;
-    uint4* d_items = nullptr;
-    uint64_t item_cap = 0;
-    Ctrl* d_ctrl = nullptr;
-    uint64_t* d_dist_internal = nullptr;   // lazily allocated for sssp_solve_host
-    Ctrl* h_ctrl = nullptr;                // pinned readback
-    uint32_t last_grid = 0;
-    std::mutex mu;                         // guards lazy allocations / attributes
-};
+// struct sssp_graph is defined in sssp_internal.h
+
 
 namespace {
 
@@ -116,6 +96,8 @@ int sssp_graph_create(uint32_t n, uint64_t m, const uint64_t* offsets, const uin
     // exact capacities of the relaxation records one Extract can produce:
     // each vertex is queued at most once, so at most every vertex at once
     uint64_t small_cap = 0, item_cap = 0;
+    unsigned __int128 wsum = 0;
+    for (uint64_t e = 0; e < m; ++e) wsum += weights[e];
     for (uint32_t u = 0; u < n; ++u) {
         const uint64_t deg = offsets[u + 1] - offsets[u];
         if (deg == 0) continue;
@@ -136,6 +118,7 @@ int sssp_graph_create(uint32_t n, uint64_t m, const uint64_t* offsets, const uin
     uint32_t* d_tgt = nullptr;
     uint32_t* d_w = nullptr;
     g->fsmall_cap = small_cap + 1;
+    g->mean_w = m ? (double)wsum / (double)m : 1.0;
     g->item_cap = item_cap + 1;
     if ((e = dalloc(&g->d_off, (uint64_t)n + 1)) != cudaSuccess ||
         (e = dalloc(&g->d_edges, m_alloc)) != cudaSuccess ||

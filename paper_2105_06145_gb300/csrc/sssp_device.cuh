@@ -1,0 +1,348 @@
+// sssp_device.cuh -- device helpers shared by the solve kernels of libsssp
+// (single solve: sssp_kernels.cu; batched solves: sssp_batch.cu).
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "sssp_internal.h"
+
+namespace sssp {
+
+#define FULL_MASK 0xFFFFFFFFu
+
+// ---------------------------------------------------------------------------
+// small helpers
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ uint64_t ldcg64(const uint64_t* p)
+{
+    return __ldcg(reinterpret_cast<const unsigned long long*>(p));
+}
+__device__ __forceinline__ uint32_t ldcg32(const uint32_t* p) { return __ldcg(p); }
+
+// Load of delta[v] for the relaxation pre-check.  Within a solve delta only
+// decreases after the init barrier, so a value served from a non-coherent L1
+// line can only be too high: the pre-check then lets an extra atomicMin
+// through, never skips a needed one.
+__device__ __forceinline__ uint64_t ld_precheck(const uint64_t* p)
+{
+#ifdef SSSP_PRECHECK_L1
+    return __ldca(reinterpret_cast<const unsigned long long*>(p));
+#else
+    return __ldcg(reinterpret_cast<const unsigned long long*>(p));
+#endif
+}
+
+__device__ __forceinline__ unsigned long long global_timer_ns()
+{
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+__device__ __forceinline__ unsigned long long ld_acquire_u64(const unsigned long long* p)
+{
+    unsigned long long v;
+    asm volatile("ld.acquire.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+    return v;
+}
+
+__device__ __forceinline__ void set_status(int* status, int code) { atomicCAS(status, 0, code); }
+
+// splitmix64 (Steele, Lea, Flood 2014): output k of the generator started at
+// state `seed` is mix(seed + (k+1) * golden_gamma).
+__device__ __forceinline__ uint64_t splitmix64_at(uint64_t seed, uint64_t k)
+{
+    uint64_t z = seed + (k + 1ull) * 0x9E3779B97F4A7C15ull;
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    return z ^ (z >> 31);
+}
+
+__device__ __forceinline__ uint64_t sat_mul(uint64_t a, uint64_t b)
+{
+    return (b != 0 && a > kInf / b) ? kInf : a * b;
+}
+
+// ---------------------------------------------------------------------------
+// bounded grid barrier (all blocks are co-resident: cooperative launch)
+// ---------------------------------------------------------------------------
+static __device__ __noinline__ bool grid_sync(unsigned long long* bar, int* status, unsigned long long* target,
+                                      uint64_t timeout_ns)
+{
+    __shared__ int s_ok;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        const unsigned long long tgt = *target + gridDim.x;
+        *target = tgt;
+        __threadfence();
+        atomicAdd(bar, 1ull);
+        int ok = 1;
+        const unsigned long long t0 = global_timer_ns();
+        unsigned int spins = 0;
+        while (ld_acquire_u64(bar) < tgt) {
+            if ((++spins & 31u) == 0) {
+                if (*reinterpret_cast<volatile int*>(status) != 0) { ok = 0; break; }
+                if (global_timer_ns() - t0 > timeout_ns) { set_status(status, SSSP_ERR_TIMEOUT); ok = 0; break; }
+            }
+        }
+        __threadfence();
+        // an error recorded before the barrier (timeout, capacity, step or time
+        // guard) is visible to every block after it: all of them leave together
+        if (ok && *reinterpret_cast<volatile int*>(status) != 0) ok = 0;
+        s_ok = ok;
+    }
+    __syncthreads();
+    return s_ok != 0;
+}
+
+// ---------------------------------------------------------------------------
+// block-wide scans / reductions (kBlock threads)
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ uint64_t warp_incl_scan64(uint64_t x, uint32_t lane)
+{
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        uint64_t y = __shfl_up_sync(FULL_MASK, x, o);
+        if (lane >= (uint32_t)o) x += y;
+    }
+    return x;
+}
+
+// Exclusive scan of x over the block; *total receives the block sum.
+// s_tmp holds kWarps entries; callers __syncthreads() before reusing it.
+__device__ __forceinline__ uint64_t block_excl_scan64(uint64_t x, uint64_t* s_tmp, uint64_t* total)
+{
+    const uint32_t lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    uint64_t incl = warp_incl_scan64(x, lane);
+    if (lane == 31) s_tmp[wid] = incl;
+    __syncthreads();
+    if (wid == 0) {
+        uint64_t v = lane < (uint32_t)kWarps ? s_tmp[lane] : 0;
+        v = warp_incl_scan64(v, lane);
+        if (lane < (uint32_t)kWarps) s_tmp[lane] = v;
+    }
+    __syncthreads();
+    *total = s_tmp[kWarps - 1];
+    return (wid ? s_tmp[wid - 1] : 0) + incl - x;
+}
+
+__device__ __forceinline__ uint64_t block_reduce_add64(uint64_t x, uint64_t* s_tmp)
+{
+    const uint32_t lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(FULL_MASK, x, o);
+    __syncthreads();
+    if (lane == 0) s_tmp[wid] = x;
+    __syncthreads();
+    uint64_t r = 0;
+    if (threadIdx.x == 0)
+        for (int i = 0; i < kWarps; ++i) r += s_tmp[i];
+    return r;  // valid in thread 0
+}
+
+__device__ __forceinline__ uint64_t block_reduce_min64(uint64_t x, uint64_t* s_tmp)
+{
+    const uint32_t lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        uint64_t y = __shfl_xor_sync(FULL_MASK, x, o);
+        x = y < x ? y : x;
+    }
+    __syncthreads();
+    if (lane == 0) s_tmp[wid] = x;
+    __syncthreads();
+    uint64_t r = kInf;
+    if (threadIdx.x == 0)
+        for (int i = 0; i < kWarps; ++i) r = s_tmp[i] < r ? s_tmp[i] : r;
+    return r;  // valid in thread 0
+}
+
+// ---------------------------------------------------------------------------
+// ExtDist of rho-Stepping (Table 2; Sec. 6 "Threshold estimation"; App. B).
+// Every block evaluates it redundantly from the same inputs (queue list and
+// delta are stable between the previous barrier and the Extract), so no
+// extra device-wide wait is needed.  Returns the same value in all threads.
+// ---------------------------------------------------------------------------
+static __device__ __noinline__ uint64_t rho_extdist_block(const uint32_t* Q, uint32_t q, const uint64_t* dist, uint32_t n,
+                                      uint64_t rho, uint64_t seed, uint64_t step, uint32_t dense_before,
+                                      uint64_t* skeys, uint32_t cap, int* err)
+{
+    __shared__ uint64_t s_theta;
+    uint64_t rho_eff = rho;
+    if ((uint64_t)q * 20ull > (uint64_t)n && dense_before < 2) {
+        rho_eff = rho / 10ull;
+        if (rho_eff < 1) rho_eff = 1;
+    }
+    if ((uint64_t)q <= rho_eff) return kInf;  // extract every queued vertex
+    const uint64_t lg = 63u - (uint32_t)__clzll((long long)((uint64_t)q + 1ull));
+    uint64_t s = 10ull * (((uint64_t)q + rho_eff - 1ull) / rho_eff + 1ull + lg);
+    if (s > kMaxSamples) s = kMaxSamples;
+    uint32_t P = 1;
+    while (P < s) P <<= 1;
+    if (P > cap) {  // smem sized too small by the host: never expected
+        if (threadIdx.x == 0) *err = 1;
+        return kInf;
+    }
+    for (uint32_t j = threadIdx.x; j < P; j += blockDim.x) {
+        uint64_t key = kInf;
+        if (j < s) {
+            const uint64_t h = splitmix64_at(seed, (step << 32) | j);
+            const uint32_t pos = (uint32_t)__umul64hi(h, (uint64_t)q);
+            key = ldcg64(&dist[ldcg32(&Q[pos])]);
+        }
+        skeys[j] = key;
+    }
+    __syncthreads();
+    // bitonic sort of skeys[0..P), ascending
+    for (uint32_t k = 2; k <= P; k <<= 1) {
+        for (uint32_t j = k >> 1; j > 0; j >>= 1) {
+            for (uint32_t i = threadIdx.x; i < P; i += blockDim.x) {
+                const uint32_t ixj = i ^ j;
+                if (ixj > i) {
+                    const uint64_t a = skeys[i], b = skeys[ixj];
+                    const bool up = (i & k) == 0;
+                    if ((a > b) == up) { skeys[i] = b; skeys[ixj] = a; }
+                }
+            }
+            __syncthreads();
+        }
+    }
+    uint64_t r = rho_eff * s / (uint64_t)q;
+    if (r > s - 1) r = s - 1;
+    if (threadIdx.x == 0) s_theta = skeys[r];
+    __syncthreads();
+    const uint64_t th = s_theta;
+    __syncthreads();
+    return th;
+}
+
+// ---------------------------------------------------------------------------
+// Relaxation helpers
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ uint4 make_rec(uint64_t start, uint64_t len, uint64_t du)
+{
+    const uint64_t a = start | (len << 40);
+    return make_uint4((uint32_t)a, (uint32_t)(a >> 32), (uint32_t)du, (uint32_t)(du >> 32));
+}
+__device__ __forceinline__ uint64_t rec_start(uint4 r) { return ((uint64_t)r.x | ((uint64_t)(r.y & 0xFFu) << 32)); }
+__device__ __forceinline__ uint32_t rec_len(uint4 r) { return r.y >> 8; }
+__device__ __forceinline__ uint64_t rec_du(uint4 r) { return (uint64_t)r.z | ((uint64_t)r.w << 32); }
+
+// Warp-uniform: add the lanes' pushes to the warp's staging buffer.
+__device__ __forceinline__ void stage_push(bool push, uint32_t v, uint32_t* stage, uint32_t& stc,
+                                           uint32_t lane)
+{
+    const uint32_t b = __ballot_sync(FULL_MASK, push);
+    if (push) stage[stc + __popc(b & ((1u << lane) - 1u))] = v;
+    stc += __popc(b);
+}
+
+// Warp-uniform: one batch of (up to) 4 relaxations per lane.
+//   1. load delta[v] for the pre-check (4 gathers in flight),
+//   2. for every candidate with cand < delta[v]: WriteMin(delta[v], cand)
+//      (Sec. 2) as a fire-and-forget atomic minimum, then Update(v): the
+//      test-and-set of v's queue bit (all test-and-sets of the batch in flight),
+//   3. stage the ids whose bit was clear for the next queue list.
+// A candidate that passes the pre-check but loses the race to a smaller one
+// still marks v: the winner lowered delta[v] in this same phase and queues v
+// too, so the queued set is exactly the set whose distance dropped, and the
+// bit keeps each vertex at most once in the queue.
+__device__ __forceinline__ void relax_batch4(uint64_t* dist, uint32_t* inq, const uint32_t (&v)[4],
+                                             const uint64_t (&cand)[4], const bool (&ok)[4],
+                                             uint32_t* stage, uint32_t& stc, uint32_t lane,
+                                             uint64_t& lmin, uint32_t& lupd)
+{
+    uint64_t dv[4];
+#pragma unroll
+    for (int t = 0; t < 4; ++t) dv[t] = ok[t] ? ld_precheck(&dist[v[t]]) : 0ull;
+    uint32_t prev[4];
+    uint32_t pass = 0;
+#pragma unroll
+    for (int t = 0; t < 4; ++t) {
+        prev[t] = ~0u;
+        if (ok[t] && cand[t] < dv[t]) {
+            atomicMin(reinterpret_cast<unsigned long long*>(&dist[v[t]]), (unsigned long long)cand[t]);
+            ++lupd;
+            lmin = cand[t] < lmin ? cand[t] : lmin;
+            prev[t] = atomicOr(&inq[v[t] >> 5], 1u << (v[t] & 31u));
+            pass |= 1u << t;
+        }
+    }
+#pragma unroll
+    for (int t = 0; t < 4; ++t) {
+        const bool push = ((pass >> t) & 1u) && (prev[t] & (1u << (v[t] & 31u))) == 0;
+        stage_push(push, v[t], stage, stc, lane);
+    }
+}
+
+// Warp-uniform: move the staged ids to the next queue list (one atomic per flush).
+__device__ __forceinline__ void stage_flush(uint32_t* stage, uint32_t& stc, uint32_t lane, unsigned int* qsize,
+                                            int* status, uint32_t* Qnext, uint32_t cap)
+{
+    __syncwarp();
+    if (stc == 0) return;
+    uint32_t base = 0;
+    if (lane == 0) base = atomicAdd(qsize, stc);
+    base = __shfl_sync(FULL_MASK, base, 0);
+    if ((uint64_t)base + stc > (uint64_t)cap) {
+        if (lane == 0) set_status(status, SSSP_ERR_INTERNAL);
+    } else {
+        for (uint32_t i = lane; i < stc; i += 32) Qnext[base + i] = stage[i];
+    }
+    __syncwarp();
+    stc = 0;
+}
+
+// Warp-uniform: relax the edges of one chunk record (<= kChunk edges of one
+// vertex, within one kChunk-aligned block of the edge array), read as 16-byte
+// pairs of packed edges.
+__device__ __forceinline__ void relax_chunk(uint4 rec, uint64_t du, const uint4* __restrict__ pairs,
+                                            uint64_t* dist, uint32_t* inq, uint32_t* stage, uint32_t& stc,
+                                            uint32_t lane, uint64_t& lmin, uint32_t& lupd)
+{
+    const uint64_t cs = rec_start(rec), ce = cs + rec_len(rec);
+    const uint64_t p0 = cs >> 1, p1 = (ce + 1) >> 1;
+#pragma unroll 1
+    for (uint32_t h = 0; h < kChunkPairs; h += 64) {
+        if (p0 + h >= p1) break;  // warp-uniform
+        uint32_t vv[4];
+        uint64_t cand[4];
+        bool ok[4];
+#pragma unroll
+        for (int t = 0; t < 2; ++t) {
+            const uint64_t P = p0 + h + 32u * t + lane;
+            const bool okp = P < p1;
+            const uint4 pr = okp ? __ldcs(&pairs[P]) : make_uint4(0, 0, 0, 0);
+            vv[2 * t] = pr.x; cand[2 * t] = du + pr.y; ok[2 * t] = okp && 2 * P >= cs;       // 2P < ce when P < p1
+            vv[2 * t + 1] = pr.z; cand[2 * t + 1] = du + pr.w; ok[2 * t + 1] = okp && 2 * P + 1 < ce;  // 2P+1 >= cs when P >= p0
+        }
+        relax_batch4(dist, inq, vv, cand, ok, stage, stc, lane, lmin, lupd);
+    }
+}
+
+// Block-wide reduction of two sums and a minimum; results valid in thread 0.
+__device__ __forceinline__ void block_reduce_2add_min(uint64_t& a, uint64_t& b, uint64_t& mn, uint64_t* s_tmp)
+{
+    const uint32_t lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        a += __shfl_xor_sync(FULL_MASK, a, o);
+        b += __shfl_xor_sync(FULL_MASK, b, o);
+        const uint64_t y = __shfl_xor_sync(FULL_MASK, mn, o);
+        mn = y < mn ? y : mn;
+    }
+    __syncthreads();
+    if (lane == 0) { s_tmp[wid] = a; s_tmp[kWarps + wid] = b; s_tmp[2 * kWarps + wid] = mn; }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        a = 0; b = 0; mn = kInf;
+        for (int i = 0; i < kWarps; ++i) {
+            a += s_tmp[i];
+            b += s_tmp[kWarps + i];
+            mn = s_tmp[2 * kWarps + i] < mn ? s_tmp[2 * kWarps + i] : mn;
+        }
+    }
+}
+
+}  // namespace sssp

@@ -3,6 +3,7 @@
 #pragma once
 
 #include <cstdint>
+#include <mutex>
 #include <cuda_runtime.h>
 
 #include "../../include/sssp.h"
@@ -112,4 +113,43 @@ cudaError_t launch_rho_threshold(const uint32_t* queue, uint32_t q, const uint64
                                  cudaStream_t st);
 uint32_t rho_sample_bound(uint32_t n, uint64_t rho);   // power-of-two smem keys needed
 
+// Batched solves (sssp_batch.cu).
+constexpr uint32_t kMaxBatch = 2048;        // instances per batched launch
+const void* batch_kernel_ptr();
+
 }  // namespace sssp
+
+// Library-side state of one graph handle (host ABI and batched solves).
+struct sssp_graph {
+    uint32_t n = 0;
+    uint64_t m = 0;
+    int device = 0;
+    int num_sms = 0;
+    uint64_t* d_off = nullptr;
+    uint2* d_edges = nullptr;
+    // scratch
+    uint32_t* d_inq = nullptr;
+    uint32_t* d_qa = nullptr;
+    uint32_t* d_qb = nullptr;
+    uint4* d_fsmall = nullptr;
+    uint64_t fsmall_cap = 0;
+    uint4* d_items = nullptr;
+    uint64_t item_cap = 0;
+    sssp::Ctrl* d_ctrl = nullptr;
+    uint64_t* d_dist_internal = nullptr;   // lazily allocated for sssp_solve_host
+    sssp::Ctrl* h_ctrl = nullptr;                // pinned readback
+    uint32_t last_grid = 0;
+    double mean_w = 1.0;                   // mean edge weight (default Delta)
+    std::mutex mu;                         // guards lazy allocations / attributes
+};
+
+// Parameter used when a batched call passes no per-instance parameters: for
+// rho-Stepping rho = max(64, n/16) (the best of the rho sweep on the RMAT
+// scale-22 workload is 2^18 = n/16), for Delta*-Stepping Delta = max(1,
+// mean weight / 4) (best of the Delta sweep there), 0 for Bellman-Ford.
+inline uint64_t sssp_default_param(uint32_t n, uint64_t /*m*/, sssp_algo algo, double mean_w = 4.0)
+{
+    if (algo == SSSP_RHO) return n / 16 > 64 ? n / 16 : 64;
+    if (algo == SSSP_DELTA_STAR) { const double d = mean_w / 4.0; return d > 1.0 ? (uint64_t)d : 1; }
+    return 0;
+}

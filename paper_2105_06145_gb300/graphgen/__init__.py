@@ -60,6 +60,12 @@ def _L():
         lib.graphgen_road.argtypes = [u32, u64, dbl, dbl, u64,
                                       ctypes.POINTER(u32), ctypes.POINTER(u64), PP, PP, PP]
         lib.graphgen_road.restype = i32
+        lib.graphgen_road_w.argtypes = [u32, u64, dbl, dbl, u64, u32, u64,
+                                        ctypes.POINTER(u32), ctypes.POINTER(u64), PP, PP, PP]
+        lib.graphgen_road_w.restype = i32
+        lib.graphgen_rmat_n.argtypes = [u32, u32, dbl, dbl, dbl, u64, u64, u32, u32,
+                                        ctypes.POINTER(u32), ctypes.POINTER(u64), PP, PP, PP]
+        lib.graphgen_rmat_n.restype = i32
         lib.graphgen_random.argtypes = [u32, u64, u32, u32, u64, i32,
                                         ctypes.POINTER(u64), PP, PP, PP]
         lib.graphgen_random.restype = i32
@@ -175,14 +181,14 @@ def rmat(scale: int, edgefactor: int = 16, a: float = 0.57, b: float = 0.19, c: 
     return g
 
 
-def _rmat(scale, edgefactor, a, b, c, gen_seed, wseed, wmax_excl) -> CSR:
+def _rmat(scale, edgefactor, a, b, c, gen_seed, wseed, wmax_excl, n_keep=0) -> CSR:
     lib = _L()
     n = ctypes.c_uint32()
     m = ctypes.c_uint64()
     po, pt, pw = ctypes.c_void_p(), ctypes.c_void_p(), ctypes.c_void_p()
-    rc = lib.graphgen_rmat(scale, edgefactor, a, b, c, gen_seed, wseed, wmax_excl,
-                           ctypes.byref(n), ctypes.byref(m),
-                           ctypes.byref(po), ctypes.byref(pt), ctypes.byref(pw))
+    rc = lib.graphgen_rmat_n(scale, edgefactor, a, b, c, gen_seed, wseed, wmax_excl, n_keep,
+                             ctypes.byref(n), ctypes.byref(m),
+                             ctypes.byref(po), ctypes.byref(pt), ctypes.byref(pw))
     if rc != 0:
         raise MemoryError("graphgen_rmat failed")
     nn, mm = n.value, m.value
@@ -202,14 +208,15 @@ def road(side: int, keep: float = 0.75, seed: int = 5, jitter: float = 0.4,
     return g
 
 
-def _road(side, keep, seed, jitter, wscale) -> CSR:
+def _road(side, keep, seed, jitter, wscale, wmax_excl=0, wseed=0) -> CSR:
     lib = _L()
     keep_num = min((1 << 64) - 1, int(round(keep * float(1 << 64))))
     n = ctypes.c_uint32()
     m = ctypes.c_uint64()
     po, pt, pw = ctypes.c_void_p(), ctypes.c_void_p(), ctypes.c_void_p()
-    rc = lib.graphgen_road(side, keep_num, jitter, wscale, seed, ctypes.byref(n), ctypes.byref(m),
-                           ctypes.byref(po), ctypes.byref(pt), ctypes.byref(pw))
+    rc = lib.graphgen_road_w(side, keep_num, jitter, wscale, seed, wmax_excl, wseed,
+                             ctypes.byref(n), ctypes.byref(m),
+                             ctypes.byref(po), ctypes.byref(pt), ctypes.byref(pw))
     if rc != 0:
         raise MemoryError("graphgen_road failed")
     nn, mm = n.value, m.value
@@ -329,3 +336,45 @@ def workload_road(side: int = 4096) -> tuple[CSR, int]:
             if 0 <= v < g.n and lab[v]:
                 return g, int(v)
         d += 1
+
+
+def rmat_n(n: int, edgefactor: int, gen_seed: int, wseed: int, wmax_excl: int = WMAX_EXCL) -> CSR:
+    """RMAT at scale ceil(log2 n) with the edges that have an endpoint >= n
+    rejected (after the relabelling), so the graph has exactly n vertices."""
+    scale = max(1, int(n - 1).bit_length())
+    g = _rmat(scale, edgefactor, 0.57, 0.19, 0.19, gen_seed, wseed, wmax_excl, n)
+    g.name = f"rmat_n{n}"
+    return g
+
+
+def jittered_grid_uniform(side: int, seed: int, wseed: int, keep: float = 0.75,
+                          wmax_excl: int = WMAX_EXCL) -> CSR:
+    """The road generator's topology (jittered side x side grid, edges kept with
+    probability `keep`) with weights uniform in [1, wmax_excl)."""
+    g = _road(side, keep, seed, 0.4, 1000.0, wmax_excl, wseed)
+    g.name = f"jgrid{side}"
+    return g
+
+
+def workload_multi(count: int = 512, lo_log2: int = 10, hi_log2: int = 18, seed: int = 7,
+                   rmat_edgefactor: int = 6) -> list[tuple[CSR, int]]:
+    """Many independent graphs of uneven size: n log-uniform in
+    [2^lo_log2, 2^hi_log2]; the first half jittered grids (side ceil(sqrt n),
+    edges kept with probability 0.75), the second half RMAT at scale
+    ceil(log2 n) with out-of-range endpoints rejected (edge factor 6 keeps the
+    total near 2^27 directed edges for the default 512 graphs); weights uniform
+    in [1, 2^18); one source per graph uniform in its largest component."""
+    out = []
+    for i in range(count):
+        u = (_sm64(seed, 3 * i) >> 11) * (1.0 / (1 << 53))
+        n = int(round(2.0 ** (lo_log2 + (hi_log2 - lo_log2) * u)))
+        gseed = _sm64(seed, 3 * i + 1) & 0x7FFFFFFF
+        wseed = _sm64(seed, 3 * i + 2) & 0x7FFFFFFF
+        if i < count // 2:
+            side = int(np.ceil(np.sqrt(n)))
+            g = jittered_grid_uniform(side, gseed, wseed)
+        else:
+            g = rmat_n(n, rmat_edgefactor, gseed, wseed)
+        src = pick_sources(g, 1, gseed)[0]
+        out.append((g, src))
+    return out

@@ -154,10 +154,26 @@ static int64_t gg_symmetrise(uint64_t* keys, uint64_t cnt, int sh)
 /* no noise, then a seeded random relabelling of the vertices, then         */
 /* symmetrise, drop self-loops, sort, unique.                                */
 /* ------------------------------------------------------------------------ */
+int graphgen_rmat_n(uint32_t scale, uint32_t edgefactor, double a, double b, double c,
+                    uint64_t gen_seed, uint64_t wseed, uint32_t wmax_excl, uint32_t n_keep,
+                    uint32_t* n_out, uint64_t* m_out,
+                    uint64_t** off, uint32_t** tgt, uint32_t** w);
+
 int graphgen_rmat(uint32_t scale, uint32_t edgefactor, double a, double b, double c,
                   uint64_t gen_seed, uint64_t wseed, uint32_t wmax_excl,
                   uint32_t* n_out, uint64_t* m_out,
                   uint64_t** off, uint32_t** tgt, uint32_t** w)
+{
+    return graphgen_rmat_n(scale, edgefactor, a, b, c, gen_seed, wseed, wmax_excl, 0,
+                           n_out, m_out, off, tgt, w);
+}
+
+/* As graphgen_rmat; when 0 < n_keep < 2^scale, edges with an endpoint >= n_keep
+ * (after the relabelling) are rejected and the graph has n_keep vertices. */
+int graphgen_rmat_n(uint32_t scale, uint32_t edgefactor, double a, double b, double c,
+                    uint64_t gen_seed, uint64_t wseed, uint32_t wmax_excl, uint32_t n_keep,
+                    uint32_t* n_out, uint64_t* m_out,
+                    uint64_t** off, uint32_t** tgt, uint32_t** w)
 {
     if (scale < 1 || scale > 30) return -1;
     uint32_t n = 1u << scale;
@@ -194,16 +210,20 @@ int graphgen_rmat(uint32_t scale, uint32_t edgefactor, double a, double b, doubl
         uint32_t t = perm[i]; perm[i] = perm[j]; perm[j] = t;
     }
     uint64_t mask = ((uint64_t)1 << scale) - 1u;
+    uint32_t nk = (n_keep > 0 && n_keep < n) ? n_keep : n;
+    uint64_t kept = 0;
     for (uint64_t e = 0; e < E; ++e) {
         uint32_t u = perm[keys[e] >> scale], v = perm[keys[e] & mask];
-        keys[e] = ((uint64_t)u << scale) | v;
+        if (u >= nk || v >= nk) continue;
+        keys[kept++] = ((uint64_t)u << scale) | v;
     }
     free(perm);
-    int64_t m = gg_symmetrise(keys, E, (int)scale);
+    int64_t m = gg_symmetrise(keys, kept, (int)scale);
     if (m < 0) { free(keys); return -1; }
-    int rc = gg_keys_to_csr(keys, (uint64_t)m, n, (int)scale, wseed, wmax_excl, off, tgt, w);
+    int rc = gg_keys_to_csr(keys, (uint64_t)m, nk, (int)scale, wseed, wmax_excl, off, tgt, w);
     free(keys);
     if (rc) return rc;
+    n = nk;
     *n_out = n;
     *m_out = (uint64_t)m;
     return 0;
@@ -217,9 +237,22 @@ int graphgen_rmat(uint32_t scale, uint32_t edgefactor, double a, double b, doubl
 /* ------------------------------------------------------------------------ */
 static inline double gg_unit(uint64_t h) { return (double)(h >> 11) * (1.0 / 9007199254740992.0); }
 
+int graphgen_road_w(uint32_t side, uint64_t keep_num, double jitter, double wscale,
+                    uint64_t seed, uint32_t wmax_excl, uint64_t wseed, uint32_t* n_out, uint64_t* m_out,
+                    uint64_t** off_out, uint32_t** tgt_out, uint32_t** w_out);
+
 int graphgen_road(uint32_t side, uint64_t keep_num, double jitter, double wscale,
                   uint64_t seed, uint32_t* n_out, uint64_t* m_out,
                   uint64_t** off_out, uint32_t** tgt_out, uint32_t** w_out)
+{
+    return graphgen_road_w(side, keep_num, jitter, wscale, seed, 0, 0, n_out, m_out, off_out, tgt_out, w_out);
+}
+
+/* As graphgen_road; wmax_excl > 0 replaces the geometric weights by weights
+ * uniform in [1, wmax_excl) drawn from wseed (same topology). */
+int graphgen_road_w(uint32_t side, uint64_t keep_num, double jitter, double wscale,
+                    uint64_t seed, uint32_t wmax_excl, uint64_t wseed, uint32_t* n_out, uint64_t* m_out,
+                    uint64_t** off_out, uint32_t** tgt_out, uint32_t** w_out)
 {
     uint64_t n64 = (uint64_t)side * side;
     if (side == 0 || n64 > 0xFFFFFFFFull) return -1;
@@ -269,7 +302,8 @@ int graphgen_road(uint32_t side, uint64_t keep_num, double jitter, double wscale
                 double dy = py[nb[j]] - py[id];
                 double len = sqrt(dx * dx + dy * dy);
                 tgt[e] = (uint32_t)nb[j];
-                w[e] = (uint32_t)floor(wscale * len) + 1u;
+                w[e] = wmax_excl ? gg_pair_weight(wseed, (uint32_t)id, (uint32_t)nb[j], wmax_excl)
+                                 : (uint32_t)floor(wscale * len) + 1u;
                 ++e;
             }
         }

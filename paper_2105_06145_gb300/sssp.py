@@ -88,12 +88,21 @@ _lib.sssp_rho_threshold.argtypes = [_P, _u32, _P, _u32, _u64, _u64, _u64, _u32, 
 _lib.sssp_rho_threshold.restype = _i32
 _lib.sssp_solve_noalloc.argtypes = [_u32, _u64, _P, _P, _u32, _i32, _u64, _P, _P, _P]
 _lib.sssp_solve_noalloc.restype = _i32
+_lib.sssp_solve_sources.argtypes = [_P, _P, _u32, _i32, _P, _P, _P]
+_lib.sssp_solve_sources.restype = _i32
+_lib.sssp_solve_multi.argtypes = [_P, _P, _u32, _i32, _P, _P, _P]
+_lib.sssp_solve_multi.restype = _i32
+_lib.sssp_batch_last_stats.argtypes = [_P, _u32, _P]
+_lib.sssp_batch_last_stats.restype = _i32
 _lib.sssp_status_string.argtypes = [_i32]
 _lib.sssp_status_string.restype = ctypes.c_char_p
 
 EXPORTED = ["sssp_graph_create", "sssp_graph_destroy", "sssp_graph_info", "sssp_solve",
             "sssp_solve_ex", "sssp_solve_host", "sssp_last_status", "sssp_last_stats",
-            "sssp_rho_threshold", "sssp_status_string", "sssp_solve_noalloc"]
+            "sssp_rho_threshold", "sssp_status_string", "sssp_solve_noalloc", "sssp_solve_sources",
+            "sssp_solve_multi", "sssp_batch_last_stats"]
+
+MAX_BATCH = 2048
 
 NOALLOC_MAX_VERTICES = 1 << 18
 NOALLOC_MAX_EDGES = 1 << 22
@@ -200,6 +209,38 @@ def sssp_solve_noalloc(n: int, m: int, offsets_ptr: int, edges_ptr: int, source:
     rc = _lib.sssp_solve_noalloc(n, m, offsets_ptr or None, edges_ptr or None, source, algo, param,
                                  dist_out_ptr or None, stats_out_ptr or None, stream or None)
     return _check(rc, "sssp_solve_noalloc") if check else rc
+
+
+def sssp_solve_sources(g: int, sources, algo: int, params, dist_out_ptr: int, stream: int = 0,
+                       check: bool = True) -> int:
+    """k sources on one graph; dist_out_ptr: device uint64[k*n] (instance-major)."""
+    src = np.ascontiguousarray(sources, dtype=np.uint32)
+    prm = None if params is None else np.ascontiguousarray(params, dtype=np.uint64)
+    rc = _lib.sssp_solve_sources(g, src.ctypes.data, src.size, algo,
+                                 prm.ctypes.data if prm is not None else None, dist_out_ptr, stream or None)
+    return _check(rc, "sssp_solve_sources") if check else rc
+
+
+def sssp_solve_multi(graphs, sources, algo: int, params, dist_out_ptrs, stream: int = 0,
+                     check: bool = True) -> int:
+    """One source per graph; graphs: sequence of handles; dist_out_ptrs: device pointers."""
+    k = len(graphs)
+    gs = (ctypes.c_void_p * k)(*graphs)
+    outs = (ctypes.c_void_p * k)(*dist_out_ptrs)
+    src = np.ascontiguousarray(sources, dtype=np.uint32)
+    prm = None if params is None else np.ascontiguousarray(params, dtype=np.uint64)
+    rc = _lib.sssp_solve_multi(gs, src.ctypes.data, k, algo, prm.ctypes.data if prm is not None else None,
+                               outs, stream or None)
+    return _check(rc, "sssp_solve_multi") if check else rc
+
+
+def sssp_batch_last_stats(k: int, stream: int = 0) -> tuple[int, list]:
+    """(device status, per-instance stats dicts) of the last batched call."""
+    arr = (sssp_stats * max(k, 1))()
+    rc = _lib.sssp_batch_last_stats(arr, k, stream or None)
+    if rc < 0 and rc not in (SSSP_ERR_TIMEOUT, SSSP_ERR_INTERNAL):
+        raise SSSPError(rc, "sssp_batch_last_stats")
+    return rc, [arr[i].as_dict() for i in range(k)]
 
 
 class Graph:

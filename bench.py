@@ -190,6 +190,52 @@ def run_reference(args, g, srcs, label, rank, world):
     print(json.dumps(line), flush=True)
 
 
+def measure_batched(sssp, G, g, torch, stream, stream_obj) -> dict:
+    """configs[3]: (a) 64 sources on this graph in one launch, (b) 512 graphs of
+    uneven size in one launch; each against the plain loop of single solves."""
+    from paper_2105_06145_gb300 import graphgen as gg
+
+    def timed(fn):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        with torch.cuda.stream(stream_obj):
+            fn()
+            torch.cuda.synchronize()
+            e0.record(stream_obj)
+            fn()
+            e1.record(stream_obj)
+            torch.cuda.synchronize()
+        return e0.elapsed_time(e1)
+
+    res = {}
+    srcs = gg.pick_sources(g, 64, 6)
+    out = torch.empty(64 * g.n, dtype=torch.int64, device="cuda")
+    one = torch.empty(g.n, dtype=torch.int64, device="cuda")
+    rho = 1 << 18
+    tb = timed(lambda: sssp.sssp_solve_sources(G.handle, srcs, sssp.SSSP_RHO, [rho] * 64, out.data_ptr(), stream))
+    st, _ = sssp.sssp_batch_last_stats(64, stream)
+    tp = timed(lambda: [G.solve(s_, sssp.SSSP_RHO, rho, one, stream) for s_ in srcs])
+    same = bool(torch.equal(out.view(64, g.n)[-1], one))
+    res["sources64_rmat22"] = {"queries_per_s": 64e3 / tb, "plain_queries_per_s": 64e3 / tp,
+                               "speedup": tp / tb, "status": st, "last_equal_to_single": same}
+    del out, one
+    W = gg.workload_multi()
+    Gs = [sssp.Graph(h) for h, _ in W]
+    outs = [torch.empty(h.n, dtype=torch.int64, device="cuda") for h, _ in W]
+    hs, ss, ptrs = [x.handle for x in Gs], [s_ for _, s_ in W], [o.data_ptr() for o in outs]
+    tb = timed(lambda: sssp.sssp_solve_multi(hs, ss, sssp.SSSP_RHO, None, ptrs, stream))
+    st, _ = sssp.sssp_batch_last_stats(len(W), stream)
+    keep = [o.clone() for o in outs[:8]]
+    tp = timed(lambda: [Gx.solve(s_, sssp.SSSP_RHO, max(64, h.n // 16), o, stream)
+                        for (h, s_), Gx, o in zip(W, Gs, outs)])
+    same = all(bool(torch.equal(a, b)) for a, b in zip(keep, outs[:8]))
+    res["graphs512"] = {"queries_per_s": len(W) * 1e3 / tb, "plain_queries_per_s": len(W) * 1e3 / tp,
+                        "speedup": tp / tb, "status": st, "edges_total": int(sum(h.m for h, _ in W)),
+                        "first8_equal_to_single": same}
+    for Gx in Gs:
+        Gx.close()
+    return res
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -203,6 +249,7 @@ def main():
     ap.add_argument("--cpu-baseline-sources", type=int, default=3)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-batch", action="store_true", help="skip the batched-solve measurements")
     args = ap.parse_args()
 
     rank, world, local = dist_env()
@@ -320,6 +367,12 @@ def main():
                "note": "graph resident; per step the source id and parameter go in as launch "
                        "arguments and the uint64 distance array comes back to pinned host memory"}
 
+    # batched solves (SURVEY pattern 2): queries/s of one batched launch vs the
+    # plain loop of single solves on the same GPU, identical distances
+    batched = None
+    if rank == 0 and not args.no_batch and args.workload == "rmat" and args.scale == 22:
+        batched = measure_batched(sssp, G, g, torch, stream, stream_obj)
+
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
         import oracle
@@ -353,6 +406,7 @@ def main():
                          "gather_ceiling": gather},
             "cpu_baseline": cpu,
             "e2e": e2e,
+            "batched": batched,
             "gpu_launches": K,
             "clocks": clk,
         }

@@ -214,6 +214,70 @@ int sssp_solve_multi(const sssp_graph* const* gs, const uint32_t* sources, uint3
  */
 int sssp_batch_last_stats(sssp_stats* out, uint32_t k, void* stream);
 
+/* ------------------------------------------------------------------------ */
+/* Serving: a query server with continuous batching over resident graphs.    */
+/* Queries (one source each) are admitted into device slots as slots free up;*/
+/* a query that arrives while others run joins them at the next step        */
+/* boundary of a long-lived persistent launch, so their steps overlap on the */
+/* device.  Each result equals the single solve of the same source.         */
+/* ------------------------------------------------------------------------ */
+
+typedef struct sssp_server sssp_server;
+
+typedef struct {
+    uint32_t slots;        /* queries on the device at once; 0 = as many as fit      */
+    sssp_algo algo;        /* ExtDist rule of every query                            */
+    uint64_t param;        /* rho / Delta; 0 = max(64, n/16) / max(1, mean weight/4) */
+    uint64_t idle_ns;      /* the device loop exits after this long without a query  */
+                           /* (0 = 2 ms; at most 1 s); it restarts on the next query */
+    double hbm_fraction;   /* share of free HBM the slots may take (0 = 0.5)         */
+} sssp_server_config;
+
+typedef struct {
+    int32_t status;        /* device status of the query (SSSP_OK, ...)              */
+    uint32_t steps;        /* steps the query took                                   */
+    uint64_t latency_ns;   /* host: submit -> completion seen by the server thread   */
+    uint64_t device_ns;    /* device: admission -> completion                        */
+    uint64_t device_admit_ns, device_done_ns; /* device clock at admission / completion */
+    uint64_t edges;        /* edges the query scanned                                */
+} sssp_query_info;
+
+/*
+ * Create a server for graph g.  Slots are admitted by free HBM: each slot's
+ * working memory (queue bitmap, two queue lists, extraction records) comes out
+ * of hbm_fraction of the free device memory, capped at SSSP_MAX_BATCH and at
+ * cfg->slots.  Starts a host thread that assigns queries to slots, keeps the
+ * device loop running while there is work and collects completions (through
+ * host-mapped memory).  While the device loop runs it occupies every SM.
+ * Errors: INVALID_ARG, OUT_OF_MEMORY (not one slot fits), CUDA.
+ */
+int sssp_server_create(const sssp_graph* g, const sssp_server_config* cfg, sssp_server** out);
+
+/* Number of slots the server got. */
+int sssp_server_slots(const sssp_server* s, uint32_t* slots);
+
+/*
+ * Queue a query; non-blocking, thread-safe.  dist_out: caller-owned DEVICE
+ * uint64[n] that receives the distances (it must stay valid and untouched
+ * until the query completes).  *ticket identifies the query.
+ */
+int sssp_server_submit(sssp_server* s, uint32_t source, uint64_t* dist_out, uint64_t* ticket);
+
+/* 1 and *info when the query is complete (the ticket is then released), 0 while
+ * pending, a negative status on error. */
+int sssp_server_poll(sssp_server* s, uint64_t ticket, sssp_query_info* info);
+
+/* As sssp_server_poll, but blocks until completion or timeout_ns (0 = 60 s;
+ * SSSP_ERR_TIMEOUT then). */
+int sssp_server_wait(sssp_server* s, uint64_t ticket, uint64_t timeout_ns, sssp_query_info* info);
+
+/* Device-loop launches so far, slots in use, queries waiting for a slot. */
+int sssp_server_stats(const sssp_server* s, uint64_t* launches, uint32_t* busy_slots, uint64_t* pending);
+
+/* Stop the device loop and the host thread, release everything.  Queries not
+ * yet complete are abandoned. */
+int sssp_server_destroy(sssp_server* s);
+
 /* Largest graph sssp_solve_noalloc accepts. */
 #define SSSP_NOALLOC_MAX_VERTICES (1u << 18)   /* 262,144 vertices            */
 #define SSSP_NOALLOC_MAX_EDGES (1ull << 22)    /* 4,194,304 directed edges     */

@@ -17,10 +17,17 @@
 // An instance whose queue is empty simply has no work.  The fixed per-step
 // costs (barriers, phase latencies) are paid once for all instances.
 
+#include <atomic>
+#include <chrono>
+#include <condition_variable>
 #include <cstdint>
 #include <cstring>
+#include <deque>
 #include <mutex>
+#include <thread>
+#include <unordered_map>
 #include <vector>
+#include <new>
 
 #include <cuda_runtime.h>
 
@@ -40,6 +47,11 @@ struct InstCtrl {
     unsigned int dense_seen;       // rho-Stepping: dense steps so far
     unsigned int last_step;        // steps the instance took (set when its queue empties)
     unsigned long long queued, extracted, edges, updates_total;
+    unsigned long long admit_step; // global step at which the instance's first queue is read
+    unsigned int running;          // the instance takes part in the steps
+    unsigned int seq;              // serving: sequence number of the admitted query
+    unsigned long long t_admit_ns; // serving: device time of admission
+    unsigned long long ticket;     // serving: ticket of the admitted query
 };
 
 // Per-instance pointers and sizes (device, read-only during the launch).
@@ -68,7 +80,7 @@ struct BatchCtrl {
 };
 
 struct BatchParams {
-    const InstDesc* inst;
+    InstDesc* inst;
     InstCtrl* ictrl;
     BatchCtrl* ctrl;
     uint32_t k;
@@ -108,247 +120,256 @@ __device__ __forceinline__ uint32_t find_segment(const uint32_t* s_pre, uint32_t
     return lo;
 }
 
-__global__ void __launch_bounds__(kBlock, 1) batch_kernel(BatchParams p)
-{
-    extern __shared__ __align__(16) unsigned char s_dyn[];
-    uint32_t* s_stage = reinterpret_cast<uint32_t*>(s_dyn);  // [kWarps][kStage]
-    uint64_t* s_keys = reinterpret_cast<uint64_t*>(s_dyn);   // rho samples (aliases the empty staging)
-    __shared__ uint32_t s_pre0[kMaxBatch + 1];
-    __shared__ uint32_t s_pre1[kMaxBatch + 1];
-    __shared__ uint64_t s_tmp[3 * kWarps];
-    __shared__ uint32_t s_base[3];
-    __shared__ unsigned long long s_bar_target, s_t_start;
-    __shared__ int s_err;
+// Shared memory of the batched kernels.
+struct BatchSmem {
+    uint32_t pre0[kMaxBatch + 1];
+    uint32_t pre1[kMaxBatch + 1];
+    uint64_t tmp[3 * kWarps];
+    uint32_t base[3];
+    unsigned long long bar_target;
+    unsigned long long t_start;
+    int err;
+    int flag;
+};
 
+// Init of instance i's state for a solve whose first queue is read at global
+// step k0: delta <- inf, delta[s] <- 0, Q = {s} (Algorithm 1).  The distance
+// fill is grid-strided; the rest is done by one thread.
+__device__ __forceinline__ void init_instance_fill(const InstDesc& d, uint64_t gtid, uint64_t gthreads)
+{
+    for (uint64_t v = gtid; v < d.n; v += gthreads) d.dist[v] = (v == d.source) ? 0ull : kInf;
+    const uint32_t nwords = (d.n + 31u) >> 5;
+    for (uint64_t w = gtid; w < nwords; w += gthreads)
+        d.inq[w] = (w == (d.source >> 5)) ? (1u << (d.source & 31u)) : 0u;
+}
+__device__ __forceinline__ void init_instance_ctrl(const InstDesc& d, InstCtrl* C, uint64_t k0)
+{
+    ((k0 & 1) ? d.qa : d.qb)[0] = d.source;
+    for (int r = 0; r < 3; ++r) {
+        C->qsize[r] = 0; C->fsmall[r] = 0; C->fchunk[r] = 0; C->fcount[r] = 0;
+        C->qmin[r] = kInf; C->fedges[r] = 0; C->updates[r] = 0;
+    }
+    C->qsize[k0 % 3] = 1;
+    C->qmin[k0 % 3] = 0;
+    C->delta_i = 1;
+    C->dense_seen = 0;
+    C->last_step = 0;
+    C->queued = 0; C->extracted = 0; C->edges = 0; C->updates_total = 0;
+    C->admit_step = k0;
+    C->running = 1;
+}
+
+// Phase T: bookkeeping and theta_i for the running instances (instances spread
+// over blocks).
+__device__ void phase_T(const BatchParams& p, uint64_t k, BatchSmem& S, uint64_t* s_keys)
+{
+    const uint32_t tid = threadIdx.x;
+    const int c = (int)(k % 3), pv = (int)((k + 2) % 3);
+    for (uint32_t i = blockIdx.x; i < p.k; i += gridDim.x) {
+        InstCtrl* C = &p.ictrl[i];
+        const InstDesc& D = p.inst[i];
+        if (!ldcg32(&C->running)) continue;  // block-uniform
+        uint32_t q = ldcg32(&C->qsize[c]);
+        q = q < D.n ? q : D.n;
+        if (tid == 0) {
+            if (k > ldcg64((const uint64_t*)&C->admit_step)) {
+                C->queued += ldcg32(&C->qsize[pv]);
+                C->extracted += ldcg32(&C->fcount[pv]);
+                C->edges += ldcg64((const uint64_t*)&C->fedges[pv]);
+                C->updates_total += ldcg64((const uint64_t*)&C->updates[pv]);
+            }
+            if (q == 0 && C->last_step == 0) C->last_step = (unsigned)(k - C->admit_step);
+            C->qsize[pv] = 0; C->fsmall[pv] = 0; C->fchunk[pv] = 0; C->fcount[pv] = 0;
+            C->fedges[pv] = 0; C->updates[pv] = 0; C->qmin[pv] = kInf;
+        }
+        if (q == 0) { __syncthreads(); continue; }  // block-uniform
+        uint64_t theta;
+        if (p.algo == SSSP_BELLMAN_FORD) {
+            theta = kInf;
+        } else if (p.algo == SSSP_DELTA_STAR) {
+            const uint64_t qmin = ldcg64((const uint64_t*)&C->qmin[c]);
+            uint64_t cur = ldcg64((const uint64_t*)&C->delta_i);
+            theta = sat_mul(cur, D.param);
+            if (qmin > theta) {
+                cur = qmin / D.param + ((qmin % D.param) != 0);
+                theta = sat_mul(cur, D.param);
+            }
+            __syncthreads();
+            if (tid == 0) C->delta_i = cur + 1;
+        } else {
+            const uint32_t* Qcur = (k & 1) ? D.qa : D.qb;
+            const uint32_t dense_seen = ldcg32(&C->dense_seen);
+            const uint64_t lstep = k - ldcg64((const uint64_t*)&C->admit_step) + 1;  // the instance's own step
+            theta = rho_extdist_block(Qcur, q, D.dist, D.n, D.param, D.seed, lstep, dense_seen, s_keys,
+                                      p.sample_cap, &S.err);
+            if (tid == 0 && (uint64_t)q * 20ull > (uint64_t)D.n) C->dense_seen = dense_seen + 1;
+        }
+        if (tid == 0) C->theta = theta;
+        __syncthreads();
+    }
+}
+
+// Phase E: Extract(theta_i) of every running instance, in tiles that each lie
+// within one instance.  Returns false (in every block) when no instance has
+// queued vertices.
+__device__ bool phase_E(const BatchParams& p, uint64_t k, BatchSmem& S)
+{
+    const uint32_t tid = threadIdx.x, lane = tid & 31u;
+    const int c = (int)(k % 3), nx = (int)((k + 1) % 3);
+    const uint32_t K = p.k;
+    int* status = &p.ctrl->status;
+    const uint32_t tileq = (uint32_t)kBlock * kExtractItems;
+    for (uint32_t i = tid; i < K; i += kBlock) {
+        uint32_t q = ldcg32(&p.ictrl[i].running) ? ldcg32(&p.ictrl[i].qsize[c]) : 0u;
+        const uint32_t n_i = p.inst[i].n;
+        q = q < n_i ? q : n_i;
+        S.pre0[i] = (q + tileq - 1) / tileq;  // tiles of instance i
+    }
+    __syncthreads();
+    const uint64_t ntiles = block_prefix_inplace(S.pre0, K, S.tmp);
+    if (ntiles == 0) return false;
+    for (uint64_t t = blockIdx.x; t < ntiles; t += gridDim.x) {
+        const uint32_t i = find_segment(S.pre0, K, t);
+        const InstDesc& D = p.inst[i];
+        InstCtrl* C = &p.ictrl[i];
+        const uint32_t n = D.n;
+        uint32_t q = ldcg32(&C->qsize[c]);
+        q = q < n ? q : n;
+        const uint64_t theta = ldcg64((const uint64_t*)&C->theta);
+        const uint32_t* Qcur = (k & 1) ? D.qa : D.qb;
+        uint32_t* Qnext = (k & 1) ? D.qb : D.qa;
+        const uint64_t base = (t - S.pre0[i]) * (uint64_t)tileq;
+        uint32_t v[kExtractItems];
+        uint64_t d[kExtractItems];
+        uint32_t kind[kExtractItems];  // 0 none, 1 keep, 2 small, 3 chunked, 4 extracted w/o edges
+#pragma unroll
+        for (int j = 0; j < kExtractItems; ++j) {
+            const uint64_t idx = base + (uint64_t)j * kBlock + tid;
+            v[j] = idx < q ? ldcg32(&Qcur[idx]) : 0u;
+        }
+#pragma unroll
+        for (int j = 0; j < kExtractItems; ++j) {
+            const uint64_t idx = base + (uint64_t)j * kBlock + tid;
+            d[j] = idx < q ? ldcg64(&D.dist[v[j]]) : kInf;
+        }
+        uint32_t nkeep = 0, nsmall = 0, nchunks = 0;
+        uint64_t l_fcount = 0, l_fedges = 0, l_kmin = kInf;
+#pragma unroll
+        for (int j = 0; j < kExtractItems; ++j) {
+            const uint64_t idx = base + (uint64_t)j * kBlock + tid;
+            kind[j] = 0;
+            if (idx < q) {
+                if (d[j] <= theta) {
+                    atomicAnd(&D.inq[v[j] >> 5], ~(1u << (v[j] & 31u)));
+                    const uint64_t b = __ldg(&D.off[v[j]]);
+                    const uint64_t e = __ldg(&D.off[v[j] + 1]);
+                    const uint64_t deg = e - b;
+                    l_fcount += 1;
+                    l_fedges += deg;
+                    if (deg == 0) {
+                        kind[j] = 4;
+                    } else if (deg <= kSmallDeg) {
+                        kind[j] = 2; ++nsmall;
+                    } else {
+                        kind[j] = 3;
+                        nchunks += (uint32_t)((e - 1) / kChunk - b / kChunk + 1);
+                    }
+                } else {
+                    kind[j] = 1; ++nkeep;
+                    l_kmin = d[j] < l_kmin ? d[j] : l_kmin;
+                }
+            }
+        }
+        const uint64_t packed = (uint64_t)nkeep | ((uint64_t)nsmall << 16) | ((uint64_t)nchunks << 32);
+        uint64_t tot;
+        const uint64_t ex = block_excl_scan64(packed, S.tmp, &tot);
+        if (tid == 0) {
+            const uint32_t tk = (uint32_t)(tot & 0xFFFFu), ts = (uint32_t)((tot >> 16) & 0xFFFFu);
+            const uint32_t tc = (uint32_t)(tot >> 32);
+            S.base[0] = tk ? atomicAdd(&C->qsize[nx], tk) : 0u;
+            S.base[1] = ts ? atomicAdd(&C->fsmall[c], ts) : 0u;
+            S.base[2] = tc ? atomicAdd(&C->fchunk[c], tc) : 0u;
+            if ((uint64_t)S.base[0] + tk > n || (uint64_t)S.base[1] + ts > D.fsmall_cap ||
+                (uint64_t)S.base[2] + tc > D.item_cap)
+                set_status(status, SSSP_ERR_INTERNAL);
+        }
+        __syncthreads();
+        uint32_t pk = S.base[0] + (uint32_t)(ex & 0xFFFFu);
+        uint64_t ps = (uint64_t)S.base[1] + ((ex >> 16) & 0xFFFFu);
+        uint64_t pc = (uint64_t)S.base[2] + (ex >> 32);
+#pragma unroll
+        for (int j = 0; j < kExtractItems; ++j) {
+            uint64_t bj = 0, ej = 0;
+            if (kind[j] >= 2) { bj = __ldg(&D.off[v[j]]); ej = __ldg(&D.off[v[j] + 1]); }
+            const uint64_t nch = kind[j] == 3 ? (ej - 1) / kChunk - bj / kChunk + 1 : 0;
+            if (kind[j] == 1) {
+                if (pk < n) Qnext[pk] = v[j];
+                ++pk;
+            } else if (kind[j] == 2) {
+                if (ps < D.fsmall_cap) D.fsmall[ps] = make_rec(bj, ej - bj, d[j]);
+                ++ps;
+            } else if (kind[j] == 3 && nch <= 4) {
+                for (uint64_t c0 = bj / kChunk * kChunk; c0 < ej; c0 += kChunk, ++pc) {
+                    const uint64_t cs = bj > c0 ? bj : c0;
+                    const uint64_t ce = ej < c0 + kChunk ? ej : c0 + kChunk;
+                    if (pc < D.item_cap) D.items[pc] = make_rec(cs, ce - cs, v[j]);
+                }
+            }
+            uint32_t many = __ballot_sync(FULL_MASK, kind[j] == 3 && nch > 4);
+            while (many) {
+                const int src = __ffs(many) - 1;
+                many &= many - 1;
+                const uint64_t sb = __shfl_sync(FULL_MASK, bj, src);
+                const uint64_t se = __shfl_sync(FULL_MASK, ej, src);
+                const uint32_t sv = __shfl_sync(FULL_MASK, v[j], src);
+                const uint64_t sp = __shfl_sync(FULL_MASK, pc, src);
+                const uint64_t sn = (se - 1) / kChunk - sb / kChunk + 1;
+                for (uint64_t tt = lane; tt < sn; tt += 32) {
+                    const uint64_t c0 = (sb / kChunk + tt) * kChunk;
+                    const uint64_t cs = sb > c0 ? sb : c0;
+                    const uint64_t ce = se < c0 + kChunk ? se : c0 + kChunk;
+                    if (sp + tt < D.item_cap) D.items[sp + tt] = make_rec(cs, ce - cs, sv);
+                }
+            }
+            if (kind[j] == 3 && nch > 4) pc += nch;
+        }
+        uint64_t bf = l_fcount, be = l_fedges, bm = l_kmin;
+        block_reduce_2add_min(bf, be, bm, S.tmp);
+        if (tid == 0) {
+            if (bf) atomicAdd(&C->fcount[c], (unsigned int)bf);
+            if (be) atomicAdd(&C->fedges[c], (unsigned long long)be);
+            if (p.algo == SSSP_DELTA_STAR && bm != kInf) atomicMin(&C->qmin[nx], (unsigned long long)bm);
+        }
+        __syncthreads();
+    }
+    return true;
+}
+
+// Phase R: relaxation of every running instance's extracted vertices, work
+// spread over all warps.
+__device__ void phase_R(const BatchParams& p, uint64_t k, BatchSmem& S, uint32_t* stage)
+{
     const uint32_t tid = threadIdx.x, lane = tid & 31u, wid = tid >> 5;
-    const uint64_t gthreads = (uint64_t)gridDim.x * kBlock;
-    const uint64_t gtid = (uint64_t)blockIdx.x * kBlock + tid;
     const uint32_t gwarp = blockIdx.x * kWarps + wid;
     const uint32_t nwarps = gridDim.x * kWarps;
+    const int c = (int)(k % 3), nx = (int)((k + 1) % 3);
     const uint32_t K = p.k;
-    BatchCtrl* bctrl = p.ctrl;
-    int* status = &bctrl->status;
-    uint32_t* stage = s_stage + wid * kStage;
-
-    if (tid == 0) {
-        s_bar_target = 0;
-        s_t_start = global_timer_ns();
-        s_err = 0;
+    int* status = &p.ctrl->status;
+    for (uint32_t i = tid; i < K; i += kBlock) {
+        const InstCtrl* C = &p.ictrl[i];
+        const bool run = ldcg32(&C->running) != 0;
+        uint64_t fs = run ? ldcg32(&C->fsmall[c]) : 0;
+        const uint64_t cap = p.inst[i].fsmall_cap;
+        fs = fs < cap ? fs : cap;
+        uint64_t fc = run ? ldcg32(&C->fchunk[c]) : 0;
+        const uint64_t icap = p.inst[i].item_cap;
+        fc = fc < icap ? fc : icap;
+        S.pre0[i] = (uint32_t)((fs + 31u) >> 5);  // low-degree groups
+        S.pre1[i] = (uint32_t)fc;                 // chunk records
     }
-
-    // ---- init of every instance: delta <- inf, delta[s] <- 0, Q = {s} ----
-    for (uint32_t i = 0; i < K; ++i) {
-        const InstDesc d = p.inst[i];
-        for (uint64_t v = gtid; v < d.n; v += gthreads) d.dist[v] = (v == d.source) ? 0ull : kInf;
-        const uint32_t nwords = (d.n + 31u) >> 5;
-        for (uint64_t w = gtid; w < nwords; w += gthreads)
-            d.inq[w] = (w == (d.source >> 5)) ? (1u << (d.source & 31u)) : 0u;
-    }
-    for (uint64_t i = gtid; i < K; i += gthreads) {
-        InstCtrl* C = &p.ictrl[i];
-        p.inst[i].qa[0] = p.inst[i].source;
-        C->qsize[1] = 1;
-        C->qmin[0] = kInf;
-        C->qmin[1] = 0;
-        C->qmin[2] = kInf;
-        C->delta_i = 1;
-    }
-    if (!grid_sync(&bctrl->bar, status, &s_bar_target, p.timeout_ns)) return;
-
-    uint64_t k = 1;
-    for (;; ++k) {
-        const int c = (int)(k % 3), nx = (int)((k + 1) % 3), pv = (int)((k + 2) % 3);
-
-        // ---------------- phase T: bookkeeping and theta_i ----------------
-        for (uint32_t i = blockIdx.x; i < K; i += gridDim.x) {
-            InstCtrl* C = &p.ictrl[i];
-            const InstDesc& D = p.inst[i];
-            uint32_t q = ldcg32(&C->qsize[c]);
-            q = q < D.n ? q : D.n;
-            if (tid == 0) {
-                if (k > 1) {
-                    C->queued += ldcg32(&C->qsize[pv]);
-                    C->extracted += ldcg32(&C->fcount[pv]);
-                    C->edges += ldcg64((const uint64_t*)&C->fedges[pv]);
-                    C->updates_total += ldcg64((const uint64_t*)&C->updates[pv]);
-                }
-                if (q == 0 && C->last_step == 0) C->last_step = (unsigned)(k - 1);
-                C->qsize[pv] = 0; C->fsmall[pv] = 0; C->fchunk[pv] = 0; C->fcount[pv] = 0;
-                C->fedges[pv] = 0; C->updates[pv] = 0; C->qmin[pv] = kInf;
-            }
-            if (q == 0) { __syncthreads(); continue; }  // block-uniform
-            uint64_t theta;
-            if (p.algo == SSSP_BELLMAN_FORD) {
-                theta = kInf;
-            } else if (p.algo == SSSP_DELTA_STAR) {
-                const uint64_t qmin = ldcg64((const uint64_t*)&C->qmin[c]);
-                uint64_t cur = ldcg64((const uint64_t*)&C->delta_i);
-                theta = sat_mul(cur, D.param);
-                if (qmin > theta) {
-                    cur = qmin / D.param + ((qmin % D.param) != 0);
-                    theta = sat_mul(cur, D.param);
-                }
-                __syncthreads();
-                if (tid == 0) C->delta_i = cur + 1;
-            } else {
-                const uint32_t* Qcur = (k & 1) ? D.qa : D.qb;
-                const uint32_t dense_seen = ldcg32(&C->dense_seen);
-                theta = rho_extdist_block(Qcur, q, D.dist, D.n, D.param, D.seed, k, dense_seen, s_keys,
-                                          p.sample_cap, &s_err);
-                if (tid == 0 && (uint64_t)q * 20ull > (uint64_t)D.n) C->dense_seen = dense_seen + 1;
-            }
-            if (tid == 0) C->theta = theta;
-            __syncthreads();
-        }
-        if (tid == 0) {
-            if (s_err) set_status(status, SSSP_ERR_INTERNAL);
-            if (blockIdx.x == 0 && global_timer_ns() - s_t_start > p.solve_timeout_ns)
-                set_status(status, SSSP_ERR_TIMEOUT);
-        }
-        if (!grid_sync(&bctrl->bar, status, &s_bar_target, p.timeout_ns)) return;
-
-        // ---------------- phase E: Extract(theta_i) ----------------
-        const uint32_t tileq = (uint32_t)kBlock * kExtractItems;
-        for (uint32_t i = tid; i < K; i += kBlock) {
-            uint32_t q = ldcg32(&p.ictrl[i].qsize[c]);
-            const uint32_t n_i = p.inst[i].n;
-            q = q < n_i ? q : n_i;
-            s_pre0[i] = (q + tileq - 1) / tileq;  // tiles of instance i
-        }
-        __syncthreads();
-        const uint64_t ntiles = block_prefix_inplace(s_pre0, K, s_tmp);
-        if (ntiles == 0) break;  // every queue is empty: all blocks agree
-        for (uint64_t t = blockIdx.x; t < ntiles; t += gridDim.x) {
-            const uint32_t i = find_segment(s_pre0, K, t);
-            const InstDesc& D = p.inst[i];
-            InstCtrl* C = &p.ictrl[i];
-            const uint32_t n = D.n;
-            uint32_t q = ldcg32(&C->qsize[c]);
-            q = q < n ? q : n;
-            const uint64_t theta = ldcg64((const uint64_t*)&C->theta);
-            const uint32_t* Qcur = (k & 1) ? D.qa : D.qb;
-            uint32_t* Qnext = (k & 1) ? D.qb : D.qa;
-            const uint64_t base = (t - s_pre0[i]) * (uint64_t)tileq;
-            uint32_t v[kExtractItems];
-            uint64_t d[kExtractItems];
-            uint32_t kind[kExtractItems];  // 0 none, 1 keep, 2 small, 3 chunked, 4 extracted w/o edges
-#pragma unroll
-            for (int j = 0; j < kExtractItems; ++j) {
-                const uint64_t idx = base + (uint64_t)j * kBlock + tid;
-                v[j] = idx < q ? ldcg32(&Qcur[idx]) : 0u;
-            }
-#pragma unroll
-            for (int j = 0; j < kExtractItems; ++j) {
-                const uint64_t idx = base + (uint64_t)j * kBlock + tid;
-                d[j] = idx < q ? ldcg64(&D.dist[v[j]]) : kInf;
-            }
-            uint32_t nkeep = 0, nsmall = 0, nchunks = 0;
-            uint64_t l_fcount = 0, l_fedges = 0, l_kmin = kInf;
-#pragma unroll
-            for (int j = 0; j < kExtractItems; ++j) {
-                const uint64_t idx = base + (uint64_t)j * kBlock + tid;
-                kind[j] = 0;
-                if (idx < q) {
-                    if (d[j] <= theta) {
-                        atomicAnd(&D.inq[v[j] >> 5], ~(1u << (v[j] & 31u)));
-                        const uint64_t b = __ldg(&D.off[v[j]]);
-                        const uint64_t e = __ldg(&D.off[v[j] + 1]);
-                        const uint64_t deg = e - b;
-                        l_fcount += 1;
-                        l_fedges += deg;
-                        if (deg == 0) {
-                            kind[j] = 4;
-                        } else if (deg <= kSmallDeg) {
-                            kind[j] = 2; ++nsmall;
-                        } else {
-                            kind[j] = 3;
-                            nchunks += (uint32_t)((e - 1) / kChunk - b / kChunk + 1);
-                        }
-                    } else {
-                        kind[j] = 1; ++nkeep;
-                        l_kmin = d[j] < l_kmin ? d[j] : l_kmin;
-                    }
-                }
-            }
-            const uint64_t packed = (uint64_t)nkeep | ((uint64_t)nsmall << 16) | ((uint64_t)nchunks << 32);
-            uint64_t tot;
-            const uint64_t ex = block_excl_scan64(packed, s_tmp, &tot);
-            if (tid == 0) {
-                const uint32_t tk = (uint32_t)(tot & 0xFFFFu), ts = (uint32_t)((tot >> 16) & 0xFFFFu);
-                const uint32_t tc = (uint32_t)(tot >> 32);
-                s_base[0] = tk ? atomicAdd(&C->qsize[nx], tk) : 0u;
-                s_base[1] = ts ? atomicAdd(&C->fsmall[c], ts) : 0u;
-                s_base[2] = tc ? atomicAdd(&C->fchunk[c], tc) : 0u;
-                if ((uint64_t)s_base[0] + tk > n || (uint64_t)s_base[1] + ts > D.fsmall_cap ||
-                    (uint64_t)s_base[2] + tc > D.item_cap)
-                    set_status(status, SSSP_ERR_INTERNAL);
-            }
-            __syncthreads();
-            uint32_t pk = s_base[0] + (uint32_t)(ex & 0xFFFFu);
-            uint64_t ps = (uint64_t)s_base[1] + ((ex >> 16) & 0xFFFFu);
-            uint64_t pc = (uint64_t)s_base[2] + (ex >> 32);
-#pragma unroll
-            for (int j = 0; j < kExtractItems; ++j) {
-                uint64_t bj = 0, ej = 0;
-                if (kind[j] >= 2) { bj = __ldg(&D.off[v[j]]); ej = __ldg(&D.off[v[j] + 1]); }
-                const uint64_t nch = kind[j] == 3 ? (ej - 1) / kChunk - bj / kChunk + 1 : 0;
-                if (kind[j] == 1) {
-                    if (pk < n) Qnext[pk] = v[j];
-                    ++pk;
-                } else if (kind[j] == 2) {
-                    if (ps < D.fsmall_cap) D.fsmall[ps] = make_rec(bj, ej - bj, d[j]);
-                    ++ps;
-                } else if (kind[j] == 3 && nch <= 4) {
-                    for (uint64_t c0 = bj / kChunk * kChunk; c0 < ej; c0 += kChunk, ++pc) {
-                        const uint64_t cs = bj > c0 ? bj : c0;
-                        const uint64_t ce = ej < c0 + kChunk ? ej : c0 + kChunk;
-                        if (pc < D.item_cap) D.items[pc] = make_rec(cs, ce - cs, v[j]);
-                    }
-                }
-                uint32_t many = __ballot_sync(FULL_MASK, kind[j] == 3 && nch > 4);
-                while (many) {
-                    const int src = __ffs(many) - 1;
-                    many &= many - 1;
-                    const uint64_t sb = __shfl_sync(FULL_MASK, bj, src);
-                    const uint64_t se = __shfl_sync(FULL_MASK, ej, src);
-                    const uint32_t sv = __shfl_sync(FULL_MASK, v[j], src);
-                    const uint64_t sp = __shfl_sync(FULL_MASK, pc, src);
-                    const uint64_t sn = (se - 1) / kChunk - sb / kChunk + 1;
-                    for (uint64_t tt = lane; tt < sn; tt += 32) {
-                        const uint64_t c0 = (sb / kChunk + tt) * kChunk;
-                        const uint64_t cs = sb > c0 ? sb : c0;
-                        const uint64_t ce = se < c0 + kChunk ? se : c0 + kChunk;
-                        if (sp + tt < D.item_cap) D.items[sp + tt] = make_rec(cs, ce - cs, sv);
-                    }
-                }
-                if (kind[j] == 3 && nch > 4) pc += nch;
-            }
-            uint64_t bf = l_fcount, be = l_fedges, bm = l_kmin;
-            block_reduce_2add_min(bf, be, bm, s_tmp);
-            if (tid == 0) {
-                if (bf) atomicAdd(&C->fcount[c], (unsigned int)bf);
-                if (be) atomicAdd(&C->fedges[c], (unsigned long long)be);
-                if (p.algo == SSSP_DELTA_STAR && bm != kInf) atomicMin(&C->qmin[nx], (unsigned long long)bm);
-            }
-            __syncthreads();
-        }
-        if (!grid_sync(&bctrl->bar, status, &s_bar_target, p.timeout_ns)) return;
-
-        // ---------------- phase R: relax every instance's extracted vertices ----------------
-        for (uint32_t i = tid; i < K; i += kBlock) {
-            const InstCtrl* C = &p.ictrl[i];
-            uint64_t fs = ldcg32(&C->fsmall[c]);
-            const uint64_t cap = p.inst[i].fsmall_cap;
-            fs = fs < cap ? fs : cap;
-            uint64_t fc = ldcg32(&C->fchunk[c]);
-            const uint64_t icap = p.inst[i].item_cap;
-            fc = fc < icap ? fc : icap;
-            s_pre0[i] = (uint32_t)((fs + 31u) >> 5);  // low-degree groups
-            s_pre1[i] = (uint32_t)fc;                 // chunk records
-        }
-        __syncthreads();
-        const uint64_t ngroups = block_prefix_inplace(s_pre0, K, s_tmp);
-        const uint64_t nchunks_all = block_prefix_inplace(s_pre1, K, s_tmp);
+    __syncthreads();
+    const uint64_t ngroups = block_prefix_inplace(S.pre0, K, S.tmp);
+    const uint64_t nchunks_all = block_prefix_inplace(S.pre1, K, S.tmp);
         {
             uint32_t cur = 0xFFFFFFFFu;  // instance whose ids are staged / whose counters accumulate
             uint32_t stc = 0;
@@ -382,7 +403,7 @@ __global__ void __launch_bounds__(kBlock, 1) batch_kernel(BatchParams p)
 
             // (a) low-degree vertices: 32 records per warp, edges flattened across lanes
             for (uint64_t g = gwarp; g < ngroups; g += nwarps) {
-                const uint32_t i = find_segment(s_pre0, K, g);
+                const uint32_t i = find_segment(S.pre0, K, g);
                 SWITCH_INSTANCE(i);
                 const InstDesc* Dp = &p.inst[i];
                 uint64_t* const idist = Dp->dist;
@@ -391,7 +412,7 @@ __global__ void __launch_bounds__(kBlock, 1) batch_kernel(BatchParams p)
                 const uint64_t fcap = Dp->fsmall_cap;
                 uint64_t fs = ldcg32(&p.ictrl[i].fsmall[c]);
                 fs = fs < fcap ? fs : fcap;
-                const uint64_t lg = g - s_pre0[i];
+                const uint64_t lg = g - S.pre0[i];
                 const uint4 rec = (lg * 32u + lane < fs) ? __ldcg(&Dp->fsmall[lg * 32u + lane]) : make_uint4(0, 0, 0, 0);
                 const uint64_t b = rec_start(rec);
                 const uint32_t deg = rec_len(rec);
@@ -436,11 +457,11 @@ __global__ void __launch_bounds__(kBlock, 1) batch_kernel(BatchParams p)
             }
             // (b) higher-degree vertices: one warp per chunk record
             for (uint64_t it = gwarp; it < nchunks_all; it += nwarps) {
-                const uint32_t i = find_segment(s_pre1, K, it);
+                const uint32_t i = find_segment(S.pre1, K, it);
                 SWITCH_INSTANCE(i);
                 const InstDesc* Dp = &p.inst[i];
                 uint64_t* const idist = Dp->dist;
-                const uint4 rc = __ldcg(&Dp->items[it - s_pre1[i]]);
+                const uint4 rc = __ldcg(&Dp->items[it - S.pre1[i]]);
                 const uint64_t du = ldcg64(&idist[rc.z]);
                 relax_chunk(rc, du, reinterpret_cast<const uint4*>(Dp->edges), idist, Dp->inq, stage, stc, lane,
                             lmin, lupd);
@@ -452,16 +473,253 @@ __global__ void __launch_bounds__(kBlock, 1) batch_kernel(BatchParams p)
             SWITCH_INSTANCE(0xFFFFFFFEu);  // flush what is left
 #undef SWITCH_INSTANCE
         }
-        if (!grid_sync(&bctrl->bar, status, &s_bar_target, p.timeout_ns)) return;
-    }
+}
 
-    // every queue is empty: record the step counts
-    for (uint64_t i = gtid; i < K; i += gthreads) {
+__global__ void __launch_bounds__(kBlock, 1) batch_kernel(BatchParams p)
+{
+    extern __shared__ __align__(16) unsigned char s_dyn[];
+    uint32_t* s_stage = reinterpret_cast<uint32_t*>(s_dyn);  // [kWarps][kStage]
+    uint64_t* s_keys = reinterpret_cast<uint64_t*>(s_dyn);   // rho samples (aliases the empty staging)
+    __shared__ BatchSmem S;
+    const uint32_t tid = threadIdx.x, wid = tid >> 5;
+    const uint64_t gthreads = (uint64_t)gridDim.x * kBlock;
+    const uint64_t gtid = (uint64_t)blockIdx.x * kBlock + tid;
+    BatchCtrl* bctrl = p.ctrl;
+    int* status = &bctrl->status;
+    uint32_t* stage = s_stage + wid * kStage;
+    if (tid == 0) {
+        S.bar_target = 0;
+        S.t_start = global_timer_ns();
+        S.err = 0;
+    }
+    for (uint32_t i = 0; i < p.k; ++i) init_instance_fill(p.inst[i], gtid, gthreads);
+    for (uint64_t i = gtid; i < p.k; i += gthreads) init_instance_ctrl(p.inst[i], &p.ictrl[i], 1);
+    if (!grid_sync(&bctrl->bar, status, &S.bar_target, p.timeout_ns)) return;
+
+    uint64_t k = 1;
+    for (;; ++k) {
+        phase_T(p, k, S, s_keys);
+        if (tid == 0) {
+            if (S.err) set_status(status, SSSP_ERR_INTERNAL);
+            if (blockIdx.x == 0 && global_timer_ns() - S.t_start > p.solve_timeout_ns)
+                set_status(status, SSSP_ERR_TIMEOUT);
+        }
+        if (!grid_sync(&bctrl->bar, status, &S.bar_target, p.timeout_ns)) return;
+        if (!phase_E(p, k, S)) break;  // every queue is empty: all blocks agree
+        if (!grid_sync(&bctrl->bar, status, &S.bar_target, p.timeout_ns)) return;
+        phase_R(p, k, S, stage);
+        if (!grid_sync(&bctrl->bar, status, &S.bar_target, p.timeout_ns)) return;
+    }
+    for (uint64_t i = gtid; i < p.k; i += gthreads) {
         InstCtrl* C = &p.ictrl[i];
         if (C->last_step == 0) C->last_step = (unsigned)(k - 1);
     }
     if (gtid == 0) bctrl->steps = k - 1;
 }
+
+// ---------------------------------------------------------------------------
+// Serving: a long-lived persistent loop over S query slots.  At every step
+// boundary block 0 retires finished queries (completion records in host-mapped
+// memory) and admits newly submitted ones (commands in host-mapped memory);
+// admitted queries join the running ones at the next step, so their work
+// overlaps on the device (continuous batching).  With no query left the loop
+// waits a bounded idle time for new commands, then the kernel exits.
+// ---------------------------------------------------------------------------
+struct SlotCmd {                  // written by the host
+    unsigned long long ticket;
+    unsigned long long dist_ptr;  // caller-owned device uint64[n]
+    unsigned int source;
+    unsigned int seq;             // written last
+};
+struct SlotDone {                 // written by the device
+    unsigned long long ticket;
+    unsigned long long t_admit_ns, t_done_ns;
+    unsigned long long edges, extracted;
+    unsigned int steps;
+    int status;
+    unsigned int seq;             // written last
+    unsigned int pad;
+};
+struct ServeShared {              // host-mapped
+    unsigned long long submitted; // host: commands written so far (monotone)
+    unsigned int stop;            // host: leave the loop
+    unsigned int pad;
+};
+struct ServeState {               // device memory, kept across launches
+    unsigned long long seen_submitted;
+    unsigned long long step;      // last global step run
+    unsigned int nadmit;
+    unsigned int exit_flag;
+    unsigned int admit[kMaxBatch];
+};
+struct ServeParams {
+    BatchParams b;
+    SlotCmd* cmd;
+    SlotDone* done;
+    ServeShared* shared;
+    ServeState* state;
+    uint64_t idle_ns;
+    uint64_t param;
+};
+
+__device__ __forceinline__ unsigned int ld_acquire_sys_u32(const unsigned int* p)
+{
+    unsigned int v;
+    asm volatile("ld.acquire.sys.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+__device__ __forceinline__ unsigned long long ld_acquire_sys_u64(const unsigned long long* p)
+{
+    unsigned long long v;
+    asm volatile("ld.acquire.sys.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+    return v;
+}
+__device__ __forceinline__ void st_release_sys_u32(unsigned int* p, unsigned int v)
+{
+    asm volatile("st.release.sys.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
+// Block 0 only: retire finished slots, admit new commands; returns (in every
+// thread of block 0) false when the loop should exit.
+__device__ bool serve_admission(const ServeParams& sp, uint64_t k, BatchSmem& S)
+{
+    const BatchParams& p = sp.b;
+    const uint32_t tid = threadIdx.x;
+    const int c = (int)(k % 3), pv = (int)((k + 2) % 3);
+    ServeState* st = sp.state;
+    for (;;) {
+        // retire: running slots whose queue for step k is empty finished at step k-1
+        for (uint32_t i = tid; i < p.k; i += kBlock) {
+            InstCtrl* C = &p.ictrl[i];
+            if (!C->running || ldcg32(&C->qsize[c]) != 0) continue;
+            if (k > C->admit_step) {
+                C->queued += ldcg32(&C->qsize[pv]);
+                C->extracted += ldcg32(&C->fcount[pv]);
+                C->edges += ldcg64((const uint64_t*)&C->fedges[pv]);
+                C->updates_total += ldcg64((const uint64_t*)&C->updates[pv]);
+            }
+            SlotDone* D = &sp.done[i];
+            D->ticket = C->ticket;
+            D->t_admit_ns = C->t_admit_ns;
+            D->t_done_ns = global_timer_ns();
+            D->edges = C->edges;
+            D->extracted = C->extracted;
+            D->steps = (unsigned int)(k - C->admit_step);
+            D->status = *reinterpret_cast<volatile int*>(&p.ctrl->status);
+            __threadfence_system();
+            st_release_sys_u32(&D->seq, C->seq);
+            C->running = 0;
+            for (int r = 0; r < 3; ++r) {
+                C->qsize[r] = 0; C->fsmall[r] = 0; C->fchunk[r] = 0; C->fcount[r] = 0;
+                C->fedges[r] = 0; C->updates[r] = 0; C->qmin[r] = kInf;
+            }
+        }
+        __syncthreads();
+        // admit: free slots whose command carries a new sequence number
+        if (tid == 0) {
+            const unsigned long long sub = ld_acquire_sys_u64(&sp.shared->submitted);
+            S.flag = sub != st->seen_submitted;
+            st->seen_submitted = sub;
+        }
+        __syncthreads();
+        if (S.flag) {
+            for (uint32_t i = tid; i < p.k; i += kBlock) {
+                InstCtrl* C = &p.ictrl[i];
+                if (C->running) continue;
+                const unsigned int cs = ld_acquire_sys_u32(&sp.cmd[i].seq);
+                if (cs == C->seq) continue;
+                const volatile SlotCmd* cm = &sp.cmd[i];
+                InstDesc* d = &p.inst[i];
+                d->dist = reinterpret_cast<uint64_t*>(cm->dist_ptr);
+                d->source = cm->source < d->n ? cm->source : 0u;
+                d->seed = 0x2105061450000000ull ^ (uint64_t)d->source;
+                d->param = sp.param;
+                init_instance_ctrl(*d, C, k);
+                C->seq = cs;
+                C->ticket = cm->ticket;
+                C->t_admit_ns = global_timer_ns();
+                st->admit[atomicAdd(&st->nadmit, 1u)] = i;
+            }
+        }
+        __syncthreads();
+        // anything running?
+        uint32_t nrun = 0;
+        for (uint32_t i = tid; i < p.k; i += kBlock) nrun += p.ictrl[i].running ? 1u : 0u;
+        nrun = __syncthreads_count(nrun != 0);
+        if (tid == 0) {
+            S.flag = 0;
+            if (ld_acquire_sys_u32(&sp.shared->stop)) {
+                S.flag = 2;  // leave now
+            } else if (nrun == 0) {
+                // idle: wait (bounded) for a new command
+                const unsigned long long t0 = global_timer_ns();
+                S.flag = 2;
+                while (global_timer_ns() - t0 < sp.idle_ns) {
+                    if (ld_acquire_sys_u64(&sp.shared->submitted) != st->seen_submitted) { S.flag = 1; break; }
+                    if (ld_acquire_sys_u32(&sp.shared->stop)) break;
+                    __nanosleep(2000);
+                }
+            }
+        }
+        __syncthreads();
+        if (S.flag == 0) return true;   // work to do
+        if (S.flag == 2) return false;  // idle or stopped: exit
+        // S.flag == 1: a command arrived while idle; admit it
+    }
+}
+
+__global__ void __launch_bounds__(kBlock, 1) serve_kernel(ServeParams sp)
+{
+    extern __shared__ __align__(16) unsigned char s_dyn[];
+    uint32_t* s_stage = reinterpret_cast<uint32_t*>(s_dyn);
+    uint64_t* s_keys = reinterpret_cast<uint64_t*>(s_dyn);
+    __shared__ BatchSmem S;
+    const BatchParams& p = sp.b;
+    const uint32_t tid = threadIdx.x, wid = tid >> 5;
+    const uint64_t gthreads = (uint64_t)gridDim.x * kBlock;
+    const uint64_t gtid = (uint64_t)blockIdx.x * kBlock + tid;
+    BatchCtrl* bctrl = p.ctrl;
+    int* status = &bctrl->status;
+    uint32_t* stage = s_stage + wid * kStage;
+    ServeState* st = sp.state;
+    if (tid == 0) {
+        S.bar_target = 0;
+        S.err = 0;
+    }
+    __syncthreads();
+    uint64_t k = ldcg64((const uint64_t*)&st->step) + 1;
+    for (;; ++k) {
+        // ---- phase A: retire and admit (block 0) ----
+        if (blockIdx.x == 0) {
+            const bool go = serve_admission(sp, k, S);
+            if (tid == 0) st->exit_flag = go ? 0u : 1u;
+        }
+        if (!grid_sync(&bctrl->bar, status, &S.bar_target, p.timeout_ns)) return;
+        if (ldcg32(&st->exit_flag)) break;
+        // ---- phase I + T: initialise admitted slots, thresholds ----
+        const uint32_t na = ldcg32(&st->nadmit);
+        for (uint32_t a = 0; a < na; ++a) {
+            const uint32_t i = ldcg32(&st->admit[a]);
+            InstDesc d;
+            d.dist = p.inst[i].dist; d.inq = p.inst[i].inq; d.n = p.inst[i].n; d.source = p.inst[i].source;
+            init_instance_fill(d, gtid, gthreads);
+        }
+        phase_T(p, k, S, s_keys);
+        if (tid == 0 && S.err) set_status(status, SSSP_ERR_INTERNAL);
+        if (!grid_sync(&bctrl->bar, status, &S.bar_target, p.timeout_ns)) return;
+        if (blockIdx.x == 0 && tid == 0) st->nadmit = 0;
+        // ---- phase E, R ----
+        if (phase_E(p, k, S)) {
+            if (!grid_sync(&bctrl->bar, status, &S.bar_target, p.timeout_ns)) return;
+            phase_R(p, k, S, stage);
+        }
+        if (blockIdx.x == 0 && tid == 0) st->step = k;
+        if (!grid_sync(&bctrl->bar, status, &S.bar_target, p.timeout_ns)) return;
+    }
+    if (gtid == 0) st->step = k;
+}
+
+const void* serve_kernel_ptr() { return reinterpret_cast<const void*>(&serve_kernel); }
 
 const void* batch_kernel_ptr() { return reinterpret_cast<const void*>(&batch_kernel); }
 
@@ -629,6 +887,172 @@ int solve_batch(const sssp_graph* const* gs, const uint32_t* sources, uint32_t k
 }  // namespace
 }  // namespace sssp
 
+// ---------------------------------------------------------------------------
+// Host side of the server.
+// ---------------------------------------------------------------------------
+struct sssp_server {
+    const sssp_graph* g = nullptr;
+    int device = 0;
+    uint32_t S = 0;
+    sssp_algo algo = SSSP_RHO;
+    uint64_t param = 0;
+    uint64_t idle_ns = 2000000;
+    uint32_t grid = 0;
+    uint32_t sample_cap = 1;
+    void* scratch = nullptr;
+    sssp::InstDesc* d_desc = nullptr;
+    sssp::InstCtrl* d_ictrl = nullptr;
+    sssp::BatchCtrl* d_ctrl = nullptr;
+    sssp::ServeState* d_state = nullptr;
+    sssp::SlotCmd* h_cmd = nullptr;       // mapped
+    sssp::SlotDone* h_done = nullptr;     // mapped
+    sssp::ServeShared* h_shared = nullptr;  // mapped
+    sssp::SlotCmd* d_cmd = nullptr;
+    sssp::SlotDone* d_done = nullptr;
+    sssp::ServeShared* d_shared = nullptr;
+    cudaStream_t stream = nullptr;
+    std::thread worker;
+    std::mutex mu;
+    std::condition_variable cv;
+    bool stopping = false;
+    struct Pending { uint64_t ticket; uint32_t source; uint64_t dist; uint64_t t_submit; };
+    std::deque<Pending> pending;
+    struct Slot { bool busy = false; uint32_t seq = 0; uint64_t ticket = 0; uint64_t t_submit = 0; };
+    std::vector<Slot> slots;
+    struct Result { bool done = false; sssp_query_info info{}; uint64_t t_submit = 0; };
+    std::unordered_map<uint64_t, Result> results;
+    uint64_t next_ticket = 1;
+    bool kernel_running = false;
+    uint64_t launches = 0;
+    int fatal = SSSP_OK;
+};
+
+namespace sssp {
+namespace {
+
+uint64_t host_ns()
+{
+    return (uint64_t)std::chrono::duration_cast<std::chrono::nanoseconds>(
+               std::chrono::steady_clock::now().time_since_epoch()).count();
+}
+
+void server_loop(sssp_server* s)
+{
+    cudaSetDevice(s->device);
+    ServeParams sp;
+    memset(&sp, 0, sizeof sp);
+    sp.b.inst = s->d_desc;
+    sp.b.ictrl = s->d_ictrl;
+    sp.b.ctrl = s->d_ctrl;
+    sp.b.k = s->S;
+    sp.b.algo = (int)s->algo;
+    sp.b.timeout_ns = 2000000000ull;
+    sp.b.solve_timeout_ns = ~0ull;
+    sp.b.sample_cap = s->sample_cap;
+    sp.cmd = s->d_cmd;
+    sp.done = s->d_done;
+    sp.shared = s->d_shared;
+    sp.state = s->d_state;
+    sp.idle_ns = s->idle_ns;
+    sp.param = s->param;
+    unsigned long long submitted = 0;
+    for (;;) {
+        bool progress = false;
+        bool any_busy = false;
+        {
+            std::unique_lock<std::mutex> lk(s->mu);
+            if (s->stopping) break;
+            bool assigned = false;
+            for (uint32_t i = 0; i < s->S && !s->pending.empty(); ++i) {
+                sssp_server::Slot& sl = s->slots[i];
+                if (sl.busy) continue;
+                const sssp_server::Pending pd = s->pending.front();
+                s->pending.pop_front();
+                sl.busy = true;
+                sl.seq += 1;
+                sl.ticket = pd.ticket;
+                sl.t_submit = pd.t_submit;
+                SlotCmd* cm = &s->h_cmd[i];
+                __atomic_store_n(&cm->ticket, pd.ticket, __ATOMIC_RELAXED);
+                __atomic_store_n(&cm->dist_ptr, pd.dist, __ATOMIC_RELAXED);
+                __atomic_store_n(&cm->source, pd.source, __ATOMIC_RELAXED);
+                __atomic_store_n(&cm->seq, sl.seq, __ATOMIC_RELEASE);
+                assigned = true;
+            }
+            if (assigned) {
+                ++submitted;
+                __atomic_store_n(&s->h_shared->submitted, submitted, __ATOMIC_RELEASE);
+                progress = true;
+            }
+            // completions
+            for (uint32_t i = 0; i < s->S; ++i) {
+                sssp_server::Slot& sl = s->slots[i];
+                if (!sl.busy) continue;
+                any_busy = true;
+                const SlotDone* dn = &s->h_done[i];
+                if (__atomic_load_n(&dn->seq, __ATOMIC_ACQUIRE) != sl.seq) continue;
+                sssp_server::Result& r = s->results[sl.ticket];
+                r.done = true;
+                r.info.status = __atomic_load_n(&dn->status, __ATOMIC_RELAXED);
+                r.info.steps = __atomic_load_n(&dn->steps, __ATOMIC_RELAXED);
+                r.info.edges = __atomic_load_n(&dn->edges, __ATOMIC_RELAXED);
+                const uint64_t ta = __atomic_load_n(&dn->t_admit_ns, __ATOMIC_RELAXED);
+                const uint64_t td = __atomic_load_n(&dn->t_done_ns, __ATOMIC_RELAXED);
+                r.info.device_ns = td - ta;
+                r.info.device_admit_ns = ta;
+                r.info.device_done_ns = td;
+                r.info.latency_ns = host_ns() - sl.t_submit;
+                sl.busy = false;
+                progress = true;
+            }
+            if (progress) s->cv.notify_all();
+        }
+        // keep the device loop alive while there is work
+        if (s->kernel_running && cudaStreamQuery(s->stream) == cudaSuccess) {
+            s->kernel_running = false;
+            BatchCtrl hc;
+            if (cudaMemcpy(&hc, s->d_ctrl, sizeof hc, cudaMemcpyDeviceToHost) == cudaSuccess && hc.status != 0) {
+                std::lock_guard<std::mutex> lk(s->mu);
+                s->fatal = hc.status;
+                s->cv.notify_all();
+                break;
+            }
+        }
+        if (!s->kernel_running) {
+            bool need;
+            {
+                std::lock_guard<std::mutex> lk(s->mu);
+                need = false;
+                for (uint32_t i = 0; i < s->S; ++i) need |= s->slots[i].busy;
+                need |= !s->pending.empty();
+            }
+            if (need) {
+                void* args[] = {&sp};
+                cudaError_t e = cudaMemsetAsync(s->d_ctrl, 0, sizeof(BatchCtrl), s->stream);
+                if (e == cudaSuccess)
+                    e = cudaLaunchCooperativeKernel(serve_kernel_ptr(), dim3(s->grid), dim3(kBlock), args,
+                                                    kSolveDynSmem, s->stream);
+                if (e != cudaSuccess) {
+                    std::lock_guard<std::mutex> lk(s->mu);
+                    s->fatal = SSSP_ERR_CUDA;
+                    s->cv.notify_all();
+                    break;
+                }
+                s->kernel_running = true;
+                ++s->launches;
+                progress = true;
+            }
+        }
+        if (!progress) std::this_thread::sleep_for(std::chrono::microseconds(any_busy ? 5 : 50));
+    }
+    // shutting down: make the device loop leave and wait for it
+    __atomic_store_n(&s->h_shared->stop, 1u, __ATOMIC_RELEASE);
+    cudaStreamSynchronize(s->stream);
+}
+
+}  // namespace
+}  // namespace sssp
+
 using namespace sssp;
 
 extern "C" {
@@ -673,6 +1097,185 @@ int sssp_batch_last_stats(sssp_stats* out, uint32_t k, void* stream)
         out[i].grid = w.grid;
     }
     return w.h_ctrl->status;
+}
+
+int sssp_server_create(const sssp_graph* g, const sssp_server_config* cfg, sssp_server** out)
+{
+    if (!g || !out) return SSSP_ERR_INVALID_ARG;
+    *out = nullptr;
+    sssp_server_config c;
+    memset(&c, 0, sizeof c);
+    if (cfg) c = *cfg;
+    if (c.algo != SSSP_RHO && c.algo != SSSP_DELTA_STAR && c.algo != SSSP_BELLMAN_FORD) return SSSP_ERR_INVALID_ARG;
+    if (c.idle_ns > 1000000000ull) return SSSP_ERR_INVALID_ARG;
+    cudaError_t e = cudaSetDevice(g->device);
+    if (e != cudaSuccess) return fail(e);
+    sssp_server* s = new (std::nothrow) sssp_server();
+    if (!s) return SSSP_ERR_OUT_OF_MEMORY;
+    s->g = g;
+    s->device = g->device;
+    s->algo = c.algo;
+    s->param = c.param ? c.param : sssp_default_param(g->n, g->m, c.algo, g->mean_w);
+    if (s->algo != SSSP_BELLMAN_FORD && s->param == 0) { delete s; return SSSP_ERR_INVALID_ARG; }
+    s->idle_ns = c.idle_ns ? c.idle_ns : 2000000ull;
+    // admission by free HBM: per-slot working memory out of a fraction of what is free
+    const size_t per_slot = instance_scratch_bytes(g->n, g->fsmall_cap, g->item_cap);
+    size_t free_b = 0, total_b = 0;
+    if ((e = cudaMemGetInfo(&free_b, &total_b)) != cudaSuccess) { delete s; return fail(e); }
+    const double frac = (c.hbm_fraction > 0.0 && c.hbm_fraction <= 1.0) ? c.hbm_fraction : 0.5;
+    uint64_t fit = (uint64_t)((double)free_b * frac) / (per_slot ? per_slot : 1);
+    uint64_t want = c.slots ? c.slots : kMaxBatch;
+    if (want > kMaxBatch) want = kMaxBatch;
+    if (fit < want) want = fit;
+    if (want == 0) { delete s; return SSSP_ERR_OUT_OF_MEMORY; }
+    s->S = (uint32_t)want;
+    s->slots.resize(s->S);
+    int rc = batch_blocks(g->device, &s->grid);
+    if (rc != SSSP_OK) { delete s; return rc; }
+    {
+        const void* fn = serve_kernel_ptr();
+        e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSolveDynSmem);
+        int bps = 0;
+        if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, fn, kBlock, kSolveDynSmem);
+        if (e != cudaSuccess || bps < 1) { delete s; return e != cudaSuccess ? fail(e) : SSSP_ERR_CUDA; }
+        int sms = 0;
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, g->device);
+        s->grid = (uint32_t)(bps * sms);
+    }
+    s->sample_cap = s->algo == SSSP_RHO ? rho_sample_bound(g->n, s->param) : 1;
+    const size_t S = s->S;
+    if ((e = cudaMalloc(&s->scratch, per_slot * S)) != cudaSuccess ||
+        (e = cudaMalloc(reinterpret_cast<void**>(&s->d_desc), sizeof(InstDesc) * S)) != cudaSuccess ||
+        (e = cudaMalloc(reinterpret_cast<void**>(&s->d_ictrl), sizeof(InstCtrl) * S)) != cudaSuccess ||
+        (e = cudaMalloc(reinterpret_cast<void**>(&s->d_ctrl), sizeof(BatchCtrl))) != cudaSuccess ||
+        (e = cudaMalloc(reinterpret_cast<void**>(&s->d_state), sizeof(ServeState))) != cudaSuccess ||
+        (e = cudaHostAlloc(reinterpret_cast<void**>(&s->h_cmd), sizeof(SlotCmd) * S, cudaHostAllocMapped)) != cudaSuccess ||
+        (e = cudaHostAlloc(reinterpret_cast<void**>(&s->h_done), sizeof(SlotDone) * S, cudaHostAllocMapped)) != cudaSuccess ||
+        (e = cudaHostAlloc(reinterpret_cast<void**>(&s->h_shared), sizeof(ServeShared), cudaHostAllocMapped)) != cudaSuccess ||
+        (e = cudaHostGetDevicePointer(reinterpret_cast<void**>(&s->d_cmd), s->h_cmd, 0)) != cudaSuccess ||
+        (e = cudaHostGetDevicePointer(reinterpret_cast<void**>(&s->d_done), s->h_done, 0)) != cudaSuccess ||
+        (e = cudaHostGetDevicePointer(reinterpret_cast<void**>(&s->d_shared), s->h_shared, 0)) != cudaSuccess ||
+        (e = cudaStreamCreateWithFlags(&s->stream, cudaStreamNonBlocking)) != cudaSuccess) {
+        sssp_server_destroy(s);
+        return fail(e);
+    }
+    memset(s->h_cmd, 0, sizeof(SlotCmd) * S);
+    memset(s->h_done, 0, sizeof(SlotDone) * S);
+    memset(s->h_shared, 0, sizeof(ServeShared));
+    std::vector<InstDesc> desc(S);
+    unsigned char* base = static_cast<unsigned char*>(s->scratch);
+    for (size_t i = 0; i < S; ++i) {
+        InstDesc& d = desc[i];
+        memset(&d, 0, sizeof d);
+        d.off = g->d_off;
+        d.edges = g->d_edges;
+        d.n = g->n;
+        d.param = s->param;
+        d.fsmall_cap = g->fsmall_cap;
+        d.item_cap = g->item_cap;
+        d.inq = reinterpret_cast<uint32_t*>(base); base += align256(4ull * ((g->n + 31ull) / 32));
+        d.qa = reinterpret_cast<uint32_t*>(base); base += align256(4ull * g->n);
+        d.qb = reinterpret_cast<uint32_t*>(base); base += align256(4ull * g->n);
+        d.fsmall = reinterpret_cast<uint4*>(base); base += align256(16ull * g->fsmall_cap);
+        d.items = reinterpret_cast<uint4*>(base); base += align256(16ull * g->item_cap);
+    }
+    if ((e = cudaMemcpy(s->d_desc, desc.data(), sizeof(InstDesc) * S, cudaMemcpyHostToDevice)) != cudaSuccess ||
+        (e = cudaMemset(s->d_ictrl, 0, sizeof(InstCtrl) * S)) != cudaSuccess ||
+        (e = cudaMemset(s->d_state, 0, sizeof(ServeState))) != cudaSuccess) {
+        sssp_server_destroy(s);
+        return fail(e);
+    }
+    s->worker = std::thread(server_loop, s);
+    *out = s;
+    return SSSP_OK;
+}
+
+int sssp_server_slots(const sssp_server* s, uint32_t* slots)
+{
+    if (!s || !slots) return SSSP_ERR_INVALID_ARG;
+    *slots = s->S;
+    return SSSP_OK;
+}
+
+int sssp_server_submit(sssp_server* s, uint32_t source, uint64_t* dist_out, uint64_t* ticket)
+{
+    if (!s || !dist_out || !ticket || source >= s->g->n) return SSSP_ERR_INVALID_ARG;
+    std::lock_guard<std::mutex> lk(s->mu);
+    if (s->fatal != SSSP_OK) return s->fatal;
+    if (s->stopping) return SSSP_ERR_INVALID_ARG;
+    const uint64_t t = s->next_ticket++;
+    sssp_server::Pending pd;
+    pd.ticket = t;
+    pd.source = source;
+    pd.dist = reinterpret_cast<uint64_t>(dist_out);
+    pd.t_submit = host_ns();
+    s->pending.push_back(pd);
+    s->results[t].t_submit = pd.t_submit;
+    *ticket = t;
+    return SSSP_OK;
+}
+
+int sssp_server_poll(sssp_server* s, uint64_t ticket, sssp_query_info* info)
+{
+    if (!s) return SSSP_ERR_INVALID_ARG;
+    std::lock_guard<std::mutex> lk(s->mu);
+    auto it = s->results.find(ticket);
+    if (it == s->results.end()) return SSSP_ERR_INVALID_ARG;
+    if (!it->second.done) return s->fatal != SSSP_OK ? s->fatal : 0;
+    if (info) *info = it->second.info;
+    s->results.erase(it);
+    return 1;
+}
+
+int sssp_server_wait(sssp_server* s, uint64_t ticket, uint64_t timeout_ns, sssp_query_info* info)
+{
+    if (!s) return SSSP_ERR_INVALID_ARG;
+    std::unique_lock<std::mutex> lk(s->mu);
+    auto it = s->results.find(ticket);
+    if (it == s->results.end()) return SSSP_ERR_INVALID_ARG;
+    const auto deadline = std::chrono::steady_clock::now() + std::chrono::nanoseconds(timeout_ns ? timeout_ns : 60000000000ull);
+    while (!s->results[ticket].done && s->fatal == SSSP_OK) {
+        if (s->cv.wait_until(lk, deadline) == std::cv_status::timeout) return SSSP_ERR_TIMEOUT;
+    }
+    auto& r = s->results[ticket];
+    if (!r.done) return s->fatal;
+    if (info) *info = r.info;
+    s->results.erase(ticket);
+    return 1;
+}
+
+int sssp_server_stats(const sssp_server* s, uint64_t* launches, uint32_t* busy_slots, uint64_t* pending)
+{
+    if (!s) return SSSP_ERR_INVALID_ARG;
+    sssp_server* m = const_cast<sssp_server*>(s);
+    std::lock_guard<std::mutex> lk(m->mu);
+    uint32_t b = 0;
+    for (const auto& sl : m->slots) b += sl.busy ? 1u : 0u;
+    if (launches) *launches = m->launches;
+    if (busy_slots) *busy_slots = b;
+    if (pending) *pending = m->pending.size();
+    return SSSP_OK;
+}
+
+int sssp_server_destroy(sssp_server* s)
+{
+    if (!s) return SSSP_ERR_INVALID_ARG;
+    {
+        std::lock_guard<std::mutex> lk(s->mu);
+        s->stopping = true;
+    }
+    if (s->worker.joinable()) s->worker.join();
+    if (s->stream) { cudaStreamSynchronize(s->stream); cudaStreamDestroy(s->stream); }
+    cudaFree(s->scratch);
+    cudaFree(s->d_desc);
+    cudaFree(s->d_ictrl);
+    cudaFree(s->d_ctrl);
+    cudaFree(s->d_state);
+    if (s->h_cmd) cudaFreeHost(s->h_cmd);
+    if (s->h_done) cudaFreeHost(s->h_done);
+    if (s->h_shared) cudaFreeHost(s->h_shared);
+    delete s;
+    return SSSP_OK;
 }
 
 }  // extern "C"

@@ -116,6 +116,7 @@ uint32_t rho_sample_bound(uint32_t n, uint64_t rho);   // power-of-two smem keys
 // Batched solves (sssp_batch.cu).
 constexpr uint32_t kMaxBatch = 2048;        // instances per batched launch
 const void* batch_kernel_ptr();
+const void* serve_kernel_ptr();
 
 }  // namespace sssp
 

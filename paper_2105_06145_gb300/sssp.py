@@ -94,13 +94,43 @@ _lib.sssp_solve_multi.argtypes = [_P, _P, _u32, _i32, _P, _P, _P]
 _lib.sssp_solve_multi.restype = _i32
 _lib.sssp_batch_last_stats.argtypes = [_P, _u32, _P]
 _lib.sssp_batch_last_stats.restype = _i32
+class sssp_server_config(ctypes.Structure):
+    _fields_ = [("slots", ctypes.c_uint32), ("algo", ctypes.c_int), ("param", ctypes.c_uint64),
+                ("idle_ns", ctypes.c_uint64), ("hbm_fraction", ctypes.c_double)]
+
+
+class sssp_query_info(ctypes.Structure):
+    _fields_ = [("status", ctypes.c_int32), ("steps", ctypes.c_uint32), ("latency_ns", ctypes.c_uint64),
+                ("device_ns", ctypes.c_uint64), ("device_admit_ns", ctypes.c_uint64),
+                ("device_done_ns", ctypes.c_uint64), ("edges", ctypes.c_uint64)]
+
+    def as_dict(self) -> dict:
+        return {k: int(getattr(self, k)) for k, _ in self._fields_}
+
+
+_lib.sssp_server_create.argtypes = [_P, ctypes.POINTER(sssp_server_config), ctypes.POINTER(_P)]
+_lib.sssp_server_create.restype = _i32
+_lib.sssp_server_slots.argtypes = [_P, ctypes.POINTER(_u32)]
+_lib.sssp_server_slots.restype = _i32
+_lib.sssp_server_submit.argtypes = [_P, _u32, _P, ctypes.POINTER(_u64)]
+_lib.sssp_server_submit.restype = _i32
+_lib.sssp_server_poll.argtypes = [_P, _u64, ctypes.POINTER(sssp_query_info)]
+_lib.sssp_server_poll.restype = _i32
+_lib.sssp_server_wait.argtypes = [_P, _u64, _u64, ctypes.POINTER(sssp_query_info)]
+_lib.sssp_server_wait.restype = _i32
+_lib.sssp_server_stats.argtypes = [_P, ctypes.POINTER(_u64), ctypes.POINTER(_u32), ctypes.POINTER(_u64)]
+_lib.sssp_server_stats.restype = _i32
+_lib.sssp_server_destroy.argtypes = [_P]
+_lib.sssp_server_destroy.restype = _i32
 _lib.sssp_status_string.argtypes = [_i32]
 _lib.sssp_status_string.restype = ctypes.c_char_p
 
 EXPORTED = ["sssp_graph_create", "sssp_graph_destroy", "sssp_graph_info", "sssp_solve",
             "sssp_solve_ex", "sssp_solve_host", "sssp_last_status", "sssp_last_stats",
             "sssp_rho_threshold", "sssp_status_string", "sssp_solve_noalloc", "sssp_solve_sources",
-            "sssp_solve_multi", "sssp_batch_last_stats"]
+            "sssp_solve_multi", "sssp_batch_last_stats", "sssp_server_create", "sssp_server_slots",
+            "sssp_server_submit", "sssp_server_poll", "sssp_server_wait", "sssp_server_stats",
+            "sssp_server_destroy"]
 
 MAX_BATCH = 2048
 
@@ -241,6 +271,53 @@ def sssp_batch_last_stats(k: int, stream: int = 0) -> tuple[int, list]:
     if rc < 0 and rc not in (SSSP_ERR_TIMEOUT, SSSP_ERR_INTERNAL):
         raise SSSPError(rc, "sssp_batch_last_stats")
     return rc, [arr[i].as_dict() for i in range(k)]
+
+
+def sssp_server_create(g: int, slots: int = 0, algo: int = SSSP_RHO, param: int = 0, idle_ns: int = 0,
+                       hbm_fraction: float = 0.0) -> int:
+    cfg = sssp_server_config(slots, algo, param, idle_ns, hbm_fraction)
+    h = _P()
+    _check(_lib.sssp_server_create(g, ctypes.byref(cfg), ctypes.byref(h)), "sssp_server_create")
+    return h.value
+
+
+def sssp_server_slots(s: int) -> int:
+    v = _u32()
+    _check(_lib.sssp_server_slots(s, ctypes.byref(v)), "sssp_server_slots")
+    return v.value
+
+
+def sssp_server_submit(s: int, source: int, dist_out_ptr: int) -> int:
+    t = _u64()
+    _check(_lib.sssp_server_submit(s, source, dist_out_ptr, ctypes.byref(t)), "sssp_server_submit")
+    return t.value
+
+
+def sssp_server_poll(s: int, ticket: int):
+    """None while pending, else the query info dict."""
+    info = sssp_query_info()
+    rc = _lib.sssp_server_poll(s, ticket, ctypes.byref(info))
+    if rc < 0:
+        raise SSSPError(rc, "sssp_server_poll")
+    return info.as_dict() if rc == 1 else None
+
+
+def sssp_server_wait(s: int, ticket: int, timeout_ns: int = 0) -> dict:
+    info = sssp_query_info()
+    rc = _lib.sssp_server_wait(s, ticket, timeout_ns, ctypes.byref(info))
+    if rc != 1:
+        raise SSSPError(rc, "sssp_server_wait")
+    return info.as_dict()
+
+
+def sssp_server_stats(s: int) -> dict:
+    a, b, c = _u64(), _u32(), _u64()
+    _check(_lib.sssp_server_stats(s, ctypes.byref(a), ctypes.byref(b), ctypes.byref(c)), "sssp_server_stats")
+    return {"launches": a.value, "busy_slots": b.value, "pending": c.value}
+
+
+def sssp_server_destroy(s: int) -> None:
+    _check(_lib.sssp_server_destroy(s), "sssp_server_destroy")
 
 
 class Graph:

@@ -1,0 +1,90 @@
+"""The query server (continuous batching): queries that arrive while others
+run are admitted at the next step boundary and run alongside them; every
+result equals the oracle and the single solve of the same source (the same
+alone and in the mix); more queries than slots wait for a free slot; the
+device loop exits when idle and restarts on the next query."""
+import time
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_2105_06145_gb300 import graphgen as gg
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def lib():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2105_06145_gb300 import sssp
+    return sssp
+
+
+def _single(lib, G, n, s, algo, param):
+    d = torch.empty(n, dtype=torch.int64, device="cuda")
+    stream = torch.cuda.current_stream().cuda_stream
+    G.solve(s, algo, param, d, stream)
+    assert G.status(stream) == 0
+    return d.cpu().numpy().view(np.uint64).copy()
+
+
+@pytest.mark.parametrize("algo,param", [(0, 2048), (1, 1 << 14), (2, 0)])
+def test_overlapping_queries_equal_alone(lib, algo, param):
+    g = gg.road(200, 0.75, seed=3)                       # ~250 steps per query: queries overlap
+    srcs = gg.pick_sources(g, 24, 17)
+    G = lib.Graph(g)
+    srv = lib.sssp_server_create(G.handle, slots=6, algo=algo, param=param)
+    outs = [torch.full((g.n,), 9, dtype=torch.int64, device="cuda") for _ in srcs]
+    torch.cuda.synchronize()
+    tickets = []
+    rng = np.random.default_rng(1)
+    for s, o in zip(srcs, outs):
+        tickets.append(lib.sssp_server_submit(srv, s, o.data_ptr()))
+        time.sleep(float(rng.uniform(0, 0.002)))       # staggered arrivals
+    infos = [lib.sssp_server_wait(srv, t, 60_000_000_000) for t in tickets]
+    assert all(i["status"] == 0 and i["steps"] >= 1 for i in infos)
+    for s, o in zip(srcs, outs):
+        got = o.cpu().numpy().view(np.uint64)
+        assert np.array_equal(got, oracle.dijkstra(g, s))
+    for j in (0, 11, 23):
+        assert np.array_equal(outs[j].cpu().numpy().view(np.uint64), _single(lib, G, g.n, srcs[j], algo, param))
+    # continuous batching: some query was admitted while another was running
+    iv = sorted((i["device_admit_ns"], i["device_done_ns"]) for i in infos)
+    joined = any(iv[b][0] > iv[a][0] and iv[b][0] < iv[a][1] for a in range(len(iv)) for b in range(a + 1, len(iv)))
+    assert joined
+    lib.sssp_server_destroy(srv)
+    G.close()
+
+
+def test_backpressure_idle_restart_and_destroy(lib):
+    g = gg.rmat(14, 16, gen_seed=41, wseed=42)
+    srcs = gg.pick_sources(g, 40, 3)
+    G = lib.Graph(g)
+    srv = lib.sssp_server_create(G.handle, slots=4, algo=0, param=1 << 10, idle_ns=1_000_000)
+    assert lib.sssp_server_slots(srv) == 4
+    outs = [torch.empty(g.n, dtype=torch.int64, device="cuda") for _ in srcs]
+    torch.cuda.synchronize()
+    tickets = [lib.sssp_server_submit(srv, s, o.data_ptr()) for s, o in zip(srcs, outs)]  # 10x the slots
+    for t in tickets:
+        assert lib.sssp_server_wait(srv, t)["status"] == 0
+    for s, o in list(zip(srcs, outs))[::7]:
+        assert np.array_equal(o.cpu().numpy().view(np.uint64), oracle.dijkstra(g, s))
+    launches = lib.sssp_server_stats(srv)["launches"]
+    time.sleep(0.05)                                    # > idle: the device loop exits
+    t = lib.sssp_server_submit(srv, srcs[0], outs[0].data_ptr())
+    assert lib.sssp_server_wait(srv, t)["status"] == 0
+    assert lib.sssp_server_stats(srv)["launches"] > launches
+    assert np.array_equal(outs[0].cpu().numpy().view(np.uint64), oracle.dijkstra(g, srcs[0]))
+    # poll interface, then destroy with queries still queued
+    t = lib.sssp_server_submit(srv, srcs[1], outs[1].data_ptr())
+    while lib.sssp_server_poll(srv, t) is None:
+        time.sleep(0.0005)
+    for s, o in zip(srcs[:12], outs[:12]):
+        lib.sssp_server_submit(srv, s, o.data_ptr())
+    lib.sssp_server_destroy(srv)
+    # the context is still usable
+    assert np.array_equal(_single(lib, G, g.n, srcs[2], 2, 0), oracle.dijkstra(g, srcs[2]))
+    G.close()

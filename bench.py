@@ -163,6 +163,11 @@ def build_workload(name: str, scale: int):
     return g, srcs, label
 
 
+def gg_sources(g, k=256, seed=9):
+    from paper_2105_06145_gb300 import graphgen as gg
+    return gg.pick_sources(g, k, seed)
+
+
 def run_reference(args, g, srcs, label, rank, world):
     """CPU oracle (binary-heap Dijkstra, one core) timed on the same metric."""
     import oracle
@@ -236,6 +241,115 @@ def measure_batched(sssp, G, g, torch, stream, stream_obj) -> dict:
     return res
 
 
+def measure_serving(sssp, G, g, torch, sources, rates, window_s=1.0, hard_s=10.0, slots=0,
+                    algo=None, param=0, seed=8) -> dict:
+    """Serving (SURVEY pattern 5): a Poisson query stream at each offered rate
+    for `window_s` seconds against the resident graph; queries go to the
+    continuous-batching server as client-side result buffers allow.  Latency
+    is from the scheduled arrival to the completion seen by the client; the
+    plain loop (one sssp_solve at a time) is measured on the same sources."""
+    algo = sssp.SSSP_RHO if algo is None else algo
+    srv = sssp.sssp_server_create(G.handle, slots=slots, algo=algo, param=param)
+    S = sssp.sssp_server_slots(srv)
+    nbuf = S + 32
+    free_b, _ = torch.cuda.mem_get_info()
+    nbuf = int(max(1, min(nbuf, (free_b * 0.8) // (8 * g.n))))
+    bufs = [torch.empty(g.n, dtype=torch.int64, device="cuda") for _ in range(nbuf)]
+    torch.cuda.synchronize()
+    # plain loop: one query at a time, result synchronised
+    stream = torch.cuda.current_stream().cuda_stream
+    prm = param or (max(64, g.n // 16) if algo == sssp.SSSP_RHO else 0)
+    G.solve(sources[0], algo, prm, bufs[0], stream)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    nplain = min(10, len(sources))
+    for s_ in sources[:nplain]:
+        G.solve(s_, algo, prm, bufs[0], stream)
+        torch.cuda.synchronize()
+    plain_qps = nplain / (time.perf_counter() - t0)
+    rng = np.random.default_rng(seed)
+    out = {"slots": S, "result_buffers": nbuf, "plain_queries_per_s": plain_qps, "rates": []}
+    for rate in rates:
+        arr = np.cumsum(rng.exponential(1.0 / rate, size=int(rate * window_s * 1.2) + 16))
+        arr = arr[arr < window_s]
+        srcs = rng.choice(np.asarray(sources), size=arr.size)
+        free = list(range(nbuf))
+        outstanding = {}
+        lat = []
+        i = 0
+        t0 = time.perf_counter()
+        last_done = t0
+        while (i < arr.size or outstanding) and time.perf_counter() - t0 < hard_s:
+            now = time.perf_counter() - t0
+            progressed = False
+            while i < arr.size and arr[i] <= now and free:
+                b = free.pop()
+                tk = sssp.sssp_server_submit(srv, int(srcs[i]), bufs[b].data_ptr())
+                outstanding[tk] = (arr[i], b)
+                i += 1
+                progressed = True
+            done = sssp.sssp_server_drain(srv)
+            if done:
+                tnow = time.perf_counter()
+                for tk, info in done:
+                    a_, b = outstanding.pop(tk)
+                    lat.append(tnow - t0 - a_)
+                    free.append(b)
+                last_done = tnow
+                progressed = True
+            if not progressed:
+                time.sleep(0.00005)
+        elapsed = last_done - t0
+        backlog = int(arr.size - i)
+        lat_ms = np.asarray(lat) * 1e3
+        out["rates"].append({
+            "offered_per_s": rate, "arrived": int(arr.size), "completed": len(lat),
+            "not_admitted_in_window": backlog,
+            "queries_per_s": len(lat) / elapsed if elapsed > 0 else 0.0,
+            "p50_ms": float(np.percentile(lat_ms, 50)) if lat else None,
+            "p99_ms": float(np.percentile(lat_ms, 99)) if lat else None})
+        # let anything still outstanding finish before the next rate
+        for tk in list(outstanding):
+            sssp.sssp_server_wait(srv, tk, 120_000_000_000)
+        sssp.sssp_server_drain(srv)
+    best = max(r["queries_per_s"] for r in out["rates"])
+    out["saturation_queries_per_s"] = best
+    out["speedup_vs_plain"] = best / plain_qps
+    out["launches"] = sssp.sssp_server_stats(srv)["launches"]
+    sssp.sssp_server_destroy(srv)
+    del bufs
+    torch.cuda.empty_cache()
+    return out
+
+
+def run_serve_sweep(args):
+    """--serve: the configs[4] sweep over resident graphs (RMAT scale 25, the
+    4096^2 road-like grid, the 2M-point k-NN graph)."""
+    import torch
+    from paper_2105_06145_gb300 import graphgen as gg, sssp
+    rates = [int(x) for x in args.serve_rates.split(",")]
+    for name in args.serve_workloads.split(","):
+        if name == "rmat25":
+            g = gg.rmat(25, 16, 0.57, 0.19, 0.19, gen_seed=8, wseed=8)
+        elif name == "road":
+            g, _ = gg.workload_road(4096)
+        elif name == "knn":
+            g = gg.knn(2_000_000, 64, 0.02, 10, float(1 << 20), seed=10)
+        elif name == "rmat22":
+            g, _ = gg.workload_rmat(22)
+        else:
+            raise SystemExit(f"unknown serving workload {name}")
+        lab = gg.largest_cc(g)
+        sources = gg.pick_sources(g, 256, 9, mask=np.ones(g.n, np.uint8) if name == "knn" else lab)
+        G = sssp.Graph(g)
+        res = measure_serving(sssp, G, g, torch, sources, rates, window_s=args.serve_window,
+                              slots=args.serve_slots)
+        print(json.dumps({"serve_workload": name, "n": g.n, "m": g.m, **res}), flush=True)
+        G.close()
+        del G
+        torch.cuda.empty_cache()
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -250,9 +364,18 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-batch", action="store_true", help="skip the batched-solve measurements")
+    ap.add_argument("--no-serve", action="store_true", help="skip the serving measurement")
+    ap.add_argument("--serve", action="store_true", help="run the serving sweep (configs[4]) only")
+    ap.add_argument("--serve-workloads", default="rmat25,road,knn")
+    ap.add_argument("--serve-rates", default="1000,2000,5000,10000,20000,50000")
+    ap.add_argument("--serve-window", type=float, default=1.0)
+    ap.add_argument("--serve-slots", type=int, default=0)
     args = ap.parse_args()
 
     rank, world, local = dist_env()
+    if args.serve:
+        run_serve_sweep(args)
+        return
     g, srcs, label = build_workload(args.workload, args.scale)
 
     if args.impl == "reference":
@@ -373,6 +496,11 @@ def main():
     if rank == 0 and not args.no_batch and args.workload == "rmat" and args.scale == 22:
         batched = measure_batched(sssp, G, g, torch, stream, stream_obj)
 
+    served = None
+    if rank == 0 and not args.no_serve and args.workload == "rmat" and args.scale == 22:
+        served = measure_serving(sssp, G, g, torch, gg_sources(g), [1000, 10000], window_s=0.5, hard_s=6.0,
+                                 slots=64)
+
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
         import oracle
@@ -407,6 +535,7 @@ def main():
             "cpu_baseline": cpu,
             "e2e": e2e,
             "batched": batched,
+            "served": served,
             "gpu_launches": K,
             "clocks": clk,
         }

@@ -271,6 +271,11 @@ int sssp_server_poll(sssp_server* s, uint64_t ticket, sssp_query_info* info);
  * SSSP_ERR_TIMEOUT then). */
 int sssp_server_wait(sssp_server* s, uint64_t ticket, uint64_t timeout_ns, sssp_query_info* info);
 
+/* Completion queue: copies up to max completed, not yet collected queries to
+ * HOST tickets[] / infos[] (in completion order; they are then released) and
+ * returns how many (0 when none; a negative status after a device failure). */
+int sssp_server_drain(sssp_server* s, uint64_t* tickets, sssp_query_info* infos, uint32_t max);
+
 /* Device-loop launches so far, slots in use, queries waiting for a slot. */
 int sssp_server_stats(const sssp_server* s, uint64_t* launches, uint32_t* busy_slots, uint64_t* pending);
 

@@ -921,6 +921,7 @@ struct sssp_server {
     std::vector<Slot> slots;
     struct Result { bool done = false; sssp_query_info info{}; uint64_t t_submit = 0; };
     std::unordered_map<uint64_t, Result> results;
+    std::deque<uint64_t> completed;   // tickets completed and not yet drained
     uint64_t next_ticket = 1;
     bool kernel_running = false;
     uint64_t launches = 0;
@@ -1002,6 +1003,7 @@ void server_loop(sssp_server* s)
                 r.info.device_admit_ns = ta;
                 r.info.device_done_ns = td;
                 r.info.latency_ns = host_ns() - sl.t_submit;
+                s->completed.push_back(sl.ticket);
                 sl.busy = false;
                 progress = true;
             }
@@ -1242,6 +1244,25 @@ int sssp_server_wait(sssp_server* s, uint64_t ticket, uint64_t timeout_ns, sssp_
     if (info) *info = r.info;
     s->results.erase(ticket);
     return 1;
+}
+
+int sssp_server_drain(sssp_server* s, uint64_t* tickets, sssp_query_info* infos, uint32_t max)
+{
+    if (!s || (max > 0 && (!tickets || !infos))) return SSSP_ERR_INVALID_ARG;
+    std::lock_guard<std::mutex> lk(s->mu);
+    uint32_t got = 0;
+    while (got < max && !s->completed.empty()) {
+        const uint64_t t = s->completed.front();
+        s->completed.pop_front();
+        auto it = s->results.find(t);
+        if (it == s->results.end()) continue;  // already collected by poll / wait
+        tickets[got] = t;
+        infos[got] = it->second.info;
+        s->results.erase(it);
+        ++got;
+    }
+    if (got == 0 && s->fatal != SSSP_OK) return s->fatal;
+    return (int)got;
 }
 
 int sssp_server_stats(const sssp_server* s, uint64_t* launches, uint32_t* busy_slots, uint64_t* pending)

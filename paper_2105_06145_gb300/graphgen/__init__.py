@@ -31,9 +31,12 @@ def build(force: bool = False) -> str:
     """Compile libgraphgen.so with gcc (portable flags, no FMA contraction)."""
     if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
         tmp = _LIB + f".tmp{os.getpid()}"
-        subprocess.check_call(["gcc", "-O2", "-std=gnu11", "-fPIC", "-shared",
-                               "-ffp-contract=off", "-fno-fast-math",
-                               _SRC, "-o", tmp, "-lm"])
+        base = ["gcc", "-O2", "-std=gnu11", "-fPIC", "-shared", "-ffp-contract=off", "-fno-fast-math",
+                _SRC, "-o", tmp, "-lm"]
+        try:  # OpenMP when the toolchain has it; results do not depend on the thread count
+            subprocess.check_call(base + ["-fopenmp"], stderr=subprocess.DEVNULL)
+        except subprocess.CalledProcessError:
+            subprocess.check_call(base)
         os.replace(tmp, _LIB)
     return _LIB
 
@@ -69,6 +72,8 @@ def _L():
         lib.graphgen_random.argtypes = [u32, u64, u32, u32, u64, i32,
                                         ctypes.POINTER(u64), PP, PP, PP]
         lib.graphgen_random.restype = i32
+        lib.graphgen_knn.argtypes = [u32, u32, dbl, u32, dbl, u64, ctypes.POINTER(u64), PP, PP, PP, P]
+        lib.graphgen_knn.restype = i32
         lib.graphgen_largest_cc.argtypes = [u32, P, P, P]
         lib.graphgen_largest_cc.restype = i64
         lib.graphgen_kth_labelled.argtypes = [u32, P, u64]
@@ -378,3 +383,38 @@ def workload_multi(count: int = 512, lo_log2: int = 10, hi_log2: int = 18, seed:
         src = pick_sources(g, 1, gseed)[0]
         out.append((g, src))
     return out
+
+
+def knn(npts: int = 2_000_000, clusters: int = 64, sigma: float = 0.02, k: int = 10,
+        wscale: float = float(1 << 20), seed: int = 10, with_points: bool = False):
+    """Symmetrised k-NN graph of points from a 3-D cluster mixture (see
+    graphgen_knn); weight floor(2^20 * distance) + 1.  Returns the CSR (and the
+    points when with_points)."""
+    key = f"knn_{npts}_{clusters}_{sigma}_{k}_{wscale}_{seed}"
+
+    def make():
+        lib = _L()
+        m = ctypes.c_uint64()
+        po, pt, pw = ctypes.c_void_p(), ctypes.c_void_p(), ctypes.c_void_p()
+        rc = lib.graphgen_knn(npts, clusters, sigma, k, wscale, seed, ctypes.byref(m),
+                              ctypes.byref(po), ctypes.byref(pt), ctypes.byref(pw), None)
+        if rc != 0:
+            raise MemoryError("graphgen_knn failed")
+        mm = m.value
+        return CSR(npts, _take(po, np.uint64, npts + 1), _take(pt, np.uint32, mm), _take(pw, np.uint32, mm))
+
+    g = _cached(key, make)
+    g.name = f"knn{npts}"
+    g.meta = {"npts": npts, "clusters": clusters, "sigma": sigma, "k": k, "seed": seed}
+    if with_points:
+        lib = _L()
+        pts = np.zeros(3 * npts, dtype=np.float64)
+        m = ctypes.c_uint64()
+        po, pt, pw = ctypes.c_void_p(), ctypes.c_void_p(), ctypes.c_void_p()
+        rc = lib.graphgen_knn(npts, clusters, sigma, k, wscale, seed, ctypes.byref(m),
+                              ctypes.byref(po), ctypes.byref(pt), ctypes.byref(pw), pts.ctypes.data)
+        assert rc == 0
+        for ptr in (po, pt, pw):
+            lib.graphgen_free(ptr)
+        return g, pts.reshape(npts, 3)
+    return g

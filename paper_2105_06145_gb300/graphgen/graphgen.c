@@ -19,6 +19,9 @@
 #include <stdint.h>
 #include <stdlib.h>
 #include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
 
 static inline uint64_t gg_sm64(uint64_t seed, uint64_t k)
 {
@@ -89,16 +92,48 @@ static int gg_radix_sort(uint64_t* keys, uint64_t count, int bits)
     const int D = 11;
     uint64_t* src = keys;
     uint64_t* dst = tmp;
+#ifdef _OPENMP
+    int T = omp_get_max_threads();
+#else
+    int T = 1;
+#endif
+    if (count < (1u << 20)) T = 1;
+    uint64_t* hist = (uint64_t*)malloc(sizeof(uint64_t) * 2048u * (size_t)T);
+    if (!hist) { free(tmp); return -1; }
     for (int shift = 0; shift < bits; shift += D) {
-        uint64_t hist[1u << 11];
-        memset(hist, 0, sizeof hist);
-        for (uint64_t i = 0; i < count; ++i) hist[(src[i] >> shift) & 2047u]++;
-        uint64_t sum = 0;
-        for (int d = 0; d < 2048; ++d) { uint64_t t = hist[d]; hist[d] = sum; sum += t; }
-        for (uint64_t i = 0; i < count; ++i) dst[hist[(src[i] >> shift) & 2047u]++] = src[i];
+        /* stable LSD pass: thread t owns the contiguous chunk [lo_t, hi_t) */
+        memset(hist, 0, sizeof(uint64_t) * 2048u * (size_t)T);
+#ifdef _OPENMP
+#pragma omp parallel num_threads(T)
+#endif
+        {
+#ifdef _OPENMP
+            int t = omp_get_thread_num();
+#else
+            int t = 0;
+#endif
+            uint64_t lo = count * (uint64_t)t / (uint64_t)T, hi = count * (uint64_t)(t + 1) / (uint64_t)T;
+            uint64_t* h = hist + 2048u * (size_t)t;
+            for (uint64_t i = lo; i < hi; ++i) h[(src[i] >> shift) & 2047u]++;
+#ifdef _OPENMP
+#pragma omp barrier
+#pragma omp single
+#endif
+            {
+                uint64_t sum = 0;
+                for (int d = 0; d < 2048; ++d)
+                    for (int tt = 0; tt < T; ++tt) {
+                        uint64_t c = hist[2048u * (size_t)tt + d];
+                        hist[2048u * (size_t)tt + d] = sum;
+                        sum += c;
+                    }
+            }
+            for (uint64_t i = lo; i < hi; ++i) dst[h[(src[i] >> shift) & 2047u]++] = src[i];
+        }
         uint64_t* t = src; src = dst; dst = t;
     }
     if (src != keys) memcpy(keys, src, sizeof(uint64_t) * count);
+    free(hist);
     free(tmp);
     return 0;
 }
@@ -114,9 +149,12 @@ static int gg_keys_to_csr(const uint64_t* keys, uint64_t m, uint32_t n, int sh,
     uint32_t* w = (uint32_t*)malloc(sizeof(uint32_t) * (m ? m : 1));
     if (!off || !tgt || !w) { free(off); free(tgt); free(w); return -1; }
     uint64_t mask = (sh >= 64) ? ~0ull : ((1ull << sh) - 1u);
+    for (uint64_t i = 0; i < m; ++i) off[(uint32_t)(keys[i] >> sh) + 1]++;
+#ifdef _OPENMP
+#pragma omp parallel for schedule(static)
+#endif
     for (uint64_t i = 0; i < m; ++i) {
         uint32_t u = (uint32_t)(keys[i] >> sh), v = (uint32_t)(keys[i] & mask);
-        off[u + 1]++;
         tgt[i] = v;
         w[i] = wmax_excl ? gg_pair_weight(wseed, u, v, wmax_excl) : 1u;
     }
@@ -186,6 +224,9 @@ int graphgen_rmat_n(uint32_t scale, uint32_t edgefactor, double a, double b, dou
     uint64_t tb = ta + (uint64_t)(b * (double)two32);
     uint64_t tc = tb + (uint64_t)(c * (double)two32);
     uint64_t per_edge = (scale + 1) / 2;
+#ifdef _OPENMP
+#pragma omp parallel for schedule(static)
+#endif
     for (uint64_t e = 0; e < E; ++e) {
         uint32_t u = 0, v = 0;
         uint64_t h = 0;
@@ -211,12 +252,16 @@ int graphgen_rmat_n(uint32_t scale, uint32_t edgefactor, double a, double b, dou
     }
     uint64_t mask = ((uint64_t)1 << scale) - 1u;
     uint32_t nk = (n_keep > 0 && n_keep < n) ? n_keep : n;
-    uint64_t kept = 0;
+#ifdef _OPENMP
+#pragma omp parallel for schedule(static)
+#endif
     for (uint64_t e = 0; e < E; ++e) {
         uint32_t u = perm[keys[e] >> scale], v = perm[keys[e] & mask];
-        if (u >= nk || v >= nk) continue;
-        keys[kept++] = ((uint64_t)u << scale) | v;
+        keys[e] = (u >= nk || v >= nk) ? ~0ull : (((uint64_t)u << scale) | v);
     }
+    uint64_t kept = 0;
+    for (uint64_t e = 0; e < E; ++e)
+        if (keys[e] != ~0ull) keys[kept++] = keys[e];
     free(perm);
     int64_t m = gg_symmetrise(keys, kept, (int)scale);
     if (m < 0) { free(keys); return -1; }
@@ -393,4 +438,142 @@ int64_t graphgen_kth_labelled(uint32_t n, const uint8_t* label, uint64_t k)
     for (uint32_t v = 0; v < n; ++v)
         if (label[v]) { if (k == 0) return v; --k; }
     return -1;
+}
+
+/* ------------------------------------------------------------------------ */
+/* k-nearest-neighbour graph of points from a 3-D mixture of `clusters`      */
+/* clusters: centres uniform in the unit cube, offsets sigma * z per         */
+/* coordinate with z the Irwin-Hall sum of 12 uniforms minus 6 (an           */
+/* approximately standard normal variate built from uniforms only, so the    */
+/* points are bit-identical on every platform); a point outside the cube is  */
+/* redrawn.  Each point links to its k nearest other points (Euclidean,      */
+/* ties by index); the union is symmetrised; w = floor(wscale * d) + 1.      */
+/* ------------------------------------------------------------------------ */
+static double gg_irwin_hall(uint64_t seed, uint64_t base)
+{
+    double s = 0.0;
+    for (int j = 0; j < 12; ++j) s += gg_unit(gg_sm64(seed, base + (uint64_t)j));
+    return s - 6.0;
+}
+
+int graphgen_knn(uint32_t npts, uint32_t clusters, double sigma, uint32_t k, double wscale, uint64_t seed,
+                 uint64_t* m_out, uint64_t** off_out, uint32_t** tgt_out, uint32_t** w_out, double* xyz_out)
+{
+    if (npts < 2 || clusters == 0 || k == 0 || k >= npts) return -1;
+    const uint32_t n = npts;
+    double* P = xyz_out ? xyz_out : (double*)malloc(sizeof(double) * 3 * (size_t)n);
+    double* C = (double*)malloc(sizeof(double) * 3 * (size_t)clusters);
+    if (!P || !C) { if (!xyz_out) free(P); free(C); return -1; }
+    const uint64_t cseed = seed ^ 0x1234567887654321ULL;
+    for (uint32_t j = 0; j < clusters; ++j)
+        for (int d = 0; d < 3; ++d) C[3 * j + d] = gg_unit(gg_sm64(cseed, 3ull * j + d));
+#ifdef _OPENMP
+#pragma omp parallel for schedule(static)
+#endif
+    for (uint32_t i = 0; i < n; ++i) {
+        const uint32_t cl = (uint32_t)gg_mulhi(gg_sm64(seed, (uint64_t)i << 20), clusters);
+        for (uint64_t attempt = 0;; ++attempt) {
+            const uint64_t base = ((uint64_t)i << 20) + 1 + attempt * 36;
+            double x = C[3 * cl] + sigma * gg_irwin_hall(seed, base);
+            double y = C[3 * cl + 1] + sigma * gg_irwin_hall(seed, base + 12);
+            double z = C[3 * cl + 2] + sigma * gg_irwin_hall(seed, base + 24);
+            if (x >= 0.0 && x < 1.0 && y >= 0.0 && y < 1.0 && z >= 0.0 && z < 1.0) {
+                P[3 * (size_t)i] = x; P[3 * (size_t)i + 1] = y; P[3 * (size_t)i + 2] = z;
+                break;
+            }
+        }
+    }
+    free(C);
+    /* uniform grid, G^3 cells; points sorted by cell */
+    const uint32_t G = 128;
+    const double h = 1.0 / G;
+    uint64_t ncell = (uint64_t)G * G * G;
+    uint32_t* cstart = (uint32_t*)calloc(ncell + 1, sizeof(uint32_t));
+    uint32_t* order = (uint32_t*)malloc(sizeof(uint32_t) * (size_t)n);
+    uint32_t* cellof = (uint32_t*)malloc(sizeof(uint32_t) * (size_t)n);
+    uint64_t* keys = (uint64_t*)malloc(sizeof(uint64_t) * 2 * (size_t)n * k);
+    if (!cstart || !order || !cellof || !keys) {
+        free(cstart); free(order); free(cellof); free(keys); if (!xyz_out) free(P); return -1;
+    }
+    for (uint32_t i = 0; i < n; ++i) {
+        uint32_t cx = (uint32_t)(P[3 * (size_t)i] * G), cy = (uint32_t)(P[3 * (size_t)i + 1] * G),
+                 cz = (uint32_t)(P[3 * (size_t)i + 2] * G);
+        if (cx >= G) cx = G - 1;
+        if (cy >= G) cy = G - 1;
+        if (cz >= G) cz = G - 1;
+        cellof[i] = (cz * G + cy) * G + cx;
+        cstart[cellof[i] + 1]++;
+    }
+    for (uint64_t c = 0; c < ncell; ++c) cstart[c + 1] += cstart[c];
+    {
+        uint32_t* pos = (uint32_t*)malloc(sizeof(uint32_t) * (size_t)ncell);
+        if (!pos) { free(cstart); free(order); free(cellof); free(keys); if (!xyz_out) free(P); return -1; }
+        memcpy(pos, cstart, sizeof(uint32_t) * (size_t)ncell);
+        for (uint32_t i = 0; i < n; ++i) order[pos[cellof[i]]++] = i;  /* ascending index within a cell */
+        free(pos);
+    }
+    const int scale = 1 + (int)(63 - __builtin_clzll((unsigned long long)n));  /* bits for an id */
+#ifdef _OPENMP
+#pragma omp parallel for schedule(dynamic, 256)
+#endif
+    for (uint32_t i = 0; i < n; ++i) {
+        /* k best (d2, index) kept sorted ascending */
+        double bd[64];
+        uint32_t bi[64];
+        uint32_t cnt = 0;
+        const double px = P[3 * (size_t)i], py = P[3 * (size_t)i + 1], pz = P[3 * (size_t)i + 2];
+        const int cx = (int)(cellof[i] % G), cy = (int)((cellof[i] / G) % G), cz = (int)(cellof[i] / G / G);
+        for (int r = 0; r < (int)G; ++r) {
+            for (int dz = -r; dz <= r; ++dz)
+                for (int dy = -r; dy <= r; ++dy)
+                    for (int dx = -r; dx <= r; ++dx) {
+                        if (dx != -r && dx != r && dy != -r && dy != r && dz != -r && dz != r) continue;
+                        const int x = cx + dx, y = cy + dy, z = cz + dz;
+                        if (x < 0 || y < 0 || z < 0 || x >= (int)G || y >= (int)G || z >= (int)G) continue;
+                        const uint32_t c = ((uint32_t)z * G + (uint32_t)y) * G + (uint32_t)x;
+                        for (uint32_t t = cstart[c]; t < cstart[c + 1]; ++t) {
+                            const uint32_t j = order[t];
+                            if (j == i) continue;
+                            const double ex = P[3 * (size_t)j] - px, ey = P[3 * (size_t)j + 1] - py,
+                                         ez = P[3 * (size_t)j + 2] - pz;
+                            const double d2 = ex * ex + ey * ey + ez * ez;
+                            if (cnt == k && (d2 > bd[k - 1] || (d2 == bd[k - 1] && j > bi[k - 1]))) continue;
+                            uint32_t q = cnt < k ? cnt++ : k - 1;
+                            while (q > 0 && (bd[q - 1] > d2 || (bd[q - 1] == d2 && bi[q - 1] > j))) {
+                                bd[q] = bd[q - 1]; bi[q] = bi[q - 1]; --q;
+                            }
+                            bd[q] = d2; bi[q] = j;
+                        }
+                    }
+            /* every point beyond ring r is at least r*h away */
+            if (cnt == k && bd[k - 1] <= ((double)r * h) * ((double)r * h)) break;
+        }
+        for (uint32_t q = 0; q < k; ++q)
+            keys[(size_t)i * k + q] = ((uint64_t)i << scale) | (q < cnt ? bi[q] : i);
+    }
+    free(order); free(cellof); free(cstart);
+    int64_t m = gg_symmetrise(keys, (uint64_t)n * k, scale);
+    if (m < 0) { free(keys); if (!xyz_out) free(P); return -1; }
+    uint64_t* off = (uint64_t*)calloc((size_t)n + 1, sizeof(uint64_t));
+    uint32_t* tgt = (uint32_t*)malloc(sizeof(uint32_t) * (size_t)(m ? m : 1));
+    uint32_t* w = (uint32_t*)malloc(sizeof(uint32_t) * (size_t)(m ? m : 1));
+    if (!off || !tgt || !w) { free(off); free(tgt); free(w); free(keys); if (!xyz_out) free(P); return -1; }
+    const uint64_t mask = (1ull << scale) - 1u;
+    for (int64_t e = 0; e < m; ++e) off[(keys[e] >> scale) + 1]++;
+    for (uint32_t u = 0; u < n; ++u) off[u + 1] += off[u];
+#ifdef _OPENMP
+#pragma omp parallel for schedule(static)
+#endif
+    for (int64_t e = 0; e < m; ++e) {
+        const uint32_t u = (uint32_t)(keys[e] >> scale), v = (uint32_t)(keys[e] & mask);
+        const uint32_t a = u < v ? u : v, b = u < v ? v : u;
+        const double ex = P[3 * (size_t)a] - P[3 * (size_t)b], ey = P[3 * (size_t)a + 1] - P[3 * (size_t)b + 1],
+                     ez = P[3 * (size_t)a + 2] - P[3 * (size_t)b + 2];
+        tgt[e] = v;
+        w[e] = (uint32_t)floor(wscale * sqrt(ex * ex + ey * ey + ez * ez)) + 1u;
+    }
+    free(keys);
+    if (!xyz_out) free(P);
+    *m_out = (uint64_t)m; *off_out = off; *tgt_out = tgt; *w_out = w;
+    return 0;
 }

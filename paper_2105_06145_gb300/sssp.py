@@ -118,6 +118,8 @@ _lib.sssp_server_poll.argtypes = [_P, _u64, ctypes.POINTER(sssp_query_info)]
 _lib.sssp_server_poll.restype = _i32
 _lib.sssp_server_wait.argtypes = [_P, _u64, _u64, ctypes.POINTER(sssp_query_info)]
 _lib.sssp_server_wait.restype = _i32
+_lib.sssp_server_drain.argtypes = [_P, _P, _P, _u32]
+_lib.sssp_server_drain.restype = _i32
 _lib.sssp_server_stats.argtypes = [_P, ctypes.POINTER(_u64), ctypes.POINTER(_u32), ctypes.POINTER(_u64)]
 _lib.sssp_server_stats.restype = _i32
 _lib.sssp_server_destroy.argtypes = [_P]
@@ -130,7 +132,7 @@ EXPORTED = ["sssp_graph_create", "sssp_graph_destroy", "sssp_graph_info", "sssp_
             "sssp_rho_threshold", "sssp_status_string", "sssp_solve_noalloc", "sssp_solve_sources",
             "sssp_solve_multi", "sssp_batch_last_stats", "sssp_server_create", "sssp_server_slots",
             "sssp_server_submit", "sssp_server_poll", "sssp_server_wait", "sssp_server_stats",
-            "sssp_server_destroy"]
+            "sssp_server_destroy", "sssp_server_drain"]
 
 MAX_BATCH = 2048
 
@@ -308,6 +310,16 @@ def sssp_server_wait(s: int, ticket: int, timeout_ns: int = 0) -> dict:
     if rc != 1:
         raise SSSPError(rc, "sssp_server_wait")
     return info.as_dict()
+
+
+def sssp_server_drain(s: int, max_items: int = 1024) -> list:
+    """[(ticket, info dict)] of queries completed since the last drain."""
+    tk = (ctypes.c_uint64 * max_items)()
+    inf = (sssp_query_info * max_items)()
+    rc = _lib.sssp_server_drain(s, tk, inf, max_items)
+    if rc < 0:
+        raise SSSPError(rc, "sssp_server_drain")
+    return [(int(tk[i]), inf[i].as_dict()) for i in range(rc)]
 
 
 def sssp_server_stats(s: int) -> dict:

@@ -163,6 +163,24 @@ def build_workload(name: str, scale: int):
     return g, srcs, label
 
 
+def rank_sources(srcs: list, rank: int) -> list:
+    """Each rank cycles through the workload's sources starting at its own offset
+    (replicas solve different sources; no data-path collective)."""
+    nsrc = len(srcs)
+    return [srcs[(i + rank) % nsrc] for i in range(nsrc)]
+
+
+def aggregate(total_ms: float, K: int, m: int, world: int, pg=None, device="cuda") -> tuple[float, float]:
+    """Whole-job GTEPS over all ranks: every rank solved K sources of an m-edge
+    graph; the time is the maximum over ranks.  Returns (gteps, max_ms)."""
+    if pg is not None and world > 1:
+        import torch
+        t = torch.tensor([total_ms], dtype=torch.float64, device=device)
+        pg.all_reduce(t, op=pg.ReduceOp.MAX)
+        total_ms = float(t.item())
+    return world * K * m / (total_ms * 1e-3) / 1e9, total_ms
+
+
 def gg_sources(g, k=256, seed=9):
     from paper_2105_06145_gb300 import graphgen as gg
     return gg.pick_sources(g, k, seed)
@@ -401,7 +419,7 @@ def main():
     stream = stream_obj.cuda_stream
     dist_out = torch.empty(g.n, dtype=torch.int64, device="cuda")
     nsrc = len(srcs)
-    rank_srcs = [srcs[(i + rank) % nsrc] for i in range(nsrc)]
+    rank_srcs = rank_sources(srcs, rank)
 
     K, W = args.steps, args.warmup
     stats_buf = torch.zeros((K, sssp.STATS_BYTES // 8), dtype=torch.int64, device="cuda")
@@ -436,12 +454,7 @@ def main():
                       "edges": int(r[3]), "updates": int(r[4]),
                       "status": int(np.int32(r[5] & np.uint64(0xFFFFFFFF)))})
     assert all(s["status"] == 0 for s in stats), stats
-    if pg:
-        t = torch.tensor([total_ms], dtype=torch.float64, device="cuda")
-        pg.all_reduce(t, op=pg.ReduceOp.MAX)
-        total_ms = float(t.item())
-
-    gteps = world * K * g.m / (total_ms * 1e-3) / 1e9
+    gteps, total_ms = aggregate(total_ms, K, g.m, world, pg)
     peak, peak_kind = load_peaks()
     abytes = [algorithmic_bytes(s) for s in stats]
     ach_gbs = float(np.mean([b / (t * 1e-3) / 1e9 for b, t in zip(abytes, per_ms)]))

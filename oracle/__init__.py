@@ -10,6 +10,7 @@ What it computes (see oracle.c for the passages each function follows):
   dijkstra        -- d(s, .), the plain definition of the output (pinned)
   bellman_ford    -- brute force, pins dijkstra on tiny graphs
   stepping        -- Algorithm 1 run sequentially with the ExtDist of Table 2
+                     (rho, Delta*, Bellman-Ford, Delta with FinishCheck, Dijkstra)
   rho_extdist     -- the sampled rho-th smallest threshold (Sec. 6, App. B)
   delta_extdist   -- theta = i * Delta (Delta*-Stepping, Table 2)
   splitmix64      -- the counter-based generator the sampler uses
@@ -28,7 +29,7 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "oracle.c")
 _LIB = os.path.join(_HERE, "liboracle.so")
 
-RHO, DELTA_STAR, BELLMAN_FORD = 0, 1, 2
+RHO, DELTA_STAR, BELLMAN_FORD, DELTA, DIJKSTRA = 0, 1, 2, 3, 4
 INF = np.uint64(0xFFFFFFFFFFFFFFFF)
 
 
@@ -76,6 +77,10 @@ def _L():
         lib.oracle_rho_extdist.restype = u64
         lib.oracle_delta_extdist.argtypes = [ctypes.POINTER(u64), u64, u64]
         lib.oracle_delta_extdist.restype = u64
+        lib.oracle_delta_theta.argtypes = [ctypes.POINTER(u64), u64, u64]
+        lib.oracle_delta_theta.restype = u64
+        lib.oracle_delta_finish.argtypes = [ctypes.POINTER(u64), u64, u64]
+        lib.oracle_delta_finish.restype = None
         lib.oracle_stepping.argtypes = [u32, P, P, P, u32, i32, u64, u64, P, P,
                                         ctypes.POINTER(Stats)]
         lib.oracle_stepping.restype = i32
@@ -159,6 +164,20 @@ def delta_extdist(i: int, delta: int, qmin: int) -> tuple[int, int]:
     ii = ctypes.c_uint64(i)
     th = int(_L().oracle_delta_extdist(ctypes.byref(ii), delta, qmin))
     return th, int(ii.value)
+
+
+def delta_theta(i: int, delta: int, qmin: int) -> tuple[int, int]:
+    """Original Delta-Stepping: (theta, i after the empty-bucket jump)."""
+    ii = ctypes.c_uint64(i)
+    th = int(_L().oracle_delta_theta(ctypes.byref(ii), delta, qmin))
+    return th, int(ii.value)
+
+
+def delta_finish(i: int, theta: int, min_new: int) -> int:
+    """Original Delta-Stepping FinishCheck: the next i."""
+    ii = ctypes.c_uint64(i)
+    _L().oracle_delta_finish(ctypes.byref(ii), theta, min_new)
+    return int(ii.value)
 
 
 def stepping(g, s: int, algo: int, param: int, seed: int = 0,

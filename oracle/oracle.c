@@ -390,6 +390,31 @@ uint64_t oracle_delta_extdist(uint64_t* i, uint64_t delta, uint64_t qmin)
     return theta;
 }
 
+/*
+ * Original Delta-Stepping (Table 2: theta <- i*Delta; FinishCheck: if no new
+ * delta[v] < i*Delta, i <- i+1).  Readings: i starts at 1; "new delta[v]" are
+ * the values written by successful WriteMin calls of the step just finished;
+ * when i advances past an empty bucket it jumps to ceil(qmin/Delta) at the
+ * next ExtDist (as for Delta*).  oracle_delta_theta returns theta for the
+ * current i (applying the jump); oracle_delta_finish applies FinishCheck.
+ */
+uint64_t oracle_delta_theta(uint64_t* i, uint64_t delta, uint64_t qmin)
+{
+    uint64_t cur = *i;
+    uint64_t theta = (cur > UINT64_MAX / delta) ? ORC_INF : cur * delta;
+    if (qmin > theta) {
+        cur = qmin / delta + ((qmin % delta) != 0);
+        theta = (cur > UINT64_MAX / delta) ? ORC_INF : cur * delta;
+    }
+    *i = cur;
+    return theta;
+}
+
+void oracle_delta_finish(uint64_t* i, uint64_t theta, uint64_t min_new)
+{
+    if (!(min_new < theta)) *i += 1;
+}
+
 /* Statistics of one oracle_stepping run. */
 typedef struct {
     uint64_t steps;          /* iterations of the while loop of Algorithm 1 */
@@ -402,17 +427,20 @@ typedef struct {
     uint32_t pad;
 } oracle_stats;
 
-enum { ORC_RHO = 0, ORC_DELTA_STAR = 1, ORC_BELLMAN_FORD = 2 };
+enum { ORC_RHO = 0, ORC_DELTA_STAR = 1, ORC_BELLMAN_FORD = 2, ORC_DELTA = 3, ORC_DIJKSTRA = 4 };
 
 /*
  * Algorithm 1 (the stepping framework), executed sequentially on the
  * array-based LaB-PQ of Sec. 4.3 (a flag per vertex; Update sets the flag and
  * appends the id, Extract scans the queued ids and packs those with key <=
- * theta).  algo selects the ExtDist of Table 2:
+ * theta).  algo selects the ExtDist (and FinishCheck) of Table 2:
  *   ORC_RHO          theta from oracle_rho_extdist (param = rho >= 1)
  *   ORC_DELTA_STAR   theta from oracle_delta_extdist (param = Delta >= 1)
  *   ORC_BELLMAN_FORD theta = +infinity (param ignored)
- * None of the three has a FinishCheck.  The relaxation reads delta[u] when it
+ *   ORC_DELTA        theta = i*Delta with FinishCheck (oracle_delta_theta /
+ *                    oracle_delta_finish; param = Delta >= 1)
+ *   ORC_DIJKSTRA     theta = min over Q of delta (param ignored)
+ * Only ORC_DELTA has a FinishCheck.  The relaxation reads delta[u] when it
  * relaxes (Algorithm 1's WriteMin line), and WriteMin succeeds only on a
  * strictly smaller value (Sec. 2, the WriteMin definition).
  * ext_count (optional, n entries) receives how often each vertex was
@@ -424,8 +452,8 @@ int oracle_stepping(uint32_t n, const uint64_t* off, const uint32_t* tgt,
                     oracle_stats* st)
 {
     if (s >= n) return -1;
-    if (algo != ORC_BELLMAN_FORD && param == 0) return -1;
-    if (algo < 0 || algo > 2) return -1;
+    if (algo != ORC_BELLMAN_FORD && algo != ORC_DIJKSTRA && param == 0) return -1;
+    if (algo < 0 || algo > 4) return -1;
     uint8_t* inq = (uint8_t*)calloc(n, 1);
     uint32_t* Q = (uint32_t*)malloc(sizeof(uint32_t) * (size_t)n);
     uint32_t* F = (uint32_t*)malloc(sizeof(uint32_t) * (size_t)n);
@@ -447,13 +475,17 @@ int oracle_stepping(uint32_t n, const uint64_t* off, const uint32_t* tgt,
         z.steps++;
         /* ExtDist */
         uint64_t theta;
+        uint64_t qmin = ORC_INF;
+        for (uint32_t i = 0; i < qlen; ++i)
+            if (dist[Q[i]] < qmin) qmin = dist[Q[i]];
         if (algo == ORC_BELLMAN_FORD) {
             theta = ORC_INF;
         } else if (algo == ORC_DELTA_STAR) {
-            uint64_t qmin = ORC_INF;
-            for (uint32_t i = 0; i < qlen; ++i)
-                if (dist[Q[i]] < qmin) qmin = dist[Q[i]];
             theta = oracle_delta_extdist(&delta_i, param, qmin);
+        } else if (algo == ORC_DELTA) {
+            theta = oracle_delta_theta(&delta_i, param, qmin);
+        } else if (algo == ORC_DIJKSTRA) {
+            theta = qmin;
         } else {
             int dense = (uint64_t)qlen * 20u > (uint64_t)n;
             uint64_t rho_eff = param;
@@ -471,6 +503,7 @@ int oracle_stepping(uint32_t n, const uint64_t* off, const uint32_t* tgt,
         }
         qlen = keep;
         z.extracted += flen;
+        uint64_t min_new = ORC_INF;
         /* relax the out-edges of every extracted id */
         for (uint32_t i = 0; i < flen; ++i) {
             uint32_t u = F[i];
@@ -482,10 +515,12 @@ int oracle_stepping(uint32_t n, const uint64_t* off, const uint32_t* tgt,
                 if (cand < dist[v]) {           /* WriteMin succeeded */
                     dist[v] = cand;
                     z.updates++;
+                    if (cand < min_new) min_new = cand;
                     if (!inq[v]) { inq[v] = 1; Q[qlen++] = v; } /* Update(v) */
                 }
             }
         }
+        if (algo == ORC_DELTA) oracle_delta_finish(&delta_i, theta, min_new); /* FinishCheck */
     }
     for (uint32_t v = 0; v < n; ++v) if (cnt[v] > z.max_ext) z.max_ext = cnt[v];
     if (ext_count) memcpy(ext_count, cnt, sizeof(uint32_t) * (size_t)n);

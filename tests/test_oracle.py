@@ -240,7 +240,8 @@ def test_rho_extdist_dense_rule():
 def _algo_cases():
     return [(oracle.RHO, 1), (oracle.RHO, 2), (oracle.RHO, 31), (oracle.RHO, 1 << 10),
             (oracle.RHO, (1 << 32) - 1), (oracle.DELTA_STAR, 1), (oracle.DELTA_STAR, 1 << 13),
-            (oracle.DELTA_STAR, INF), (oracle.BELLMAN_FORD, 0)]
+            (oracle.DELTA_STAR, INF), (oracle.BELLMAN_FORD, 0), (oracle.DELTA, 1),
+            (oracle.DELTA, 1 << 13), (oracle.DELTA, INF), (oracle.DIJKSTRA, 0)]
 
 
 @pytest.mark.parametrize("algo,param", _algo_cases())
@@ -330,3 +331,44 @@ def test_bruteforce_hops_tiny():
                 assert h[v] == 0xFFFFFFFF
             else:
                 assert h[v] == best[v]
+
+
+def test_delta_finishcheck_closed_form():
+    # theta = i * Delta; the jump past empty buckets
+    assert oracle.delta_theta(1, 100, 0) == (100, 1)
+    assert oracle.delta_theta(1, 100, 1234) == (1300, 13)
+    # FinishCheck: stay while the step wrote a value below theta, else advance
+    assert oracle.delta_finish(3, 300, 299) == 3
+    assert oracle.delta_finish(3, 300, 300) == 4
+    assert oracle.delta_finish(3, 300, oracle.INF) == 4
+
+
+def test_dijkstra_in_framework_settles_one_distance_per_step():
+    """theta = min_Q delta (Table 2, Dijkstra row): with positive weights every
+    step extracts exactly the vertices at the smallest queued distance, each
+    vertex once, so the step count is the number of distinct finite distances."""
+    for g in (gg.grid(30, 30, wseed=4), gg.rmat(11, 8, gen_seed=3, wseed=4),
+              gg.random_graph(800, 5000, 1, 50, seed=2, drop_self_loops=True)):
+        s = int(np.flatnonzero(gg.largest_cc(g))[0])
+        d = oracle.dijkstra(g, s)
+        ds, st, ext = oracle.stepping(g, s, oracle.DIJKSTRA, 0, want_ext=True)
+        fin = d[d != oracle.INF]
+        assert np.array_equal(ds, d)
+        assert st["steps"] == np.unique(fin).size
+        assert np.all(ext[d != oracle.INF] == 1) and st["extracted"] == fin.size
+
+
+def test_delta_stepping_distances_and_extraction_bound():
+    """Original Delta-Stepping reaches d, and Lemma 5.1 (each vertex extracted
+    at most h(v) times) holds for it as for every stepping algorithm."""
+    g = gg.road(40, 0.75, seed=2)
+    s = int(np.flatnonzero(gg.largest_cc(g))[0])
+    d = oracle.dijkstra(g, s)
+    h, kn = oracle.hops(g, s)
+    hv = h.astype(np.int64)
+    hv[s] = 1
+    reach = d != oracle.INF
+    for delta in (1, 200, 5000, 1 << 20):
+        ds, st, ext = oracle.stepping(g, s, oracle.DELTA, delta, want_ext=True)
+        assert np.array_equal(ds, d)
+        assert np.all(ext[reach].astype(np.int64) <= hv[reach])

@@ -41,7 +41,10 @@ typedef struct sssp_graph sssp_graph; /* opaque; device copy of one CSR graph */
 typedef enum {
     SSSP_RHO = 0,           /* theta = sampled rho-th smallest queued distance (Sec. 6, App. B) */
     SSSP_DELTA_STAR = 1,    /* theta = i * Delta, i advancing every step (Table 2, Thm. 5.5)    */
-    SSSP_BELLMAN_FORD = 2   /* theta = +infinity (Table 2)                                       */
+    SSSP_BELLMAN_FORD = 2,  /* theta = +infinity (Table 2)                                       */
+    SSSP_DELTA = 3,         /* theta = i * Delta with FinishCheck: i advances only after a step  */
+                            /* that wrote no distance below i * Delta (Table 2, Delta-Stepping)  */
+    SSSP_DIJKSTRA = 4       /* theta = min over Q of delta (Table 2, Dijkstra)                   */
 } sssp_algo;
 
 typedef enum {
@@ -123,8 +126,8 @@ int sssp_graph_info(const sssp_graph* g, uint32_t* n, uint64_t* m);
 /*
  * Distances from `source` (Algorithm 1 with the ExtDist of Table 2).
  *   source    vertex id < n
- *   algo      SSSP_RHO (param = rho >= 1), SSSP_DELTA_STAR (param = Delta >= 1),
- *             SSSP_BELLMAN_FORD (param ignored)
+ *   algo      SSSP_RHO (param = rho >= 1), SSSP_DELTA_STAR and SSSP_DELTA
+ *             (param = Delta >= 1), SSSP_BELLMAN_FORD and SSSP_DIJKSTRA (param ignored)
  *   dist_out  caller-owned DEVICE uint64[n]; receives d(source, v), UINT64_MAX if
  *             unreachable.  It doubles as the tentative-distance array delta of
  *             Algorithm 1 during the solve.

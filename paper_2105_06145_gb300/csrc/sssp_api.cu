@@ -170,8 +170,8 @@ int sssp_solve_ex(const sssp_graph* gc, uint32_t source, sssp_algo algo, uint64_
     sssp_graph* g = const_cast<sssp_graph*>(gc);
     if (!g || !dist_out) return SSSP_ERR_INVALID_ARG;
     if (source >= g->n) return SSSP_ERR_INVALID_ARG;
-    if (algo != SSSP_RHO && algo != SSSP_DELTA_STAR && algo != SSSP_BELLMAN_FORD) return SSSP_ERR_INVALID_ARG;
-    if (algo != SSSP_BELLMAN_FORD && param == 0) return SSSP_ERR_INVALID_ARG;
+    if (!algo_valid(algo)) return SSSP_ERR_INVALID_ARG;
+    if (algo_needs_param(algo) && param == 0) return SSSP_ERR_INVALID_ARG;
     sssp_options o;
     memset(&o, 0, sizeof o);
     if (opt) o = *opt;

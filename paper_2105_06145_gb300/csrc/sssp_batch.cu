@@ -42,6 +42,7 @@ namespace sssp {
 struct InstCtrl {
     unsigned int qsize[3], fsmall[3], fchunk[3], fcount[3];
     unsigned long long qmin[3], fedges[3], updates[3];
+    unsigned long long umin[3];    // smallest distance written by a step's relaxation (slot of its next queue)
     unsigned long long theta;      // theta of the current step
     unsigned long long delta_i;    // Delta*-Stepping bucket index
     unsigned int dense_seen;       // rho-Stepping: dense steps so far
@@ -147,7 +148,7 @@ __device__ __forceinline__ void init_instance_ctrl(const InstDesc& d, InstCtrl* 
     ((k0 & 1) ? d.qa : d.qb)[0] = d.source;
     for (int r = 0; r < 3; ++r) {
         C->qsize[r] = 0; C->fsmall[r] = 0; C->fchunk[r] = 0; C->fcount[r] = 0;
-        C->qmin[r] = kInf; C->fedges[r] = 0; C->updates[r] = 0;
+        C->qmin[r] = kInf; C->fedges[r] = 0; C->updates[r] = 0; C->umin[r] = kInf;
     }
     C->qsize[k0 % 3] = 1;
     C->qmin[k0 % 3] = 0;
@@ -180,22 +181,29 @@ __device__ void phase_T(const BatchParams& p, uint64_t k, BatchSmem& S, uint64_t
             }
             if (q == 0 && C->last_step == 0) C->last_step = (unsigned)(k - C->admit_step);
             C->qsize[pv] = 0; C->fsmall[pv] = 0; C->fchunk[pv] = 0; C->fcount[pv] = 0;
-            C->fedges[pv] = 0; C->updates[pv] = 0; C->qmin[pv] = kInf;
+            C->fedges[pv] = 0; C->updates[pv] = 0; C->qmin[pv] = kInf; C->umin[pv] = kInf;
         }
         if (q == 0) { __syncthreads(); continue; }  // block-uniform
         uint64_t theta;
         if (p.algo == SSSP_BELLMAN_FORD) {
             theta = kInf;
-        } else if (p.algo == SSSP_DELTA_STAR) {
+        } else if (p.algo == SSSP_DELTA_STAR || p.algo == SSSP_DELTA) {
             const uint64_t qmin = ldcg64((const uint64_t*)&C->qmin[c]);
             uint64_t cur = ldcg64((const uint64_t*)&C->delta_i);
+            if (p.algo == SSSP_DELTA && k > ldcg64((const uint64_t*)&C->admit_step)) {
+                // FinishCheck: advance unless the previous step wrote below its threshold
+                const uint64_t umin = ldcg64((const uint64_t*)&C->umin[c]);
+                if (!(umin < ldcg64((const uint64_t*)&C->theta))) cur += 1;
+            }
             theta = sat_mul(cur, D.param);
             if (qmin > theta) {
                 cur = qmin / D.param + ((qmin % D.param) != 0);
                 theta = sat_mul(cur, D.param);
             }
             __syncthreads();
-            if (tid == 0) C->delta_i = cur + 1;
+            if (tid == 0) C->delta_i = p.algo == SSSP_DELTA_STAR ? cur + 1 : cur;
+        } else if (p.algo == SSSP_DIJKSTRA) {
+            theta = ldcg64((const uint64_t*)&C->qmin[c]);
         } else {
             const uint32_t* Qcur = (k & 1) ? D.qa : D.qb;
             const uint32_t dense_seen = ldcg32(&C->dense_seen);
@@ -338,7 +346,7 @@ __device__ bool phase_E(const BatchParams& p, uint64_t k, BatchSmem& S)
         if (tid == 0) {
             if (bf) atomicAdd(&C->fcount[c], (unsigned int)bf);
             if (be) atomicAdd(&C->fedges[c], (unsigned long long)be);
-            if (p.algo == SSSP_DELTA_STAR && bm != kInf) atomicMin(&C->qmin[nx], (unsigned long long)bm);
+            if (algo_tracks_qmin(p.algo) && bm != kInf) atomicMin(&C->qmin[nx], (unsigned long long)bm);
         }
         __syncthreads();
     }
@@ -392,8 +400,10 @@ __device__ void phase_R(const BatchParams& p, uint64_t k, BatchSmem& S, uint32_t
                     m_ = y_ < m_ ? y_ : m_;                                                      \
                 }                                                                                \
                 if (lane == 0 && u_) atomicAdd(&Cc->updates[c], (unsigned long long)u_);         \
-                if (lane == 0 && p.algo == SSSP_DELTA_STAR && m_ != kInf)                        \
+                if (lane == 0 && algo_tracks_qmin(p.algo) && m_ != kInf) {                       \
                     atomicMin(&Cc->qmin[nx], (unsigned long long)m_);                            \
+                    atomicMin(&Cc->umin[nx], (unsigned long long)m_);                            \
+                }                                                                                \
                 lupd = 0;                                                                        \
                 lmin = kInf;                                                                     \
             }                                                                                    \
@@ -812,7 +822,7 @@ int solve_batch(const sssp_graph* const* gs, const uint32_t* sources, uint32_t k
                 const uint64_t* params, uint64_t* const* outs, void* stream)
 {
     if (k == 0 || k > kMaxBatch || !gs || !sources || !outs) return SSSP_ERR_INVALID_ARG;
-    if (algo != SSSP_RHO && algo != SSSP_DELTA_STAR && algo != SSSP_BELLMAN_FORD) return SSSP_ERR_INVALID_ARG;
+    if (!algo_valid(algo)) return SSSP_ERR_INVALID_ARG;
     int dev = -1;
     size_t scratch = 0;
     uint32_t min_n = 0xFFFFFFFFu;
@@ -821,7 +831,7 @@ int solve_batch(const sssp_graph* const* gs, const uint32_t* sources, uint32_t k
         if (!g || !outs[i] || sources[i] >= g->n) return SSSP_ERR_INVALID_ARG;
         if (dev < 0) dev = g->device; else if (g->device != dev) return SSSP_ERR_INVALID_ARG;
         const uint64_t prm = params ? params[i] : sssp_default_param(g->n, g->m, algo, g->mean_w);
-        if (algo != SSSP_BELLMAN_FORD && prm == 0) return SSSP_ERR_INVALID_ARG;
+        if (algo_needs_param(algo) && prm == 0) return SSSP_ERR_INVALID_ARG;
         scratch += instance_scratch_bytes(g->n, g->fsmall_cap, g->item_cap);
         min_n = g->n < min_n ? g->n : min_n;
     }
@@ -1108,7 +1118,7 @@ int sssp_server_create(const sssp_graph* g, const sssp_server_config* cfg, sssp_
     sssp_server_config c;
     memset(&c, 0, sizeof c);
     if (cfg) c = *cfg;
-    if (c.algo != SSSP_RHO && c.algo != SSSP_DELTA_STAR && c.algo != SSSP_BELLMAN_FORD) return SSSP_ERR_INVALID_ARG;
+    if (!algo_valid(c.algo)) return SSSP_ERR_INVALID_ARG;
     if (c.idle_ns > 1000000000ull) return SSSP_ERR_INVALID_ARG;
     cudaError_t e = cudaSetDevice(g->device);
     if (e != cudaSuccess) return fail(e);
@@ -1118,7 +1128,7 @@ int sssp_server_create(const sssp_graph* g, const sssp_server_config* cfg, sssp_
     s->device = g->device;
     s->algo = c.algo;
     s->param = c.param ? c.param : sssp_default_param(g->n, g->m, c.algo, g->mean_w);
-    if (s->algo != SSSP_BELLMAN_FORD && s->param == 0) { delete s; return SSSP_ERR_INVALID_ARG; }
+    if (algo_needs_param(s->algo) && s->param == 0) { delete s; return SSSP_ERR_INVALID_ARG; }
     s->idle_ns = c.idle_ns ? c.idle_ns : 2000000ull;
     // admission by free HBM: per-slot working memory out of a fraction of what is free
     const size_t per_slot = instance_scratch_bytes(g->n, g->fsmall_cap, g->item_cap);

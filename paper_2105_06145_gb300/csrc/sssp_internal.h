@@ -57,6 +57,7 @@ struct Ctrl {
     unsigned long long qmin[3];
     unsigned long long fedges[3];
     unsigned long long updates[3];
+    unsigned long long umin[3];   // smallest distance written by the relaxation of the step (slot of Q_{k+1})
     // totals, written by block 0 when the solve ends
     unsigned long long steps, queued, extracted, edges, updates_total;
 };
@@ -151,6 +152,17 @@ struct sssp_graph {
 inline uint64_t sssp_default_param(uint32_t n, uint64_t /*m*/, sssp_algo algo, double mean_w = 4.0)
 {
     if (algo == SSSP_RHO) return n / 16 > 64 ? n / 16 : 64;
-    if (algo == SSSP_DELTA_STAR) { const double d = mean_w / 4.0; return d > 1.0 ? (uint64_t)d : 1; }
+    if (algo == SSSP_DELTA_STAR || algo == SSSP_DELTA) { const double d = mean_w / 4.0; return d > 1.0 ? (uint64_t)d : 1; }
     return 0;
+}
+
+// The ExtDist rules that need the smallest queued distance each step.
+inline __host__ __device__ bool algo_tracks_qmin(int algo)
+{
+    return algo == SSSP_DELTA_STAR || algo == SSSP_DELTA || algo == SSSP_DIJKSTRA;
+}
+inline __host__ __device__ bool algo_valid(int algo) { return algo >= SSSP_RHO && algo <= SSSP_DIJKSTRA; }
+inline __host__ __device__ bool algo_needs_param(int algo)
+{
+    return algo == SSSP_RHO || algo == SSSP_DELTA_STAR || algo == SSSP_DELTA;
 }

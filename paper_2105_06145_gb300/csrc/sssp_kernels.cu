@@ -87,11 +87,15 @@ __global__ void __launch_bounds__(kBlock, 1) solve_kernel(SolveParams p)
         ctrl->qmin[0] = kInf;
         ctrl->qmin[1] = 0;
         ctrl->qmin[2] = kInf;
+        ctrl->umin[0] = kInf;
+        ctrl->umin[1] = kInf;
+        ctrl->umin[2] = kInf;
     }
     if (p.exit_block != 0 && blockIdx.x == p.exit_block - 1) return;  // fault-injection test
     if (!grid_sync(&ctrl->bar, &ctrl->status, &s_bar_target, p.timeout_ns)) return;
 
-    uint64_t delta_i = 1;          // Delta*-Stepping bucket index (Table 2)
+    uint64_t delta_i = 1;          // Delta*- / Delta-Stepping bucket index (Table 2)
+    uint64_t prev_theta = 0;       // theta of the previous step (Delta-Stepping FinishCheck)
     uint32_t dense_seen = 0;       // rho-Stepping: dense steps so far (Sec. 6)
 
     uint64_t k = 1;
@@ -119,7 +123,7 @@ __global__ void __launch_bounds__(kBlock, 1) solve_kernel(SolveParams p)
             }
             s_prev_t = global_timer_ns() - s_t_start;
             ctrl->qsize[pv] = 0; ctrl->fsmall[pv] = 0; ctrl->fchunk[pv] = 0; ctrl->fcount[pv] = 0;
-            ctrl->fedges[pv] = 0; ctrl->updates[pv] = 0; ctrl->qmin[pv] = kInf;
+            ctrl->fedges[pv] = 0; ctrl->updates[pv] = 0; ctrl->qmin[pv] = kInf; ctrl->umin[pv] = kInf;
         }
         if (q == 0) break;
         if (p.max_steps != 0 && k > p.max_steps) {
@@ -135,15 +139,24 @@ __global__ void __launch_bounds__(kBlock, 1) solve_kernel(SolveParams p)
         uint64_t theta;
         if (p.algo == SSSP_BELLMAN_FORD) {
             theta = kInf;
-        } else if (p.algo == SSSP_DELTA_STAR) {
+        } else if (p.algo == SSSP_DELTA_STAR || p.algo == SSSP_DELTA) {
             const uint64_t qmin = ldcg64((const uint64_t*)&ctrl->qmin[c]);
+            if (p.algo == SSSP_DELTA && k > 1) {
+                // FinishCheck: advance the bucket unless the previous step
+                // wrote a distance below its threshold
+                const uint64_t umin = ldcg64((const uint64_t*)&ctrl->umin[c]);
+                if (!(umin < prev_theta)) delta_i += 1;
+            }
             uint64_t cur = delta_i;
             theta = sat_mul(cur, p.param);
             if (qmin > theta) {  // skip empty buckets
                 cur = qmin / p.param + ((qmin % p.param) != 0);
                 theta = sat_mul(cur, p.param);
             }
-            delta_i = cur + 1;
+            delta_i = p.algo == SSSP_DELTA_STAR ? cur + 1 : cur;
+            prev_theta = theta;
+        } else if (p.algo == SSSP_DIJKSTRA) {
+            theta = ldcg64((const uint64_t*)&ctrl->qmin[c]);  // min over Q (Table 2)
         } else {
             theta = rho_extdist_block(Qcur, q, dist, n, p.param, p.seed, k, dense_seen, s_keys,
                                       p.sample_cap, &s_err);
@@ -265,7 +278,7 @@ __global__ void __launch_bounds__(kBlock, 1) solve_kernel(SolveParams p)
             if (tid == 0) {
                 if (bf) atomicAdd(&ctrl->fcount[c], (unsigned int)bf);
                 if (be) atomicAdd(&ctrl->fedges[c], (unsigned long long)be);
-                if (p.algo == SSSP_DELTA_STAR && bm != kInf) atomicMin(&ctrl->qmin[nx], (unsigned long long)bm);
+                if (algo_tracks_qmin(p.algo) && bm != kInf) atomicMin(&ctrl->qmin[nx], (unsigned long long)bm);
             }
         }
         if (p.trace && tid == 0 && k - 1 < p.trace_cap)
@@ -370,7 +383,10 @@ __global__ void __launch_bounds__(kBlock, 1) solve_kernel(SolveParams p)
             block_reduce_2add_min(bu, unused, bm, s_tmp);
             if (tid == 0) {
                 if (bu) atomicAdd(&ctrl->updates[c], (unsigned long long)bu);
-                if (p.algo == SSSP_DELTA_STAR && bm != kInf) atomicMin(&ctrl->qmin[nx], (unsigned long long)bm);
+                if (algo_tracks_qmin(p.algo) && bm != kInf) {
+                    atomicMin(&ctrl->qmin[nx], (unsigned long long)bm);
+                    atomicMin(&ctrl->umin[nx], (unsigned long long)bm);
+                }
                 if (p.trace && k - 1 < p.trace_cap) {
                     const unsigned long long now = global_timer_ns() - s_t_start;
                     atomicMin((unsigned long long*)&p.trace[k - 1].t_relax_end_min, now);

@@ -84,8 +84,8 @@ extern "C" int sssp_solve_noalloc(uint32_t n, uint64_t m, const uint64_t* offset
     if (!offsets || !dist_out || (m > 0 && !edges)) return SSSP_ERR_INVALID_ARG;
     if ((reinterpret_cast<uintptr_t>(edges) & 15u) != 0) return SSSP_ERR_INVALID_ARG;
     if (source >= n) return SSSP_ERR_INVALID_ARG;
-    if (algo != SSSP_RHO && algo != SSSP_DELTA_STAR && algo != SSSP_BELLMAN_FORD) return SSSP_ERR_INVALID_ARG;
-    if (algo != SSSP_BELLMAN_FORD && param == 0) return SSSP_ERR_INVALID_ARG;
+    if (!algo_valid(algo)) return SSSP_ERR_INVALID_ARG;
+    if (algo_needs_param(algo) && param == 0) return SSSP_ERR_INVALID_ARG;
 
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess) return SSSP_ERR_CUDA;

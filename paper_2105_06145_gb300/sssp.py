@@ -18,8 +18,9 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 # SSSP_LIB may name another build of the same library (e.g. a variant for A/B timing)
 LIB_PATH = os.environ.get("SSSP_LIB") or os.path.join(_HERE, "libsssp.so")
 
-SSSP_RHO, SSSP_DELTA_STAR, SSSP_BELLMAN_FORD = 0, 1, 2
-ALGOS = {"rho": SSSP_RHO, "delta_star": SSSP_DELTA_STAR, "bellman_ford": SSSP_BELLMAN_FORD}
+SSSP_RHO, SSSP_DELTA_STAR, SSSP_BELLMAN_FORD, SSSP_DELTA, SSSP_DIJKSTRA = 0, 1, 2, 3, 4
+ALGOS = {"rho": SSSP_RHO, "delta_star": SSSP_DELTA_STAR, "bellman_ford": SSSP_BELLMAN_FORD,
+         "delta": SSSP_DELTA, "dijkstra": SSSP_DIJKSTRA}
 SSSP_OK = 0
 SSSP_ERR_INVALID_ARG, SSSP_ERR_OUT_OF_MEMORY, SSSP_ERR_CUDA = -1, -2, -3
 SSSP_ERR_TIMEOUT, SSSP_ERR_INTERNAL = -4, -5

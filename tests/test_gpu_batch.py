@@ -32,7 +32,8 @@ def _single(lib, G, n, s, algo, param):
     return d.cpu().numpy().view(np.uint64).copy()
 
 
-@pytest.mark.parametrize("algo,param", [(0, 256), (0, 1 << 14), (1, 1 << 15), (2, 0), (0, None)])
+@pytest.mark.parametrize("algo,param", [(0, 256), (0, 1 << 14), (1, 1 << 15), (2, 0), (0, None), (3, 1 << 15),
+                                        (4, None)])
 def test_sources_on_one_graph(lib, algo, param):
     g = gg.rmat(15, 16, gen_seed=31, wseed=32)
     srcs = gg.pick_sources(g, 24, 5) + [int(np.flatnonzero(gg.largest_cc(g) == 0)[0])]  # + an isolated vertex
@@ -50,7 +51,7 @@ def test_sources_on_one_graph(lib, algo, param):
     # alone and in the mix: the batched result equals the single solve
     for i in (0, 7, k - 1):
         p_i = param if param is not None else max(64, g.n // 16) if algo == 0 else param
-        if algo == 1 and param is None:
+        if algo in (1, 3) and param is None:
             continue
         assert np.array_equal(got[i], _single(lib, G, g.n, srcs[i], algo, p_i if p_i else 0))
     G.close()
@@ -65,7 +66,8 @@ def test_many_graphs_of_uneven_size(lib):
     Gs = [lib.Graph(g) for g, _ in W]
     outs = [torch.full((g.n,), 1, dtype=torch.int64, device="cuda") for g, _ in W]
     srcs = [s for _, s in W]
-    for algo, params in ((0, [max(1, g.n // 8) for g, _ in W]), (1, [1 << 16] * len(W)), (2, None), (0, None)):
+    for algo, params in ((0, [max(1, g.n // 8) for g, _ in W]), (1, [1 << 16] * len(W)), (2, None), (0, None),
+                         (3, [1 << 15] * len(W)), (4, None)):
         lib.sssp_solve_multi([G.handle for G in Gs], srcs, algo, params, [o.data_ptr() for o in outs], _stream())
         st, stats = lib.sssp_batch_last_stats(len(W), _stream())
         assert st == 0

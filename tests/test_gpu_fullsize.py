@@ -39,7 +39,8 @@ def _run(lib, g, sources, cases):
 def test_rmat22_all_rules(lib):
     g, s = gg.workload_rmat(22)
     extra = gg.pick_sources(g, 3, 77)
-    cases = [(0, 1 << 18), (0, 1 << 20), (0, 1 << 22), (1, 1 << 13), (1, 1 << 15), (1, 1 << 17), (2, 0)]
+    cases = [(0, 1 << 18), (0, 1 << 20), (0, 1 << 22), (1, 1 << 13), (1, 1 << 15), (1, 1 << 17), (2, 0),
+             (3, 1 << 15), (4, 0)]
     _run(lib, g, [s], cases)
     _run(lib, g, extra, [(0, 1 << 20)])
 
@@ -47,4 +48,4 @@ def test_rmat22_all_rules(lib):
 def test_road4096(lib):
     g, s = gg.workload_road(4096)
     assert g.n == 4096 * 4096
-    _run(lib, g, [s], [(0, 1 << 20), (0, 1 << 14), (1, 1 << 13), (1, 1 << 15)])
+    _run(lib, g, [s], [(0, 1 << 20), (0, 1 << 14), (1, 1 << 13), (1, 1 << 15), (3, 1 << 13)])

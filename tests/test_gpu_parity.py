@@ -41,7 +41,8 @@ def solve(lib, g, s, algo, param, opts=None, G=None):
 
 
 ALGO_PARAMS = [(0, 1), (0, 2), (0, 31), (0, 1 << 10), (0, 65536), (0, (1 << 32) - 1),
-               (1, 1), (1, 1 << 13), (1, 1 << 17), (1, INF), (2, 0)]
+               (1, 1), (1, 1 << 13), (1, 1 << 17), (1, INF), (2, 0),
+               (3, 1), (3, 1 << 13), (3, INF), (4, 0)]
 
 
 def test_grid256_all_rules(lib):
@@ -55,7 +56,7 @@ def test_grid256_all_rules(lib):
     G.close()
 
 
-@pytest.mark.parametrize("algo,param", [(0, 1 << 12), (1, 1 << 15), (2, 0), (0, 3)])
+@pytest.mark.parametrize("algo,param", [(0, 1 << 12), (1, 1 << 15), (2, 0), (0, 3), (3, 1 << 15), (4, 0)])
 def test_rmat16_and_road(lib, algo, param):
     for g in (gg.rmat(16, 16, gen_seed=11, wseed=12), gg.road(300, 0.75, seed=3)):
         s = gg.pick_sources(g, 1, 5)[0]
@@ -82,7 +83,7 @@ def test_edge_case_graphs(lib):
     ]
     for g, s in cases:
         want = oracle.dijkstra(g, s)
-        for algo, param in ((0, 1), (0, 64), (0, INF), (1, 1), (1, 1000), (2, 0)):
+        for algo, param in ((0, 1), (0, 64), (0, INF), (1, 1), (1, 1000), (2, 0), (3, 1000), (4, 0)):
             got, st = solve(lib, g, s, algo, param)
             assert st["status"] == 0, (g.name, algo, param)
             assert np.array_equal(got, want), (g.name, s, algo, param)
@@ -152,7 +153,7 @@ def test_step_bounds_and_counters(lib):
         h, kn = oracle.hops(g, s)
         L = int(g.w.max())
         G = lib.Graph(g)
-        for algo, param in ((0, 64), (0, 1 << 12), (1, 1 << 12), (1, 1 << 16), (2, 0)):
+        for algo, param in ((0, 64), (0, 1 << 12), (1, 1 << 12), (1, 1 << 16), (2, 0), (3, 1 << 12), (4, 0)):
             ext = torch.zeros(g.n, dtype=torch.int32, device="cuda")
             cap = 100000
             trace = torch.zeros(cap * lib.TRACE_RECORD_BYTES // 8, dtype=torch.int64, device="cuda")
@@ -171,6 +172,11 @@ def test_step_bounds_and_counters(lib):
                 assert st["steps"] <= kn + 1
             elif algo == 1:
                 assert st["steps"] <= math.ceil(kn * L / param) + kn + 1
+            elif algo == 4:
+                # theta = min_Q delta with positive weights: one distance settled per
+                # step, every reachable vertex extracted exactly once
+                assert st["steps"] == np.unique(want[reach]).size
+                assert np.all(e[reach] == 1)
             rec = np.frombuffer(trace.cpu().numpy().tobytes(),
                                 dtype=np.dtype(lib.TRACE_DTYPE))[: st["steps"]]
             assert np.all(np.diff(rec["t_ns"].astype(np.int64)) >= 0)
@@ -233,7 +239,7 @@ def test_invalid_arguments(lib):
     g = gg.grid(8, 8)
     G = lib.Graph(g)
     dist = torch.empty(g.n, dtype=torch.int64, device="cuda")
-    for src, algo, param in ((64, 0, 1), (0, 0, 0), (0, 1, 0), (0, 7, 1)):
+    for src, algo, param in ((64, 0, 1), (0, 0, 0), (0, 1, 0), (0, 7, 1), (0, 3, 0)):
         rc = lib.sssp_solve_ex(G.handle, src, algo, param, dist.data_ptr(), None, 0, check=False)
         assert rc == lib.SSSP_ERR_INVALID_ARG
     G.close()

@@ -97,8 +97,23 @@ typedef struct {
                                 here when it ends (grid is left 0), so a sequence of
                                 solves can be measured without host synchronisation       */
     uint64_t solve_timeout_ns; /* bound on the whole solve; 0 = 60 s (SSSP_ERR_TIMEOUT)  */
-    uint32_t reserved[2];
+    uint32_t flags;          /* SSSP_SOLVE_* bits                                         */
+    uint32_t reserved;
 } sssp_options;
+
+/* sssp_options.flags */
+#define SSSP_SOLVE_BIDIRECTIONAL 1u /* bidirectional relaxation (Sec. 6, "Bidirectional
+                                       relaxation for undirected graphs"): before an extracted
+                                       vertex u pushes to its neighbours it first takes
+                                       min(delta[u], delta[v] + w) over them (WriteMin on u with
+                                       the usual Update).  Needs a graph created with
+                                       SSSP_GRAPH_SYMMETRIC (INVALID_ARG otherwise).  Applied to
+                                       vertices of degree > 32.                                 */
+
+/* sssp_graph_create_ex flags */
+#define SSSP_GRAPH_SYMMETRIC 1u     /* every edge (u,v,w) has its reverse (v,u,w)         */
+#define SSSP_GRAPH_VERIFY 2u        /* check SSSP_GRAPH_SYMMETRIC on the host, O(m log d);
+                                       INVALID_ARG when it does not hold                  */
 
 /*
  * Copy a CSR graph (host arrays) to the device.
@@ -116,6 +131,10 @@ typedef struct {
  */
 int sssp_graph_create(uint32_t n, uint64_t m, const uint64_t* offsets, const uint32_t* targets,
                       const uint32_t* weights, sssp_graph** out);
+
+/* sssp_graph_create with SSSP_GRAPH_* flags (0 = sssp_graph_create). */
+int sssp_graph_create_ex(uint32_t n, uint64_t m, const uint64_t* offsets, const uint32_t* targets,
+                         const uint32_t* weights, uint32_t flags, sssp_graph** out);
 
 /* Release a graph and its scratch.  Synchronises the device first. */
 int sssp_graph_destroy(sssp_graph* g);
@@ -152,6 +171,10 @@ int sssp_solve_ex(const sssp_graph* g, uint32_t source, sssp_algo algo, uint64_t
  */
 int sssp_solve_host(const sssp_graph* g, uint32_t source, sssp_algo algo, uint64_t param,
                     uint64_t* host_dist_out, void* stream);
+
+/* sssp_solve_host with options (opt may be NULL = defaults). */
+int sssp_solve_host_ex(const sssp_graph* g, uint32_t source, sssp_algo algo, uint64_t param,
+                       uint64_t* host_dist_out, const sssp_options* opt, void* stream);
 
 /* Waits for `stream`, then returns the device status of the last solve on g. */
 int sssp_last_status(const sssp_graph* g, void* stream);

@@ -7,7 +7,9 @@
 #include <cstdint>
 #include <cstdlib>
 #include <cstring>
+#include <algorithm>
 #include <new>
+#include <vector>
 
 #include <cuda_runtime.h>
 
@@ -83,6 +85,36 @@ const char* sssp_status_string(int status)
 int sssp_graph_create(uint32_t n, uint64_t m, const uint64_t* offsets, const uint32_t* targets,
                       const uint32_t* weights, sssp_graph** out)
 {
+    return sssp_graph_create_ex(n, m, offsets, targets, weights, 0, out);
+}
+
+namespace {
+
+// Every edge (u,v,w) has a reverse (v,u,w): each adjacency is sorted by
+// (target, weight) in a copy and searched.
+bool verify_symmetric(uint32_t n, const uint64_t* off, const uint32_t* tgt, const uint32_t* w)
+{
+    const uint64_t m = off[n];
+    std::vector<uint64_t> key(m);
+    for (uint32_t u = 0; u < n; ++u) {
+        for (uint64_t e = off[u]; e < off[u + 1]; ++e) key[e] = ((uint64_t)tgt[e] << 32) | w[e];
+        std::sort(key.begin() + (ptrdiff_t)off[u], key.begin() + (ptrdiff_t)off[u + 1]);
+    }
+    for (uint32_t u = 0; u < n; ++u)
+        for (uint64_t e = off[u]; e < off[u + 1]; ++e) {
+            const uint32_t v = tgt[e];
+            const uint64_t want = ((uint64_t)u << 32) | w[e];
+            if (!std::binary_search(key.begin() + (ptrdiff_t)off[v], key.begin() + (ptrdiff_t)off[v + 1], want))
+                return false;
+        }
+    return true;
+}
+
+}  // namespace
+
+int sssp_graph_create_ex(uint32_t n, uint64_t m, const uint64_t* offsets, const uint32_t* targets,
+                         const uint32_t* weights, uint32_t flags, sssp_graph** out)
+{
     if (!out) return SSSP_ERR_INVALID_ARG;
     *out = nullptr;
     if (n == 0 || !offsets || (m > 0 && (!targets || !weights))) return SSSP_ERR_INVALID_ARG;
@@ -92,6 +124,10 @@ int sssp_graph_create(uint32_t n, uint64_t m, const uint64_t* offsets, const uin
         if (offsets[u + 1] < offsets[u]) return SSSP_ERR_INVALID_ARG;
     for (uint64_t e = 0; e < m; ++e)
         if (targets[e] >= n) return SSSP_ERR_INVALID_ARG;
+    if (flags & ~(SSSP_GRAPH_SYMMETRIC | SSSP_GRAPH_VERIFY)) return SSSP_ERR_INVALID_ARG;
+    if ((flags & SSSP_GRAPH_VERIFY) && (flags & SSSP_GRAPH_SYMMETRIC) &&
+        !verify_symmetric(n, offsets, targets, weights))
+        return SSSP_ERR_INVALID_ARG;
 
     // exact capacities of the relaxation records one Extract can produce:
     // each vertex is queued at most once, so at most every vertex at once
@@ -109,6 +145,7 @@ int sssp_graph_create(uint32_t n, uint64_t m, const uint64_t* offsets, const uin
     if (!g) return SSSP_ERR_OUT_OF_MEMORY;
     g->n = n;
     g->m = m;
+    g->flags = flags & SSSP_GRAPH_SYMMETRIC;
     cudaError_t e = cudaGetDevice(&g->device);
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&g->num_sms, cudaDevAttrMultiProcessorCount, g->device);
     if (e != cudaSuccess) { free_graph(g); return cuda_fail(e); }
@@ -204,6 +241,9 @@ int sssp_solve_ex(const sssp_graph* gc, uint32_t source, sssp_algo algo, uint64_
     p.trace_cap = o.trace_cap;
     p.exit_block = o.test_exit_block;
     p.stats_out = o.stats_out;
+    if (o.flags & ~SSSP_SOLVE_BIDIRECTIONAL) return SSSP_ERR_INVALID_ARG;
+    if ((o.flags & SSSP_SOLVE_BIDIRECTIONAL) && !(g->flags & SSSP_GRAPH_SYMMETRIC)) return SSSP_ERR_INVALID_ARG;
+    p.bidir = (o.flags & SSSP_SOLVE_BIDIRECTIONAL) ? 1 : 0;
     p.sample_cap = (algo == SSSP_RHO) ? rho_sample_bound(g->n, param) : 0;
 
     const size_t dyn_smem = kSolveDynSmem;
@@ -264,8 +304,14 @@ int sssp_last_status(const sssp_graph* g, void* stream)
     return s.status;
 }
 
-int sssp_solve_host(const sssp_graph* gc, uint32_t source, sssp_algo algo, uint64_t param,
+int sssp_solve_host(const sssp_graph* g, uint32_t source, sssp_algo algo, uint64_t param,
                     uint64_t* host_dist_out, void* stream)
+{
+    return sssp_solve_host_ex(g, source, algo, param, host_dist_out, nullptr, stream);
+}
+
+int sssp_solve_host_ex(const sssp_graph* gc, uint32_t source, sssp_algo algo, uint64_t param,
+                       uint64_t* host_dist_out, const sssp_options* opt, void* stream)
 {
     sssp_graph* g = const_cast<sssp_graph*>(gc);
     if (!g || !host_dist_out) return SSSP_ERR_INVALID_ARG;
@@ -276,7 +322,7 @@ int sssp_solve_host(const sssp_graph* gc, uint32_t source, sssp_algo algo, uint6
             if (e != cudaSuccess) { g->d_dist_internal = nullptr; return cuda_fail(e); }
         }
     }
-    int rc = sssp_solve_ex(g, source, algo, param, g->d_dist_internal, nullptr, stream);
+    int rc = sssp_solve_ex(g, source, algo, param, g->d_dist_internal, opt, stream);
     if (rc != SSSP_OK) return rc;
     cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
     cudaError_t e = cudaMemcpyAsync(host_dist_out, g->d_dist_internal, sizeof(uint64_t) * (size_t)g->n,

@@ -473,8 +473,8 @@ __device__ void phase_R(const BatchParams& p, uint64_t k, BatchSmem& S, uint32_t
                 uint64_t* const idist = Dp->dist;
                 const uint4 rc = __ldcg(&Dp->items[it - S.pre1[i]]);
                 const uint64_t du = ldcg64(&idist[rc.z]);
-                relax_chunk(rc, du, reinterpret_cast<const uint4*>(Dp->edges), idist, Dp->inq, stage, stc, lane,
-                            lmin, lupd);
+                relax_chunk<false>(rc, du, reinterpret_cast<const uint4*>(Dp->edges), idist, Dp->inq, stage, stc,
+                                   lane, lmin, lupd);
                 if (stc > (uint32_t)(kStage - 256)) {
                     uint32_t* Qn = (k & 1) ? Dp->qb : Dp->qa;
                     stage_flush(stage, stc, lane, &p.ictrl[i].qsize[nx], status, Qn, Dp->n);

@@ -238,24 +238,21 @@ __device__ __forceinline__ void stage_push(bool push, uint32_t v, uint32_t* stag
     stc += __popc(b);
 }
 
-// Warp-uniform: one batch of (up to) 4 relaxations per lane.
-//   1. load delta[v] for the pre-check (4 gathers in flight),
-//   2. for every candidate with cand < delta[v]: WriteMin(delta[v], cand)
-//      (Sec. 2) as a fire-and-forget atomic minimum, then Update(v): the
-//      test-and-set of v's queue bit (all test-and-sets of the batch in flight),
-//   3. stage the ids whose bit was clear for the next queue list.
+// Warp-uniform: the second half of a batch of (up to) 4 relaxations per lane,
+// given the pre-check values dv[t] = delta[v[t]]:
+//   for every candidate with cand < delta[v]: WriteMin(delta[v], cand)
+//   (Sec. 2) as a fire-and-forget atomic minimum, then Update(v): the
+//   test-and-set of v's queue bit (all test-and-sets of the batch in flight);
+//   the ids whose bit was clear are staged for the next queue list.
 // A candidate that passes the pre-check but loses the race to a smaller one
 // still marks v: the winner lowered delta[v] in this same phase and queues v
 // too, so the queued set is exactly the set whose distance dropped, and the
 // bit keeps each vertex at most once in the queue.
-__device__ __forceinline__ void relax_batch4(uint64_t* dist, uint32_t* inq, const uint32_t (&v)[4],
-                                             const uint64_t (&cand)[4], const bool (&ok)[4],
-                                             uint32_t* stage, uint32_t& stc, uint32_t lane,
-                                             uint64_t& lmin, uint32_t& lupd)
+__device__ __forceinline__ void relax_apply4(uint64_t* dist, uint32_t* inq, const uint32_t (&v)[4],
+                                             const uint64_t (&cand)[4], const uint64_t (&dv)[4],
+                                             const bool (&ok)[4], uint32_t* stage, uint32_t& stc,
+                                             uint32_t lane, uint64_t& lmin, uint32_t& lupd)
 {
-    uint64_t dv[4];
-#pragma unroll
-    for (int t = 0; t < 4; ++t) dv[t] = ok[t] ? ld_precheck(&dist[v[t]]) : 0ull;
     uint32_t prev[4];
     uint32_t pass = 0;
 #pragma unroll
@@ -276,6 +273,19 @@ __device__ __forceinline__ void relax_batch4(uint64_t* dist, uint32_t* inq, cons
     }
 }
 
+// Warp-uniform: one batch of (up to) 4 relaxations per lane (4 gathers of
+// delta[v] in flight, then relax_apply4).
+__device__ __forceinline__ void relax_batch4(uint64_t* dist, uint32_t* inq, const uint32_t (&v)[4],
+                                             const uint64_t (&cand)[4], const bool (&ok)[4],
+                                             uint32_t* stage, uint32_t& stc, uint32_t lane,
+                                             uint64_t& lmin, uint32_t& lupd)
+{
+    uint64_t dv[4];
+#pragma unroll
+    for (int t = 0; t < 4; ++t) dv[t] = ok[t] ? ld_precheck(&dist[v[t]]) : 0ull;
+    relax_apply4(dist, inq, v, cand, dv, ok, stage, stc, lane, lmin, lupd);
+}
+
 // Warp-uniform: move the staged ids to the next queue list (one atomic per flush).
 __device__ __forceinline__ void stage_flush(uint32_t* stage, uint32_t& stc, uint32_t lane, unsigned int* qsize,
                                             int* status, uint32_t* Qnext, uint32_t cap)
@@ -294,9 +304,14 @@ __device__ __forceinline__ void stage_flush(uint32_t* stage, uint32_t& stc, uint
     stc = 0;
 }
 
-// Warp-uniform: relax the edges of one chunk record (<= kChunk edges of one
-// vertex, within one kChunk-aligned block of the edge array), read as 16-byte
-// pairs of packed edges.
+// Warp-uniform: relax the edges of one chunk record (<= kChunk edges of vertex
+// u, within one kChunk-aligned block of the edge array), read as 16-byte pairs
+// of packed edges.  With kPull (bidirectional relaxation for undirected
+// graphs, Sec. 6): the delta[v] values gathered for the pre-check first relax
+// u itself -- WriteMin(delta[u], min over the chunk of delta[v] + w), with the
+// usual Update(u) -- and the improved delta[u] is then pushed to the chunk's
+// neighbours.
+template <bool kPull>
 __device__ __forceinline__ void relax_chunk(uint4 rec, uint64_t du, const uint4* __restrict__ pairs,
                                             uint64_t* dist, uint32_t* inq, uint32_t* stage, uint32_t& stc,
                                             uint32_t lane, uint64_t& lmin, uint32_t& lupd)
@@ -306,18 +321,47 @@ __device__ __forceinline__ void relax_chunk(uint4 rec, uint64_t du, const uint4*
 #pragma unroll 1
     for (uint32_t h = 0; h < kChunkPairs; h += 64) {
         if (p0 + h >= p1) break;  // warp-uniform
-        uint32_t vv[4];
-        uint64_t cand[4];
+        uint32_t vv[4], ww[4];
         bool ok[4];
 #pragma unroll
         for (int t = 0; t < 2; ++t) {
             const uint64_t P = p0 + h + 32u * t + lane;
             const bool okp = P < p1;
             const uint4 pr = okp ? __ldcs(&pairs[P]) : make_uint4(0, 0, 0, 0);
-            vv[2 * t] = pr.x; cand[2 * t] = du + pr.y; ok[2 * t] = okp && 2 * P >= cs;       // 2P < ce when P < p1
-            vv[2 * t + 1] = pr.z; cand[2 * t + 1] = du + pr.w; ok[2 * t + 1] = okp && 2 * P + 1 < ce;  // 2P+1 >= cs when P >= p0
+            vv[2 * t] = pr.x; ww[2 * t] = pr.y; ok[2 * t] = okp && 2 * P >= cs;       // 2P < ce when P < p1
+            vv[2 * t + 1] = pr.z; ww[2 * t + 1] = pr.w; ok[2 * t + 1] = okp && 2 * P + 1 < ce;  // 2P+1 >= cs when P >= p0
         }
-        relax_batch4(dist, inq, vv, cand, ok, stage, stc, lane, lmin, lupd);
+        uint64_t dv[4];
+#pragma unroll
+        for (int t = 0; t < 4; ++t) dv[t] = ok[t] ? ld_precheck(&dist[vv[t]]) : 0ull;
+        if (kPull) {
+            uint64_t pull = kInf;
+#pragma unroll
+            for (int t = 0; t < 4; ++t)
+                if (ok[t] && dv[t] != kInf && dv[t] + ww[t] < pull) pull = dv[t] + ww[t];
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) {
+                const uint64_t y = __shfl_xor_sync(FULL_MASK, pull, o);
+                pull = y < pull ? y : pull;
+            }
+            bool push_u = false;
+            if (pull < du) {  // warp-uniform
+                du = pull;
+                if (lane == 0) {
+                    const uint32_t u = rec.z;
+                    atomicMin(reinterpret_cast<unsigned long long*>(&dist[u]), (unsigned long long)pull);
+                    ++lupd;
+                    lmin = pull < lmin ? pull : lmin;
+                    const uint32_t prev = atomicOr(&inq[u >> 5], 1u << (u & 31u));
+                    push_u = (prev & (1u << (u & 31u))) == 0;
+                }
+            }
+            stage_push(push_u, rec.z, stage, stc, lane);
+        }
+        uint64_t cand[4];
+#pragma unroll
+        for (int t = 0; t < 4; ++t) cand[t] = du + ww[t];
+        relax_apply4(dist, inq, vv, cand, dv, ok, stage, stc, lane, lmin, lupd);
     }
 }
 

@@ -89,6 +89,7 @@ struct SolveParams {
     uint32_t exit_block;          // testing: 1 + block that leaves before the first wait
     uint32_t sample_cap;          // power of two >= the largest sample count (<= kMaxSamples)
     sssp_stats* stats_out;        // optional device copy of the totals
+    int bidir;                    // bidirectional relaxation of chunk records (symmetric graphs)
 };
 
 // Chunk records of one vertex: its edge range [b, e) cut at multiples of kChunk.
@@ -142,6 +143,7 @@ struct sssp_graph {
     sssp::Ctrl* h_ctrl = nullptr;                // pinned readback
     uint32_t last_grid = 0;
     double mean_w = 1.0;                   // mean edge weight (default Delta)
+    uint32_t flags = 0;                    // SSSP_GRAPH_* flags given at creation
     std::mutex mu;                         // guards lazy allocations / attributes
 };
 

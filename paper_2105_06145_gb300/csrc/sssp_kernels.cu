@@ -358,7 +358,10 @@ __global__ void __launch_bounds__(kBlock, 1) solve_kernel(SolveParams p)
                     const uint64_t nit = it + nwarps;
                     rn = nit < fc ? __ldcg(&p.items[nit]) : make_uint4(0, 0, 0, 0);
                     const uint64_t du = ldcg64(&dist[rc.z]);
-                    relax_chunk(rc, du, pairs, dist, inq, stage, stc, lane, lmin, lupd);
+                    if (p.bidir)
+                        relax_chunk<true>(rc, du, pairs, dist, inq, stage, stc, lane, lmin, lupd);
+                    else
+                        relax_chunk<false>(rc, du, pairs, dist, inq, stage, stc, lane, lmin, lupd);
                     if (stc > (uint32_t)(kStage - 256)) stage_flush(stage, stc, lane, &ctrl->qsize[nx], &ctrl->status, Qnext, n);
                 }
             }

@@ -21,6 +21,8 @@ LIB_PATH = os.environ.get("SSSP_LIB") or os.path.join(_HERE, "libsssp.so")
 SSSP_RHO, SSSP_DELTA_STAR, SSSP_BELLMAN_FORD, SSSP_DELTA, SSSP_DIJKSTRA = 0, 1, 2, 3, 4
 ALGOS = {"rho": SSSP_RHO, "delta_star": SSSP_DELTA_STAR, "bellman_ford": SSSP_BELLMAN_FORD,
          "delta": SSSP_DELTA, "dijkstra": SSSP_DIJKSTRA}
+SSSP_SOLVE_BIDIRECTIONAL = 1
+SSSP_GRAPH_SYMMETRIC, SSSP_GRAPH_VERIFY = 1, 2
 SSSP_OK = 0
 SSSP_ERR_INVALID_ARG, SSSP_ERR_OUT_OF_MEMORY, SSSP_ERR_CUDA = -1, -2, -3
 SSSP_ERR_TIMEOUT, SSSP_ERR_INTERNAL = -4, -5
@@ -62,7 +64,7 @@ class sssp_options(ctypes.Structure):
                 ("trace", ctypes.c_void_p), ("trace_cap", ctypes.c_uint32),
                 ("grid_limit", ctypes.c_uint32), ("test_exit_block", ctypes.c_uint32),
                 ("stats_out", ctypes.c_void_p), ("solve_timeout_ns", ctypes.c_uint64),
-                ("reserved", ctypes.c_uint32 * 2)]
+                ("flags", ctypes.c_uint32), ("reserved", ctypes.c_uint32)]
 
 
 TRACE_RECORD_BYTES = ctypes.sizeof(sssp_step_trace)
@@ -71,6 +73,8 @@ STATS_BYTES = ctypes.sizeof(sssp_stats)
 _P, _u32, _u64, _i32 = ctypes.c_void_p, ctypes.c_uint32, ctypes.c_uint64, ctypes.c_int
 _lib.sssp_graph_create.argtypes = [_u32, _u64, _P, _P, _P, ctypes.POINTER(_P)]
 _lib.sssp_graph_create.restype = _i32
+_lib.sssp_graph_create_ex.argtypes = [_u32, _u64, _P, _P, _P, _u32, ctypes.POINTER(_P)]
+_lib.sssp_graph_create_ex.restype = _i32
 _lib.sssp_graph_destroy.argtypes = [_P]
 _lib.sssp_graph_destroy.restype = _i32
 _lib.sssp_graph_info.argtypes = [_P, ctypes.POINTER(_u32), ctypes.POINTER(_u64)]
@@ -81,6 +85,8 @@ _lib.sssp_solve_ex.argtypes = [_P, _u32, _i32, _u64, _P, ctypes.POINTER(sssp_opt
 _lib.sssp_solve_ex.restype = _i32
 _lib.sssp_solve_host.argtypes = [_P, _u32, _i32, _u64, _P, _P]
 _lib.sssp_solve_host.restype = _i32
+_lib.sssp_solve_host_ex.argtypes = [_P, _u32, _i32, _u64, _P, ctypes.POINTER(sssp_options), _P]
+_lib.sssp_solve_host_ex.restype = _i32
 _lib.sssp_last_status.argtypes = [_P, _P]
 _lib.sssp_last_status.restype = _i32
 _lib.sssp_last_stats.argtypes = [_P, ctypes.POINTER(sssp_stats), _P]
@@ -133,7 +139,7 @@ EXPORTED = ["sssp_graph_create", "sssp_graph_destroy", "sssp_graph_info", "sssp_
             "sssp_rho_threshold", "sssp_status_string", "sssp_solve_noalloc", "sssp_solve_sources",
             "sssp_solve_multi", "sssp_batch_last_stats", "sssp_server_create", "sssp_server_slots",
             "sssp_server_submit", "sssp_server_poll", "sssp_server_wait", "sssp_server_stats",
-            "sssp_server_destroy", "sssp_server_drain"]
+            "sssp_server_destroy", "sssp_server_drain", "sssp_graph_create_ex", "sssp_solve_host_ex"]
 
 MAX_BATCH = 2048
 
@@ -159,13 +165,18 @@ def sssp_status_string(code: int) -> str:
 
 def sssp_graph_create(n: int, m: int, offsets: np.ndarray, targets: np.ndarray,
                       weights: np.ndarray) -> int:
+    return sssp_graph_create_ex(n, m, offsets, targets, weights, 0)
+
+
+def sssp_graph_create_ex(n: int, m: int, offsets: np.ndarray, targets: np.ndarray,
+                         weights: np.ndarray, flags: int) -> int:
     offsets = np.ascontiguousarray(offsets, dtype=np.uint64)
     targets = np.ascontiguousarray(targets, dtype=np.uint32)
     weights = np.ascontiguousarray(weights, dtype=np.uint32)
     h = _P()
-    _check(_lib.sssp_graph_create(n, m, offsets.ctypes.data, targets.ctypes.data if m else None,
-                                  weights.ctypes.data if m else None, ctypes.byref(h)),
-           "sssp_graph_create")
+    _check(_lib.sssp_graph_create_ex(n, m, offsets.ctypes.data, targets.ctypes.data if m else None,
+                                     weights.ctypes.data if m else None, flags, ctypes.byref(h)),
+           "sssp_graph_create_ex")
     return h.value
 
 
@@ -187,7 +198,7 @@ def sssp_solve(g: int, source: int, algo: int, param: int, dist_out_ptr: int, st
 def make_options(seed: int = 0, timeout_ns: int = 0, max_steps: int = 0, ext_count_ptr: int = 0,
                  trace_ptr: int = 0, trace_cap: int = 0, grid_limit: int = 0,
                  test_exit_block: int = 0, stats_out_ptr: int = 0,
-                 solve_timeout_ns: int = 0) -> sssp_options:
+                 solve_timeout_ns: int = 0, flags: int = 0) -> sssp_options:
     o = sssp_options()
     o.seed, o.timeout_ns, o.max_steps = seed, timeout_ns, max_steps
     o.ext_count = ext_count_ptr or None
@@ -195,6 +206,7 @@ def make_options(seed: int = 0, timeout_ns: int = 0, max_steps: int = 0, ext_cou
     o.trace_cap, o.grid_limit, o.test_exit_block = trace_cap, grid_limit, test_exit_block
     o.stats_out = stats_out_ptr or None
     o.solve_timeout_ns = solve_timeout_ns
+    o.flags = flags
     return o
 
 
@@ -213,9 +225,10 @@ def sssp_solve_host(g: int, source: int, algo: int, param: int, host_out: np.nda
 
 
 def sssp_solve_host_ptr(g: int, source: int, algo: int, param: int, host_ptr: int,
-                        stream: int = 0) -> int:
-    """sssp_solve_host with a raw host pointer (e.g. a pinned torch tensor)."""
-    return _lib.sssp_solve_host(g, source, algo, param, host_ptr, stream or None)
+                        stream: int = 0, opts: sssp_options | None = None) -> int:
+    """sssp_solve_host_ex with a raw host pointer (e.g. a pinned torch tensor)."""
+    return _lib.sssp_solve_host_ex(g, source, algo, param, host_ptr,
+                                   ctypes.byref(opts) if opts is not None else None, stream or None)
 
 
 def sssp_last_status(g: int, stream: int = 0) -> int:
@@ -337,10 +350,10 @@ class Graph:
     """Owning wrapper of an sssp_graph handle built from a CSR (graphgen.CSR or
     any object with n, off, tgt, w)."""
 
-    def __init__(self, csr):
+    def __init__(self, csr, flags: int = 0):
         self.n = int(csr.n)
         self.m = int(csr.tgt.shape[0])
-        self.handle = sssp_graph_create(self.n, self.m, csr.off, csr.tgt, csr.w)
+        self.handle = sssp_graph_create_ex(self.n, self.m, csr.off, csr.tgt, csr.w, flags)
 
     def close(self) -> None:
         if self.handle:

@@ -47,3 +47,22 @@ def test_host_validation_without_gpu():
     assert sssp._lib.sssp_rho_threshold(None, 4, None, 8, 1, 0, 1, 0, None, None) == \
         sssp.SSSP_ERR_INVALID_ARG
     assert sssp.sssp_status_string(sssp.SSSP_ERR_TIMEOUT) == "device-wide wait timed out"
+
+
+def test_symmetry_verification_without_gpu():
+    """SSSP_GRAPH_VERIFY rejects a graph that is not symmetric before any device
+    work (an asymmetric edge or a reverse edge with another weight)."""
+    from paper_2105_06145_gb300 import sssp
+    off = np.array([0, 1, 2, 2], dtype=np.uint64)
+    tgt = np.array([1, 2], dtype=np.uint32)            # 0->1, 1->2: no reverses
+    w = np.array([5, 6], dtype=np.uint32)
+    with pytest.raises(sssp.SSSPError) as e:
+        sssp.sssp_graph_create_ex(3, 2, off, tgt, w, sssp.SSSP_GRAPH_SYMMETRIC | sssp.SSSP_GRAPH_VERIFY)
+    assert e.value.code == sssp.SSSP_ERR_INVALID_ARG
+    off = np.array([0, 1, 2], dtype=np.uint64)
+    tgt = np.array([1, 0], dtype=np.uint32)
+    w = np.array([5, 6], dtype=np.uint32)              # weights differ
+    with pytest.raises(sssp.SSSPError):
+        sssp.sssp_graph_create_ex(2, 2, off, tgt, w, sssp.SSSP_GRAPH_SYMMETRIC | sssp.SSSP_GRAPH_VERIFY)
+    with pytest.raises(sssp.SSSPError):
+        sssp.sssp_graph_create_ex(2, 2, off, tgt, w, 1 << 7)  # unknown flag

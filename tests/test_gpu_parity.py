@@ -243,3 +243,24 @@ def test_invalid_arguments(lib):
         rc = lib.sssp_solve_ex(G.handle, src, algo, param, dist.data_ptr(), None, 0, check=False)
         assert rc == lib.SSSP_ERR_INVALID_ARG
     G.close()
+
+
+def test_bidirectional_relaxation(lib):
+    """Sec. 6 bidirectional relaxation on symmetric graphs (verified at create):
+    distances unchanged for every rule; refused on a graph not declared symmetric."""
+    flags = lib.SSSP_GRAPH_SYMMETRIC | lib.SSSP_GRAPH_VERIFY
+    for g in (gg.rmat(15, 16, gen_seed=7, wseed=8), gg.road(150, 0.75, seed=4), gg.grid(90, 90, wseed=6)):
+        s = gg.pick_sources(g, 1, 2)[0]
+        want = oracle.dijkstra(g, s)
+        G = lib.Graph(g, flags)
+        for algo, param in ((0, 64), (0, 1 << 12), (1, 1 << 14), (2, 0), (3, 1 << 14), (4, 0)):
+            opts = lib.make_options(flags=lib.SSSP_SOLVE_BIDIRECTIONAL)
+            got, st = solve(lib, g, s, algo, param, opts=opts, G=G)
+            assert st["status"] == 0 and np.array_equal(got, want), (g.name, algo, param)
+        G.close()
+    g = gg.rmat(12, 8)
+    G = lib.Graph(g)   # not declared symmetric
+    dist = torch.empty(g.n, dtype=torch.int64, device="cuda")
+    rc = lib.sssp_solve_ex(G.handle, 0, 0, 64, dist.data_ptr(), lib.make_options(flags=1), 0, check=False)
+    assert rc == lib.SSSP_ERR_INVALID_ARG
+    G.close()

@@ -98,7 +98,17 @@ typedef struct {
                                 solves can be measured without host synchronisation       */
     uint64_t solve_timeout_ns; /* bound on the whole solve; 0 = 60 s (SSSP_ERR_TIMEOUT)  */
     uint32_t flags;          /* SSSP_SOLVE_* bits                                         */
-    uint32_t reserved;
+    uint32_t local_budget;   /* local relaxation of super-sparse steps (Sec. 6, "local
+                                BFS"); 0 = off.  rho- and Delta*-Stepping only
+                                (INVALID_ARG for another rule when nonzero).  In a step
+                                with 20*|Q| <= n whose extracted vertices have average
+                                out-degree < 20, every warp keeps relaxing from the
+                                vertices it has just queued while their distance is
+                                <= theta (degree <= 32 each), 32 at a time, until it has
+                                relaxed local_budget such vertices or runs out of
+                                them in that step.  The distances are the same;
+                                steps, edges and updates change (edges then counts the
+                                local relaxations too).                                  */
 } sssp_options;
 
 /* sssp_options.flags */

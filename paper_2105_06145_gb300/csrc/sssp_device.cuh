@@ -365,6 +365,94 @@ __device__ __forceinline__ void relax_chunk(uint4 rec, uint64_t du, const uint4*
     }
 }
 
+// Warp-uniform: relax the out-edges of up to 32 vertices at once, one per lane
+// (lane j: first edge b_j, degree deg_j -- 0 for none -- and distance du_j),
+// with the edges of all of them spread over the lanes 32 at a time.  The
+// lanes with deg > 0 are first packed to the front so that the k-th edge run
+// belongs to lane k.  When allow_flush, staged ids are flushed whenever fewer
+// than 256 staging slots are left; otherwise the caller guarantees room for
+// every push (at most the total degree).
+__device__ __forceinline__ void relax_flat(uint64_t b, uint32_t deg, uint64_t du, const uint2* __restrict__ edges,
+                                           uint64_t* dist, uint32_t* inq, uint32_t* stage, uint32_t& stc,
+                                           uint32_t lane, uint64_t& lmin, uint32_t& lupd, bool allow_flush,
+                                           unsigned int* qsize, int* status, uint32_t* Qnext, uint32_t qcap)
+{
+    const uint32_t active = __ballot_sync(FULL_MASK, deg > 0);
+    if (active == 0) return;
+    if ((active & (active + 1u)) != 0) {  // the active lanes are not a prefix: pack them to the front
+        const uint32_t cnt = __popc(active);
+        uint32_t rest = active;  // position of the lane-th set bit of active
+        for (uint32_t i = 0; i < lane && i < cnt; ++i) rest &= rest - 1u;
+        const int src = lane < cnt ? __ffs(rest) - 1 : (int)lane;
+        const uint64_t b2 = __shfl_sync(FULL_MASK, b, src);
+        const uint32_t d2 = __shfl_sync(FULL_MASK, deg, src);
+        const uint64_t u2 = __shfl_sync(FULL_MASK, du, src);
+        b = lane < cnt ? b2 : 0ull;
+        deg = lane < cnt ? d2 : 0u;
+        du = lane < cnt ? u2 : 0ull;
+    }
+    const uint32_t lmask = lane == 31 ? FULL_MASK : ((2u << lane) - 1u);
+    const uint32_t incl = (uint32_t)warp_incl_scan64(deg, lane);
+    const uint32_t excl = incl - deg;
+    const uint32_t total = __shfl_sync(FULL_MASK, incl, 31);
+    uint32_t started = 0;
+    for (uint32_t r0 = 0; r0 < total; r0 += 32 * kSmallRounds) {
+        uint64_t eidx[kSmallRounds], cdu[kSmallRounds];
+        bool ok[kSmallRounds];
+#pragma unroll
+        for (int t = 0; t < kSmallRounds; ++t) {
+            const uint32_t rb = r0 + 32u * t;
+            const uint32_t contrib = (deg > 0 && excl >= rb && excl < rb + 32u) ? (1u << (excl - rb)) : 0u;
+            const uint32_t starts = __reduce_or_sync(FULL_MASK, contrib);
+            const uint32_t e = rb + lane;
+            ok[t] = e < total;
+            int owner = (int)(started + __popc(starts & lmask)) - 1;
+            owner = owner < 0 ? 0 : owner;
+            started += __popc(starts);
+            const uint64_t ob = __shfl_sync(FULL_MASK, b, owner);
+            const uint32_t oe = __shfl_sync(FULL_MASK, excl, owner);
+            cdu[t] = __shfl_sync(FULL_MASK, du, owner);
+            eidx[t] = ob + (e - oe);
+        }
+        uint32_t vv[kSmallRounds];
+        uint64_t cand[kSmallRounds];
+#pragma unroll
+        for (int t = 0; t < kSmallRounds; ++t) {
+            const uint2 ed = ok[t] ? __ldcs(&edges[eidx[t]]) : make_uint2(0, 0);
+            vv[t] = ed.x;
+            cand[t] = cdu[t] + ed.y;
+        }
+        relax_batch4(dist, inq, vv, cand, ok, stage, stc, lane, lmin, lupd);
+        if (allow_flush && stc > (uint32_t)(kStage - 256)) stage_flush(stage, stc, lane, qsize, status, Qnext, qcap);
+    }
+}
+
+// Warp-uniform: move the first `done` staged ids to the next queue list and
+// shift the rest of the staging buffer down.
+__device__ __forceinline__ void stage_flush_prefix(uint32_t* stage, uint32_t& stc, uint32_t done, uint32_t lane,
+                                                   unsigned int* qsize, int* status, uint32_t* Qnext, uint32_t cap)
+{
+    __syncwarp();
+    if (done == 0) return;
+    uint32_t base = 0;
+    if (lane == 0) base = atomicAdd(qsize, done);
+    base = __shfl_sync(FULL_MASK, base, 0);
+    if ((uint64_t)base + done > (uint64_t)cap) {
+        if (lane == 0) set_status(status, SSSP_ERR_INTERNAL);
+    } else {
+        for (uint32_t i = lane; i < done; i += 32) Qnext[base + i] = stage[i];
+    }
+    __syncwarp();
+    for (uint32_t i0 = 0; i0 + done < stc; i0 += 32) {
+        const uint32_t i = i0 + lane;
+        const uint32_t x = (i + done < stc) ? stage[i + done] : 0u;
+        __syncwarp();
+        if (i + done < stc) stage[i] = x;
+        __syncwarp();
+    }
+    stc -= done;
+}
+
 // Block-wide reduction of two sums and a minimum; results valid in thread 0.
 __device__ __forceinline__ void block_reduce_2add_min(uint64_t& a, uint64_t& b, uint64_t& mn, uint64_t* s_tmp)
 {

@@ -58,6 +58,7 @@ struct Ctrl {
     unsigned long long fedges[3];
     unsigned long long updates[3];
     unsigned long long umin[3];   // smallest distance written by the relaxation of the step (slot of Q_{k+1})
+    unsigned long long ledges[3]; // edges relaxed by the local relaxation of super-sparse steps
     // totals, written by block 0 when the solve ends
     unsigned long long steps, queued, extracted, edges, updates_total;
 };
@@ -90,6 +91,7 @@ struct SolveParams {
     uint32_t sample_cap;          // power of two >= the largest sample count (<= kMaxSamples)
     sssp_stats* stats_out;        // optional device copy of the totals
     int bidir;                    // bidirectional relaxation of chunk records (symmetric graphs)
+    uint32_t local_budget;        // local relaxation of super-sparse steps: vertices per warp and step (0 = off)
 };
 
 // Chunk records of one vertex: its edge range [b, e) cut at multiples of kChunk.

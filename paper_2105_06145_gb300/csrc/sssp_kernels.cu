@@ -28,6 +28,62 @@
 namespace sssp {
 
 // ---------------------------------------------------------------------------
+// Local relaxation of super-sparse steps (Sec. 6, local BFS).
+//
+// The warp's staging buffer is its local frontier: entries [0, lq) have been
+// looked at, [lq, stc) wait.  Up to 32 waiting vertices at a time, a vertex
+// whose distance is still <= theta and whose out-degree is 1..kSmallDeg has its
+// out-edges relaxed at once (WriteMin and Update as in the main relaxation);
+// the ids that queues are appended behind and are looked at in turn.  Every id
+// stays staged and so reaches Q_next: a vertex relaxed here is extracted again
+// in a later step (a vertex this step would have extracted next).  Stops after
+// `budget` relaxed vertices, or when the frontier is exhausted.  Returns the
+// edges relaxed.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ uint64_t local_relax(uint64_t theta, uint32_t budget, const uint64_t* __restrict__ off,
+                                                const uint2* __restrict__ edges, uint64_t* dist, uint32_t* inq,
+                                                uint32_t* stage, uint32_t& stc, uint32_t lane, uint64_t& lmin,
+                                                uint32_t& lupd, unsigned int* qsize, int* status, uint32_t* Qnext,
+                                                uint32_t n)
+{
+    uint32_t lq = 0, done = 0;
+    uint64_t scanned = 0;
+    while (lq < stc && done < budget) {  // warp-uniform
+        if (stc + 256u > (uint32_t)kStage) {
+            // make room: the looked-at prefix goes to the next queue list
+            stage_flush_prefix(stage, stc, lq, lane, qsize, status, Qnext, n);
+            lq = 0;
+            if (stc + (uint32_t)kSmallDeg > (uint32_t)kStage) break;
+        }
+        __syncwarp();
+        uint32_t cnt = stc - lq;
+        cnt = cnt < 32u ? cnt : 32u;
+        uint64_t b = 0, du = 0;
+        uint32_t deg = 0;
+        if (lane < cnt) {
+            const uint32_t x = stage[lq + lane];
+            du = ldcg64(&dist[x]);
+            if (du <= theta) {
+                b = off[x];
+                const uint64_t d = off[x + 1] - b;
+                deg = d <= (uint64_t)kSmallDeg ? (uint32_t)d : 0u;
+            }
+        }
+        // take the lanes whose edges fit in the staging room left (a prefix,
+        // never empty: the room is >= kSmallDeg)
+        const uint32_t room = (uint32_t)kStage - stc;
+        const uint32_t incl = (uint32_t)warp_incl_scan64(deg, lane);
+        const uint32_t take = __popc(__ballot_sync(FULL_MASK, lane < cnt && incl <= room));
+        if (lane >= take) deg = 0;
+        done += __popc(__ballot_sync(FULL_MASK, deg > 0));
+        scanned += __shfl_sync(FULL_MASK, incl, take - 1);
+        lq += take;
+        relax_flat(b, deg, du, edges, dist, inq, stage, stc, lane, lmin, lupd, false, qsize, status, Qnext, n);
+    }
+    return lane == 0 ? scanned : 0;
+}
+
+// ---------------------------------------------------------------------------
 // The persistent solve kernel
 // ---------------------------------------------------------------------------
 __global__ void __launch_bounds__(kBlock, 1) solve_kernel(SolveParams p)
@@ -114,16 +170,18 @@ __global__ void __launch_bounds__(kBlock, 1) solve_kernel(SolveParams p)
                 const uint32_t ff = ldcg32(&ctrl->fcount[pv]);
                 const uint64_t ee = ldcg64((const uint64_t*)&ctrl->fedges[pv]);
                 const uint64_t uu = ldcg64((const uint64_t*)&ctrl->updates[pv]);
-                ctrl->queued += qq; ctrl->extracted += ff; ctrl->edges += ee; ctrl->updates_total += uu;
+                const uint64_t le = ldcg64((const uint64_t*)&ctrl->ledges[pv]);
+                ctrl->queued += qq; ctrl->extracted += ff; ctrl->edges += ee + le; ctrl->updates_total += uu;
                 if (p.trace && k - 2 < p.trace_cap) {
                     sssp_step_trace* rec = &p.trace[k - 2];  // time extremes are filled by all blocks
                     rec->theta = s_prev_theta; rec->queued = qq; rec->extracted = ff;
-                    rec->edges = ee; rec->updates = uu; rec->t_ns = s_prev_t; rec->t_relax_ns = s_prev_tr;
+                    rec->edges = ee + le; rec->updates = uu; rec->t_ns = s_prev_t; rec->t_relax_ns = s_prev_tr;
                 }
             }
             s_prev_t = global_timer_ns() - s_t_start;
             ctrl->qsize[pv] = 0; ctrl->fsmall[pv] = 0; ctrl->fchunk[pv] = 0; ctrl->fcount[pv] = 0;
             ctrl->fedges[pv] = 0; ctrl->updates[pv] = 0; ctrl->qmin[pv] = kInf; ctrl->umin[pv] = kInf;
+            ctrl->ledges[pv] = 0;
         }
         if (q == 0) break;
         if (p.max_steps != 0 && k > p.max_steps) {
@@ -298,7 +356,6 @@ __global__ void __launch_bounds__(kBlock, 1) solve_kernel(SolveParams p)
 
             // (a) low-degree vertices: 32 records per warp, edges flattened across lanes
             const uint64_t ngroups = (fs + 31u) >> 5;
-            const uint32_t lmask = lane == 31 ? FULL_MASK : ((2u << lane) - 1u);
             uint64_t g = gwarp;
             uint4 rnext = make_uint4(0, 0, 0, 0);
             if (g < ngroups && g * 32u + lane < fs) rnext = __ldcg(&p.fsmall[g * 32u + lane]);
@@ -307,43 +364,8 @@ __global__ void __launch_bounds__(kBlock, 1) solve_kernel(SolveParams p)
                 const uint64_t gn = g + nwarps;  // prefetch the next group's records
                 rnext = (gn < ngroups && gn * 32u + lane < fs) ? __ldcg(&p.fsmall[gn * 32u + lane])
                                                               : make_uint4(0, 0, 0, 0);
-                const uint64_t b = rec_start(rec);
-                const uint32_t deg = rec_len(rec);
-                const uint64_t du = rec_du(rec);
-                const uint32_t incl = (uint32_t)warp_incl_scan64(deg, lane);
-                const uint32_t excl = incl - deg;
-                const uint32_t total = __shfl_sync(FULL_MASK, incl, 31);
-                uint32_t started = 0;
-                for (uint32_t r0 = 0; r0 < total; r0 += 32 * kSmallRounds) {
-                    uint64_t eidx[kSmallRounds], cdu[kSmallRounds];
-                    bool ok[kSmallRounds];
-#pragma unroll
-                    for (int t = 0; t < kSmallRounds; ++t) {
-                        const uint32_t rb = r0 + 32u * t;
-                        const uint32_t contrib =
-                            (deg > 0 && excl >= rb && excl < rb + 32u) ? (1u << (excl - rb)) : 0u;
-                        const uint32_t starts = __reduce_or_sync(FULL_MASK, contrib);
-                        const uint32_t e = rb + lane;
-                        ok[t] = e < total;
-                        int owner = (int)(started + __popc(starts & lmask)) - 1;
-                        owner = owner < 0 ? 0 : owner;
-                        started += __popc(starts);
-                        const uint64_t ob = __shfl_sync(FULL_MASK, b, owner);
-                        const uint32_t oe = __shfl_sync(FULL_MASK, excl, owner);
-                        cdu[t] = __shfl_sync(FULL_MASK, du, owner);
-                        eidx[t] = ob + (e - oe);
-                    }
-                    uint32_t vv[kSmallRounds];
-                    uint64_t cand[kSmallRounds];
-#pragma unroll
-                    for (int t = 0; t < kSmallRounds; ++t) {
-                        const uint2 ed = ok[t] ? __ldcs(&edges[eidx[t]]) : make_uint2(0, 0);
-                        vv[t] = ed.x;
-                        cand[t] = cdu[t] + ed.y;
-                    }
-                    relax_batch4(dist, inq, vv, cand, ok, stage, stc, lane, lmin, lupd);
-                    if (stc > (uint32_t)(kStage - 256)) stage_flush(stage, stc, lane, &ctrl->qsize[nx], &ctrl->status, Qnext, n);
-                }
+                relax_flat(rec_start(rec), rec_len(rec), rec_du(rec), edges, dist, inq, stage, stc, lane, lmin,
+                           lupd, true, &ctrl->qsize[nx], &ctrl->status, Qnext, n);
             }
 
             // (b) higher-degree vertices: one warp per chunk record; the next
@@ -366,6 +388,17 @@ __global__ void __launch_bounds__(kBlock, 1) solve_kernel(SolveParams p)
                 }
             }
 
+            // (d) super-sparse steps (Sec. 6, local BFS): keep relaxing from the
+            //     vertices this warp has just queued while they are within theta
+            uint64_t ledg = 0;
+            if (p.local_budget != 0 && (uint64_t)q * 20ull <= (uint64_t)n) {
+                const uint64_t fcnt = ldcg32(&ctrl->fcount[c]);
+                const uint64_t fed = ldcg64((const uint64_t*)&ctrl->fedges[c]);
+                if (fed < 20ull * fcnt)
+                    ledg = local_relax(theta, p.local_budget, off, edges, dist, inq, stage, stc, lane, lmin, lupd,
+                                       &ctrl->qsize[nx], &ctrl->status, Qnext, n);
+            }
+
             // (c) block-aggregated flush of what is left in the warps' staging
             if (lane == 0) s_wcnt[wid] = stc;
             __syncthreads();
@@ -382,10 +415,11 @@ __global__ void __launch_bounds__(kBlock, 1) solve_kernel(SolveParams p)
                 const uint32_t wb = s_base[0] + s_wcnt[wid];
                 for (uint32_t i = lane; i < stc; i += 32) Qnext[wb + i] = stage[i];
             }
-            uint64_t bu = lupd, unused = 0, bm = lmin;
-            block_reduce_2add_min(bu, unused, bm, s_tmp);
+            uint64_t bu = lupd, bl = ledg, bm = lmin;
+            block_reduce_2add_min(bu, bl, bm, s_tmp);
             if (tid == 0) {
                 if (bu) atomicAdd(&ctrl->updates[c], (unsigned long long)bu);
+                if (bl) atomicAdd(&ctrl->ledges[c], (unsigned long long)bl);
                 if (algo_tracks_qmin(p.algo) && bm != kInf) {
                     atomicMin(&ctrl->qmin[nx], (unsigned long long)bm);
                     atomicMin(&ctrl->umin[nx], (unsigned long long)bm);

@@ -64,7 +64,7 @@ class sssp_options(ctypes.Structure):
                 ("trace", ctypes.c_void_p), ("trace_cap", ctypes.c_uint32),
                 ("grid_limit", ctypes.c_uint32), ("test_exit_block", ctypes.c_uint32),
                 ("stats_out", ctypes.c_void_p), ("solve_timeout_ns", ctypes.c_uint64),
-                ("flags", ctypes.c_uint32), ("reserved", ctypes.c_uint32)]
+                ("flags", ctypes.c_uint32), ("local_budget", ctypes.c_uint32)]
 
 
 TRACE_RECORD_BYTES = ctypes.sizeof(sssp_step_trace)
@@ -198,7 +198,7 @@ def sssp_solve(g: int, source: int, algo: int, param: int, dist_out_ptr: int, st
 def make_options(seed: int = 0, timeout_ns: int = 0, max_steps: int = 0, ext_count_ptr: int = 0,
                  trace_ptr: int = 0, trace_cap: int = 0, grid_limit: int = 0,
                  test_exit_block: int = 0, stats_out_ptr: int = 0,
-                 solve_timeout_ns: int = 0, flags: int = 0) -> sssp_options:
+                 solve_timeout_ns: int = 0, flags: int = 0, local_budget: int = 0) -> sssp_options:
     o = sssp_options()
     o.seed, o.timeout_ns, o.max_steps = seed, timeout_ns, max_steps
     o.ext_count = ext_count_ptr or None
@@ -207,6 +207,7 @@ def make_options(seed: int = 0, timeout_ns: int = 0, max_steps: int = 0, ext_cou
     o.stats_out = stats_out_ptr or None
     o.solve_timeout_ns = solve_timeout_ns
     o.flags = flags
+    o.local_budget = local_budget
     return o
 
 

@@ -264,3 +264,43 @@ def test_bidirectional_relaxation(lib):
     rc = lib.sssp_solve_ex(G.handle, 0, 0, 64, dist.data_ptr(), lib.make_options(flags=1), 0, check=False)
     assert rc == lib.SSSP_ERR_INVALID_ARG
     G.close()
+
+
+def test_local_relaxation_of_super_sparse_steps(lib):
+    """Sec. 6 local BFS in super-sparse steps: distances equal the oracle's for
+    rho- and Delta*-Stepping over budgets from tiny to large (including the
+    room-making path of the warp's local frontier), with and without
+    bidirectional relaxation; edges count the local relaxations too; refused
+    for the other rules."""
+    flags = lib.SSSP_GRAPH_SYMMETRIC | lib.SSSP_GRAPH_VERIFY
+    graphs = [gg.road(150, 0.75, seed=4), gg.grid(90, 90, wseed=6), gg.rmat(14, 8, gen_seed=3, wseed=4),
+              gg.chain(3000, wseed=5, both=True), gg.knn(20000, clusters=8, k=6, seed=3)]
+    for g in graphs:
+        s = gg.pick_sources(g, 1, 9)[0]
+        want = oracle.dijkstra(g, s)
+        G = lib.Graph(g, flags)
+        for algo, param in ((0, 64), (0, 1 << 10), (0, max(64, g.n // 16)), (1, 1 << 12), (1, 1 << 16)):
+            for budget in (1, 32, 4096, 1 << 20):
+                for fl in (0, lib.SSSP_SOLVE_BIDIRECTIONAL):
+                    opts = lib.make_options(local_budget=budget, flags=fl)
+                    got, st = solve(lib, g, s, algo, param, opts=opts, G=G)
+                    assert st["status"] == 0 and np.array_equal(got, want), (g.name, algo, param, budget, fl)
+                    assert st["extracted"] >= 1 and st["updates"] >= 1 or g.n == 1
+        G.close()
+    # the local relaxation takes several hops per step: far fewer steps on a
+    # road-like graph with a small rho
+    g = gg.road(200, 0.75, seed=8)
+    s = gg.pick_sources(g, 1, 1)[0]
+    want = oracle.dijkstra(g, s)
+    _, base = solve(lib, g, s, 0, 256)
+    got, loc = solve(lib, g, s, 0, 256, opts=lib.make_options(local_budget=1 << 12))
+    assert np.array_equal(got, want)
+    assert loc["steps"] < base["steps"], (loc, base)
+    # only rho- and Delta*-Stepping have it
+    G = lib.Graph(g)
+    dist = torch.empty(g.n, dtype=torch.int64, device="cuda")
+    for algo, param in ((2, 0), (3, 1 << 10), (4, 0)):
+        rc = lib.sssp_solve_ex(G.handle, s, algo, param, dist.data_ptr(), lib.make_options(local_budget=8), 0,
+                               check=False)
+        assert rc == lib.SSSP_ERR_INVALID_ARG
+    G.close()

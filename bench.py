@@ -214,7 +214,7 @@ def run_reference(args, g, srcs, label, rank, world):
 
 
 def measure_batched(sssp, G, g, torch, stream, stream_obj) -> dict:
-    """configs[3]: (a) 64 sources on this graph in one launch, (b) 512 graphs of
+    """Batched solves: (a) 64 sources on this graph in one launch, (b) 512 graphs of
     uneven size in one launch; each against the plain loop of single solves."""
     from paper_2105_06145_gb300 import graphgen as gg
 
@@ -261,7 +261,7 @@ def measure_batched(sssp, G, g, torch, stream, stream_obj) -> dict:
 
 def measure_serving(sssp, G, g, torch, sources, rates, window_s=1.0, hard_s=10.0, slots=0,
                     algo=None, param=0, seed=8) -> dict:
-    """Serving (SURVEY pattern 5): a Poisson query stream at each offered rate
+    """Serving: a Poisson query stream at each offered rate
     for `window_s` seconds against the resident graph; queries go to the
     continuous-batching server as client-side result buffers allow.  Latency
     is from the scheduled arrival to the completion seen by the client; the
@@ -341,7 +341,7 @@ def measure_serving(sssp, G, g, torch, sources, rates, window_s=1.0, hard_s=10.0
 
 
 def run_serve_sweep(args):
-    """--serve: the configs[4] sweep over resident graphs (RMAT scale 25, the
+    """--serve: the serving sweep over resident graphs (RMAT scale 25, the
     4096^2 road-like grid, the 2M-point k-NN graph)."""
     import torch
     from paper_2105_06145_gb300 import graphgen as gg, sssp
@@ -384,7 +384,7 @@ def main():
     ap.add_argument("--no-bidir", action="store_true", help="plain push relaxation only")
     ap.add_argument("--no-batch", action="store_true", help="skip the batched-solve measurements")
     ap.add_argument("--no-serve", action="store_true", help="skip the serving measurement")
-    ap.add_argument("--serve", action="store_true", help="run the serving sweep (configs[4]) only")
+    ap.add_argument("--serve", action="store_true", help="run the serving sweep (RMAT-25, road, k-NN) only")
     ap.add_argument("--serve-workloads", default="rmat25,road,knn")
     ap.add_argument("--serve-rates", default="1000,2000,5000,10000,20000,50000")
     ap.add_argument("--serve-window", type=float, default=1.0)
@@ -509,7 +509,7 @@ def main():
                "note": "graph resident; per step the source id and parameter go in as launch "
                        "arguments and the uint64 distance array comes back to pinned host memory"}
 
-    # batched solves (SURVEY pattern 2): queries/s of one batched launch vs the
+    # batched solves: queries/s of one batched launch vs the
     # plain loop of single solves on the same GPU, identical distances
     batched = None
     if rank == 0 and not args.no_batch and args.workload == "rmat" and args.scale == 22:

@@ -115,7 +115,7 @@ def test_batch_argument_errors(lib):
 
 @pytest.mark.slow
 def test_full_size_64_sources_rmat22(lib):
-    """configs[3](a): 64 sources on the RMAT scale-22 graph in one launch; every
+    """Batching, many sources: 64 sources on the RMAT scale-22 graph in one launch; every
     instance equals the single solve, four of them also the oracle."""
     g, _ = gg.workload_rmat(22)
     srcs = gg.pick_sources(g, 64, 6)
@@ -137,7 +137,7 @@ def test_full_size_64_sources_rmat22(lib):
 
 @pytest.mark.slow
 def test_full_size_512_graphs(lib):
-    """configs[3](b): 512 graphs, n log-uniform in [2^10, 2^18], ~2^27 edges."""
+    """Batching, many graphs: 512 graphs, n log-uniform in [2^10, 2^18], ~2^27 edges."""
     W = gg.workload_multi()
     Gs = [lib.Graph(g) for g, _ in W]
     outs = [torch.empty(g.n, dtype=torch.int64, device="cuda") for g, _ in W]

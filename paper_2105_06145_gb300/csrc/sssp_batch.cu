@@ -807,10 +807,10 @@ int batch_blocks(int dev, uint32_t* grid)
     static std::mutex mu;
     std::lock_guard<std::mutex> lk(mu);
     const void* fn = batch_kernel_ptr();
-    cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSolveDynSmem);
+    cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kBatchDynSmem);
     if (e != cudaSuccess) return fail(e);
     int bps = 0, sms = 0;
-    if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, fn, kBlock, kSolveDynSmem)) != cudaSuccess) return fail(e);
+    if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, fn, kBlock, kBatchDynSmem)) != cudaSuccess) return fail(e);
     if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return fail(e);
     if (bps < 1) return SSSP_ERR_CUDA;
     *grid = (uint32_t)(bps * sms);
@@ -887,7 +887,7 @@ int solve_batch(const sssp_graph* const* gs, const uint32_t* sources, uint32_t k
     p.solve_timeout_ns = 120000000000ull;
     p.sample_cap = sample_cap;
     void* args[] = {&p};
-    e = cudaLaunchCooperativeKernel(batch_kernel_ptr(), dim3(w.grid), dim3(kBlock), args, kSolveDynSmem, st);
+    e = cudaLaunchCooperativeKernel(batch_kernel_ptr(), dim3(w.grid), dim3(kBlock), args, kBatchDynSmem, st);
     if (e != cudaSuccess) return fail(e);
     w.last_k = k;
     (void)min_n;
@@ -1043,7 +1043,7 @@ void server_loop(sssp_server* s)
                 cudaError_t e = cudaMemsetAsync(s->d_ctrl, 0, sizeof(BatchCtrl), s->stream);
                 if (e == cudaSuccess)
                     e = cudaLaunchCooperativeKernel(serve_kernel_ptr(), dim3(s->grid), dim3(kBlock), args,
-                                                    kSolveDynSmem, s->stream);
+                                                    kBatchDynSmem, s->stream);
                 if (e != cudaSuccess) {
                     std::lock_guard<std::mutex> lk(s->mu);
                     s->fatal = SSSP_ERR_CUDA;
@@ -1146,9 +1146,9 @@ int sssp_server_create(const sssp_graph* g, const sssp_server_config* cfg, sssp_
     if (rc != SSSP_OK) { delete s; return rc; }
     {
         const void* fn = serve_kernel_ptr();
-        e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSolveDynSmem);
+        e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kBatchDynSmem);
         int bps = 0;
-        if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, fn, kBlock, kSolveDynSmem);
+        if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, fn, kBlock, kBatchDynSmem);
         if (e != cudaSuccess || bps < 1) { delete s; return e != cudaSuccess ? fail(e) : SSSP_ERR_CUDA; }
         int sms = 0;
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, g->device);

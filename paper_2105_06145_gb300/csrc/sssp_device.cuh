@@ -96,6 +96,46 @@ static __device__ __noinline__ bool grid_sync(unsigned long long* bar, int* stat
     return s_ok != 0;
 }
 
+// Variant for kernels whose every error path also raises kBarErr in the
+// barrier word (raise_error): the error reaches waiting blocks through the
+// word they spin on, so the wait needs no separate status load, and blocks
+// waiting for a block that failed are released at once.
+constexpr unsigned long long kBarErr = 1ull << 62;
+
+__device__ __forceinline__ void raise_error(unsigned long long* bar, int* status, int code)
+{
+    atomicCAS(status, 0, code);
+    atomicOr(bar, kBarErr);
+}
+
+static __device__ __noinline__ bool grid_sync_err(unsigned long long* bar, int* status, unsigned long long* target,
+                                                  uint64_t timeout_ns)
+{
+    __shared__ int s_ok;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        const unsigned long long tgt = *target + gridDim.x;
+        *target = tgt;
+        __threadfence();
+        atomicAdd(bar, 1ull);
+        int ok = 1;
+        const unsigned long long t0 = global_timer_ns();
+        unsigned int spins = 0;
+        unsigned long long v;
+        while ((v = ld_acquire_u64(bar)) < tgt) {
+            if ((++spins & 31u) == 0 && global_timer_ns() - t0 > timeout_ns) {
+                raise_error(bar, status, SSSP_ERR_TIMEOUT);
+                ok = 0;
+                break;
+            }
+        }
+        if (v & kBarErr) ok = 0;
+        s_ok = ok;
+    }
+    __syncthreads();
+    return s_ok != 0;
+}
+
 // ---------------------------------------------------------------------------
 // block-wide scans / reductions (kBlock threads)
 // ---------------------------------------------------------------------------
@@ -160,61 +200,115 @@ __device__ __forceinline__ uint64_t block_reduce_min64(uint64_t x, uint64_t* s_t
 
 // ---------------------------------------------------------------------------
 // ExtDist of rho-Stepping (Table 2; Sec. 6 "Threshold estimation"; App. B).
-// Every block evaluates it redundantly from the same inputs (queue list and
-// delta are stable between the previous barrier and the Extract), so no
-// extra device-wide wait is needed.  Returns the same value in all threads.
+//
+// Sample count s, rank r and the effective rho' of a step with q queued ids:
+// rho' = max(1, rho/10) in the first two dense steps (20 q > n), else rho;
+// s = min(4096, 10 (ceil(q/rho') + 1 + floor(log2(q+1)))); r = min(s-1,
+// floor(rho' s / q)); theta is the r-th smallest (0-based) of the s sampled
+// keys.  Returns false when q <= rho' (theta = +inf: extract every queued id).
 // ---------------------------------------------------------------------------
-static __device__ __noinline__ uint64_t rho_extdist_block(const uint32_t* Q, uint32_t q, const uint64_t* dist, uint32_t n,
-                                      uint64_t rho, uint64_t seed, uint64_t step, uint32_t dense_before,
-                                      uint64_t* skeys, uint32_t cap, int* err)
+__device__ __forceinline__ bool rho_sample_plan(uint32_t q, uint32_t n, uint64_t rho, uint32_t dense_before,
+                                                uint32_t* s_out, uint32_t* r_out)
 {
-    __shared__ uint64_t s_theta;
     uint64_t rho_eff = rho;
     if ((uint64_t)q * 20ull > (uint64_t)n && dense_before < 2) {
         rho_eff = rho / 10ull;
         if (rho_eff < 1) rho_eff = 1;
     }
-    if ((uint64_t)q <= rho_eff) return kInf;  // extract every queued vertex
+    if ((uint64_t)q <= rho_eff) return false;
     const uint64_t lg = 63u - (uint32_t)__clzll((long long)((uint64_t)q + 1ull));
     uint64_t s = 10ull * (((uint64_t)q + rho_eff - 1ull) / rho_eff + 1ull + lg);
     if (s > kMaxSamples) s = kMaxSamples;
-    uint32_t P = 1;
-    while (P < s) P <<= 1;
-    if (P > cap) {  // smem sized too small by the host: never expected
-        if (threadIdx.x == 0) *err = 1;
-        return kInf;
-    }
-    for (uint32_t j = threadIdx.x; j < P; j += blockDim.x) {
-        uint64_t key = kInf;
-        if (j < s) {
-            const uint64_t h = splitmix64_at(seed, (step << 32) | j);
-            const uint32_t pos = (uint32_t)__umul64hi(h, (uint64_t)q);
-            key = ldcg64(&dist[ldcg32(&Q[pos])]);
-        }
-        skeys[j] = key;
-    }
-    __syncthreads();
-    // bitonic sort of skeys[0..P), ascending
-    for (uint32_t k = 2; k <= P; k <<= 1) {
-        for (uint32_t j = k >> 1; j > 0; j >>= 1) {
-            for (uint32_t i = threadIdx.x; i < P; i += blockDim.x) {
-                const uint32_t ixj = i ^ j;
-                if (ixj > i) {
-                    const uint64_t a = skeys[i], b = skeys[ixj];
-                    const bool up = (i & k) == 0;
-                    if ((a > b) == up) { skeys[i] = b; skeys[ixj] = a; }
-                }
-            }
-            __syncthreads();
-        }
-    }
     uint64_t r = rho_eff * s / (uint64_t)q;
     if (r > s - 1) r = s - 1;
-    if (threadIdx.x == 0) s_theta = skeys[r];
+    *s_out = (uint32_t)s;
+    *r_out = (uint32_t)r;
+    return true;
+}
+
+// Queue position of sample j of step `step`: splitmix64 output step*2^32 + j
+// from state `seed`, reduced to [0, q) by multiply-high.
+__device__ __forceinline__ uint32_t rho_sample_pos(uint64_t seed, uint64_t step, uint32_t j, uint32_t q)
+{
+    const uint64_t h = splitmix64_at(seed, (step << 32) | j);
+    return (uint32_t)__umul64hi(h, (uint64_t)q);
+}
+
+// Block-wide: the r-th smallest (0-based) of the s keys, all threads get it.
+// s <= blockDim: thread i holds key i in `x` (threads i >= s pass anything)
+// and a bitonic network sorts the P = pow2(s) keys in registers -- shuffles
+// for partner distances < 32, shared memory `xbuf` (blockDim keys) beyond.
+// Larger s: the keys are in skeys[0..s) and are sorted there (P <= cap).
+__device__ __forceinline__ uint64_t block_select(uint64_t x, uint32_t s, uint32_t r, uint64_t* skeys, uint32_t cap,
+                                                 int* err)
+{
+    __shared__ uint64_t s_sel;
+    const uint32_t i = threadIdx.x;
+    uint32_t P = 1;
+    while (P < s) P <<= 1;
+    if (P <= blockDim.x) {
+        x = i < s ? x : kInf;
+        for (uint32_t k = 2; k <= P; k <<= 1) {
+            for (uint32_t j = k >> 1; j > 0; j >>= 1) {
+                uint64_t y;
+                if (j >= 32) {
+                    __syncthreads();
+                    skeys[i] = x;
+                    __syncthreads();
+                    y = skeys[i ^ j];
+                } else {
+                    y = __shfl_xor_sync(FULL_MASK, x, j);
+                }
+                const bool up = (i & k) == 0, lower = (i & j) == 0;
+                x = (lower == up) ? (y < x ? y : x) : (y < x ? x : y);
+            }
+        }
+        if (i == r) s_sel = x;
+    } else {
+        if (P > cap) {  // shared memory sized too small by the host: never expected
+            if (i == 0) { *err = 1; s_sel = kInf; }
+        } else {
+            for (uint32_t j = s + i; j < P; j += blockDim.x) skeys[j] = kInf;
+            __syncthreads();
+            for (uint32_t k = 2; k <= P; k <<= 1) {
+                for (uint32_t j = k >> 1; j > 0; j >>= 1) {
+                    for (uint32_t t = i; t < P; t += blockDim.x) {
+                        const uint32_t tj = t ^ j;
+                        if (tj > t) {
+                            const uint64_t a = skeys[t], b = skeys[tj];
+                            const bool up = (t & k) == 0;
+                            if ((a > b) == up) { skeys[t] = b; skeys[tj] = a; }
+                        }
+                    }
+                    __syncthreads();
+                }
+            }
+            if (i == 0) s_sel = skeys[r];
+        }
+    }
     __syncthreads();
-    const uint64_t th = s_theta;
+    const uint64_t th = s_sel;
     __syncthreads();
     return th;
+}
+
+// The whole ExtDist of rho-Stepping in one block (used by the threshold entry
+// point; the solve kernel runs the same steps with its Extract loads in flight).
+static __device__ __noinline__ uint64_t rho_extdist_block(const uint32_t* Q, uint32_t q, const uint64_t* dist, uint32_t n,
+                                      uint64_t rho, uint64_t seed, uint64_t step, uint32_t dense_before,
+                                      uint64_t* skeys, uint32_t cap, int* err)
+{
+    uint32_t s, r;
+    if (!rho_sample_plan(q, n, rho, dense_before, &s, &r)) return kInf;  // extract every queued vertex
+    uint64_t x = kInf;
+    if (s <= blockDim.x) {
+        if (threadIdx.x < s) x = ldcg64(&dist[ldcg32(&Q[rho_sample_pos(seed, step, threadIdx.x, q)])]);
+    } else {
+        for (uint32_t j = threadIdx.x; j < s; j += blockDim.x)
+            skeys[j] = ldcg64(&dist[ldcg32(&Q[rho_sample_pos(seed, step, j, q)])]);
+        __syncthreads();
+    }
+    return block_select(x, s, r, skeys, cap, err);
 }
 
 // ---------------------------------------------------------------------------
@@ -467,12 +561,16 @@ __device__ __forceinline__ void block_reduce_2add_min(uint64_t& a, uint64_t& b, 
     __syncthreads();
     if (lane == 0) { s_tmp[wid] = a; s_tmp[kWarps + wid] = b; s_tmp[2 * kWarps + wid] = mn; }
     __syncthreads();
-    if (threadIdx.x == 0) {
-        a = 0; b = 0; mn = kInf;
-        for (int i = 0; i < kWarps; ++i) {
-            a += s_tmp[i];
-            b += s_tmp[kWarps + i];
-            mn = s_tmp[2 * kWarps + i] < mn ? s_tmp[2 * kWarps + i] : mn;
+    if (wid == 0) {
+        a = lane < (uint32_t)kWarps ? s_tmp[lane] : 0;
+        b = lane < (uint32_t)kWarps ? s_tmp[kWarps + lane] : 0;
+        mn = lane < (uint32_t)kWarps ? s_tmp[2 * kWarps + lane] : kInf;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            a += __shfl_xor_sync(FULL_MASK, a, o);
+            b += __shfl_xor_sync(FULL_MASK, b, o);
+            const uint64_t y = __shfl_xor_sync(FULL_MASK, mn, o);
+            mn = y < mn ? y : mn;
         }
     }
 }

@@ -13,7 +13,11 @@ namespace sssp {
 #ifndef SSSP_BLOCK
 #define SSSP_BLOCK 1024
 #endif
-constexpr int kBlock = SSSP_BLOCK;                // threads per block of the persistent kernel (1 per SM)
+#ifndef SSSP_MIN_BLOCKS
+#define SSSP_MIN_BLOCKS 1
+#endif
+constexpr int kBlock = SSSP_BLOCK;                // threads per block of the persistent kernels
+constexpr int kMinBlocks = SSSP_MIN_BLOCKS;       // resident blocks per SM the solve kernel is built for
 constexpr int kWarps = kBlock / 32;
 #ifndef SSSP_SMALL_DEG
 #define SSSP_SMALL_DEG 32
@@ -30,13 +34,22 @@ constexpr int kStage = 512;                 // per-warp staging slots for re-que
 constexpr uint32_t kMaxSamples = 4096;      // cap on the rho sampler's sample count
 constexpr uint64_t kInf = ~0ull;
 
-// Dynamic shared memory of the solve kernel: per warp kStage re-queue staging
-// slots; the rho sampler's keys reuse the same region at the start of a step
-// (the staging slots are empty between steps).  Kept small so that most of
-// the SM's unified L1/shared storage stays L1 cache.
+// Dynamic shared memory.  Per warp kStage re-queue staging slots (relaxation
+// phase); the rho sampler's keys reuse the same region at the start of a step
+// (the staging slots are empty between steps).
 constexpr uint32_t kStageBytes = kWarps * (uint32_t)kStage * 4u;        // 64 KB
-constexpr uint32_t kSolveDynSmem = kStageBytes;
-static_assert(kMaxSamples * 8u <= kStageBytes, "sample keys must fit the staging region");
+// Batched / serving kernels: staging (and the sampler's keys).
+constexpr uint32_t kBatchDynSmem = kStageBytes > kMaxSamples * 8u ? kStageBytes : kMaxSamples * 8u;
+// Single solve: Extract stages one round of up to kExtractCap queue entries
+// of the block's slice (a 16-byte record and a kind byte each) in the same
+// region (Extract, the sampler and the relaxation never overlap in time).
+#ifndef SSSP_EXTRACT_PER
+#define SSSP_EXTRACT_PER 4
+#endif
+constexpr int kExtractPer = SSSP_EXTRACT_PER;                           // entries per thread per round
+constexpr uint32_t kExtractCap = (uint32_t)kBlock * kExtractPer;        // 4096
+constexpr uint32_t kExtractBytes = kExtractCap * 16u + kExtractCap;     // 68 KB
+constexpr uint32_t kSolveDynSmem = kExtractBytes > kBatchDynSmem ? kExtractBytes : kBatchDynSmem;
 
 // Relaxation record written by Extract and read by the relaxation: a run of
 // at most kChunk out-edges of one extracted vertex u.  x,y = first edge index
@@ -61,6 +74,7 @@ struct Ctrl {
     unsigned long long ledges[3]; // edges relaxed by the local relaxation of super-sparse steps
     // totals, written by block 0 when the solve ends
     unsigned long long steps, queued, extracted, edges, updates_total;
+    unsigned long long t0;        // solve start on the device clock (block 0), the origin of trace times
 };
 
 struct SolveParams {

@@ -84,9 +84,34 @@ __device__ __forceinline__ uint64_t local_relax(uint64_t theta, uint32_t budget,
 }
 
 // ---------------------------------------------------------------------------
+// Block 0, one thread: add the counters of step `step` (ring slot `slot`) to
+// the solve's totals and to its trace record, then reset the slot for reuse.
+// Called during step step+1 (the slot is complete by then and is not written
+// again before step step+2), and once more when the loop ends.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void fold_step(const SolveParams& p, Ctrl* ctrl, int slot, uint64_t step)
+{
+    if (step >= 1) {
+        const uint32_t qq = ldcg32(&ctrl->qsize[slot]);
+        const uint32_t ff = ldcg32(&ctrl->fcount[slot]);
+        const uint64_t ee = ldcg64((const uint64_t*)&ctrl->fedges[slot]);
+        const uint64_t uu = ldcg64((const uint64_t*)&ctrl->updates[slot]);
+        const uint64_t le = ldcg64((const uint64_t*)&ctrl->ledges[slot]);
+        ctrl->queued += qq; ctrl->extracted += ff; ctrl->edges += ee + le; ctrl->updates_total += uu;
+        if (p.trace && step - 1 < p.trace_cap) {
+            sssp_step_trace* rec = &p.trace[step - 1];  // theta and times are written during the step
+            rec->queued = qq; rec->extracted = ff; rec->edges = ee + le; rec->updates = uu;
+        }
+    }
+    ctrl->qsize[slot] = 0; ctrl->fsmall[slot] = 0; ctrl->fchunk[slot] = 0; ctrl->fcount[slot] = 0;
+    ctrl->fedges[slot] = 0; ctrl->updates[slot] = 0; ctrl->qmin[slot] = kInf; ctrl->umin[slot] = kInf;
+    ctrl->ledges[slot] = 0;
+}
+
+// ---------------------------------------------------------------------------
 // The persistent solve kernel
 // ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(kBlock, 1) solve_kernel(SolveParams p)
+__global__ void __launch_bounds__(kBlock, kMinBlocks) solve_kernel(SolveParams p)
 {
     extern __shared__ __align__(16) unsigned char s_dyn[];
     uint32_t* s_stage = reinterpret_cast<uint32_t*>(s_dyn);  // [kWarps][kStage]
@@ -100,16 +125,11 @@ __global__ void __launch_bounds__(kBlock, 1) solve_kernel(SolveParams p)
     const uint32_t n = p.n;
     const uint64_t gthreads = (uint64_t)gridDim.x * kBlock;
     const uint64_t gtid = (uint64_t)blockIdx.x * kBlock + tid;
-    const uint32_t gwarp = blockIdx.x * kWarps + wid;
-    const uint32_t nwarps = gridDim.x * kWarps;
     Ctrl* ctrl = p.ctrl;
     uint64_t* dist = p.dist;
     uint32_t* inq = p.inq;
     __shared__ unsigned long long s_bar_target;   // thread 0: barrier arrivals expected so far
     __shared__ unsigned long long s_t_start;      // solve start (globaltimer)
-    __shared__ unsigned long long s_prev_theta;   // block 0: theta of the previous step (trace)
-    __shared__ unsigned long long s_prev_t;       // block 0: start time of the previous step (trace)
-    __shared__ unsigned long long s_prev_tr;      // block 0: start of the previous step's relaxation
     const uint64_t* __restrict__ off = p.off;
     const uint2* __restrict__ edges = p.edges;
     const uint4* __restrict__ pairs = reinterpret_cast<const uint4*>(p.edges);
@@ -119,9 +139,6 @@ __global__ void __launch_bounds__(kBlock, 1) solve_kernel(SolveParams p)
         s_err = 0;
         s_bar_target = 0;
         s_t_start = global_timer_ns();
-        s_prev_theta = 0;
-        s_prev_t = 0;
-        s_prev_tr = 0;
     }
 
     // ---- init: delta <- inf, delta[s] <- 0, Q.Update(s) (Algorithm 1) ----
@@ -138,6 +155,7 @@ __global__ void __launch_bounds__(kBlock, 1) solve_kernel(SolveParams p)
             p.trace[i].t_relax_end_max = 0;
         }
     if (blockIdx.x == 0 && tid == 0) {
+        ctrl->t0 = s_t_start;
         p.qa[0] = p.source;
         ctrl->qsize[1] = 1;
         ctrl->qmin[0] = kInf;
@@ -148,61 +166,59 @@ __global__ void __launch_bounds__(kBlock, 1) solve_kernel(SolveParams p)
         ctrl->umin[2] = kInf;
     }
     if (p.exit_block != 0 && blockIdx.x == p.exit_block - 1) return;  // fault-injection test
-    if (!grid_sync(&ctrl->bar, &ctrl->status, &s_bar_target, p.timeout_ns)) return;
+    const bool started = grid_sync_err(&ctrl->bar, &ctrl->status, &s_bar_target, p.timeout_ns);
+    if (tid == 0) s_t_start = ldcg64((const uint64_t*)&ctrl->t0);  // one time origin for every block
+    __syncthreads();
 
     uint64_t delta_i = 1;          // Delta*- / Delta-Stepping bucket index (Table 2)
     uint64_t prev_theta = 0;       // theta of the previous step (Delta-Stepping FinishCheck)
     uint32_t dense_seen = 0;       // rho-Stepping: dense steps so far (Sec. 6)
 
     uint64_t k = 1;
-    for (;; ++k) {
+    for (; started; ++k) {
         const int c = (int)(k % 3), nx = (int)((k + 1) % 3), pv = (int)((k + 2) % 3);
         const uint32_t* Qcur = (k & 1) ? p.qa : p.qb;
         uint32_t* Qnext = (k & 1) ? p.qb : p.qa;
+        // the step's inputs, loaded together: |Q_k|, min_Q delta, and the
+        // smallest distance the previous step wrote
         uint32_t q = ldcg32(&ctrl->qsize[c]);
+        const uint64_t qmin_c = algo_tracks_qmin(p.algo) ? ldcg64((const uint64_t*)&ctrl->qmin[c]) : kInf;
+        const uint64_t umin_c = p.algo == SSSP_DELTA ? ldcg64((const uint64_t*)&ctrl->umin[c]) : kInf;
         q = q < n ? q : n;  // a capacity fault is reported via status; never read past a list
 
-        if (blockIdx.x == 0 && tid == 0) {
-            // step k-1 is complete: fold its counters into the totals and
-            // recycle its slot for Q_{k+2}.
-            if (k > 1) {
-                const uint32_t qq = ldcg32(&ctrl->qsize[pv]);
-                const uint32_t ff = ldcg32(&ctrl->fcount[pv]);
-                const uint64_t ee = ldcg64((const uint64_t*)&ctrl->fedges[pv]);
-                const uint64_t uu = ldcg64((const uint64_t*)&ctrl->updates[pv]);
-                const uint64_t le = ldcg64((const uint64_t*)&ctrl->ledges[pv]);
-                ctrl->queued += qq; ctrl->extracted += ff; ctrl->edges += ee + le; ctrl->updates_total += uu;
-                if (p.trace && k - 2 < p.trace_cap) {
-                    sssp_step_trace* rec = &p.trace[k - 2];  // time extremes are filled by all blocks
-                    rec->theta = s_prev_theta; rec->queued = qq; rec->extracted = ff;
-                    rec->edges = ee + le; rec->updates = uu; rec->t_ns = s_prev_t; rec->t_relax_ns = s_prev_tr;
-                }
-            }
-            s_prev_t = global_timer_ns() - s_t_start;
-            ctrl->qsize[pv] = 0; ctrl->fsmall[pv] = 0; ctrl->fchunk[pv] = 0; ctrl->fcount[pv] = 0;
-            ctrl->fedges[pv] = 0; ctrl->updates[pv] = 0; ctrl->qmin[pv] = kInf; ctrl->umin[pv] = kInf;
-            ctrl->ledges[pv] = 0;
-        }
-        if (q == 0) break;
-        if (p.max_steps != 0 && k > p.max_steps) {
-            if (blockIdx.x == 0 && tid == 0) set_status(&ctrl->status, SSSP_ERR_INTERNAL);
+        if (q == 0) {
+            if (blockIdx.x == 0 && tid == 0) fold_step(p, ctrl, pv, k - 1);
             break;
         }
-        // whole-solve time guard: block 0 records it; every block leaves at the
-        // next barrier
-        if (blockIdx.x == 0 && tid == 0 && global_timer_ns() - s_t_start > p.solve_timeout_ns)
-            set_status(&ctrl->status, SSSP_ERR_TIMEOUT);
+        if (p.max_steps != 0 && k > p.max_steps) {
+            if (blockIdx.x == 0 && tid == 0) {
+                fold_step(p, ctrl, pv, k - 1);
+                raise_error(&ctrl->bar, &ctrl->status, SSSP_ERR_INTERNAL);
+            }
+            break;
+        }
+        const uint32_t gwarp = blockIdx.x * kWarps + wid;
+        const uint32_t nwarps = gridDim.x * kWarps;
+        if (blockIdx.x == 0 && tid == 0) {
+            const unsigned long long now = global_timer_ns() - s_t_start;
+            if (p.trace && k - 1 < p.trace_cap) p.trace[k - 1].t_ns = now;
+            // whole-solve time guard: block 0 records it; every block leaves at
+            // the next barrier
+            if (now > p.solve_timeout_ns) raise_error(&ctrl->bar, &ctrl->status, SSSP_ERR_TIMEOUT);
+        }
 
         // ---------------- ExtDist ----------------
         uint64_t theta;
+        bool rho_sample = false;  // rho-Stepping with q > rho': theta from samples
+        uint32_t s_cnt = 0, r_idx = 0;
         if (p.algo == SSSP_BELLMAN_FORD) {
             theta = kInf;
         } else if (p.algo == SSSP_DELTA_STAR || p.algo == SSSP_DELTA) {
-            const uint64_t qmin = ldcg64((const uint64_t*)&ctrl->qmin[c]);
+            const uint64_t qmin = qmin_c;
             if (p.algo == SSSP_DELTA && k > 1) {
                 // FinishCheck: advance the bucket unless the previous step
                 // wrote a distance below its threshold
-                const uint64_t umin = ldcg64((const uint64_t*)&ctrl->umin[c]);
+                const uint64_t umin = umin_c;
                 if (!(umin < prev_theta)) delta_i += 1;
             }
             uint64_t cur = delta_i;
@@ -214,67 +230,121 @@ __global__ void __launch_bounds__(kBlock, 1) solve_kernel(SolveParams p)
             delta_i = p.algo == SSSP_DELTA_STAR ? cur + 1 : cur;
             prev_theta = theta;
         } else if (p.algo == SSSP_DIJKSTRA) {
-            theta = ldcg64((const uint64_t*)&ctrl->qmin[c]);  // min over Q (Table 2)
+            theta = qmin_c;  // min over Q (Table 2)
         } else {
-            theta = rho_extdist_block(Qcur, q, dist, n, p.param, p.seed, k, dense_seen, s_keys,
-                                      p.sample_cap, &s_err);
+            // rho-Stepping: theta is selected from s sampled keys in the first
+            // Extract round below, with that round's loads in flight
+            theta = kInf;
+            rho_sample = rho_sample_plan(q, n, p.param, dense_seen, &s_cnt, &r_idx);
             if ((uint64_t)q * 20ull > (uint64_t)n) ++dense_seen;
-            if (s_err) {
-                if (tid == 0) set_status(&ctrl->status, SSSP_ERR_INTERNAL);
-            }
         }
-        if (blockIdx.x == 0 && tid == 0) s_prev_theta = theta;
 
         // ---------------- Extract(theta) ----------------
-        // kept ids -> next queue list; extracted ids -> relaxation records
+        // Each block takes a contiguous slice of Q_k and processes it in rounds
+        // of at most kExtractCap entries staged in shared memory: (1) ids and
+        // keys are loaded with every load of the round in flight; (2) the
+        // extracted ids leave Q (queue bit cleared) and their edge ranges are
+        // read; (3) one block scan and one atomic per output list reserve the
+        // block's output ranges; (4) the staged records are written out.
+        // Kept ids -> next queue list; extracted ids -> relaxation records
         // (degree <= kSmallDeg: one record in fsmall; larger: one record per
         // kChunk-aligned run of its edges in items).
         {
+            uint4* s_rec = reinterpret_cast<uint4*>(s_dyn);                      // [kExtractCap]
+            uint8_t* s_kind = s_dyn + (size_t)kExtractCap * sizeof(uint4);      // [kExtractCap]
+            enum : uint8_t { kNone = 0, kKeep = 1, kSmall = 2, kChunked = 3, kNoEdges = 4 };
             uint64_t l_fcount = 0, l_fedges = 0, l_kmin = kInf;
-            const uint64_t tile = (uint64_t)kBlock * kExtractItems;
-            for (uint64_t base = (uint64_t)blockIdx.x * tile; base < q; base += (uint64_t)gridDim.x * tile) {
-                uint32_t v[kExtractItems];
-                uint64_t d[kExtractItems];
-                uint32_t kind[kExtractItems];  // 0 none, 1 keep, 2 small, 3 chunked, 4 extracted w/o edges
+            const uint64_t slo = (uint64_t)q * blockIdx.x / gridDim.x;
+            const uint64_t shi = (uint64_t)q * (blockIdx.x + 1) / gridDim.x;
+            // every block runs the first round (possibly empty) so that every
+            // block knows theta
+            for (uint64_t r0 = slo; r0 < shi || r0 == slo; r0 += kExtractCap) {
+                const uint32_t L = (uint32_t)(r0 >= shi ? 0 : (shi - r0) < kExtractCap ? (shi - r0) : kExtractCap);
+                const bool select_now = rho_sample && r0 == slo;
+                const bool sel_in_regs = select_now && s_cnt <= (uint32_t)kBlock;
+                // (1) ids, keys, and the keep / extract decision
+                uint32_t extm = 0;  // bit j: entry j of this thread is extracted
+                {
+                    uint32_t v[kExtractPer];
+                    uint64_t d[kExtractPer];
+                    uint32_t sid = 0;
+                    if (sel_in_regs && tid < s_cnt) sid = ldcg32(&Qcur[rho_sample_pos(p.seed, k, tid, q)]);
 #pragma unroll
-                for (int j = 0; j < kExtractItems; ++j) {
-                    const uint64_t idx = base + (uint64_t)j * kBlock + tid;
-                    v[j] = idx < q ? ldcg32(&Qcur[idx]) : 0u;
-                }
+                    for (int j = 0; j < kExtractPer; ++j) {
+                        const uint32_t i = tid + (uint32_t)j * kBlock;
+                        v[j] = i < L ? ldcg32(&Qcur[r0 + i]) : 0u;
+                    }
+                    uint64_t skey = kInf;
+                    if (sel_in_regs && tid < s_cnt) skey = ldcg64(&dist[sid]);
 #pragma unroll
-                for (int j = 0; j < kExtractItems; ++j) {
-                    const uint64_t idx = base + (uint64_t)j * kBlock + tid;
-                    d[j] = idx < q ? ldcg64(&dist[v[j]]) : kInf;
-                }
-                uint32_t nkeep = 0, nsmall = 0, nchunks = 0;
+                    for (int j = 0; j < kExtractPer; ++j) {
+                        const uint32_t i = tid + (uint32_t)j * kBlock;
+                        d[j] = i < L ? ldcg64(&dist[v[j]]) : kInf;
+                    }
+                    if (select_now) {
+                        // ExtDist of rho-Stepping (Table 2; Sec. 6; App. B)
+                        if (!sel_in_regs) {
+                            for (uint32_t j = tid; j < s_cnt; j += kBlock)
+                                s_keys[j] = ldcg64(&dist[ldcg32(&Qcur[rho_sample_pos(p.seed, k, j, q)])]);
+                            __syncthreads();
+                        }
+                        theta = block_select(skey, s_cnt, r_idx, s_keys, p.sample_cap, &s_err);
+                        if (s_err && tid == 0) raise_error(&ctrl->bar, &ctrl->status, SSSP_ERR_INTERNAL);
+                    }
 #pragma unroll
-                for (int j = 0; j < kExtractItems; ++j) {
-                    const uint64_t idx = base + (uint64_t)j * kBlock + tid;
-                    kind[j] = 0;
-                    if (idx < q) {
+                    for (int j = 0; j < kExtractPer; ++j) {
+                        const uint32_t i = tid + (uint32_t)j * kBlock;
+                        if (i >= L) continue;
                         if (d[j] <= theta) {
                             atomicAnd(&inq[v[j] >> 5], ~(1u << (v[j] & 31u)));
-                            const uint64_t b = __ldg(&off[v[j]]);
-                            const uint64_t e = __ldg(&off[v[j] + 1]);
-                            const uint64_t deg = e - b;
-                            l_fcount += 1;
-                            l_fedges += deg;
-                            if (p.ext_count) p.ext_count[v[j]] += 1u;
-                            if (deg == 0) {
-                                kind[j] = 4;
-                            } else if (deg <= kSmallDeg) {
-                                kind[j] = 2; ++nsmall;
-                            } else {
-                                kind[j] = 3;
-                                nchunks += (uint32_t)((e - 1) / kChunk - b / kChunk + 1);
-                            }
+                            extm |= 1u << j;
+                            s_rec[i] = make_uint4(v[j], (uint32_t)d[j], (uint32_t)(d[j] >> 32), 0u);
                         } else {
-                            kind[j] = 1; ++nkeep;
+                            s_rec[i].x = v[j];
                             l_kmin = d[j] < l_kmin ? d[j] : l_kmin;
                         }
                     }
                 }
-                // block scan of (keep, small, chunks) packed 16|16|32 bits
+                // (2) edge ranges of the extracted ids
+                uint32_t nkeep = 0, nsmall = 0, nchunks = 0;
+                {
+                    uint64_t b[kExtractPer], e[kExtractPer];
+#pragma unroll
+                    for (int j = 0; j < kExtractPer; ++j) {
+                        const uint32_t i = tid + (uint32_t)j * kBlock;
+                        b[j] = 0; e[j] = 0;
+                        if ((extm >> j) & 1u) {
+                            const uint32_t u = s_rec[i].x;
+                            b[j] = __ldg(&off[u]);
+                            e[j] = __ldg(&off[u + 1]);
+                        }
+                    }
+#pragma unroll
+                    for (int j = 0; j < kExtractPer; ++j) {
+                        const uint32_t i = tid + (uint32_t)j * kBlock;
+                        if (i >= L) continue;
+                        if (!((extm >> j) & 1u)) { ++nkeep; continue; }
+                        const uint4 r = s_rec[i];
+                        const uint64_t deg = e[j] - b[j];
+                        l_fcount += 1;
+                        l_fedges += deg;
+                        if (p.ext_count) p.ext_count[r.x] += 1u;
+                        if (deg == 0) {
+                            s_kind[i] = kNoEdges;
+                        } else if (deg <= kSmallDeg) {
+                            s_kind[i] = kSmall;
+                            s_rec[i] = make_rec(b[j], deg, (uint64_t)r.y | ((uint64_t)r.z << 32));
+                            ++nsmall;
+                        } else {
+                            s_kind[i] = kChunked;
+                            s_rec[i] = make_uint4(r.x, (uint32_t)b[j], (uint32_t)(b[j] >> 32),
+                                                  deg < 0xFFFFFFFFull ? (uint32_t)deg : 0xFFFFFFFFu);
+                            nchunks += (uint32_t)((e[j] - 1) / kChunk - b[j] / kChunk + 1);
+                        }
+                    }
+                }
+                // (3) block scan of the (keep, small, chunks) counts, packed
+                //     16|16|32 bits; one atomic per output list
                 const uint64_t packed = (uint64_t)nkeep | ((uint64_t)nsmall << 16) | ((uint64_t)nchunks << 32);
                 uint64_t tot;
                 const uint64_t ex = block_excl_scan64(packed, s_tmp, &tot);
@@ -286,38 +356,45 @@ __global__ void __launch_bounds__(kBlock, 1) solve_kernel(SolveParams p)
                     s_base[2] = tc ? atomicAdd(&ctrl->fchunk[c], tc) : 0u;
                     if ((uint64_t)s_base[0] + tk > n || (uint64_t)s_base[1] + ts > p.fsmall_cap ||
                         (uint64_t)s_base[2] + tc > p.item_cap)
-                        set_status(&ctrl->status, SSSP_ERR_INTERNAL);
+                        raise_error(&ctrl->bar, &ctrl->status, SSSP_ERR_INTERNAL);
                 }
                 __syncthreads();
                 uint32_t pk = s_base[0] + (uint32_t)(ex & 0xFFFFu);
                 uint64_t ps = (uint64_t)s_base[1] + ((ex >> 16) & 0xFFFFu);
                 uint64_t pc = (uint64_t)s_base[2] + (ex >> 32);
+                // (4) write the staged entries
 #pragma unroll
-                for (int j = 0; j < kExtractItems; ++j) {
-                    uint64_t bj = 0, ej = 0;  // edge range again (L1-resident since the classification)
-                    if (kind[j] >= 2) { bj = __ldg(&off[v[j]]); ej = __ldg(&off[v[j] + 1]); }
-                    const uint64_t nch = kind[j] == 3 ? (ej - 1) / kChunk - bj / kChunk + 1 : 0;
-                    if (kind[j] == 1) {
-                        if (pk < n) Qnext[pk] = v[j];
+                for (int j = 0; j < kExtractPer; ++j) {
+                    const uint32_t i = tid + (uint32_t)j * kBlock;
+                    const uint8_t kd = i < L ? (((extm >> j) & 1u) ? s_kind[i] : (uint8_t)kKeep) : (uint8_t)kNone;
+                    const uint4 r = (kd == kKeep || kd == kSmall || kd == kChunked) ? s_rec[i] : make_uint4(0, 0, 0, 0);
+                    uint64_t bj = 0, ej = 0;
+                    if (kd == kChunked) {
+                        bj = (uint64_t)r.y | ((uint64_t)r.z << 32);
+                        ej = r.w != 0xFFFFFFFFu ? bj + r.w : __ldg(&off[r.x + 1]);
+                    }
+                    const uint64_t nch = kd == kChunked ? (ej - 1) / kChunk - bj / kChunk + 1 : 0;
+                    if (kd == kKeep) {
+                        if (pk < n) Qnext[pk] = r.x;
                         ++pk;
-                    } else if (kind[j] == 2) {
-                        if (ps < p.fsmall_cap) p.fsmall[ps] = make_rec(bj, ej - bj, d[j]);
+                    } else if (kd == kSmall) {
+                        if (ps < p.fsmall_cap) p.fsmall[ps] = r;
                         ++ps;
-                    } else if (kind[j] == 3 && nch <= 4) {
+                    } else if (kd == kChunked && nch <= 4) {
                         for (uint64_t c0 = bj / kChunk * kChunk; c0 < ej; c0 += kChunk, ++pc) {
                             const uint64_t cs = bj > c0 ? bj : c0;
                             const uint64_t ce = ej < c0 + kChunk ? ej : c0 + kChunk;
-                            if (pc < p.item_cap) p.items[pc] = make_rec(cs, ce - cs, v[j]);
+                            if (pc < p.item_cap) p.items[pc] = make_rec(cs, ce - cs, r.x);
                         }
                     }
                     // vertices with many chunks: the whole warp writes their records
-                    uint32_t many = __ballot_sync(FULL_MASK, kind[j] == 3 && nch > 4);
+                    uint32_t many = __ballot_sync(FULL_MASK, kd == kChunked && nch > 4);
                     while (many) {
                         const int src = __ffs(many) - 1;
                         many &= many - 1;
                         const uint64_t sb = __shfl_sync(FULL_MASK, bj, src);
                         const uint64_t se = __shfl_sync(FULL_MASK, ej, src);
-                        const uint32_t sv = __shfl_sync(FULL_MASK, v[j], src);
+                        const uint32_t sv = __shfl_sync(FULL_MASK, r.x, src);
                         const uint64_t sp = __shfl_sync(FULL_MASK, pc, src);
                         const uint64_t sn = (se - 1) / kChunk - sb / kChunk + 1;
                         for (uint64_t t = lane; t < sn; t += 32) {
@@ -327,10 +404,11 @@ __global__ void __launch_bounds__(kBlock, 1) solve_kernel(SolveParams p)
                             if (sp + t < p.item_cap) p.items[sp + t] = make_rec(cs, ce - cs, sv);
                         }
                     }
-                    if (kind[j] == 3 && nch > 4) pc += nch;
+                    if (kd == kChunked && nch > 4) pc += nch;
                 }
-                __syncthreads();  // s_tmp / s_base reuse
+                __syncthreads();  // s_tmp / s_base / staging reuse
             }
+            if (blockIdx.x == 0 && tid == 0 && p.trace && k - 1 < p.trace_cap) p.trace[k - 1].theta = theta;
             uint64_t bf = l_fcount, be = l_fedges, bm = l_kmin;
             block_reduce_2add_min(bf, be, bm, s_tmp);
             if (tid == 0) {
@@ -341,11 +419,17 @@ __global__ void __launch_bounds__(kBlock, 1) solve_kernel(SolveParams p)
         }
         if (p.trace && tid == 0 && k - 1 < p.trace_cap)
             atomicMax((unsigned long long*)&p.trace[k - 1].t_extract_end_max, global_timer_ns() - s_t_start);
-        if (!grid_sync(&ctrl->bar, &ctrl->status, &s_bar_target, p.timeout_ns)) return;
+        if (!grid_sync_err(&ctrl->bar, &ctrl->status, &s_bar_target, p.timeout_ns)) break;
 
         // ---------------- relax the out-edges of F ----------------
-        if (blockIdx.x == 0 && tid == 0) s_prev_tr = global_timer_ns() - s_t_start;
+        if (blockIdx.x == 0 && tid == 0 && p.trace && k - 1 < p.trace_cap)
+            p.trace[k - 1].t_relax_ns = global_timer_ns() - s_t_start;
         {
+            // the warp's first records are loaded together with the record
+            // counts (within the arrays' capacity; used only if below the count)
+            const uint64_t i_first = (uint64_t)gwarp * 32u + lane;
+            const uint4 spec_small = i_first < p.fsmall_cap ? __ldcg(&p.fsmall[i_first]) : make_uint4(0, 0, 0, 0);
+            const uint4 spec_chunk = gwarp < p.item_cap ? __ldcg(&p.items[gwarp]) : make_uint4(0, 0, 0, 0);
             uint64_t fs = ldcg32(&ctrl->fsmall[c]);
             fs = fs < p.fsmall_cap ? fs : p.fsmall_cap;
             uint64_t fc = ldcg32(&ctrl->fchunk[c]);
@@ -357,8 +441,7 @@ __global__ void __launch_bounds__(kBlock, 1) solve_kernel(SolveParams p)
             // (a) low-degree vertices: 32 records per warp, edges flattened across lanes
             const uint64_t ngroups = (fs + 31u) >> 5;
             uint64_t g = gwarp;
-            uint4 rnext = make_uint4(0, 0, 0, 0);
-            if (g < ngroups && g * 32u + lane < fs) rnext = __ldcg(&p.fsmall[g * 32u + lane]);
+            uint4 rnext = (g < ngroups && i_first < fs) ? spec_small : make_uint4(0, 0, 0, 0);
             for (; g < ngroups; g += nwarps) {
                 const uint4 rec = rnext;
                 const uint64_t gn = g + nwarps;  // prefetch the next group's records
@@ -374,7 +457,7 @@ __global__ void __launch_bounds__(kBlock, 1) solve_kernel(SolveParams p)
             //     relaxation time; the freshest value wastes the fewest relaxations)
             {
                 uint64_t it = gwarp;
-                uint4 rn = it < fc ? __ldcg(&p.items[it]) : make_uint4(0, 0, 0, 0);
+                uint4 rn = it < fc ? spec_chunk : make_uint4(0, 0, 0, 0);
                 for (; it < fc; it += nwarps) {
                     const uint4 rc = rn;
                     const uint64_t nit = it + nwarps;
@@ -402,13 +485,20 @@ __global__ void __launch_bounds__(kBlock, 1) solve_kernel(SolveParams p)
             // (c) block-aggregated flush of what is left in the warps' staging
             if (lane == 0) s_wcnt[wid] = stc;
             __syncthreads();
-            if (tid == 0) {
-                uint32_t tot = 0;
-                for (int w = 0; w < kWarps; ++w) { const uint32_t cnt = s_wcnt[w]; s_wcnt[w] = tot; tot += cnt; }
-                uint32_t base = tot ? atomicAdd(&ctrl->qsize[nx], tot) : 0u;
-                if ((uint64_t)base + tot > (uint64_t)n) { set_status(&ctrl->status, SSSP_ERR_INTERNAL); tot = 0; }
-                s_base[0] = base;
-                s_base[1] = tot;
+            if (wid == 0) {
+                const uint32_t cnt = lane < (uint32_t)kWarps ? s_wcnt[lane] : 0u;
+                const uint32_t incl = (uint32_t)warp_incl_scan64(cnt, lane);
+                uint32_t tot = __shfl_sync(FULL_MASK, incl, 31);
+                if (lane < (uint32_t)kWarps) s_wcnt[lane] = incl - cnt;
+                if (lane == 0) {
+                    const uint32_t base = tot ? atomicAdd(&ctrl->qsize[nx], tot) : 0u;
+                    if ((uint64_t)base + tot > (uint64_t)n) { raise_error(&ctrl->bar, &ctrl->status, SSSP_ERR_INTERNAL); tot = 0; }
+                    s_base[0] = base;
+                    s_base[1] = tot;
+                }
+                // step k-1 is complete: fold its counters into the totals and
+                // recycle its slot (reused for Q_{k+2} from the next step on)
+                if (blockIdx.x == 0 && lane == 0) fold_step(p, ctrl, pv, k - 1);
             }
             __syncthreads();
             if (s_base[1] != 0) {
@@ -431,7 +521,7 @@ __global__ void __launch_bounds__(kBlock, 1) solve_kernel(SolveParams p)
                 }
             }
         }
-        if (!grid_sync(&ctrl->bar, &ctrl->status, &s_bar_target, p.timeout_ns)) return;
+        if (!grid_sync_err(&ctrl->bar, &ctrl->status, &s_bar_target, p.timeout_ns)) break;
     }
 
     if (blockIdx.x == 0 && tid == 0) {

@@ -109,6 +109,7 @@ typedef struct {
                                 them in that step.  The distances are the same;
                                 steps, edges and updates change (edges then counts the
                                 local relaxations too).                                  */
+    uint32_t shape;          /* kernel shape, SSSP_SHAPE_*; the distances do not depend on it */
 } sssp_options;
 
 /* sssp_options.flags */
@@ -119,6 +120,14 @@ typedef struct {
                                        the usual Update).  Needs a graph created with
                                        SSSP_GRAPH_SYMMETRIC (INVALID_ARG otherwise).  Applied to
                                        vertices of degree > 32.                                 */
+
+/* sssp_options.shape: thread-block shape of the persistent solve kernel.  WIDE
+   keeps the most memory operations in flight (best when steps relax many
+   edges); NARROW has fewer threads with more registers each, so the per-step
+   block-wide work is cheaper (best when a solve takes thousands of small
+   steps, e.g. road-like graphs).  sssp_autotune measures both. */
+#define SSSP_SHAPE_WIDE 0u   /* 1024 threads per block, one block per SM (default) */
+#define SSSP_SHAPE_NARROW 1u /* 512 threads per block, one block per SM            */
 
 /* sssp_graph_create_ex flags */
 #define SSSP_GRAPH_SYMMETRIC 1u     /* every edge (u,v,w) has its reverse (v,u,w)         */
@@ -361,6 +370,55 @@ int sssp_server_destroy(sssp_server* s);
 int sssp_solve_noalloc(uint32_t n, uint64_t m, const uint64_t* offsets, const uint32_t* edges,
                        uint32_t source, sssp_algo algo, uint64_t param, uint64_t* dist_out,
                        sssp_stats* stats_out, void* stream);
+
+/* ------------------------------------------------------------------------ */
+/* Autotuner.  (The paper fixes rho per graph family -- 2^21 for social and  */
+/* web graphs, 2^15 for road networks, Sec. 7 -- and sweeps it; this library */
+/* measures instead.)                                                       */
+/* ------------------------------------------------------------------------ */
+
+/* A solve configuration: the ExtDist rule and its parameter (Table 2), the
+   kernel shape, the SSSP_SOLVE_* flags and the local-relaxation budget
+   (sssp_options).  The distances do not depend on it. */
+typedef struct {
+    sssp_algo algo;          /* SSSP_RHO or SSSP_DELTA_STAR (or SSSP_BELLMAN_FORD)          */
+    uint32_t shape;          /* SSSP_SHAPE_*                                                */
+    uint64_t param;          /* rho or Delta                                                */
+    uint32_t flags;          /* SSSP_SOLVE_* (bidirectional relaxation on symmetric graphs) */
+    uint32_t local_budget;   /* sssp_options.local_budget                                   */
+    double ms;               /* autotuner: mean solve time of the choice on the samples     */
+    uint32_t candidates;     /* autotuner: configurations timed                             */
+    uint32_t reserved;
+} sssp_tuning;
+
+/*
+ * Time candidate configurations on the k sample sources (HOST uint32[k], each
+ * < n) and keep the fastest: rho in {n/4, n/16, ..., n/1024} (at least 64) and
+ * Delta in mean-weight x {1/8, 1/2, 2, 8} in the wide shape on the first
+ * source; the two best in both shapes on two sources; on graphs with mean
+ * out-degree < 20 the three best rules/parameters in the winning shape with
+ * local budgets 64, 256, 1024; the winner is re-timed on all k sources.  Bidirectional relaxation is used when the graph
+ * was created SSSP_GRAPH_SYMMETRIC.  The result is stored on the graph and in
+ * a per-class table (sssp_graph_class) that sssp_solve_tuned, sssp_solve_sources,
+ * sssp_solve_multi (params == NULL) and the server (param == 0) use for graphs
+ * of the same class that were not tuned themselves.  Synchronous on `stream`;
+ * allocates a temporary distance array.  out may be NULL.
+ */
+int sssp_autotune(sssp_graph* g, const uint32_t* sources, uint32_t k, sssp_tuning* out, void* stream);
+
+/* The tuning that applies to g (its own, else its class's); INVALID_ARG when none. */
+int sssp_graph_get_tuning(const sssp_graph* g, sssp_tuning* out);
+
+/* Attach a configuration to g (e.g. one tuned on another graph). */
+int sssp_graph_set_tuning(sssp_graph* g, const sssp_tuning* t);
+
+/* Class key of a graph: bits 0-7 ceil(log2 n), 8-15 round(4 log2(m/n)),
+   16-23 floor(log2(max out-degree / mean out-degree)), bit 24 symmetric. */
+int sssp_graph_class(const sssp_graph* g, uint64_t* key);
+
+/* sssp_solve with the configuration that applies to g (sssp_graph_get_tuning),
+   else rho-Stepping with rho = max(64, n/16). */
+int sssp_solve_tuned(const sssp_graph* g, uint32_t source, uint64_t* dist_out, void* stream);
 
 /* Static description of a status code (never NULL). */
 const char* sssp_status_string(int status);

@@ -1,8 +1,8 @@
 """Build libsssp.so (the CUDA C-ABI library) in-tree with nvcc for sm_103a.
 
 Usage: ``python -m paper_2105_06145_gb300.build`` (or ``__graft_entry__.build()``).
-The two translation units compile in parallel; the result lands next to this
-file as ``libsssp.so``.
+The translation units (and the narrow-shape build of the solve kernel) compile
+in parallel; the result lands next to this file as ``libsssp.so``.
 """
 from __future__ import annotations
 
@@ -15,10 +15,11 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libsssp.so")
-SOURCES = ["sssp_kernels.cu", "sssp_api.cu", "sssp_noalloc.cu", "sssp_batch.cu"]
+SOURCES = ["sssp_kernels.cu", "sssp_api.cu", "sssp_noalloc.cu", "sssp_batch.cu", "sssp_tune.cu"]
 HEADERS = ["sssp_internal.h", "sssp_device.cuh", os.path.join("..", "..", "include", "sssp.h")]
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
+NARROW_FLAGS = ["-Dsssp=sssp_narrow", "-DSSSP_BLOCK=512"]
 NVCC_FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr",
               "-Xptxas", "-v"] + ARCH
 
@@ -50,10 +51,14 @@ def build(force: bool = False, verbose: bool = False, extra: list[str] | None = 
     cc = nvcc()
     procs = []
     objs = []
-    for s in SOURCES:
-        obj = os.path.join(bdir, s.replace(".cu", ".o"))
+    # (source, object, extra flags): the solve kernel is also built in its narrow
+    # shape, into its own namespace
+    units = [(s, s.replace(".cu", ".o"), []) for s in SOURCES]
+    units.append(("sssp_kernels.cu", "sssp_kernels_narrow.o", NARROW_FLAGS))
+    for s, o, fl in units:
+        obj = os.path.join(bdir, o)
         log = obj + ".log"
-        cmd = [cc, *NVCC_FLAGS, *(extra or []), "-c", os.path.join(CSRC, s), "-o", obj]
+        cmd = [cc, *NVCC_FLAGS, *(extra or []), *fl, "-c", os.path.join(CSRC, s), "-o", obj]
         procs.append((subprocess.Popen(cmd, stdout=open(log, "w"), stderr=subprocess.STDOUT), cmd, log))
         objs.append(obj)
     failed = False

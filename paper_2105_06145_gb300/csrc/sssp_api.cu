@@ -50,16 +50,31 @@ void free_graph(sssp_graph* g)
     delete g;
 }
 
-// blocks per SM of the solve kernel (its dynamic shared memory is fixed)
-int solve_blocks_per_sm(int* out)
+// The two builds of the solve kernel (sssp_kernels.cu compiled twice): the
+// wide shape (1024 threads, 64 registers each: the most loads in flight, for
+// edge-heavy steps) and the narrow one (512 threads, up to 128 registers:
+// cheaper block-wide phases, for graphs whose solves take many small steps).
+struct SolveShape {
+    const void* (*kernel)();
+    int (*threads)();
+    unsigned int (*smem)();
+};
+const SolveShape kShapes[2] = {
+    {sssp::solve_kernel_ptr, sssp::solve_kernel_threads, sssp::solve_kernel_smem},
+    {sssp_narrow::solve_kernel_ptr, sssp_narrow::solve_kernel_threads, sssp_narrow::solve_kernel_smem},
+};
+
+// blocks per SM of a shape of the solve kernel (its dynamic shared memory is fixed)
+int solve_blocks_per_sm(int shape, int* out)
 {
     static std::mutex mu;
     std::lock_guard<std::mutex> lk(mu);
-    const void* fn = solve_kernel_ptr();
-    cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSolveDynSmem);
+    const SolveShape& sh = kShapes[shape];
+    const void* fn = sh.kernel();
+    cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sh.smem());
     if (e != cudaSuccess) return cuda_fail(e);
     int bps = 0;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, fn, kBlock, kSolveDynSmem);
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, fn, sh.threads(), sh.smem());
     if (e != cudaSuccess) return cuda_fail(e);
     *out = bps;
     return SSSP_OK;
@@ -134,8 +149,10 @@ int sssp_graph_create_ex(uint32_t n, uint64_t m, const uint64_t* offsets, const 
     uint64_t small_cap = 0, item_cap = 0;
     unsigned __int128 wsum = 0;
     for (uint64_t e = 0; e < m; ++e) wsum += weights[e];
+    uint64_t max_deg = 0;
     for (uint32_t u = 0; u < n; ++u) {
         const uint64_t deg = offsets[u + 1] - offsets[u];
+        max_deg = deg > max_deg ? deg : max_deg;
         if (deg == 0) continue;
         if (deg <= kSmallDeg) ++small_cap;
         else item_cap += chunk_count(offsets[u], offsets[u + 1]);
@@ -156,6 +173,7 @@ int sssp_graph_create_ex(uint32_t n, uint64_t m, const uint64_t* offsets, const 
     uint32_t* d_w = nullptr;
     g->fsmall_cap = small_cap + 1;
     g->mean_w = m ? (double)wsum / (double)m : 1.0;
+    g->max_deg = max_deg;
     g->item_cap = item_cap + 1;
     if ((e = dalloc(&g->d_off, (uint64_t)n + 1)) != cudaSuccess ||
         (e = dalloc(&g->d_edges, m_alloc)) != cudaSuccess ||
@@ -247,15 +265,16 @@ int sssp_solve_ex(const sssp_graph* gc, uint32_t source, sssp_algo algo, uint64_
     if (o.local_budget != 0 && algo != SSSP_RHO && algo != SSSP_DELTA_STAR) return SSSP_ERR_INVALID_ARG;
     p.local_budget = o.local_budget;
     p.sample_cap = (algo == SSSP_RHO) ? rho_sample_bound(g->n, param) : 0;
-
-    const size_t dyn_smem = kSolveDynSmem;
+    if (o.shape > SSSP_SHAPE_NARROW) return SSSP_ERR_INVALID_ARG;
+    const int shape = o.shape == SSSP_SHAPE_NARROW ? 1 : 0;
+    const size_t dyn_smem = kShapes[shape].smem();
     int bps = 0;
     int rc;
     {
         std::lock_guard<std::mutex> lk(g->mu);
         cudaError_t e = cudaSetDevice(g->device);
         if (e != cudaSuccess) return cuda_fail(e);
-        rc = solve_blocks_per_sm(&bps);
+        rc = solve_blocks_per_sm(shape, &bps);
     }
     if (rc != SSSP_OK) return rc;
     if (bps < 1) return SSSP_ERR_CUDA;
@@ -268,7 +287,8 @@ int sssp_solve_ex(const sssp_graph* gc, uint32_t source, sssp_algo algo, uint64_
     cudaError_t e = cudaMemsetAsync(g->d_ctrl, 0, sizeof(Ctrl), st);
     if (e != cudaSuccess) return cuda_fail(e);
     void* args[] = {&p};
-    e = cudaLaunchCooperativeKernel(solve_kernel_ptr(), dim3(grid), dim3(kBlock), args, dyn_smem, st);
+    e = cudaLaunchCooperativeKernel(kShapes[shape].kernel(), dim3(grid), dim3(kShapes[shape].threads()), args,
+                                    dyn_smem, st);
     if (e != cudaSuccess) return cuda_fail(e);
     return SSSP_OK;
 }

@@ -125,6 +125,8 @@ inline uint64_t item_capacity_bound(uint64_t n, uint64_t m)
 cudaError_t launch_pack_edges(const uint32_t* tgt, const uint32_t* w, uint2* edges, uint64_t m,
                               uint64_t m_pad, cudaStream_t st);
 const void* solve_kernel_ptr();
+int solve_kernel_threads();             // threads per block of this build of the solve kernel
+unsigned int solve_kernel_smem();       // its dynamic shared memory per block
 cudaError_t launch_rho_threshold(const uint32_t* queue, uint32_t q, const uint64_t* dist,
                                  uint32_t n, uint64_t rho, uint64_t seed, uint64_t step,
                                  uint32_t dense_before, uint64_t* theta_out, uint32_t* err_out,
@@ -137,6 +139,14 @@ const void* batch_kernel_ptr();
 const void* serve_kernel_ptr();
 
 }  // namespace sssp
+
+// The narrow build of the solve kernel (sssp_kernels.cu compiled with
+// SSSP_BLOCK=512 into this namespace; SolveParams and Ctrl have the same layout).
+namespace sssp_narrow {
+const void* solve_kernel_ptr();
+int solve_kernel_threads();
+unsigned int solve_kernel_smem();
+}
 
 // Library-side state of one graph handle (host ABI and batched solves).
 struct sssp_graph {
@@ -159,7 +169,10 @@ struct sssp_graph {
     sssp::Ctrl* h_ctrl = nullptr;                // pinned readback
     uint32_t last_grid = 0;
     double mean_w = 1.0;                   // mean edge weight (default Delta)
+    uint64_t max_deg = 0;                  // largest out-degree (graph class)
     uint32_t flags = 0;                    // SSSP_GRAPH_* flags given at creation
+    bool tuned = false;                    // tuning holds an autotuner result (or a set one)
+    sssp_tuning tuning = {};
     std::mutex mu;                         // guards lazy allocations / attributes
 };
 
@@ -184,3 +197,10 @@ inline __host__ __device__ bool algo_needs_param(int algo)
 {
     return algo == SSSP_RHO || algo == SSSP_DELTA_STAR || algo == SSSP_DELTA;
 }
+
+// Autotuner results (sssp_tune.cu): the class key of a graph (log2 n, mean
+// degree, degree skew, symmetry), the tuning that applies to a graph (its own,
+// else its class's), and the parameter a call that passes none uses.
+uint64_t sssp_class_key(const sssp_graph* g);
+bool sssp_lookup_tuning(const sssp_graph* g, sssp_tuning* out);
+uint64_t sssp_graph_param(const sssp_graph* g, sssp_algo algo);

@@ -537,6 +537,8 @@ __global__ void __launch_bounds__(kBlock, kMinBlocks) solve_kernel(SolveParams p
 }
 
 const void* solve_kernel_ptr() { return reinterpret_cast<const void*>(&solve_kernel); }
+int solve_kernel_threads() { return kBlock; }
+unsigned int solve_kernel_smem() { return kSolveDynSmem; }
 
 // ---------------------------------------------------------------------------
 // Graph upload: pack (target, weight) pairs into 8-byte edge records.

@@ -1,0 +1,266 @@
+// sssp_tune.cu -- the autotuner of libsssp (host code).
+//
+// The paper fixes the parameter per graph family (rho = 2^21 for social and
+// web graphs, 2^15 for road networks; Sec. 7) and reports the best rho of a
+// sweep beside it.  This library measures instead: sssp_autotune times
+// candidate configurations of the one persistent solve kernel on sample
+// sources of the graph itself and keeps the fastest.  A configuration is an
+// ExtDist rule with its parameter (rho-Stepping or Delta*-Stepping, Table 2),
+// the kernel shape (SSSP_SHAPE_*), bidirectional relaxation (symmetric graphs,
+// Sec. 6) and the local-relaxation budget of super-sparse steps (Sec. 6).  The
+// distances never depend on the choice, only the time does.
+//
+// Search (every solve timed with CUDA events on the caller's stream):
+//   1. every rule/parameter candidate, wide shape, no local relaxation, on the
+//      first sample source;
+//   2. the two fastest of (1) in both shapes, on up to two sources;
+//   3. sparse graphs (mean out-degree < 20): the three fastest of (1), in
+//      the winning shape, with local budgets 64, 256 and 1024;
+//   4. the winner on every sample source (sssp_tuning.ms).
+// The result is kept on the graph handle and in a per-class table (graph class
+// = size, mean degree, degree skew and symmetry; sssp_graph_class), which
+// sssp_solve_tuned and the batched and serving calls consult for graphs that
+// were not tuned themselves.
+#include <cmath>
+#include <cstdint>
+#include <cstring>
+#include <map>
+#include <mutex>
+#include <vector>
+#include <cuda_runtime.h>
+
+#include "sssp_internal.h"
+
+namespace {
+
+std::mutex g_class_mu;
+std::map<uint64_t, sssp_tuning> g_class_table;
+
+int fail(cudaError_t e) { return e == cudaErrorMemoryAllocation ? SSSP_ERR_OUT_OF_MEMORY : SSSP_ERR_CUDA; }
+
+uint32_t ceil_log2(uint64_t x)
+{
+    uint32_t l = 0;
+    while ((1ull << l) < x && l < 63) ++l;
+    return l;
+}
+
+struct Candidate {
+    sssp_algo algo;
+    uint64_t param;
+    uint32_t shape;
+    uint32_t local;
+    double ms;
+};
+
+// Mean time of one solve per source (ms); a failed solve is reported as rc.
+int time_config(const sssp_graph* g, const Candidate& c, const uint32_t* srcs, uint32_t ns, uint64_t* dist,
+                cudaStream_t st, cudaEvent_t e0, cudaEvent_t e1, double* ms_out)
+{
+    sssp_options o;
+    memset(&o, 0, sizeof o);
+    o.flags = (g->flags & SSSP_GRAPH_SYMMETRIC) ? SSSP_SOLVE_BIDIRECTIONAL : 0u;
+    o.shape = c.shape;
+    o.local_budget = c.local;
+    double total = 0;
+    for (uint32_t i = 0; i < ns; ++i) {
+        cudaError_t e = cudaEventRecord(e0, st);
+        if (e != cudaSuccess) return fail(e);
+        int rc = sssp_solve_ex(g, srcs[i], c.algo, c.param, dist, &o, st);
+        if (rc != SSSP_OK) return rc;
+        if ((e = cudaEventRecord(e1, st)) != cudaSuccess) return fail(e);
+        if ((e = cudaEventSynchronize(e1)) != cudaSuccess) return fail(e);
+        rc = sssp_last_status(g, st);
+        if (rc != SSSP_OK) return rc;
+        float t = 0;
+        if ((e = cudaEventElapsedTime(&t, e0, e1)) != cudaSuccess) return fail(e);
+        total += t;
+    }
+    *ms_out = total / ns;
+    return SSSP_OK;
+}
+
+}  // namespace
+
+uint64_t sssp_class_key(const sssp_graph* g)
+{
+    const double avg = g->n ? (double)g->m / (double)g->n : 0.0;
+    const uint32_t lg_n = ceil_log2(g->n);
+    const uint32_t lg_avg4 = avg > 1.0 ? (uint32_t)std::lround(4.0 * std::log2(avg)) : 0u;
+    const uint32_t skew = (avg > 0.0 && g->max_deg > avg) ? (uint32_t)std::floor(std::log2((double)g->max_deg / avg)) : 0u;
+    return (uint64_t)(lg_n & 0xFF) | ((uint64_t)(lg_avg4 & 0xFF) << 8) | ((uint64_t)(skew & 0xFF) << 16) |
+           ((uint64_t)((g->flags & SSSP_GRAPH_SYMMETRIC) ? 1 : 0) << 24);
+}
+
+bool sssp_lookup_tuning(const sssp_graph* g, sssp_tuning* out)
+{
+    if (g->tuned) {
+        *out = g->tuning;
+        return true;
+    }
+    std::lock_guard<std::mutex> lk(g_class_mu);
+    auto it = g_class_table.find(sssp_class_key(g));
+    if (it == g_class_table.end()) return false;
+    *out = it->second;
+    return true;
+}
+
+uint64_t sssp_graph_param(const sssp_graph* g, sssp_algo algo)
+{
+    sssp_tuning t;
+    if (sssp_lookup_tuning(g, &t) && t.algo == algo) return t.param;
+    return sssp_default_param(g->n, g->m, algo, g->mean_w);
+}
+
+extern "C" {
+
+int sssp_graph_class(const sssp_graph* g, uint64_t* key)
+{
+    if (!g || !key) return SSSP_ERR_INVALID_ARG;
+    *key = sssp_class_key(g);
+    return SSSP_OK;
+}
+
+int sssp_autotune(sssp_graph* g, const uint32_t* sources, uint32_t k, sssp_tuning* out, void* stream)
+{
+    if (!g || !sources || k == 0) return SSSP_ERR_INVALID_ARG;
+    for (uint32_t i = 0; i < k; ++i)
+        if (sources[i] >= g->n) return SSSP_ERR_INVALID_ARG;
+    cudaError_t e = cudaSetDevice(g->device);
+    if (e != cudaSuccess) return fail(e);
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    uint64_t* dist = nullptr;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    if ((e = cudaMalloc(reinterpret_cast<void**>(&dist), sizeof(uint64_t) * (size_t)g->n)) != cudaSuccess) return fail(e);
+    if ((e = cudaEventCreate(&e0)) != cudaSuccess || (e = cudaEventCreate(&e1)) != cudaSuccess) {
+        cudaFree(dist);
+        if (e0) cudaEventDestroy(e0);
+        return fail(e);
+    }
+    int rc = SSSP_OK;
+    uint32_t timed = 0;
+    Candidate best{SSSP_RHO, 0, SSSP_SHAPE_WIDE, 0, 0};
+    do {
+        // rule / parameter candidates: rho = n/4 ... n/1024 (>= 64), Delta =
+        // mean weight x {1/8, 1/2, 2, 8}
+        std::vector<Candidate> cand;
+        for (uint32_t j = 2; j <= 10; j += 2) {
+            uint64_t rho = (uint64_t)g->n >> j;
+            if (rho < 64) rho = 64;
+            bool dup = false;
+            for (const Candidate& c : cand) dup = dup || (c.algo == SSSP_RHO && c.param == rho);
+            if (!dup) cand.push_back({SSSP_RHO, rho, SSSP_SHAPE_WIDE, 0, 0});
+        }
+        for (double f : {0.125, 0.5, 2.0, 8.0}) {
+            const double d = g->mean_w * f;
+            cand.push_back({SSSP_DELTA_STAR, d > 1.0 ? (uint64_t)d : 1ull, SSSP_SHAPE_WIDE, 0, 0});
+        }
+        // one warm-up solve (first launch of the kernel, lazy allocations)
+        double ignore;
+        if ((rc = time_config(g, cand[0], sources, 1, dist, st, e0, e1, &ignore)) != SSSP_OK) break;
+        // (1)
+        for (Candidate& c : cand) {
+            if ((rc = time_config(g, c, sources, 1, dist, st, e0, e1, &c.ms)) != SSSP_OK) break;
+            ++timed;
+        }
+        if (rc != SSSP_OK) break;
+        std::vector<Candidate> sorted = cand;
+        for (size_t i = 0; i < sorted.size(); ++i)
+            for (size_t j = i + 1; j < sorted.size(); ++j)
+                if (sorted[j].ms < sorted[i].ms) std::swap(sorted[i], sorted[j]);
+        // (2)
+        const uint32_t ns2 = k < 2 ? k : 2;
+        best.ms = INFINITY;
+        for (size_t i = 0; i < 2 && i < sorted.size(); ++i)
+            for (uint32_t shape : {SSSP_SHAPE_WIDE, SSSP_SHAPE_NARROW}) {
+                Candidate c = sorted[i];
+                c.shape = shape;
+                if ((rc = time_config(g, c, sources, ns2, dist, st, e0, e1, &c.ms)) != SSSP_OK) break;
+                ++timed;
+                if (c.ms < best.ms) best = c;
+            }
+        if (rc != SSSP_OK) break;
+        // (3) local relaxation changes which rule and parameter win (it makes
+        //     multi-hop steps), so it is tried on the three best of (1), in the
+        //     shape that won (2)
+        if (g->n && (double)g->m / (double)g->n < 20.0) {
+            for (size_t i = 0; i < 3 && i < sorted.size() && rc == SSSP_OK; ++i)
+                for (uint32_t local : {64u, 256u, 1024u}) {
+                    Candidate c = sorted[i];
+                    c.shape = best.shape;
+                    c.local = local;
+                    if ((rc = time_config(g, c, sources, ns2, dist, st, e0, e1, &c.ms)) != SSSP_OK) break;
+                    ++timed;
+                    if (c.ms < best.ms) best = c;
+                }
+            if (rc != SSSP_OK) break;
+        }
+        // (4)
+        if ((rc = time_config(g, best, sources, k, dist, st, e0, e1, &best.ms)) != SSSP_OK) break;
+    } while (false);
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    cudaFree(dist);
+    if (rc != SSSP_OK) return rc;
+    sssp_tuning t;
+    memset(&t, 0, sizeof t);
+    t.algo = best.algo;
+    t.shape = best.shape;
+    t.param = best.param;
+    t.flags = (g->flags & SSSP_GRAPH_SYMMETRIC) ? SSSP_SOLVE_BIDIRECTIONAL : 0u;
+    t.local_budget = best.local;
+    t.ms = best.ms;
+    t.candidates = timed;
+    {
+        std::lock_guard<std::mutex> lk(g->mu);
+        g->tuning = t;
+        g->tuned = true;
+    }
+    {
+        std::lock_guard<std::mutex> lk(g_class_mu);
+        g_class_table[sssp_class_key(g)] = t;
+    }
+    if (out) *out = t;
+    return SSSP_OK;
+}
+
+int sssp_graph_get_tuning(const sssp_graph* g, sssp_tuning* out)
+{
+    if (!g || !out) return SSSP_ERR_INVALID_ARG;
+    return sssp_lookup_tuning(g, out) ? SSSP_OK : SSSP_ERR_INVALID_ARG;
+}
+
+int sssp_graph_set_tuning(sssp_graph* g, const sssp_tuning* t)
+{
+    if (!g || !t) return SSSP_ERR_INVALID_ARG;
+    if (t->algo != SSSP_RHO && t->algo != SSSP_DELTA_STAR && t->algo != SSSP_BELLMAN_FORD) return SSSP_ERR_INVALID_ARG;
+    if (algo_needs_param(t->algo) && t->param == 0) return SSSP_ERR_INVALID_ARG;
+    if (t->shape > SSSP_SHAPE_NARROW || (t->flags & ~SSSP_SOLVE_BIDIRECTIONAL)) return SSSP_ERR_INVALID_ARG;
+    if ((t->flags & SSSP_SOLVE_BIDIRECTIONAL) && !(g->flags & SSSP_GRAPH_SYMMETRIC)) return SSSP_ERR_INVALID_ARG;
+    if (t->local_budget != 0 && t->algo == SSSP_BELLMAN_FORD) return SSSP_ERR_INVALID_ARG;
+    std::lock_guard<std::mutex> lk(g->mu);
+    g->tuning = *t;
+    g->tuned = true;
+    return SSSP_OK;
+}
+
+int sssp_solve_tuned(const sssp_graph* g, uint32_t source, uint64_t* dist_out, void* stream)
+{
+    if (!g) return SSSP_ERR_INVALID_ARG;
+    sssp_tuning t;
+    if (!sssp_lookup_tuning(g, &t)) {
+        memset(&t, 0, sizeof t);
+        t.algo = SSSP_RHO;
+        t.param = sssp_default_param(g->n, g->m, SSSP_RHO, g->mean_w);
+        t.flags = (g->flags & SSSP_GRAPH_SYMMETRIC) ? SSSP_SOLVE_BIDIRECTIONAL : 0u;
+        t.shape = SSSP_SHAPE_WIDE;
+    }
+    sssp_options o;
+    memset(&o, 0, sizeof o);
+    o.flags = t.flags;
+    o.shape = t.shape;
+    o.local_budget = t.local_budget;
+    return sssp_solve_ex(g, source, t.algo, t.param, dist_out, &o, stream);
+}
+
+}  // extern "C"

@@ -22,6 +22,7 @@ SSSP_RHO, SSSP_DELTA_STAR, SSSP_BELLMAN_FORD, SSSP_DELTA, SSSP_DIJKSTRA = 0, 1, 
 ALGOS = {"rho": SSSP_RHO, "delta_star": SSSP_DELTA_STAR, "bellman_ford": SSSP_BELLMAN_FORD,
          "delta": SSSP_DELTA, "dijkstra": SSSP_DIJKSTRA}
 SSSP_SOLVE_BIDIRECTIONAL = 1
+SSSP_SHAPE_WIDE, SSSP_SHAPE_NARROW = 0, 1
 SSSP_GRAPH_SYMMETRIC, SSSP_GRAPH_VERIFY = 1, 2
 SSSP_OK = 0
 SSSP_ERR_INVALID_ARG, SSSP_ERR_OUT_OF_MEMORY, SSSP_ERR_CUDA = -1, -2, -3
@@ -64,7 +65,8 @@ class sssp_options(ctypes.Structure):
                 ("trace", ctypes.c_void_p), ("trace_cap", ctypes.c_uint32),
                 ("grid_limit", ctypes.c_uint32), ("test_exit_block", ctypes.c_uint32),
                 ("stats_out", ctypes.c_void_p), ("solve_timeout_ns", ctypes.c_uint64),
-                ("flags", ctypes.c_uint32), ("local_budget", ctypes.c_uint32)]
+                ("flags", ctypes.c_uint32), ("local_budget", ctypes.c_uint32),
+                ("shape", ctypes.c_uint32)]
 
 
 TRACE_RECORD_BYTES = ctypes.sizeof(sssp_step_trace)
@@ -139,7 +141,30 @@ EXPORTED = ["sssp_graph_create", "sssp_graph_destroy", "sssp_graph_info", "sssp_
             "sssp_rho_threshold", "sssp_status_string", "sssp_solve_noalloc", "sssp_solve_sources",
             "sssp_solve_multi", "sssp_batch_last_stats", "sssp_server_create", "sssp_server_slots",
             "sssp_server_submit", "sssp_server_poll", "sssp_server_wait", "sssp_server_stats",
-            "sssp_server_destroy", "sssp_server_drain", "sssp_graph_create_ex", "sssp_solve_host_ex"]
+            "sssp_server_destroy", "sssp_server_drain", "sssp_graph_create_ex", "sssp_solve_host_ex",
+            "sssp_autotune", "sssp_graph_get_tuning", "sssp_graph_set_tuning", "sssp_graph_class",
+            "sssp_solve_tuned"]
+
+
+class sssp_tuning(ctypes.Structure):
+    _fields_ = [("algo", ctypes.c_int), ("shape", ctypes.c_uint32), ("param", ctypes.c_uint64),
+                ("flags", ctypes.c_uint32), ("local_budget", ctypes.c_uint32), ("ms", ctypes.c_double),
+                ("candidates", ctypes.c_uint32), ("reserved", ctypes.c_uint32)]
+
+    def as_dict(self) -> dict:
+        return {k: (float(getattr(self, k)) if k == "ms" else int(getattr(self, k))) for k, _ in self._fields_}
+
+
+_lib.sssp_autotune.argtypes = [_P, _P, _u32, ctypes.POINTER(sssp_tuning), _P]
+_lib.sssp_autotune.restype = _i32
+_lib.sssp_graph_get_tuning.argtypes = [_P, ctypes.POINTER(sssp_tuning)]
+_lib.sssp_graph_get_tuning.restype = _i32
+_lib.sssp_graph_set_tuning.argtypes = [_P, ctypes.POINTER(sssp_tuning)]
+_lib.sssp_graph_set_tuning.restype = _i32
+_lib.sssp_graph_class.argtypes = [_P, ctypes.POINTER(_u64)]
+_lib.sssp_graph_class.restype = _i32
+_lib.sssp_solve_tuned.argtypes = [_P, _u32, _P, _P]
+_lib.sssp_solve_tuned.restype = _i32
 
 MAX_BATCH = 2048
 
@@ -198,7 +223,8 @@ def sssp_solve(g: int, source: int, algo: int, param: int, dist_out_ptr: int, st
 def make_options(seed: int = 0, timeout_ns: int = 0, max_steps: int = 0, ext_count_ptr: int = 0,
                  trace_ptr: int = 0, trace_cap: int = 0, grid_limit: int = 0,
                  test_exit_block: int = 0, stats_out_ptr: int = 0,
-                 solve_timeout_ns: int = 0, flags: int = 0, local_budget: int = 0) -> sssp_options:
+                 solve_timeout_ns: int = 0, flags: int = 0, local_budget: int = 0,
+                 shape: int = 0) -> sssp_options:
     o = sssp_options()
     o.seed, o.timeout_ns, o.max_steps = seed, timeout_ns, max_steps
     o.ext_count = ext_count_ptr or None
@@ -208,6 +234,7 @@ def make_options(seed: int = 0, timeout_ns: int = 0, max_steps: int = 0, ext_cou
     o.solve_timeout_ns = solve_timeout_ns
     o.flags = flags
     o.local_budget = local_budget
+    o.shape = shape
     return o
 
 
@@ -345,6 +372,37 @@ def sssp_server_stats(s: int) -> dict:
 
 def sssp_server_destroy(s: int) -> None:
     _check(_lib.sssp_server_destroy(s), "sssp_server_destroy")
+
+
+def sssp_autotune(g: int, sources, stream: int = 0) -> dict:
+    """Time candidate configurations on the sample sources; returns the choice."""
+    src = np.ascontiguousarray(sources, dtype=np.uint32)
+    t = sssp_tuning()
+    _check(_lib.sssp_autotune(g, src.ctypes.data, src.size, ctypes.byref(t), stream or None), "sssp_autotune")
+    return t.as_dict()
+
+
+def sssp_graph_get_tuning(g: int):
+    t = sssp_tuning()
+    rc = _lib.sssp_graph_get_tuning(g, ctypes.byref(t))
+    return t.as_dict() if rc == SSSP_OK else None
+
+
+def sssp_graph_set_tuning(g: int, tuning: dict) -> None:
+    t = sssp_tuning()
+    for k, v in tuning.items():
+        setattr(t, k, v)
+    _check(_lib.sssp_graph_set_tuning(g, ctypes.byref(t)), "sssp_graph_set_tuning")
+
+
+def sssp_graph_class(g: int) -> int:
+    key = ctypes.c_uint64()
+    _check(_lib.sssp_graph_class(g, ctypes.byref(key)), "sssp_graph_class")
+    return int(key.value)
+
+
+def sssp_solve_tuned(g: int, source: int, dist_out_ptr: int, stream: int = 0) -> int:
+    return _check(_lib.sssp_solve_tuned(g, source, dist_out_ptr, stream or None), "sssp_solve_tuned")
 
 
 class Graph:

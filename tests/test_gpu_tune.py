@@ -1,0 +1,144 @@
+"""The narrow kernel shape and the autotuner, through the C ABI.
+
+Every configuration the autotuner can pick must give the oracle's distances
+(they are unique), so the tests check the shape on the parity workloads and
+then check that a tuned solve, a class-table lookup and a batched solve with
+tuned parameters all still equal the oracle.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2105_06145_gb300 import graphgen as gg
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+INF = (1 << 64) - 1
+
+
+@pytest.fixture(scope="module")
+def lib():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2105_06145_gb300 import sssp
+    return sssp
+
+
+def _stream():
+    return torch.cuda.current_stream().cuda_stream
+
+
+def _solve(lib, G, n, s, algo, param, **kw):
+    dist = torch.full((n,), 7, dtype=torch.int64, device="cuda")
+    G.solve(s, algo, param, dist, _stream(), lib.make_options(**kw))
+    st = G.stats(_stream())
+    return dist.cpu().numpy().view(np.uint64).copy(), st
+
+
+@pytest.mark.parametrize("algo,param", [(0, 1), (0, 1 << 10), (0, (1 << 32) - 1), (1, 1 << 13), (1, INF),
+                                        (2, 0), (3, 1 << 13), (4, 0)])
+def test_narrow_shape_matches_oracle_on_grid(lib, algo, param):
+    g, s = gg.workload_grid256()
+    want = oracle.dijkstra(g, s)
+    G = lib.Graph(g)
+    got, st = _solve(lib, G, g.n, s, algo, param, shape=lib.SSSP_SHAPE_NARROW)
+    assert st["status"] == 0 and st["grid"] > 0
+    assert np.array_equal(got, want)
+    G.close()
+
+
+def test_narrow_shape_rmat_road_hubs_bidir_local(lib):
+    graphs = [gg.rmat(16, 16, gen_seed=11, wseed=12), gg.road(300, 0.75, seed=3)]
+    # three vertices of degree 2e5 force multi-record chunk relaxation
+    rng = np.random.default_rng(5)
+    n = 200_003
+    src = np.concatenate([np.full(n - 3, i) for i in range(3)] + [rng.integers(0, n, 4000)])
+    dst = np.concatenate([np.arange(3, n) for _ in range(3)] + [rng.integers(0, n, 4000)])
+    graphs.append(gg.from_edges(n, src, dst, rng.integers(1, 1000, src.size), "hubs"))
+    for g in graphs:
+        s = gg.pick_sources(g, 1, 5)[0] if g.name != "hubs" else 0
+        want = oracle.dijkstra(g, s)
+        G = lib.Graph(g)
+        for algo, param in ((0, 1 << 12), (1, 1 << 15), (2, 0)):
+            got, st = _solve(lib, G, g.n, s, algo, param, shape=lib.SSSP_SHAPE_NARROW)
+            assert st["status"] == 0 and np.array_equal(got, want), (g.name, algo, param)
+        G.close()
+        if g.name != "hubs":
+            Gs = lib.Graph(g, lib.SSSP_GRAPH_SYMMETRIC | lib.SSSP_GRAPH_VERIFY)
+            for kw in ({"flags": lib.SSSP_SOLVE_BIDIRECTIONAL}, {"local_budget": 256}):
+                got, st = _solve(lib, Gs, g.n, s, 0, 1 << 12, shape=lib.SSSP_SHAPE_NARROW, **kw)
+                assert st["status"] == 0 and np.array_equal(got, want), (g.name, kw)
+            Gs.close()
+
+
+def test_invalid_shape_is_rejected(lib):
+    g, s = gg.workload_grid256()
+    G = lib.Graph(g)
+    dist = torch.empty(g.n, dtype=torch.int64, device="cuda")
+    o = lib.make_options(shape=7)
+    rc = lib._lib.sssp_solve_ex(G.handle, s, 0, 64, dist.data_ptr(), o, None)
+    assert rc == lib.SSSP_ERR_INVALID_ARG
+    G.close()
+
+
+def test_autotune_then_solve_tuned(lib):
+    cases = [gg.workload_grid256()[0], gg.rmat(14, 16, gen_seed=21, wseed=22), gg.road(120, 0.75, seed=9)]
+    for g in cases:
+        G = lib.Graph(g, lib.SSSP_GRAPH_SYMMETRIC | lib.SSSP_GRAPH_VERIFY)
+        srcs = gg.pick_sources(g, 3, 17)
+        t = lib.sssp_autotune(G.handle, srcs, _stream())
+        assert t["algo"] in (lib.SSSP_RHO, lib.SSSP_DELTA_STAR)
+        assert t["param"] >= 1 and t["shape"] in (0, 1) and t["candidates"] >= 9 and t["ms"] > 0
+        assert t["flags"] == lib.SSSP_SOLVE_BIDIRECTIONAL
+        if g.m / g.n >= 20:
+            assert t["local_budget"] == 0
+        assert lib.sssp_graph_get_tuning(G.handle) == t
+        for s in srcs[:2]:
+            dist = torch.full((g.n,), 7, dtype=torch.int64, device="cuda")
+            lib.sssp_solve_tuned(G.handle, s, dist.data_ptr(), _stream())
+            assert lib.sssp_last_status(G.handle, _stream()) == 0
+            assert np.array_equal(dist.cpu().numpy().view(np.uint64), oracle.dijkstra(g, s)), g.name
+        G.close()
+
+
+def test_class_table_serves_untuned_graphs_of_the_class(lib):
+    a = gg.rmat(13, 16, gen_seed=31, wseed=32)
+    b = gg.rmat(13, 16, gen_seed=33, wseed=34)
+    Ga = lib.Graph(a, lib.SSSP_GRAPH_SYMMETRIC)
+    Gb = lib.Graph(b, lib.SSSP_GRAPH_SYMMETRIC)
+    if lib.sssp_graph_class(Ga.handle) != lib.sssp_graph_class(Gb.handle):
+        pytest.skip("the two seeds gave graphs of different classes")
+    t = lib.sssp_autotune(Ga.handle, gg.pick_sources(a, 2, 3), _stream())
+    tb = lib.sssp_graph_get_tuning(Gb.handle)
+    assert tb == t
+    # batched solve with the tuned per-instance parameter (params = NULL)
+    srcs = gg.pick_sources(b, 3, 4)
+    outs = [torch.empty(b.n, dtype=torch.int64, device="cuda") for _ in srcs]
+    lib.sssp_solve_multi([Gb.handle] * len(srcs), srcs, t["algo"], None, [o.data_ptr() for o in outs], _stream())
+    st, _ = lib.sssp_batch_last_stats(len(srcs), _stream())
+    assert st == 0
+    for s, o in zip(srcs, outs):
+        assert np.array_equal(o.cpu().numpy().view(np.uint64), oracle.dijkstra(b, s))
+    # solve_tuned on the untuned graph uses the class entry
+    dist = torch.empty(b.n, dtype=torch.int64, device="cuda")
+    lib.sssp_solve_tuned(Gb.handle, srcs[0], dist.data_ptr(), _stream())
+    assert np.array_equal(dist.cpu().numpy().view(np.uint64), oracle.dijkstra(b, srcs[0]))
+    Ga.close()
+    Gb.close()
+
+
+def test_set_tuning_validation(lib):
+    g, s = gg.workload_grid256()
+    G = lib.Graph(g)  # not created symmetric
+    good = {"algo": lib.SSSP_RHO, "param": 1024, "shape": lib.SSSP_SHAPE_NARROW, "flags": 0, "local_budget": 64}
+    lib.sssp_graph_set_tuning(G.handle, good)
+    assert lib.sssp_graph_get_tuning(G.handle)["param"] == 1024
+    for bad in ({"param": 0}, {"shape": 2}, {"flags": lib.SSSP_SOLVE_BIDIRECTIONAL}, {"algo": 9},
+                {"algo": lib.SSSP_BELLMAN_FORD, "local_budget": 64}):
+        with pytest.raises(lib.SSSPError):
+            lib.sssp_graph_set_tuning(G.handle, {**good, **bad})
+    dist = torch.empty(g.n, dtype=torch.int64, device="cuda")
+    lib.sssp_solve_tuned(G.handle, s, dist.data_ptr(), _stream())
+    assert np.array_equal(dist.cpu().numpy().view(np.uint64), oracle.dijkstra(g, s))
+    G.close()

@@ -50,7 +50,8 @@ def algorithmic_bytes(st: dict) -> int:
 def kernel_hash() -> str:
     import hashlib
     h = hashlib.sha256()
-    for f in ("paper_2105_06145_gb300/csrc/sssp_kernels.cu", "paper_2105_06145_gb300/csrc/sssp_internal.h"):
+    for f in ("paper_2105_06145_gb300/csrc/sssp_kernels.cu", "paper_2105_06145_gb300/csrc/sssp_internal.h",
+              "paper_2105_06145_gb300/csrc/sssp_device.cuh"):
         with open(os.path.join(ROOT, f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]

@@ -214,54 +214,109 @@ def run_reference(args, g, srcs, label, rank, world):
     print(json.dumps(line), flush=True)
 
 
+def _timed(torch, stream_obj, fn) -> float:
+    """ms of one call of fn (after one untimed call), CUDA events on the stream."""
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with torch.cuda.stream(stream_obj):
+        fn()
+        torch.cuda.synchronize()
+        e0.record(stream_obj)
+        fn()
+        e1.record(stream_obj)
+        torch.cuda.synchronize()
+    return e0.elapsed_time(e1)
+
+
 def measure_batched(sssp, G, g, torch, stream, stream_obj) -> dict:
     """Batched solves: (a) 64 sources on this graph in one launch, (b) 512 graphs of
-    uneven size in one launch; each against the plain loop of single solves."""
+    uneven size in one launch with per-instance rho from the autotuner (one tuning
+    per graph class); each against the plain loop of single solves, each plain
+    solve in its own tuned configuration (sssp_solve_tuned)."""
     from paper_2105_06145_gb300 import graphgen as gg
-
-    def timed(fn):
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        with torch.cuda.stream(stream_obj):
-            fn()
-            torch.cuda.synchronize()
-            e0.record(stream_obj)
-            fn()
-            e1.record(stream_obj)
-            torch.cuda.synchronize()
-        return e0.elapsed_time(e1)
-
     res = {}
     srcs = gg.pick_sources(g, 64, 6)
+    tune = sssp.sssp_autotune_ex(G.handle, srcs[:3], 1 << sssp.SSSP_RHO, stream)
     out = torch.empty(64 * g.n, dtype=torch.int64, device="cuda")
     one = torch.empty(g.n, dtype=torch.int64, device="cuda")
-    rho = 1 << 18
-    tb = timed(lambda: sssp.sssp_solve_sources(G.handle, srcs, sssp.SSSP_RHO, [rho] * 64, out.data_ptr(), stream))
+    tb = _timed(torch, stream_obj, lambda: sssp.sssp_solve_sources(G.handle, srcs, sssp.SSSP_RHO, None,
+                                                                   out.data_ptr(), stream))
     st, _ = sssp.sssp_batch_last_stats(64, stream)
-    tp = timed(lambda: [G.solve(s_, sssp.SSSP_RHO, rho, one, stream) for s_ in srcs])
+    tp = _timed(torch, stream_obj, lambda: [sssp.sssp_solve_tuned(G.handle, s_, one.data_ptr(), stream)
+                                            for s_ in srcs])
     same = bool(torch.equal(out.view(64, g.n)[-1], one))
     res["sources64_rmat22"] = {"queries_per_s": 64e3 / tb, "plain_queries_per_s": 64e3 / tp,
-                               "speedup": tp / tb, "status": st, "last_equal_to_single": same}
+                               "speedup": tp / tb, "status": st, "last_equal_to_single": same,
+                               "tuning": tune}
     del out, one
     W = gg.workload_multi()
-    Gs = [sssp.Graph(h) for h, _ in W]
+    Gs = [sssp.Graph(h, sssp.SSSP_GRAPH_SYMMETRIC) for h, _ in W]
     outs = [torch.empty(h.n, dtype=torch.int64, device="cuda") for h, _ in W]
+    classes = {}
+    for (h, s_), Gx in zip(W, Gs):
+        key = sssp.sssp_graph_class(Gx.handle)
+        if key not in classes:
+            more = gg.pick_sources(h, 1, 11)
+            classes[key] = sssp.sssp_autotune_ex(Gx.handle, [s_] + more, 1 << sssp.SSSP_RHO, stream)
     hs, ss, ptrs = [x.handle for x in Gs], [s_ for _, s_ in W], [o.data_ptr() for o in outs]
-    tb = timed(lambda: sssp.sssp_solve_multi(hs, ss, sssp.SSSP_RHO, None, ptrs, stream))
+    tb = _timed(torch, stream_obj, lambda: sssp.sssp_solve_multi(hs, ss, sssp.SSSP_RHO, None, ptrs, stream))
     st, _ = sssp.sssp_batch_last_stats(len(W), stream)
     keep = [o.clone() for o in outs[:8]]
-    tp = timed(lambda: [Gx.solve(s_, sssp.SSSP_RHO, max(64, h.n // 16), o, stream)
-                        for (h, s_), Gx, o in zip(W, Gs, outs)])
+    tp = _timed(torch, stream_obj, lambda: [sssp.sssp_solve_tuned(Gx.handle, s_, o.data_ptr(), stream)
+                                            for (h, s_), Gx, o in zip(W, Gs, outs)])
     same = all(bool(torch.equal(a, b)) for a, b in zip(keep, outs[:8]))
     res["graphs512"] = {"queries_per_s": len(W) * 1e3 / tb, "plain_queries_per_s": len(W) * 1e3 / tp,
                         "speedup": tp / tb, "status": st, "edges_total": int(sum(h.m for h, _ in W)),
-                        "first8_equal_to_single": same}
+                        "graph_classes_tuned": len(classes), "first8_equal_to_single": same}
     for Gx in Gs:
         Gx.close()
     return res
 
 
+def measure_workload(name, sssp, torch, stream, stream_obj, rates_x=(2, 10)) -> dict:
+    """Road-like (4096^2 jittered grid) or k-NN (2M points) workload: the
+    autotuner's choice as a plain loop of single solves, 64 sources in one
+    batched launch, and the continuous-batching server at offered rates of
+    rates_x times the plain loop's rate."""
+    from paper_2105_06145_gb300 import graphgen as gg
+    if name == "road4096":
+        h, _ = gg.workload_road(4096)
+        srcs = gg.pick_sources(h, 256, 9, mask=gg.largest_cc(h))
+    else:
+        h = gg.knn(2_000_000, 64, 0.02, 10, float(1 << 20), seed=10)
+        srcs = gg.pick_sources(h, 256, 9, mask=np.ones(h.n, np.uint8))
+    Gx = sssp.Graph(h, sssp.SSSP_GRAPH_SYMMETRIC)
+    t0 = time.perf_counter()
+    tune = sssp.sssp_autotune(Gx.handle, srcs[:3], stream)
+    tune_s = time.perf_counter() - t0
+    one = torch.empty(h.n, dtype=torch.int64, device="cuda")
+    tp = _timed(torch, stream_obj, lambda: [sssp.sssp_solve_tuned(Gx.handle, s_, one.data_ptr(), stream)
+                                            for s_ in srcs[:10]])
+    plain_qps = 10e3 / tp
+    out = torch.empty(64 * h.n, dtype=torch.int64, device="cuda")
+    tb = _timed(torch, stream_obj, lambda: sssp.sssp_solve_sources(Gx.handle, srcs[:64], tune["algo"], None,
+                                                                   out.data_ptr(), stream))
+    st, _ = sssp.sssp_batch_last_stats(64, stream)
+    sssp.sssp_solve_tuned(Gx.handle, srcs[63], one.data_ptr(), stream)
+    torch.cuda.synchronize()
+    same = bool(torch.equal(out.view(64, h.n)[63], one))
+    del out
+    torch.cuda.empty_cache()
+    res = {"n": h.n, "m": h.m, "tuning": tune, "tune_s": tune_s,
+           "plain": {"queries_per_s": plain_qps, "gteps": plain_qps * h.m / 1e9},
+           "batched64": {"queries_per_s": 64e3 / tb, "speedup": tp / 10 * 64 / tb, "status": st,
+                         "last_equal_to_single": same}}
+    rates = [int(max(1, round(x * plain_qps))) for x in rates_x]
+    sv = measure_serving(sssp, Gx, h, torch, srcs, rates, window_s=1.0, hard_s=8.0, slots=64,
+                         algo=tune["algo"], param=tune["param"], tuned=True)
+    res["served"] = sv
+    Gx.close()
+    del Gx
+    torch.cuda.empty_cache()
+    return res
+
+
 def measure_serving(sssp, G, g, torch, sources, rates, window_s=1.0, hard_s=10.0, slots=0,
-                    algo=None, param=0, seed=8) -> dict:
+                    algo=None, param=0, seed=8, tuned=False) -> dict:
     """Serving: a Poisson query stream at each offered rate
     for `window_s` seconds against the resident graph; queries go to the
     continuous-batching server as client-side result buffers allow.  Latency
@@ -278,13 +333,19 @@ def measure_serving(sssp, G, g, torch, sources, rates, window_s=1.0, hard_s=10.0
     # plain loop: one query at a time, result synchronised
     stream = torch.cuda.current_stream().cuda_stream
     prm = param or (max(64, g.n // 16) if algo == sssp.SSSP_RHO else 0)
-    G.solve(sources[0], algo, prm, bufs[0], stream)
-    torch.cuda.synchronize()
+
+    def plain_one(s_):
+        if tuned:  # the graph's tuned configuration (shape, flags, local relaxation)
+            sssp.sssp_solve_tuned(G.handle, s_, bufs[0].data_ptr(), stream)
+        else:
+            G.solve(s_, algo, prm, bufs[0], stream)
+        torch.cuda.synchronize()
+
+    plain_one(sources[0])
     t0 = time.perf_counter()
     nplain = min(10, len(sources))
     for s_ in sources[:nplain]:
-        G.solve(s_, algo, prm, bufs[0], stream)
-        torch.cuda.synchronize()
+        plain_one(s_)
     plain_qps = nplain / (time.perf_counter() - t0)
     rng = np.random.default_rng(seed)
     out = {"slots": S, "result_buffers": nbuf, "plain_queries_per_s": plain_qps, "rates": []}
@@ -385,6 +446,7 @@ def main():
     ap.add_argument("--no-bidir", action="store_true", help="plain push relaxation only")
     ap.add_argument("--no-batch", action="store_true", help="skip the batched-solve measurements")
     ap.add_argument("--no-serve", action="store_true", help="skip the serving measurement")
+    ap.add_argument("--no-other", action="store_true", help="skip the road-like and k-NN workloads")
     ap.add_argument("--serve", action="store_true", help="run the serving sweep (RMAT-25, road, k-NN) only")
     ap.add_argument("--serve-workloads", default="rmat25,road,knn")
     ap.add_argument("--serve-rates", default="1000,2000,5000,10000,20000,50000")
@@ -518,8 +580,21 @@ def main():
 
     served = None
     if rank == 0 and not args.no_serve and args.workload == "rmat" and args.scale == 22:
-        served = measure_serving(sssp, G, g, torch, gg_sources(g), [1000, 10000], window_s=0.5, hard_s=6.0,
-                                 slots=64)
+        tune = sssp.sssp_graph_get_tuning(G.handle)
+        served = {"rmat22": measure_serving(sssp, G, g, torch, gg_sources(g), [100, 1000], window_s=0.5,
+                                            hard_s=6.0, slots=64, algo=sssp.SSSP_RHO,
+                                            param=tune["param"] if tune else 0, tuned=tune is not None)}
+
+    # the road-like and k-NN workloads: tuned plain loop, batched and served
+    workloads = None
+    if rank == 0 and not args.no_other and args.workload == "rmat" and args.scale == 22:
+        workloads = {}
+        for wname in ("road4096", "knn2m"):
+            workloads[wname] = measure_workload(wname, sssp, torch, stream, stream_obj)
+            if batched is not None:
+                batched[f"sources64_{wname}"] = workloads[wname]["batched64"]
+            if served is not None:
+                served[wname] = workloads[wname]["served"]
 
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
@@ -557,6 +632,7 @@ def main():
             "e2e": e2e,
             "batched": batched,
             "served": served,
+            "workloads": workloads,
             "gpu_launches": K,
             "clocks": clk,
         }

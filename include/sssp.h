@@ -396,8 +396,8 @@ typedef struct {
  * < n) and keep the fastest: rho in {n/4, n/16, ..., n/1024} (at least 64) and
  * Delta in mean-weight x {1/8, 1/2, 2, 8} in the wide shape on the first
  * source; the two best in both shapes on two sources; on graphs with mean
- * out-degree < 20 the three best rules/parameters in the winning shape with
- * local budgets 64, 256, 1024; the winner is re-timed on all k sources.  Bidirectional relaxation is used when the graph
+ * out-degree < 20 the two best parameters of each rule in the winning shape
+ * with local budgets 64, 256, 1024; the winner is re-timed on all k sources.  Bidirectional relaxation is used when the graph
  * was created SSSP_GRAPH_SYMMETRIC.  The result is stored on the graph and in
  * a per-class table (sssp_graph_class) that sssp_solve_tuned, sssp_solve_sources,
  * sssp_solve_multi (params == NULL) and the server (param == 0) use for graphs
@@ -405,6 +405,12 @@ typedef struct {
  * allocates a temporary distance array.  out may be NULL.
  */
 int sssp_autotune(sssp_graph* g, const uint32_t* sources, uint32_t k, sssp_tuning* out, void* stream);
+
+/* sssp_autotune over a subset of the rules: `rules` is a bit mask of
+   (1 << SSSP_RHO) and (1 << SSSP_DELTA_STAR) (e.g. rho only, for batched calls
+   that run every instance with rho-Stepping); INVALID_ARG for other bits or 0. */
+int sssp_autotune_ex(sssp_graph* g, const uint32_t* sources, uint32_t k, uint32_t rules, sssp_tuning* out,
+                     void* stream);
 
 /* The tuning that applies to g (its own, else its class's); INVALID_ARG when none. */
 int sssp_graph_get_tuning(const sssp_graph* g, sssp_tuning* out);

@@ -14,8 +14,8 @@
 //   1. every rule/parameter candidate, wide shape, no local relaxation, on the
 //      first sample source;
 //   2. the two fastest of (1) in both shapes, on up to two sources;
-//   3. sparse graphs (mean out-degree < 20): the three fastest of (1), in
-//      the winning shape, with local budgets 64, 256 and 1024;
+//   3. sparse graphs (mean out-degree < 20): the two fastest of (1) of each
+//      rule, in the winning shape, with local budgets 64, 256 and 1024;
 //   4. the winner on every sample source (sssp_tuning.ms).
 // The result is kept on the graph handle and in a per-class table (graph class
 // = size, mean degree, degree skew and symmetry; sssp_graph_class), which
@@ -123,7 +123,14 @@ int sssp_graph_class(const sssp_graph* g, uint64_t* key)
 
 int sssp_autotune(sssp_graph* g, const uint32_t* sources, uint32_t k, sssp_tuning* out, void* stream)
 {
+    return sssp_autotune_ex(g, sources, k, (1u << SSSP_RHO) | (1u << SSSP_DELTA_STAR), out, stream);
+}
+
+int sssp_autotune_ex(sssp_graph* g, const uint32_t* sources, uint32_t k, uint32_t rules, sssp_tuning* out,
+                     void* stream)
+{
     if (!g || !sources || k == 0) return SSSP_ERR_INVALID_ARG;
+    if (rules == 0 || (rules & ~((1u << SSSP_RHO) | (1u << SSSP_DELTA_STAR)))) return SSSP_ERR_INVALID_ARG;
     for (uint32_t i = 0; i < k; ++i)
         if (sources[i] >= g->n) return SSSP_ERR_INVALID_ARG;
     cudaError_t e = cudaSetDevice(g->device);
@@ -144,7 +151,7 @@ int sssp_autotune(sssp_graph* g, const uint32_t* sources, uint32_t k, sssp_tunin
         // rule / parameter candidates: rho = n/4 ... n/1024 (>= 64), Delta =
         // mean weight x {1/8, 1/2, 2, 8}
         std::vector<Candidate> cand;
-        for (uint32_t j = 2; j <= 10; j += 2) {
+        for (uint32_t j = 2; j <= 10 && (rules & (1u << SSSP_RHO)); j += 2) {
             uint64_t rho = (uint64_t)g->n >> j;
             if (rho < 64) rho = 64;
             bool dup = false;
@@ -152,6 +159,7 @@ int sssp_autotune(sssp_graph* g, const uint32_t* sources, uint32_t k, sssp_tunin
             if (!dup) cand.push_back({SSSP_RHO, rho, SSSP_SHAPE_WIDE, 0, 0});
         }
         for (double f : {0.125, 0.5, 2.0, 8.0}) {
+            if (!(rules & (1u << SSSP_DELTA_STAR))) break;
             const double d = g->mean_w * f;
             cand.push_back({SSSP_DELTA_STAR, d > 1.0 ? (uint64_t)d : 1ull, SSSP_SHAPE_WIDE, 0, 0});
         }
@@ -181,12 +189,18 @@ int sssp_autotune(sssp_graph* g, const uint32_t* sources, uint32_t k, sssp_tunin
             }
         if (rc != SSSP_OK) break;
         // (3) local relaxation changes which rule and parameter win (it makes
-        //     multi-hop steps), so it is tried on the three best of (1), in the
-        //     shape that won (2)
+        //     multi-hop steps), so it is tried on the two best of (1) of each
+        //     rule, in the shape that won (2)
         if (g->n && (double)g->m / (double)g->n < 20.0) {
-            for (size_t i = 0; i < 3 && i < sorted.size() && rc == SSSP_OK; ++i)
+            std::vector<Candidate> base;
+            for (sssp_algo a : {SSSP_RHO, SSSP_DELTA_STAR}) {
+                int taken = 0;
+                for (const Candidate& c : sorted)
+                    if (c.algo == a && taken < 2) { base.push_back(c); ++taken; }
+            }
+            for (size_t i = 0; i < base.size() && rc == SSSP_OK; ++i)
                 for (uint32_t local : {64u, 256u, 1024u}) {
-                    Candidate c = sorted[i];
+                    Candidate c = base[i];
                     c.shape = best.shape;
                     c.local = local;
                     if ((rc = time_config(g, c, sources, ns2, dist, st, e0, e1, &c.ms)) != SSSP_OK) break;

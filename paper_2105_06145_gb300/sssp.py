@@ -143,7 +143,7 @@ EXPORTED = ["sssp_graph_create", "sssp_graph_destroy", "sssp_graph_info", "sssp_
             "sssp_server_submit", "sssp_server_poll", "sssp_server_wait", "sssp_server_stats",
             "sssp_server_destroy", "sssp_server_drain", "sssp_graph_create_ex", "sssp_solve_host_ex",
             "sssp_autotune", "sssp_graph_get_tuning", "sssp_graph_set_tuning", "sssp_graph_class",
-            "sssp_solve_tuned"]
+            "sssp_solve_tuned", "sssp_autotune_ex"]
 
 
 class sssp_tuning(ctypes.Structure):
@@ -157,6 +157,8 @@ class sssp_tuning(ctypes.Structure):
 
 _lib.sssp_autotune.argtypes = [_P, _P, _u32, ctypes.POINTER(sssp_tuning), _P]
 _lib.sssp_autotune.restype = _i32
+_lib.sssp_autotune_ex.argtypes = [_P, _P, _u32, _u32, ctypes.POINTER(sssp_tuning), _P]
+_lib.sssp_autotune_ex.restype = _i32
 _lib.sssp_graph_get_tuning.argtypes = [_P, ctypes.POINTER(sssp_tuning)]
 _lib.sssp_graph_get_tuning.restype = _i32
 _lib.sssp_graph_set_tuning.argtypes = [_P, ctypes.POINTER(sssp_tuning)]
@@ -379,6 +381,15 @@ def sssp_autotune(g: int, sources, stream: int = 0) -> dict:
     src = np.ascontiguousarray(sources, dtype=np.uint32)
     t = sssp_tuning()
     _check(_lib.sssp_autotune(g, src.ctypes.data, src.size, ctypes.byref(t), stream or None), "sssp_autotune")
+    return t.as_dict()
+
+
+def sssp_autotune_ex(g: int, sources, rules: int, stream: int = 0) -> dict:
+    """sssp_autotune restricted to the rules in the bit mask (1 << SSSP_RHO, 1 << SSSP_DELTA_STAR)."""
+    src = np.ascontiguousarray(sources, dtype=np.uint32)
+    t = sssp_tuning()
+    _check(_lib.sssp_autotune_ex(g, src.ctypes.data, src.size, rules, ctypes.byref(t), stream or None),
+           "sssp_autotune_ex")
     return t.as_dict()
 
 

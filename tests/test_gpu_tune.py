@@ -142,3 +142,17 @@ def test_set_tuning_validation(lib):
     lib.sssp_solve_tuned(G.handle, s, dist.data_ptr(), _stream())
     assert np.array_equal(dist.cpu().numpy().view(np.uint64), oracle.dijkstra(g, s))
     G.close()
+
+
+def test_autotune_restricted_to_one_rule(lib):
+    g = gg.rmat(12, 16, gen_seed=41, wseed=42)
+    G = lib.Graph(g, lib.SSSP_GRAPH_SYMMETRIC)
+    srcs = gg.pick_sources(g, 2, 5)
+    t = lib.sssp_autotune_ex(G.handle, srcs, 1 << lib.SSSP_RHO, _stream())
+    assert t["algo"] == lib.SSSP_RHO and t["candidates"] >= 5
+    t = lib.sssp_autotune_ex(G.handle, srcs, 1 << lib.SSSP_DELTA_STAR, _stream())
+    assert t["algo"] == lib.SSSP_DELTA_STAR
+    for bad in (0, 1 << lib.SSSP_BELLMAN_FORD, 1 << 7):
+        with pytest.raises(lib.SSSPError):
+            lib.sssp_autotune_ex(G.handle, srcs, bad, _stream())
+    G.close()

@@ -272,7 +272,7 @@ def measure_batched(sssp, G, g, torch, stream, stream_obj) -> dict:
     return res
 
 
-def measure_workload(name, sssp, torch, stream, stream_obj, rates_x=(2, 10)) -> dict:
+def measure_workload(name, sssp, torch, stream, stream_obj, rates_x=(2, 20)) -> dict:
     """Road-like (4096^2 jittered grid) or k-NN (2M points) workload: the
     autotuner's choice as a plain loop of single solves, 64 sources in one
     batched launch, and the continuous-batching server at offered rates of

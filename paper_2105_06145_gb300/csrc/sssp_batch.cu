@@ -71,6 +71,8 @@ struct InstDesc {
     uint32_t source;
     uint64_t param;
     uint64_t seed;
+    uint32_t bidir;          // bidirectional relaxation of chunk records (symmetric graph)
+    uint32_t local_budget;   // local relaxation of super-sparse steps (0 = off)
 };
 
 struct BatchCtrl {
@@ -353,6 +355,26 @@ __device__ bool phase_E(const BatchParams& p, uint64_t k, BatchSmem& S)
     return true;
 }
 
+// Warp-uniform: local relaxation of a super-sparse step of one instance (Sec. 6;
+// the rule of the single solve: the step's queue is at most n/20 and its
+// extracted vertices have mean degree < 20), from the ids the warp has staged
+// for that instance; the edges it relaxes are added to the step's edge count.
+__device__ __noinline__ void local_step(const BatchParams& p, const InstDesc* D, InstCtrl* C, uint64_t k,
+                                        uint32_t* stage, uint32_t& stc, uint32_t lane, uint64_t& lmin,
+                                        uint32_t& lupd)
+{
+    const int c = (int)(k % 3), nx = (int)((k + 1) % 3);
+    const uint64_t q = ldcg32(&C->qsize[c]);
+    const uint64_t fcnt = ldcg32(&C->fcount[c]);
+    const uint64_t fed = ldcg64((const uint64_t*)&C->fedges[c]);
+    const uint64_t theta = ldcg64((const uint64_t*)&C->theta);
+    if (q * 20ull > (uint64_t)D->n || fed >= 20ull * fcnt) return;
+    uint32_t* Qn = (k & 1) ? D->qb : D->qa;
+    const uint64_t le = local_relax(theta, D->local_budget, D->off, D->edges, D->dist, D->inq, stage, stc, lane,
+                                    lmin, lupd, &C->qsize[nx], &p.ctrl->status, Qn, D->n);
+    if (lane == 0 && le) atomicAdd(&C->fedges[c], (unsigned long long)le);
+}
+
 // Phase R: relaxation of every running instance's extracted vertices, work
 // spread over all warps.
 __device__ void phase_R(const BatchParams& p, uint64_t k, BatchSmem& S, uint32_t* stage)
@@ -390,8 +412,10 @@ __device__ void phase_R(const BatchParams& p, uint64_t k, BatchSmem& S, uint32_t
         if ((i_) != cur) {                                                                       \
             if (cur != 0xFFFFFFFFu) {                                                            \
                 InstCtrl* Cc = &p.ictrl[cur];                                                    \
-                uint32_t* Qn = (k & 1) ? p.inst[cur].qb : p.inst[cur].qa;                        \
-                stage_flush(stage, stc, lane, &Cc->qsize[nx], status, Qn, p.inst[cur].n);        \
+                const InstDesc* Dc = &p.inst[cur];                                               \
+                uint32_t* Qn = (k & 1) ? Dc->qb : Dc->qa;                                        \
+                if (Dc->local_budget) local_step(p, Dc, Cc, k, stage, stc, lane, lmin, lupd);    \
+                stage_flush(stage, stc, lane, &Cc->qsize[nx], status, Qn, Dc->n);                \
                 uint32_t u_ = lupd;                                                              \
                 for (int o = 16; o > 0; o >>= 1) u_ += __shfl_xor_sync(FULL_MASK, u_, o);        \
                 uint64_t m_ = lmin;                                                              \
@@ -473,8 +497,12 @@ __device__ void phase_R(const BatchParams& p, uint64_t k, BatchSmem& S, uint32_t
                 uint64_t* const idist = Dp->dist;
                 const uint4 rc = __ldcg(&Dp->items[it - S.pre1[i]]);
                 const uint64_t du = ldcg64(&idist[rc.z]);
-                relax_chunk<false>(rc, du, reinterpret_cast<const uint4*>(Dp->edges), idist, Dp->inq, stage, stc,
-                                   lane, lmin, lupd);
+                if (Dp->bidir)
+                    relax_chunk<true>(rc, du, reinterpret_cast<const uint4*>(Dp->edges), idist, Dp->inq, stage,
+                                      stc, lane, lmin, lupd);
+                else
+                    relax_chunk<false>(rc, du, reinterpret_cast<const uint4*>(Dp->edges), idist, Dp->inq, stage,
+                                       stc, lane, lmin, lupd);
                 if (stc > (uint32_t)(kStage - 256)) {
                     uint32_t* Qn = (k & 1) ? Dp->qb : Dp->qa;
                     stage_flush(stage, stc, lane, &p.ictrl[i].qsize[nx], status, Qn, Dp->n);
@@ -817,6 +845,19 @@ int batch_blocks(int dev, uint32_t* grid)
     return SSSP_OK;
 }
 
+// Bidirectional relaxation and local relaxation of an instance: those of the
+// graph's tuning (sssp_graph_get_tuning) when it is for the batch's rule.
+void batch_extras(const sssp_graph* g, sssp_algo algo, InstDesc* d)
+{
+    sssp_tuning t;
+    d->bidir = 0;
+    d->local_budget = 0;
+    if (sssp_lookup_tuning(g, &t) && t.algo == algo) {
+        d->bidir = ((t.flags & SSSP_SOLVE_BIDIRECTIONAL) && (g->flags & SSSP_GRAPH_SYMMETRIC)) ? 1u : 0u;
+        d->local_budget = (algo == SSSP_RHO || algo == SSSP_DELTA_STAR) ? t.local_budget : 0u;
+    }
+}
+
 // Common path: instance i uses graph gs[i] (n_i, caps), output outs[i].
 int solve_batch(const sssp_graph* const* gs, const uint32_t* sources, uint32_t k, sssp_algo algo,
                 const uint64_t* params, uint64_t* const* outs, void* stream)
@@ -858,6 +899,7 @@ int solve_batch(const sssp_graph* const* gs, const uint32_t* sources, uint32_t k
         d.source = sources[i];
         d.param = params ? params[i] : sssp_graph_param(g, algo);
         d.seed = 0x2105061450000000ull ^ (uint64_t)sources[i];
+        batch_extras(g, algo, &d);
         d.fsmall_cap = g->fsmall_cap;
         d.item_cap = g->item_cap;
         d.inq = reinterpret_cast<uint32_t*>(base); base += align256(4ull * ((g->n + 31ull) / 32));
@@ -1183,6 +1225,7 @@ int sssp_server_create(const sssp_graph* g, const sssp_server_config* cfg, sssp_
         d.edges = g->d_edges;
         d.n = g->n;
         d.param = s->param;
+        batch_extras(g, s->algo, &d);
         d.fsmall_cap = g->fsmall_cap;
         d.item_cap = g->item_cap;
         d.inq = reinterpret_cast<uint32_t*>(base); base += align256(4ull * ((g->n + 31ull) / 32));

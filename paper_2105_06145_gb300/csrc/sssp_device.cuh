@@ -575,4 +575,61 @@ __device__ __forceinline__ void block_reduce_2add_min(uint64_t& a, uint64_t& b, 
     }
 }
 
+// ---------------------------------------------------------------------------
+// Local relaxation of super-sparse steps (Sec. 6, local BFS).
+//
+// The warp's staging buffer is its local frontier: entries [0, lq) have been
+// looked at, [lq, stc) wait.  Up to 32 waiting vertices at a time, a vertex
+// whose distance is still <= theta and whose out-degree is 1..kSmallDeg has its
+// out-edges relaxed at once (WriteMin and Update as in the main relaxation);
+// the ids that queues are appended behind and are looked at in turn.  Every id
+// stays staged and so reaches Q_next: a vertex relaxed here is extracted again
+// in a later step (a vertex this step would have extracted next).  Stops after
+// `budget` relaxed vertices, or when the frontier is exhausted.  Returns the
+// edges relaxed.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ uint64_t local_relax(uint64_t theta, uint32_t budget, const uint64_t* __restrict__ off,
+                                                const uint2* __restrict__ edges, uint64_t* dist, uint32_t* inq,
+                                                uint32_t* stage, uint32_t& stc, uint32_t lane, uint64_t& lmin,
+                                                uint32_t& lupd, unsigned int* qsize, int* status, uint32_t* Qnext,
+                                                uint32_t n)
+{
+    uint32_t lq = 0, done = 0;
+    uint64_t scanned = 0;
+    while (lq < stc && done < budget) {  // warp-uniform
+        if (stc + 256u > (uint32_t)kStage) {
+            // make room: the looked-at prefix goes to the next queue list
+            stage_flush_prefix(stage, stc, lq, lane, qsize, status, Qnext, n);
+            lq = 0;
+            if (stc + (uint32_t)kSmallDeg > (uint32_t)kStage) break;
+        }
+        __syncwarp();
+        uint32_t cnt = stc - lq;
+        cnt = cnt < 32u ? cnt : 32u;
+        uint64_t b = 0, du = 0;
+        uint32_t deg = 0;
+        if (lane < cnt) {
+            const uint32_t x = stage[lq + lane];
+            du = ldcg64(&dist[x]);
+            if (du <= theta) {
+                b = off[x];
+                const uint64_t d = off[x + 1] - b;
+                deg = d <= (uint64_t)kSmallDeg ? (uint32_t)d : 0u;
+            }
+        }
+        // take the lanes whose edges fit in the staging room left (a prefix,
+        // never empty: the room is >= kSmallDeg)
+        const uint32_t room = (uint32_t)kStage - stc;
+        const uint32_t incl = (uint32_t)warp_incl_scan64(deg, lane);
+        const uint32_t take = __popc(__ballot_sync(FULL_MASK, lane < cnt && incl <= room));
+        if (lane >= take) deg = 0;
+        done += __popc(__ballot_sync(FULL_MASK, deg > 0));
+        scanned += __shfl_sync(FULL_MASK, incl, take - 1);
+        lq += take;
+        relax_flat(b, deg, du, edges, dist, inq, stage, stc, lane, lmin, lupd, false, qsize, status, Qnext, n);
+    }
+    return lane == 0 ? scanned : 0;
+}
+
+
 }  // namespace sssp

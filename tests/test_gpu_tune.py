@@ -156,3 +156,32 @@ def test_autotune_restricted_to_one_rule(lib):
         with pytest.raises(lib.SSSPError):
             lib.sssp_autotune_ex(G.handle, srcs, bad, _stream())
     G.close()
+
+
+@pytest.mark.parametrize("algo,param", [(0, 2048), (1, 1 << 12)])
+def test_batched_and_served_with_tuned_local_and_bidirectional_relaxation(lib, algo, param):
+    """The batched and serving kernels take the graph's tuned bidirectional and
+    local relaxation; every instance still equals the oracle."""
+    g = gg.road(200, 0.75, seed=13)
+    h = gg.rmat(13, 16, gen_seed=51, wseed=52)
+    for x in (g, h):
+        G = lib.Graph(x, lib.SSSP_GRAPH_SYMMETRIC | lib.SSSP_GRAPH_VERIFY)
+        lib.sssp_graph_set_tuning(G.handle, {"algo": algo, "param": param, "shape": 0,
+                                             "flags": lib.SSSP_SOLVE_BIDIRECTIONAL, "local_budget": 256})
+        srcs = gg.pick_sources(x, 6, 14)
+        out = torch.empty(len(srcs) * x.n, dtype=torch.int64, device="cuda")
+        lib.sssp_solve_sources(G.handle, srcs, algo, None, out.data_ptr(), _stream())
+        st, stats = lib.sssp_batch_last_stats(len(srcs), _stream())
+        assert st == 0
+        got = out.view(len(srcs), x.n).cpu().numpy().view(np.uint64)
+        for i, s in enumerate(srcs):
+            assert np.array_equal(got[i], oracle.dijkstra(x, s)), (x.name, i)
+        srv = lib.sssp_server_create(G.handle, slots=4, algo=algo, param=0)
+        bufs = [torch.full((x.n,), 7, dtype=torch.int64, device="cuda") for _ in srcs]
+        tickets = [lib.sssp_server_submit(srv, s, b.data_ptr()) for s, b in zip(srcs, bufs)]
+        for tk, s, b in zip(tickets, srcs, bufs):
+            info = lib.sssp_server_wait(srv, tk, 60_000_000_000)
+            assert info["status"] == 0
+            assert np.array_equal(b.cpu().numpy().view(np.uint64), oracle.dijkstra(x, s)), (x.name, s)
+        lib.sssp_server_destroy(srv)
+        G.close()

@@ -430,6 +430,65 @@ def run_serve_sweep(args):
         torch.cuda.empty_cache()
 
 
+def run_lbpq(args):
+    """--lbpq: the LaB-PQ comparison of App. F on the device: n records all in
+    Q with random 40-bit keys; Extract of the rho smallest (theta = the rho-th
+    smallest key) from the tournament tree (Sec. 4.2) and from the array
+    (Sec. 4.3, a scan of the whole list), 10 runs each, the extracted records
+    re-inserted between tree runs (untimed, as the paper leaves out update
+    cost)."""
+    import torch
+    from paper_2105_06145_gb300 import sssp
+    n = args.lbpq_n
+    rng = np.random.default_rng(12)
+    key = rng.integers(0, 1 << 40, n, dtype=np.uint64)
+    kd = torch.from_numpy(key.view(np.int64)).cuda()
+    del key
+    ids = torch.arange(n, dtype=torch.int32, device="cuda")
+    srt = torch.sort(kd).values
+    stream_obj = torch.cuda.current_stream()
+    st = stream_obj.cuda_stream
+    t = sssp.sssp_tourney_create(n)
+    out = torch.empty(n, dtype=torch.int32, device="cuda")
+    cnt = torch.zeros(4, dtype=torch.int32, device="cuda")
+    mn = torch.zeros(1, dtype=torch.int64, device="cuda")
+    t0 = time.perf_counter()
+    sssp.sssp_tourney_update(t, ids.data_ptr(), n, st)
+    sssp.sssp_tourney_min(t, kd.data_ptr(), mn.data_ptr(), st)  # builds every interior key
+    torch.cuda.synchronize()
+    build_s = time.perf_counter() - t0
+    ext = torch.empty(n, dtype=torch.int32, device="cuda")
+    keep = torch.empty(n, dtype=torch.int32, device="cuda")
+    rows = []
+    for lg in args.lbpq_rho.split(","):
+        rho = 1 << int(lg)
+        theta = int(srt[rho - 1].item())
+        tree_ms, arr_ms, got = 0.0, 0.0, 0
+        for _ in range(10):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream_obj)
+            sssp.sssp_tourney_extract(t, kd.data_ptr(), theta, out.data_ptr(), cnt.data_ptr(), st)
+            e1.record(stream_obj)
+            torch.cuda.synchronize()
+            tree_ms += e0.elapsed_time(e1)
+            got = int(cnt[0].item())
+            sssp.sssp_tourney_update(t, out.data_ptr(), got, st)  # back into Q, untimed
+        sssp.sssp_tourney_min(t, kd.data_ptr(), mn.data_ptr(), st)
+        for _ in range(10):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream_obj)
+            sssp.sssp_array_extract(ids.data_ptr(), n, kd.data_ptr(), theta, ext.data_ptr(), cnt.data_ptr() + 4,
+                                    keep.data_ptr(), cnt.data_ptr() + 8, st)
+            e1.record(stream_obj)
+            torch.cuda.synchronize()
+            arr_ms += e0.elapsed_time(e1)
+        arr_got = int(cnt[1].item())
+        rows.append({"rho": rho, "extracted": got, "tree_ms_10_runs": tree_ms, "array_ms_10_runs": arr_ms,
+                     "array_extracted": arr_got})
+    sssp.sssp_tourney_destroy(t)
+    print(json.dumps({"lbpq_extract": {"n": n, "tree_build_s": build_s, "rows": rows}}), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -452,11 +511,17 @@ def main():
     ap.add_argument("--serve-rates", default="1000,2000,5000,10000,20000,50000")
     ap.add_argument("--serve-window", type=float, default=1.0)
     ap.add_argument("--serve-slots", type=int, default=0)
+    ap.add_argument("--lbpq", action="store_true", help="the tournament-tree vs array LaB-PQ Extract comparison only")
+    ap.add_argument("--lbpq-n", type=int, default=100_000_000)
+    ap.add_argument("--lbpq-rho", default="10,13,16,19,22,25", help="log2 of the rho values")
     args = ap.parse_args()
 
     rank, world, local = dist_env()
     if args.serve:
         run_serve_sweep(args)
+        return
+    if args.lbpq:
+        run_lbpq(args)
         return
     g, srcs, label = build_workload(args.workload, args.scale)
 

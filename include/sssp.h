@@ -429,6 +429,46 @@ int sssp_graph_class(const sssp_graph* g, uint64_t* key);
    else rho-Stepping with rho = max(64, n/16). */
 int sssp_solve_tuned(const sssp_graph* g, uint32_t source, uint64_t* dist_out, void* stream);
 
+/* ------------------------------------------------------------------------ */
+/* Tournament-tree LaB-PQ (Sec. 4.2, Algorithm 2, Theorem 4.1) on the device, */
+/* as a stand-alone data structure: a complete binary tree over the records  */
+/* 0..n-1 whose interior nodes keep the smallest key below them.  Keys are    */
+/* read from a caller's key array (device uint64[n], "delta" of Sec. 3.1);    */
+/* every change of a record's key must be followed by an update of that       */
+/* record (as Algorithm 1 does with Update).  Calls are asynchronous on       */
+/* `stream` and must be ordered on one stream.                                */
+/* ------------------------------------------------------------------------ */
+
+typedef struct sssp_tourney sssp_tourney;
+
+/* An empty tree over n records (1 <= n <= 2^31).  Synchronous. */
+int sssp_tourney_create(uint32_t n, sssp_tourney** out);
+int sssp_tourney_destroy(sssp_tourney* t);
+
+/* LazyInsert / Update (Algorithm 2: Mark(id, 1)) of a batch of b record ids
+   (DEVICE uint32[b]; ids >= n are ignored; repeats allowed). */
+int sssp_tourney_update(sssp_tourney* t, const uint32_t* ids, uint32_t b, void* stream);
+
+/* Extract(theta) (Algorithm 2): every record in Q whose key is <= theta leaves
+   Q; their ids go to out (DEVICE uint32[n], in no particular order) and their
+   number to *count_out (DEVICE uint32). */
+int sssp_tourney_extract(sssp_tourney* t, const uint64_t* keys, uint64_t theta, uint32_t* out,
+                         uint32_t* count_out, void* stream);
+
+/* Reduce (Sec. 3.1, min): the smallest key in Q (UINT64_MAX when Q is empty)
+   to *min_out (DEVICE uint64). */
+int sssp_tourney_min(sssp_tourney* t, const uint64_t* keys, uint64_t* min_out, void* stream);
+
+/* Copy of the inQ flags (DEVICE uint32[ceil(n/32)], bit id of word id/32). */
+int sssp_tourney_inq(const sssp_tourney* t, uint32_t* inq_out, void* stream);
+
+/* Extract of the array-based LaB-PQ (Sec. 4.3) as a stand-alone operation, for
+   comparison with the tree (App. F): the ids of list[0..q) (DEVICE) whose key
+   is <= theta go to ext, the others to keep (DEVICE uint32[q] each), their
+   numbers to *ext_count / *keep_count (DEVICE uint32). */
+int sssp_array_extract(const uint32_t* list, uint32_t q, const uint64_t* keys, uint64_t theta, uint32_t* ext,
+                       uint32_t* ext_count, uint32_t* keep, uint32_t* keep_count, void* stream);
+
 /* Static description of a status code (never NULL). */
 const char* sssp_status_string(int status);
 

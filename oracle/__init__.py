@@ -16,6 +16,8 @@ What it computes (see oracle.c for the passages each function follows):
   splitmix64      -- the counter-based generator the sampler uses
   check           -- the invariants that characterise d
   hops            -- fewest-hop shortest-path depth (Sec. 2), for step bounds
+  lbpq_extract    -- LaB-PQ Extract(theta) on the plain set (Sec. 3.1, Table 1)
+  lbpq_min        -- LaB-PQ Reduce (min) on the plain set
 """
 from __future__ import annotations
 
@@ -84,6 +86,10 @@ def _L():
         lib.oracle_stepping.argtypes = [u32, P, P, P, u32, i32, u64, u64, P, P,
                                         ctypes.POINTER(Stats)]
         lib.oracle_stepping.restype = i32
+        lib.oracle_lbpq_extract.argtypes = [u32, P, P, u64, P]
+        lib.oracle_lbpq_extract.restype = u32
+        lib.oracle_lbpq_min.argtypes = [u32, P, P]
+        lib.oracle_lbpq_min.restype = u64
         _lib = lib
     return _lib
 
@@ -193,3 +199,20 @@ def stepping(g, s: int, algo: int, param: int, seed: int = 0,
     if rc != 0:
         raise ValueError("oracle_stepping failed")
     return dist, st.as_dict(), ext
+
+
+def lbpq_extract(inq: np.ndarray, key: np.ndarray, theta: int) -> np.ndarray:
+    """LaB-PQ Extract(theta) on the plain set (inq: uint8[n], updated in place):
+    the ids in Q with key <= theta, increasing."""
+    assert inq.dtype == np.uint8 and inq.flags.c_contiguous
+    key = np.ascontiguousarray(key, dtype=np.uint64)
+    out = np.empty(max(1, inq.size), dtype=np.uint32)
+    c = _L().oracle_lbpq_extract(inq.size, inq.ctypes.data, key.ctypes.data, theta, out.ctypes.data)
+    return out[:c].copy()
+
+
+def lbpq_min(inq: np.ndarray, key: np.ndarray) -> int:
+    """LaB-PQ Reduce (min): the smallest key in Q, UINT64_MAX when empty."""
+    inq = np.ascontiguousarray(inq, dtype=np.uint8)
+    key = np.ascontiguousarray(key, dtype=np.uint64)
+    return int(_L().oracle_lbpq_min(inq.size, inq.ctypes.data, key.ctypes.data))

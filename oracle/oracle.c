@@ -25,6 +25,9 @@
  *   oracle_splitmix64    -- the counter-based generator the rho sampler draws
  *                           from (Steele, Lea, Flood, OOPSLA 2014).
  *   oracle_check         -- invariants that characterise d (Sec. 2).
+ *   oracle_lbpq_extract / oracle_lbpq_min -- the LaB-PQ interface on a plain
+ *                           set (Sec. 3.1, Table 1), the definition the device
+ *                           tournament tree (Sec. 4.2) must reproduce.
  *   oracle_hops          -- fewest-hop shortest-path depth h(v) (Sec. 2,
  *                           "hop distance"), used for the step bounds of
  *                           Lemma 5.1 and Theorems 5.3 / 5.5.
@@ -527,4 +530,28 @@ int oracle_stepping(uint32_t n, const uint64_t* off, const uint32_t* tgt,
     if (st) *st = z;
     free(inq); free(Q); free(F); free(cnt);
     return 0;
+}
+
+/*
+ * The LaB-PQ interface as a plain set (Sec. 3.1, Table 1): Q holds the ids
+ * with inq[id] = 1; the key of id is key[id].  Extract(theta) returns every id
+ * in Q whose key is <= theta, in increasing id order, and removes it from Q;
+ * Reduce returns the smallest key in Q (UINT64_MAX for an empty Q).  This is
+ * the definition that any implementation -- the array of Sec. 4.3 or the
+ * tournament tree of Sec. 4.2 -- must reproduce; O(n) per call.
+ */
+uint32_t oracle_lbpq_extract(uint32_t n, uint8_t* inq, const uint64_t* key, uint64_t theta, uint32_t* out)
+{
+    uint32_t c = 0;
+    for (uint32_t v = 0; v < n; ++v)
+        if (inq[v] && key[v] <= theta) { inq[v] = 0; out[c++] = v; }
+    return c;
+}
+
+uint64_t oracle_lbpq_min(uint32_t n, const uint8_t* inq, const uint64_t* key)
+{
+    uint64_t m = ORC_INF;
+    for (uint32_t v = 0; v < n; ++v)
+        if (inq[v] && key[v] < m) m = key[v];
+    return m;
 }

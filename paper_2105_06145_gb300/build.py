@@ -15,7 +15,8 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libsssp.so")
-SOURCES = ["sssp_kernels.cu", "sssp_api.cu", "sssp_noalloc.cu", "sssp_batch.cu", "sssp_tune.cu"]
+SOURCES = ["sssp_kernels.cu", "sssp_api.cu", "sssp_noalloc.cu", "sssp_batch.cu", "sssp_tune.cu",
+           "sssp_tourney.cu"]
 HEADERS = ["sssp_internal.h", "sssp_device.cuh", os.path.join("..", "..", "include", "sssp.h")]
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]

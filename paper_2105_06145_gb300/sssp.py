@@ -143,7 +143,24 @@ EXPORTED = ["sssp_graph_create", "sssp_graph_destroy", "sssp_graph_info", "sssp_
             "sssp_server_submit", "sssp_server_poll", "sssp_server_wait", "sssp_server_stats",
             "sssp_server_destroy", "sssp_server_drain", "sssp_graph_create_ex", "sssp_solve_host_ex",
             "sssp_autotune", "sssp_graph_get_tuning", "sssp_graph_set_tuning", "sssp_graph_class",
-            "sssp_solve_tuned", "sssp_autotune_ex"]
+            "sssp_solve_tuned", "sssp_autotune_ex", "sssp_tourney_create", "sssp_tourney_destroy",
+            "sssp_tourney_update", "sssp_tourney_extract", "sssp_tourney_min", "sssp_tourney_inq",
+            "sssp_array_extract"]
+
+_lib.sssp_tourney_create.argtypes = [_u32, ctypes.POINTER(_P)]
+_lib.sssp_tourney_create.restype = _i32
+_lib.sssp_tourney_destroy.argtypes = [_P]
+_lib.sssp_tourney_destroy.restype = _i32
+_lib.sssp_tourney_update.argtypes = [_P, _P, _u32, _P]
+_lib.sssp_tourney_update.restype = _i32
+_lib.sssp_tourney_extract.argtypes = [_P, _P, _u64, _P, _P, _P]
+_lib.sssp_tourney_extract.restype = _i32
+_lib.sssp_tourney_min.argtypes = [_P, _P, _P, _P]
+_lib.sssp_tourney_min.restype = _i32
+_lib.sssp_tourney_inq.argtypes = [_P, _P, _P]
+_lib.sssp_tourney_inq.restype = _i32
+_lib.sssp_array_extract.argtypes = [_P, _u32, _P, _u64, _P, _P, _P, _P, _P]
+_lib.sssp_array_extract.restype = _i32
 
 
 class sssp_tuning(ctypes.Structure):
@@ -414,6 +431,38 @@ def sssp_graph_class(g: int) -> int:
 
 def sssp_solve_tuned(g: int, source: int, dist_out_ptr: int, stream: int = 0) -> int:
     return _check(_lib.sssp_solve_tuned(g, source, dist_out_ptr, stream or None), "sssp_solve_tuned")
+
+
+def sssp_tourney_create(n: int) -> int:
+    h = _P()
+    _check(_lib.sssp_tourney_create(n, ctypes.byref(h)), "sssp_tourney_create")
+    return h.value
+
+
+def sssp_tourney_destroy(t: int) -> None:
+    _check(_lib.sssp_tourney_destroy(t), "sssp_tourney_destroy")
+
+
+def sssp_tourney_update(t: int, ids_ptr: int, b: int, stream: int = 0) -> None:
+    _check(_lib.sssp_tourney_update(t, ids_ptr or None, b, stream or None), "sssp_tourney_update")
+
+
+def sssp_tourney_extract(t: int, keys_ptr: int, theta: int, out_ptr: int, count_ptr: int, stream: int = 0) -> None:
+    _check(_lib.sssp_tourney_extract(t, keys_ptr, theta, out_ptr, count_ptr, stream or None), "sssp_tourney_extract")
+
+
+def sssp_tourney_min(t: int, keys_ptr: int, min_ptr: int, stream: int = 0) -> None:
+    _check(_lib.sssp_tourney_min(t, keys_ptr, min_ptr, stream or None), "sssp_tourney_min")
+
+
+def sssp_tourney_inq(t: int, inq_ptr: int, stream: int = 0) -> None:
+    _check(_lib.sssp_tourney_inq(t, inq_ptr, stream or None), "sssp_tourney_inq")
+
+
+def sssp_array_extract(list_ptr: int, q: int, keys_ptr: int, theta: int, ext_ptr: int, ext_count_ptr: int,
+                       keep_ptr: int, keep_count_ptr: int, stream: int = 0) -> None:
+    _check(_lib.sssp_array_extract(list_ptr or None, q, keys_ptr, theta, ext_ptr, ext_count_ptr, keep_ptr,
+                                   keep_count_ptr, stream or None), "sssp_array_extract")
 
 
 class Graph:

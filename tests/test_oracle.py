@@ -372,3 +372,49 @@ def test_delta_stepping_distances_and_extraction_bound():
         ds, st, ext = oracle.stepping(g, s, oracle.DELTA, delta, want_ext=True)
         assert np.array_equal(ds, d)
         assert np.all(ext[reach].astype(np.int64) <= hv[reach])
+
+
+def _golden_tree():
+    from conftest import golden_path
+    vals = {}
+    for line in open(golden_path("tournament_tree_figure.txt")):
+        if line.startswith("#") or not line.strip():
+            continue
+        k, *v = line.split()
+        vals[k] = [int(x) for x in v]
+    return np.array(vals["keys"], dtype=np.uint64), vals["root"][0]
+
+
+def test_lbpq_oracle_on_the_papers_tournament_tree_example():
+    """Sec. 4.2: the tree of the figure holds records with keys 3,8,4,6,1,5 and
+    its root keeps the smallest key, 1."""
+    key, root = _golden_tree()
+    inq = np.ones(key.size, np.uint8)
+    assert oracle.lbpq_min(inq, key) == root
+    got = oracle.lbpq_extract(inq, key, 4)
+    assert sorted(key[got].tolist()) == [1, 3, 4]
+    assert oracle.lbpq_min(inq, key) == 5 and oracle.lbpq_extract(inq, key, 4).size == 0
+    assert sorted(oracle.lbpq_extract(inq, key, (1 << 64) - 1).tolist()) == [1, 3, 5]
+    assert oracle.lbpq_min(inq, key) == (1 << 64) - 1
+
+
+def test_lbpq_oracle_against_sorting():
+    """Extract(theta) returns exactly the queued records that come first in key
+    order up to theta (an order-statistics view, computed here by sorting), and
+    Reduce is the first key in that order."""
+    rng = np.random.default_rng(3)
+    for trial in range(200):
+        n = int(rng.integers(1, 300))
+        key = rng.integers(0, 50, n).astype(np.uint64)
+        inq = (rng.random(n) < 0.6).astype(np.uint8)
+        q = np.flatnonzero(inq)
+        order = q[np.argsort(key[q], kind="stable")]
+        if q.size:
+            assert oracle.lbpq_min(inq, key) == int(key[order[0]])
+        else:
+            assert oracle.lbpq_min(inq, key) == (1 << 64) - 1
+        theta = int(rng.integers(0, 60))
+        kcount = int(np.searchsorted(key[order], theta, side="right"))
+        got = oracle.lbpq_extract(inq, key, theta)
+        assert sorted(got.tolist()) == sorted(order[:kcount].tolist())
+        assert np.array_equal(np.flatnonzero(inq), np.sort(order[kcount:]))

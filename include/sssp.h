@@ -233,8 +233,9 @@ int sssp_rho_threshold(const uint32_t* queue, uint32_t q, const uint64_t* dist, 
  *   dist_out  DEVICE uint64[k * n], instance-major: instance i's distances at
  *             dist_out[i*n .. i*n + n)
  * When the graph has a tuning for `algo` (sssp_graph_get_tuning), each
- * instance also uses its bidirectional relaxation and local-relaxation budget
- * (sssp_options); the distances do not depend on them.
+ * instance also uses its bidirectional relaxation and, on graphs of at least
+ * 2^20 vertices, its local-relaxation budget (sssp_options); the distances
+ * do not depend on them.
  * Asynchronous on `stream`.  Working memory (per instance: queue bitmap, two
  * queue lists, extraction records) is a library-owned per-device workspace
  * grown to the largest batch seen; batched calls on one device share it, so

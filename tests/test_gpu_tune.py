@@ -161,14 +161,15 @@ def test_autotune_restricted_to_one_rule(lib):
 @pytest.mark.parametrize("algo,param", [(0, 2048), (1, 1 << 12)])
 def test_batched_and_served_with_tuned_local_and_bidirectional_relaxation(lib, algo, param):
     """The batched and serving kernels take the graph's tuned bidirectional and
-    local relaxation; every instance still equals the oracle."""
-    g = gg.road(200, 0.75, seed=13)
+    local relaxation (local relaxation on graphs of >= 2^20 vertices: the
+    1024^2 road-like grid); every instance still equals the oracle."""
+    g = gg.road(1024, 0.75, seed=13)
     h = gg.rmat(13, 16, gen_seed=51, wseed=52)
     for x in (g, h):
         G = lib.Graph(x, lib.SSSP_GRAPH_SYMMETRIC | lib.SSSP_GRAPH_VERIFY)
         lib.sssp_graph_set_tuning(G.handle, {"algo": algo, "param": param, "shape": 0,
                                              "flags": lib.SSSP_SOLVE_BIDIRECTIONAL, "local_budget": 256})
-        srcs = gg.pick_sources(x, 6, 14)
+        srcs = gg.pick_sources(x, 4, 14)
         out = torch.empty(len(srcs) * x.n, dtype=torch.int64, device="cuda")
         lib.sssp_solve_sources(G.handle, srcs, algo, None, out.data_ptr(), _stream())
         st, stats = lib.sssp_batch_last_stats(len(srcs), _stream())

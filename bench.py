@@ -274,9 +274,10 @@ def measure_batched(sssp, G, g, torch, stream, stream_obj) -> dict:
 
 def measure_workload(name, sssp, torch, stream, stream_obj, rates_x=(2, 20)) -> dict:
     """Road-like (4096^2 jittered grid) or k-NN (2M points) workload: the
-    autotuner's choice as a plain loop of single solves, 64 sources in one
-    batched launch, and the continuous-batching server at offered rates of
-    rates_x times the plain loop's rate."""
+    autotuner's single-solve choice as a plain loop of single solves; 64
+    sources in one batched launch and the continuous-batching server, both in
+    the batch autotuner's choice, at offered rates of rates_x times the plain
+    loop's rate."""
     from paper_2105_06145_gb300 import graphgen as gg
     if name == "road4096":
         h, _ = gg.workload_road(4096)
@@ -292,8 +293,13 @@ def measure_workload(name, sssp, torch, stream, stream_obj, rates_x=(2, 20)) -> 
     tp = _timed(torch, stream_obj, lambda: [sssp.sssp_solve_tuned(Gx.handle, s_, one.data_ptr(), stream)
                                             for s_ in srcs[:10]])
     plain_qps = 10e3 / tp
+    t0 = time.perf_counter()
+    btune = sssp.sssp_autotune_batch(Gx.handle, srcs[:64], (1 << sssp.SSSP_RHO) | (1 << sssp.SSSP_DELTA_STAR),
+                                     stream)
+    btune_s = time.perf_counter() - t0
+    torch.cuda.empty_cache()
     out = torch.empty(64 * h.n, dtype=torch.int64, device="cuda")
-    tb = _timed(torch, stream_obj, lambda: sssp.sssp_solve_sources(Gx.handle, srcs[:64], tune["algo"], None,
+    tb = _timed(torch, stream_obj, lambda: sssp.sssp_solve_sources(Gx.handle, srcs[:64], btune["algo"], None,
                                                                    out.data_ptr(), stream))
     st, _ = sssp.sssp_batch_last_stats(64, stream)
     sssp.sssp_solve_tuned(Gx.handle, srcs[63], one.data_ptr(), stream)
@@ -301,13 +307,13 @@ def measure_workload(name, sssp, torch, stream, stream_obj, rates_x=(2, 20)) -> 
     same = bool(torch.equal(out.view(64, h.n)[63], one))
     del out
     torch.cuda.empty_cache()
-    res = {"n": h.n, "m": h.m, "tuning": tune, "tune_s": tune_s,
+    res = {"n": h.n, "m": h.m, "tuning": tune, "tune_s": tune_s, "batch_tuning": btune, "batch_tune_s": btune_s,
            "plain": {"queries_per_s": plain_qps, "gteps": plain_qps * h.m / 1e9},
            "batched64": {"queries_per_s": 64e3 / tb, "speedup": tp / 10 * 64 / tb, "status": st,
                          "last_equal_to_single": same}}
     rates = [int(max(1, round(x * plain_qps))) for x in rates_x]
     sv = measure_serving(sssp, Gx, h, torch, srcs, rates, window_s=1.0, hard_s=8.0, slots=64,
-                         algo=tune["algo"], param=tune["param"], tuned=True)
+                         algo=btune["algo"], param=btune["param"], tuned=True)
     res["served"] = sv
     Gx.close()
     del Gx

@@ -416,6 +416,18 @@ int sssp_autotune(sssp_graph* g, const uint32_t* sources, uint32_t k, sssp_tunin
 int sssp_autotune_ex(sssp_graph* g, const uint32_t* sources, uint32_t k, uint32_t rules, sssp_tuning* out,
                      void* stream);
 
+/* The best configuration of batched launches of k sources on g (HOST
+   uint32[k], k <= SSSP_MAX_BATCH): rho / Delta candidates as in
+   sssp_autotune's first stage (rules: as sssp_autotune_ex), each timed as one
+   sssp_solve_sources launch over up to 8 of the sources, the two best of each
+   rule re-timed on all k; on graphs of >= 2^20 vertices and mean degree < 20
+   also local budgets 0, 64, 256 for the winner.  Kept as the graph's batch tuning, which
+   sssp_solve_sources / sssp_solve_multi (params == NULL) and the server
+   (param == 0) use before the single-solve tuning.  Synchronous; allocates k*n
+   distances for the measurements.  ms = time of one batched launch. */
+int sssp_autotune_batch(sssp_graph* g, const uint32_t* sources, uint32_t k, uint32_t rules, sssp_tuning* out,
+                        void* stream);
+
 /* The tuning that applies to g (its own, else its class's); INVALID_ARG when none. */
 int sssp_graph_get_tuning(const sssp_graph* g, sssp_tuning* out);
 

@@ -859,7 +859,7 @@ void batch_extras(const sssp_graph* g, sssp_algo algo, InstDesc* d)
     sssp_tuning t;
     d->bidir = 0;
     d->local_budget = 0;
-    if (sssp_lookup_tuning(g, &t) && t.algo == algo) {
+    if (sssp_lookup_batch_tuning(g, &t) && t.algo == algo) {
         d->bidir = ((t.flags & SSSP_SOLVE_BIDIRECTIONAL) && (g->flags & SSSP_GRAPH_SYMMETRIC)) ? 1u : 0u;
         if ((algo == SSSP_RHO || algo == SSSP_DELTA_STAR) && g->n >= kBatchLocalMinN) d->local_budget = t.local_budget;
     }
@@ -878,7 +878,7 @@ int solve_batch(const sssp_graph* const* gs, const uint32_t* sources, uint32_t k
         const sssp_graph* g = gs[i];
         if (!g || !outs[i] || sources[i] >= g->n) return SSSP_ERR_INVALID_ARG;
         if (dev < 0) dev = g->device; else if (g->device != dev) return SSSP_ERR_INVALID_ARG;
-        const uint64_t prm = params ? params[i] : sssp_graph_param(g, algo);
+        const uint64_t prm = params ? params[i] : sssp_graph_batch_param(g, algo);
         if (algo_needs_param(algo) && prm == 0) return SSSP_ERR_INVALID_ARG;
         scratch += instance_scratch_bytes(g->n, g->fsmall_cap, g->item_cap);
         min_n = g->n < min_n ? g->n : min_n;
@@ -904,7 +904,7 @@ int solve_batch(const sssp_graph* const* gs, const uint32_t* sources, uint32_t k
         d.dist = outs[i];
         d.n = g->n;
         d.source = sources[i];
-        d.param = params ? params[i] : sssp_graph_param(g, algo);
+        d.param = params ? params[i] : sssp_graph_batch_param(g, algo);
         d.seed = 0x2105061450000000ull ^ (uint64_t)sources[i];
         batch_extras(g, algo, &d);
         d.fsmall_cap = g->fsmall_cap;
@@ -1176,7 +1176,7 @@ int sssp_server_create(const sssp_graph* g, const sssp_server_config* cfg, sssp_
     s->g = g;
     s->device = g->device;
     s->algo = c.algo;
-    s->param = c.param ? c.param : sssp_graph_param(g, c.algo);
+    s->param = c.param ? c.param : sssp_graph_batch_param(g, c.algo);
     if (algo_needs_param(s->algo) && s->param == 0) { delete s; return SSSP_ERR_INVALID_ARG; }
     s->idle_ns = c.idle_ns ? c.idle_ns : 2000000ull;
     // admission by free HBM: per-slot working memory out of a fraction of what is free

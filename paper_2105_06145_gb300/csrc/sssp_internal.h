@@ -173,6 +173,8 @@ struct sssp_graph {
     uint32_t flags = 0;                    // SSSP_GRAPH_* flags given at creation
     bool tuned = false;                    // tuning holds an autotuner result (or a set one)
     sssp_tuning tuning = {};
+    bool batch_tuned = false;              // batch_tuning holds a result of sssp_autotune_batch
+    sssp_tuning batch_tuning = {};
     std::mutex mu;                         // guards lazy allocations / attributes
 };
 
@@ -204,3 +206,7 @@ inline __host__ __device__ bool algo_needs_param(int algo)
 uint64_t sssp_class_key(const sssp_graph* g);
 bool sssp_lookup_tuning(const sssp_graph* g, sssp_tuning* out);
 uint64_t sssp_graph_param(const sssp_graph* g, sssp_algo algo);
+// The tuning batched and serving launches use: the graph's batch tuning
+// (sssp_autotune_batch), else sssp_lookup_tuning's.
+bool sssp_lookup_batch_tuning(const sssp_graph* g, sssp_tuning* out);
+uint64_t sssp_graph_batch_param(const sssp_graph* g, sssp_algo algo);

@@ -112,6 +112,22 @@ uint64_t sssp_graph_param(const sssp_graph* g, sssp_algo algo)
     return sssp_default_param(g->n, g->m, algo, g->mean_w);
 }
 
+bool sssp_lookup_batch_tuning(const sssp_graph* g, sssp_tuning* out)
+{
+    if (g->batch_tuned) {
+        *out = g->batch_tuning;
+        return true;
+    }
+    return sssp_lookup_tuning(g, out);
+}
+
+uint64_t sssp_graph_batch_param(const sssp_graph* g, sssp_algo algo)
+{
+    sssp_tuning t;
+    if (sssp_lookup_batch_tuning(g, &t) && t.algo == algo) return t.param;
+    return sssp_default_param(g->n, g->m, algo, g->mean_w);
+}
+
 extern "C" {
 
 int sssp_graph_class(const sssp_graph* g, uint64_t* key)
@@ -235,6 +251,130 @@ int sssp_autotune_ex(sssp_graph* g, const uint32_t* sources, uint32_t k, uint32_
         g_class_table[sssp_class_key(g)] = t;
     }
     if (out) *out = t;
+    return SSSP_OK;
+}
+
+// Batched launches have their own best configuration (the device is shared by
+// k instances, so a rule or parameter that is fastest alone is not always
+// fastest in a batch).  Candidates as in sssp_autotune's first stage, each
+// timed as one sssp_solve_sources launch over up to 8 of the sources (with the
+// local budget the batch would use); the two best of each rule re-timed on all
+// k sources; then local budgets 0, 64 and 256 for the winner (all k sources)
+// on graphs where batched launches use local relaxation.  The result is kept as the graph's batch tuning,
+// which the batched and serving calls prefer.
+int sssp_autotune_batch(sssp_graph* g, const uint32_t* sources, uint32_t k, uint32_t rules, sssp_tuning* out,
+                        void* stream)
+{
+    if (!g || !sources || k == 0 || k > sssp::kMaxBatch) return SSSP_ERR_INVALID_ARG;
+    if (rules == 0 || (rules & ~((1u << SSSP_RHO) | (1u << SSSP_DELTA_STAR)))) return SSSP_ERR_INVALID_ARG;
+    for (uint32_t i = 0; i < k; ++i)
+        if (sources[i] >= g->n) return SSSP_ERR_INVALID_ARG;
+    cudaError_t e = cudaSetDevice(g->device);
+    if (e != cudaSuccess) return fail(e);
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    uint64_t* dist = nullptr;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    if ((e = cudaMalloc(reinterpret_cast<void**>(&dist), sizeof(uint64_t) * (size_t)g->n * k)) != cudaSuccess)
+        return fail(e);
+    if ((e = cudaEventCreate(&e0)) != cudaSuccess || (e = cudaEventCreate(&e1)) != cudaSuccess) {
+        cudaFree(dist);
+        if (e0) cudaEventDestroy(e0);
+        return fail(e);
+    }
+    const bool sym = (g->flags & SSSP_GRAPH_SYMMETRIC) != 0;
+    sssp_tuning single;
+    const uint32_t local0 = sssp_lookup_tuning(g, &single) ? single.local_budget : 0u;
+    // candidates are compared on up to kSweep of the sources; the winner is
+    // timed on all k
+    constexpr uint32_t kSweep = 8;
+    uint32_t kk = k < kSweep ? k : kSweep;
+    auto time_batch = [&](const sssp_tuning& t, double* ms) -> int {
+        {
+            std::lock_guard<std::mutex> lk(g->mu);
+            g->batch_tuning = t;
+            g->batch_tuned = true;
+        }
+        cudaError_t ee = cudaEventRecord(e0, st);
+        if (ee != cudaSuccess) return fail(ee);
+        int r = sssp_solve_sources(g, sources, kk, t.algo, nullptr, dist, stream);
+        if (r != SSSP_OK) return r;
+        if ((ee = cudaEventRecord(e1, st)) != cudaSuccess) return fail(ee);
+        if ((ee = cudaEventSynchronize(e1)) != cudaSuccess) return fail(ee);
+        sssp_stats s0;
+        r = sssp_batch_last_stats(&s0, 1, stream);
+        if (r != SSSP_OK) return r;
+        float tm = 0;
+        if ((ee = cudaEventElapsedTime(&tm, e0, e1)) != cudaSuccess) return fail(ee);
+        *ms = tm;
+        return SSSP_OK;
+    };
+    std::vector<sssp_tuning> cand;
+    auto add = [&](sssp_algo a, uint64_t prm) {
+        sssp_tuning t;
+        memset(&t, 0, sizeof t);
+        t.algo = a;
+        t.param = prm;
+        t.flags = sym ? SSSP_SOLVE_BIDIRECTIONAL : 0u;
+        t.local_budget = local0;
+        for (const sssp_tuning& c : cand) if (c.algo == a && c.param == prm) return;
+        cand.push_back(t);
+    };
+    if (rules & (1u << SSSP_RHO))
+        for (uint32_t j = 2; j <= 10; j += 2) add(SSSP_RHO, ((uint64_t)g->n >> j) < 64 ? 64 : ((uint64_t)g->n >> j));
+    if (rules & (1u << SSSP_DELTA_STAR))
+        for (double f : {0.125, 0.5, 2.0, 8.0}) {
+            const double d = g->mean_w * f;
+            add(SSSP_DELTA_STAR, d > 1.0 ? (uint64_t)d : 1ull);
+        }
+    int rc = SSSP_OK;
+    uint32_t timed = 0;
+    sssp_tuning best = cand[0];
+    double best_ms = INFINITY, ms = 0;
+    rc = time_batch(cand[0], &ms);  // warm-up (first launch, workspace growth)
+    std::vector<double> sweep(cand.size(), INFINITY);
+    for (size_t i = 0; i < cand.size() && rc == SSSP_OK; ++i) {
+        if ((rc = time_batch(cand[i], &sweep[i])) != SSSP_OK) break;
+        ++timed;
+    }
+    // the two best of each rule on the small sweep, re-timed on all k sources
+    // (a few instances are latency-bound and can rank configurations
+    // differently from a full batch)
+    kk = k;
+    for (sssp_algo a : {SSSP_RHO, SSSP_DELTA_STAR}) {
+        for (int r = 0; r < 2 && rc == SSSP_OK; ++r) {
+            size_t bi = cand.size();
+            for (size_t i = 0; i < cand.size(); ++i)
+                if (cand[i].algo == a && sweep[i] < INFINITY && (bi == cand.size() || sweep[i] < sweep[bi])) bi = i;
+            if (bi == cand.size()) break;
+            sweep[bi] = INFINITY;  // taken
+            if ((rc = time_batch(cand[bi], &ms)) != SSSP_OK) break;
+            ++timed;
+            if (ms < best_ms) { best_ms = ms; best = cand[bi]; }
+        }
+    }
+    if (rc == SSSP_OK && g->n >= (1u << 20) && g->n && (double)g->m / (double)g->n < 20.0) {
+        for (uint32_t local : {0u, 64u, 256u}) {
+            if (local == best.local_budget) continue;
+            sssp_tuning t = best;
+            t.local_budget = local;
+            if ((rc = time_batch(t, &ms)) != SSSP_OK) break;
+            ++timed;
+            if (ms < best_ms) { best_ms = ms; best = t; }
+        }
+    }
+    if (rc == SSSP_OK) rc = time_batch(best, &best_ms);  // leaves the winner as the batch tuning
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    cudaFree(dist);
+    best.ms = best_ms;
+    best.candidates = timed;
+    {
+        std::lock_guard<std::mutex> lk(g->mu);
+        if (rc == SSSP_OK) g->batch_tuning = best;
+        g->batch_tuned = rc == SSSP_OK;
+    }
+    if (rc != SSSP_OK) return rc;
+    if (out) *out = best;
     return SSSP_OK;
 }
 

@@ -145,7 +145,7 @@ EXPORTED = ["sssp_graph_create", "sssp_graph_destroy", "sssp_graph_info", "sssp_
             "sssp_autotune", "sssp_graph_get_tuning", "sssp_graph_set_tuning", "sssp_graph_class",
             "sssp_solve_tuned", "sssp_autotune_ex", "sssp_tourney_create", "sssp_tourney_destroy",
             "sssp_tourney_update", "sssp_tourney_extract", "sssp_tourney_min", "sssp_tourney_inq",
-            "sssp_array_extract"]
+            "sssp_array_extract", "sssp_autotune_batch"]
 
 _lib.sssp_tourney_create.argtypes = [_u32, ctypes.POINTER(_P)]
 _lib.sssp_tourney_create.restype = _i32
@@ -174,6 +174,8 @@ class sssp_tuning(ctypes.Structure):
 
 _lib.sssp_autotune.argtypes = [_P, _P, _u32, ctypes.POINTER(sssp_tuning), _P]
 _lib.sssp_autotune.restype = _i32
+_lib.sssp_autotune_batch.argtypes = [_P, _P, _u32, _u32, ctypes.POINTER(sssp_tuning), _P]
+_lib.sssp_autotune_batch.restype = _i32
 _lib.sssp_autotune_ex.argtypes = [_P, _P, _u32, _u32, ctypes.POINTER(sssp_tuning), _P]
 _lib.sssp_autotune_ex.restype = _i32
 _lib.sssp_graph_get_tuning.argtypes = [_P, ctypes.POINTER(sssp_tuning)]
@@ -407,6 +409,15 @@ def sssp_autotune_ex(g: int, sources, rules: int, stream: int = 0) -> dict:
     t = sssp_tuning()
     _check(_lib.sssp_autotune_ex(g, src.ctypes.data, src.size, rules, ctypes.byref(t), stream or None),
            "sssp_autotune_ex")
+    return t.as_dict()
+
+
+def sssp_autotune_batch(g: int, sources, rules: int, stream: int = 0) -> dict:
+    """Best configuration of batched launches of these sources (stored as the graph's batch tuning)."""
+    src = np.ascontiguousarray(sources, dtype=np.uint32)
+    t = sssp_tuning()
+    _check(_lib.sssp_autotune_batch(g, src.ctypes.data, src.size, rules, ctypes.byref(t), stream or None),
+           "sssp_autotune_batch")
     return t.as_dict()
 
 

@@ -186,3 +186,23 @@ def test_batched_and_served_with_tuned_local_and_bidirectional_relaxation(lib, a
             assert np.array_equal(b.cpu().numpy().view(np.uint64), oracle.dijkstra(x, s)), (x.name, s)
         lib.sssp_server_destroy(srv)
         G.close()
+
+
+def test_autotune_batch_is_used_by_batched_calls(lib):
+    g = gg.rmat(14, 16, gen_seed=61, wseed=62)
+    G = lib.Graph(g, lib.SSSP_GRAPH_SYMMETRIC)
+    srcs = gg.pick_sources(g, 8, 15)
+    single = lib.sssp_autotune(G.handle, srcs[:2], _stream())
+    tb = lib.sssp_autotune_batch(G.handle, srcs, (1 << lib.SSSP_RHO) | (1 << lib.SSSP_DELTA_STAR), _stream())
+    assert tb["algo"] in (lib.SSSP_RHO, lib.SSSP_DELTA_STAR) and tb["param"] >= 1 and tb["candidates"] >= 5
+    assert lib.sssp_graph_get_tuning(G.handle) == single  # single-solve tuning unchanged
+    out = torch.empty(len(srcs) * g.n, dtype=torch.int64, device="cuda")
+    lib.sssp_solve_sources(G.handle, srcs, tb["algo"], None, out.data_ptr(), _stream())
+    st, _ = lib.sssp_batch_last_stats(len(srcs), _stream())
+    assert st == 0
+    got = out.view(len(srcs), g.n).cpu().numpy().view(np.uint64)
+    for i, s in enumerate(srcs):
+        assert np.array_equal(got[i], oracle.dijkstra(g, s))
+    with pytest.raises(lib.SSSPError):
+        lib.sssp_autotune_batch(G.handle, srcs, 0, _stream())
+    G.close()

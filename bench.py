@@ -410,11 +410,15 @@ def measure_serving(sssp, G, g, torch, sources, rates, window_s=1.0, hard_s=10.0
 
 def run_serve_sweep(args):
     """--serve: the serving sweep over resident graphs (RMAT scale 25, the
-    4096^2 road-like grid, the 2M-point k-NN graph)."""
+    4096^2 road-like grid, the 2M-point k-NN graph): each graph is tuned for
+    single solves (the plain loop) and for batched launches (the server), then
+    a Poisson stream at every offered rate for --serve-window seconds."""
     import torch
     from paper_2105_06145_gb300 import graphgen as gg, sssp
     rates = [int(x) for x in args.serve_rates.split(",")]
+    stream = torch.cuda.current_stream().cuda_stream
     for name in args.serve_workloads.split(","):
+        t0 = time.perf_counter()
         if name == "rmat25":
             g = gg.rmat(25, 16, 0.57, 0.19, 0.19, gen_seed=8, wseed=8)
         elif name == "road":
@@ -425,12 +429,18 @@ def run_serve_sweep(args):
             g, _ = gg.workload_rmat(22)
         else:
             raise SystemExit(f"unknown serving workload {name}")
-        lab = gg.largest_cc(g)
-        sources = gg.pick_sources(g, 256, 9, mask=np.ones(g.n, np.uint8) if name == "knn" else lab)
-        G = sssp.Graph(g)
+        gen_s = time.perf_counter() - t0
+        lab = np.ones(g.n, np.uint8) if name == "knn" else gg.largest_cc(g)
+        sources = gg.pick_sources(g, 256, 9, mask=lab)
+        G = sssp.Graph(g, sssp.SSSP_GRAPH_SYMMETRIC)
+        tune = sssp.sssp_autotune(G.handle, sources[:3], stream)
+        btune = sssp.sssp_autotune_batch(G.handle, sources[:args.serve_slots or 64],
+                                         (1 << sssp.SSSP_RHO) | (1 << sssp.SSSP_DELTA_STAR), stream)
+        torch.cuda.empty_cache()
         res = measure_serving(sssp, G, g, torch, sources, rates, window_s=args.serve_window,
-                              slots=args.serve_slots)
-        print(json.dumps({"serve_workload": name, "n": g.n, "m": g.m, **res}), flush=True)
+                              slots=args.serve_slots or 64, algo=btune["algo"], param=btune["param"], tuned=True)
+        print(json.dumps({"serve_workload": name, "n": g.n, "m": g.m, "generate_s": gen_s, "tuning": tune,
+                          "batch_tuning": btune, **res}), flush=True)
         G.close()
         del G
         torch.cuda.empty_cache()

@@ -29,7 +29,7 @@ constexpr uint32_t kSmallDeg = SSSP_SMALL_DEG;  // degree <= this: warp-flattene
 constexpr int kSmallRounds = 4;             // 32-edge rounds per batch in the flattened path
 constexpr uint32_t kChunk = 256;            // edges per relaxation chunk item (even)
 constexpr uint32_t kChunkPairs = kChunk / 2;  // 16-byte edge pairs per chunk
-constexpr int kExtractItems = SSSP_EXTRACT_ITEMS;  // queue entries per thread per extract tile
+constexpr int kExtractItems = SSSP_EXTRACT_ITEMS;  // batched kernels: queue entries per thread per extract tile
 constexpr int kStage = 512;                 // per-warp staging slots for re-queued ids
 constexpr uint32_t kMaxSamples = 4096;      // cap on the rho sampler's sample count
 constexpr uint64_t kInf = ~0ull;
@@ -51,9 +51,11 @@ constexpr uint32_t kExtractCap = (uint32_t)kBlock * kExtractPer;        // 4096
 constexpr uint32_t kExtractBytes = kExtractCap * 16u + kExtractCap;     // 68 KB
 constexpr uint32_t kSolveDynSmem = kExtractBytes > kBatchDynSmem ? kExtractBytes : kBatchDynSmem;
 
-// Relaxation record written by Extract and read by the relaxation: a run of
-// at most kChunk out-edges of one extracted vertex u.  x,y = first edge index
-// | (edge count << 40); z,w = delta[u] when u was extracted.
+// Relaxation records written by Extract and read by the relaxation (16 bytes,
+// make_rec / rec_start / rec_len): x,y = first edge index | (edge count << 40);
+// z,w = delta[u] at extraction for a low-degree record (all of u's <= kSmallDeg
+// edges), z = u for a chunk record (at most kChunk edges of u within one
+// kChunk-aligned block of the edge array).
 
 // Device control block of one solve.  Zeroed by the host before each launch.
 // Per-step counters live in a ring of three slots indexed by step % 3: slot

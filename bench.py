@@ -312,7 +312,7 @@ def measure_workload(name, sssp, torch, stream, stream_obj, rates_x=(2, 20)) -> 
            "batched64": {"queries_per_s": 64e3 / tb, "speedup": tp / 10 * 64 / tb, "status": st,
                          "last_equal_to_single": same}}
     rates = [int(max(1, round(x * plain_qps))) for x in rates_x]
-    sv = measure_serving(sssp, Gx, h, torch, srcs, rates, window_s=1.0, hard_s=8.0, slots=64,
+    sv = measure_serving(sssp, Gx, h, torch, srcs, rates, window_s=1.0, hard_s=8.0, slots=0,
                          algo=btune["algo"], param=btune["param"], tuned=True)
     res["served"] = sv
     Gx.close()
@@ -438,7 +438,7 @@ def run_serve_sweep(args):
                                          (1 << sssp.SSSP_RHO) | (1 << sssp.SSSP_DELTA_STAR), stream)
         torch.cuda.empty_cache()
         res = measure_serving(sssp, G, g, torch, sources, rates, window_s=args.serve_window,
-                              slots=args.serve_slots or 64, algo=btune["algo"], param=btune["param"], tuned=True)
+                              slots=args.serve_slots, algo=btune["algo"], param=btune["param"], tuned=True)
         print(json.dumps({"serve_workload": name, "n": g.n, "m": g.m, "generate_s": gen_s, "tuning": tune,
                           "batch_tuning": btune, **res}), flush=True)
         G.close()
@@ -526,7 +526,7 @@ def main():
     ap.add_argument("--serve-workloads", default="rmat25,road,knn")
     ap.add_argument("--serve-rates", default="1000,2000,5000,10000,20000,50000")
     ap.add_argument("--serve-window", type=float, default=1.0)
-    ap.add_argument("--serve-slots", type=int, default=0)
+    ap.add_argument("--serve-slots", type=int, default=0, help="0 = the batch autotuner's slot count")
     ap.add_argument("--lbpq", action="store_true", help="the tournament-tree vs array LaB-PQ Extract comparison only")
     ap.add_argument("--lbpq-n", type=int, default=100_000_000)
     ap.add_argument("--lbpq-rho", default="10,13,16,19,22,25", help="log2 of the rho values")
@@ -661,10 +661,13 @@ def main():
 
     served = None
     if rank == 0 and not args.no_serve and args.workload == "rmat" and args.scale == 22:
-        tune = sssp.sssp_graph_get_tuning(G.handle)
+        # the server's configuration and slot count from the batch autotuner
+        btune = sssp.sssp_autotune_batch(G.handle, gg_sources(g)[:64], 1 << sssp.SSSP_RHO, stream)
+        torch.cuda.empty_cache()
         served = {"rmat22": measure_serving(sssp, G, g, torch, gg_sources(g), [100, 1000], window_s=0.5,
-                                            hard_s=6.0, slots=64, algo=sssp.SSSP_RHO,
-                                            param=tune["param"] if tune else 0, tuned=tune is not None)}
+                                            hard_s=6.0, slots=0, algo=btune["algo"], param=btune["param"],
+                                            tuned=True)}
+        served["rmat22"]["batch_tuning"] = btune
 
     # the road-like and k-NN workloads: tuned plain loop, batched and served
     workloads = None

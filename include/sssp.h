@@ -274,7 +274,8 @@ int sssp_batch_last_stats(sssp_stats* out, uint32_t k, void* stream);
 typedef struct sssp_server sssp_server;
 
 typedef struct {
-    uint32_t slots;        /* queries on the device at once; 0 = as many as fit      */
+    uint32_t slots;        /* queries on the device at once; 0 = the graph's batch   */
+                           /* tuning's slots, else as many as fit                    */
     sssp_algo algo;        /* ExtDist rule of every query                            */
     uint64_t param;        /* rho / Delta; 0 = max(64, n/16) / max(1, mean weight/4) */
     uint64_t idle_ns;      /* the device loop exits after this long without a query  */
@@ -392,7 +393,9 @@ typedef struct {
     uint32_t local_budget;   /* sssp_options.local_budget                                   */
     double ms;               /* autotuner: mean solve time of the choice on the samples     */
     uint32_t candidates;     /* autotuner: configurations timed                             */
-    uint32_t reserved;
+    uint32_t slots;          /* batch autotuner: concurrent queries with the highest
+                                throughput (the server's slot count when its config
+                                gives none); 0 = not measured                          */
 } sssp_tuning;
 
 /*
@@ -421,7 +424,9 @@ int sssp_autotune_ex(sssp_graph* g, const uint32_t* sources, uint32_t k, uint32_
    sssp_autotune's first stage (rules: as sssp_autotune_ex), each timed as one
    sssp_solve_sources launch over up to 8 of the sources, the two best of each
    rule re-timed on all k; on graphs of >= 2^20 vertices and mean degree < 20
-   also local budgets 0, 64, 256 for the winner.  Kept as the graph's batch tuning, which
+   also local budgets 0, 64, 256 for the winner; then the winner's throughput
+   with 1, 4 and 16 concurrent sources (those < k) against k, the best count
+   recorded as `slots`.  Kept as the graph's batch tuning, which
    sssp_solve_sources / sssp_solve_multi (params == NULL) and the server
    (param == 0) use before the single-solve tuning.  Synchronous; allocates k*n
    distances for the measurements.  ms = time of one batched launch. */

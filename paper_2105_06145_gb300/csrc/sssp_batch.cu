@@ -1186,6 +1186,10 @@ int sssp_server_create(const sssp_graph* g, const sssp_server_config* cfg, sssp_
     const double frac = (c.hbm_fraction > 0.0 && c.hbm_fraction <= 1.0) ? c.hbm_fraction : 0.5;
     uint64_t fit = (uint64_t)((double)free_b * frac) / (per_slot ? per_slot : 1);
     uint64_t want = c.slots ? c.slots : kMaxBatch;
+    {
+        sssp_tuning bt;
+        if (!c.slots && g->batch_tuned && sssp_lookup_batch_tuning(g, &bt) && bt.slots) want = bt.slots;
+    }
     if (want > kMaxBatch) want = kMaxBatch;
     if (fit < want) want = fit;
     if (want == 0) { delete s; return SSSP_ERR_OUT_OF_MEMORY; }

@@ -362,12 +362,27 @@ int sssp_autotune_batch(sssp_graph* g, const uint32_t* sources, uint32_t k, uint
             if (ms < best_ms) { best_ms = ms; best = t; }
         }
     }
-    if (rc == SSSP_OK) rc = time_batch(best, &best_ms);  // leaves the winner as the batch tuning
+    if (rc == SSSP_OK) rc = time_batch(best, &best_ms);
+    // throughput of the winner with fewer concurrent sources: on a graph where
+    // one solve already keeps the device busy, fewer queries at once are faster
+    uint32_t slots = k;
+    double best_rate = best_ms > 0 ? (double)k / best_ms : 0.0;
+    for (uint32_t kc : {16u, 4u, 1u}) {
+        if (rc != SSSP_OK || kc >= k) continue;
+        kk = kc;
+        double t2 = 0;
+        if ((rc = time_batch(best, &t2)) != SSSP_OK) break;
+        // a smaller batch of kc queries: compare queries per ms
+        if (t2 > 0 && (double)kc / t2 > best_rate) { best_rate = (double)kc / t2; slots = kc; }
+    }
+    kk = k;
+    best.slots = slots;
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     cudaFree(dist);
     best.ms = best_ms;
     best.candidates = timed;
+    best.slots = slots;
     {
         std::lock_guard<std::mutex> lk(g->mu);
         if (rc == SSSP_OK) g->batch_tuning = best;

@@ -166,7 +166,7 @@ _lib.sssp_array_extract.restype = _i32
 class sssp_tuning(ctypes.Structure):
     _fields_ = [("algo", ctypes.c_int), ("shape", ctypes.c_uint32), ("param", ctypes.c_uint64),
                 ("flags", ctypes.c_uint32), ("local_budget", ctypes.c_uint32), ("ms", ctypes.c_double),
-                ("candidates", ctypes.c_uint32), ("reserved", ctypes.c_uint32)]
+                ("candidates", ctypes.c_uint32), ("slots", ctypes.c_uint32)]
 
     def as_dict(self) -> dict:
         return {k: (float(getattr(self, k)) if k == "ms" else int(getattr(self, k))) for k, _ in self._fields_}

@@ -206,3 +206,20 @@ def test_autotune_batch_is_used_by_batched_calls(lib):
     with pytest.raises(lib.SSSPError):
         lib.sssp_autotune_batch(G.handle, srcs, 0, _stream())
     G.close()
+
+
+def test_server_takes_the_tuned_slot_count(lib):
+    g = gg.rmat(13, 16, gen_seed=71, wseed=72)
+    G = lib.Graph(g, lib.SSSP_GRAPH_SYMMETRIC)
+    srcs = gg.pick_sources(g, 16, 16)
+    tb = lib.sssp_autotune_batch(G.handle, srcs, 1 << lib.SSSP_RHO, _stream())
+    assert tb["slots"] in (1, 4, 16)
+    srv = lib.sssp_server_create(G.handle, slots=0, algo=tb["algo"], param=0)
+    assert lib.sssp_server_slots(srv) == tb["slots"]
+    bufs = [torch.empty(g.n, dtype=torch.int64, device="cuda") for _ in srcs[:6]]
+    tickets = [lib.sssp_server_submit(srv, s, b.data_ptr()) for s, b in zip(srcs, bufs)]
+    for tk, s, b in zip(tickets, srcs, bufs):
+        assert lib.sssp_server_wait(srv, tk, 60_000_000_000)["status"] == 0
+        assert np.array_equal(b.cpu().numpy().view(np.uint64), oracle.dijkstra(g, s))
+    lib.sssp_server_destroy(srv)
+    G.close()

@@ -560,8 +560,10 @@ def main():
         param = 1 << 13
 
     # every workload graph is symmetric: verify once at creation, then use the
-    # paper's bidirectional relaxation for undirected graphs (Sec. 6)
-    G = sssp.Graph(g, sssp.SSSP_GRAPH_SYMMETRIC | sssp.SSSP_GRAPH_VERIFY)
+    # paper's bidirectional relaxation for undirected graphs (Sec. 6); single
+    # solves run on the degree-ordered device copy (distances still come back
+    # in the generator's ids, inside the timed solve)
+    G = sssp.Graph(g, sssp.SSSP_GRAPH_SYMMETRIC | sssp.SSSP_GRAPH_VERIFY | sssp.SSSP_GRAPH_REORDER)
     bidir = not args.no_bidir
     solve_flags = sssp.SSSP_SOLVE_BIDIRECTIONAL if bidir else 0
     stream_obj = torch.cuda.Stream()
@@ -700,7 +702,7 @@ def main():
             "steps": K, "warmup": W, "ms_per_step": total_ms / K, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "u64", "data": "synthetic",
             "config": {"workload": label, "n": g.n, "m": g.m, "algo": args.algo, "param": param,
-                       "bidirectional": bidir,
+                       "bidirectional": bidir, "graph_layout": "relabelled by decreasing degree (SSSP_GRAPH_REORDER)",
                        "sources": nsrc, "parallelism": "replicas" if world > 1 else "single",
                        "l2": "inputs larger than L2 (packed edges %.2f GB > 129 MB L2)" % (8 * g.m / 1e9),
                        "per_solve_mean": mean_stats},

@@ -133,6 +133,15 @@ typedef struct {
 #define SSSP_GRAPH_SYMMETRIC 1u     /* every edge (u,v,w) has its reverse (v,u,w)         */
 #define SSSP_GRAPH_VERIFY 2u        /* check SSSP_GRAPH_SYMMETRIC on the host, O(m log d);
                                        INVALID_ARG when it does not hold                  */
+#define SSSP_GRAPH_REORDER 4u       /* single solves run on a relabelled device copy: new id
+                                       = rank by decreasing out-degree (ties by id), each
+                                       adjacency sorted by new target, so the most frequent
+                                       edge targets share cache lines; distances are
+                                       returned in the caller's ids (one more pass over n
+                                       at the end of the solve).  Costs a second copy of
+                                       the graph and 16 bytes per vertex on the device, and
+                                       O(m log d) host time at creation.  Batched and
+                                       serving calls use the caller's order.              */
 
 /*
  * Copy a CSR graph (host arrays) to the device.

@@ -9,6 +9,7 @@
 #include <cstring>
 #include <algorithm>
 #include <new>
+#include <thread>
 #include <vector>
 
 #include <cuda_runtime.h>
@@ -46,8 +47,57 @@ void free_graph(sssp_graph* g)
     cudaFree(g->d_items);
     cudaFree(g->d_ctrl);
     cudaFree(g->d_dist_internal);
+    cudaFree(g->d_off2);
+    cudaFree(g->d_edges2);
+    cudaFree(g->d_perm);
+    cudaFree(g->d_iperm);
+    cudaFree(g->d_dist2);
     if (g->h_ctrl) cudaFreeHost(g->h_ctrl);
     delete g;
+}
+
+// The relabelled copy of SSSP_GRAPH_REORDER: new id = rank by decreasing
+// out-degree (ties by id), each adjacency sorted by (new target, weight).
+// Adjacencies are rebuilt in parallel over ranges of new ids.
+void relabel_graph(uint32_t n, const uint64_t* off, const uint32_t* tgt, const uint32_t* w, std::vector<uint32_t>& perm,
+                   std::vector<uint32_t>& iperm, std::vector<uint64_t>& off2, std::vector<uint32_t>& tgt2,
+                   std::vector<uint32_t>& w2)
+{
+    const uint64_t m = off[n];
+    iperm.resize(n);
+    for (uint32_t i = 0; i < n; ++i) iperm[i] = i;
+    std::sort(iperm.begin(), iperm.end(), [off](uint32_t a, uint32_t b) {
+        const uint64_t da = off[a + 1] - off[a], db = off[b + 1] - off[b];
+        return da != db ? da > db : a < b;
+    });
+    perm.resize(n);
+    for (uint32_t i = 0; i < n; ++i) perm[iperm[i]] = i;
+    off2.resize((size_t)n + 1);
+    off2[0] = 0;
+    for (uint32_t i = 0; i < n; ++i) off2[i + 1] = off2[i] + (off[iperm[i] + 1] - off[iperm[i]]);
+    tgt2.resize(m);
+    w2.resize(m);
+    unsigned nt = std::thread::hardware_concurrency();
+    nt = nt < 1 ? 1 : (nt > 64 ? 64 : nt);
+    std::vector<std::thread> th;
+    for (unsigned t = 0; t < nt; ++t) {
+        th.emplace_back([&, t]() {
+            std::vector<uint64_t> key;
+            const uint32_t lo = (uint32_t)((uint64_t)n * t / nt), hi = (uint32_t)((uint64_t)n * (t + 1) / nt);
+            for (uint32_t u = lo; u < hi; ++u) {
+                const uint32_t o = iperm[u];
+                const uint64_t b = off[o], d = off[o + 1] - b;
+                key.resize(d);
+                for (uint64_t j = 0; j < d; ++j) key[j] = ((uint64_t)perm[tgt[b + j]] << 32) | w[b + j];
+                std::sort(key.begin(), key.end());
+                for (uint64_t j = 0; j < d; ++j) {
+                    tgt2[off2[u] + j] = (uint32_t)(key[j] >> 32);
+                    w2[off2[u] + j] = (uint32_t)key[j];
+                }
+            }
+        });
+    }
+    for (std::thread& x : th) x.join();
 }
 
 // The two builds of the solve kernel (sssp_kernels.cu compiled twice): the
@@ -139,7 +189,7 @@ int sssp_graph_create_ex(uint32_t n, uint64_t m, const uint64_t* offsets, const 
         if (offsets[u + 1] < offsets[u]) return SSSP_ERR_INVALID_ARG;
     for (uint64_t e = 0; e < m; ++e)
         if (targets[e] >= n) return SSSP_ERR_INVALID_ARG;
-    if (flags & ~(SSSP_GRAPH_SYMMETRIC | SSSP_GRAPH_VERIFY)) return SSSP_ERR_INVALID_ARG;
+    if (flags & ~(SSSP_GRAPH_SYMMETRIC | SSSP_GRAPH_VERIFY | SSSP_GRAPH_REORDER)) return SSSP_ERR_INVALID_ARG;
     if ((flags & SSSP_GRAPH_VERIFY) && (flags & SSSP_GRAPH_SYMMETRIC) &&
         !verify_symmetric(n, offsets, targets, weights))
         return SSSP_ERR_INVALID_ARG;
@@ -156,6 +206,18 @@ int sssp_graph_create_ex(uint32_t n, uint64_t m, const uint64_t* offsets, const 
         if (deg == 0) continue;
         if (deg <= kSmallDeg) ++small_cap;
         else item_cap += chunk_count(offsets[u], offsets[u + 1]);
+    }
+
+    // relabelled copy for single solves (its chunk records are counted too:
+    // the record arrays serve both layouts)
+    std::vector<uint32_t> perm, iperm, tgt2, w2;
+    std::vector<uint64_t> off2;
+    if (flags & SSSP_GRAPH_REORDER) {
+        relabel_graph(n, offsets, targets, weights, perm, iperm, off2, tgt2, w2);
+        uint64_t item_cap2 = 0;
+        for (uint32_t u = 0; u < n; ++u)
+            if (off2[u + 1] - off2[u] > kSmallDeg) item_cap2 += chunk_count(off2[u], off2[u + 1]);
+        item_cap = item_cap2 > item_cap ? item_cap2 : item_cap;
     }
 
     sssp_graph* g = new (std::nothrow) sssp_graph();
@@ -196,6 +258,20 @@ int sssp_graph_create_ex(uint32_t n, uint64_t m, const uint64_t* offsets, const 
     if (e == cudaSuccess) e = launch_pack_edges(d_tgt, d_w, g->d_edges, m, m_alloc, 0);
     if (e == cudaSuccess) e = cudaMemset(g->d_ctrl, 0, sizeof(Ctrl));
     if (e == cudaSuccess) e = cudaDeviceSynchronize();
+    if (e == cudaSuccess && (flags & SSSP_GRAPH_REORDER)) {
+        g->reordered = true;
+        g->h_perm = std::move(perm);
+        if ((e = dalloc(&g->d_off2, (uint64_t)n + 1)) == cudaSuccess && (e = dalloc(&g->d_edges2, m_alloc)) == cudaSuccess &&
+            (e = dalloc(&g->d_perm, n)) == cudaSuccess && (e = dalloc(&g->d_iperm, n)) == cudaSuccess &&
+            (e = dalloc(&g->d_dist2, n)) == cudaSuccess)
+            e = cudaMemcpy(g->d_off2, off2.data(), sizeof(uint64_t) * ((size_t)n + 1), cudaMemcpyHostToDevice);
+        if (e == cudaSuccess) e = cudaMemcpy(g->d_perm, g->h_perm.data(), sizeof(uint32_t) * n, cudaMemcpyHostToDevice);
+        if (e == cudaSuccess) e = cudaMemcpy(g->d_iperm, iperm.data(), sizeof(uint32_t) * n, cudaMemcpyHostToDevice);
+        if (e == cudaSuccess && m) e = cudaMemcpy(d_tgt, tgt2.data(), sizeof(uint32_t) * m, cudaMemcpyHostToDevice);
+        if (e == cudaSuccess && m) e = cudaMemcpy(d_w, w2.data(), sizeof(uint32_t) * m, cudaMemcpyHostToDevice);
+        if (e == cudaSuccess) e = launch_pack_edges(d_tgt, d_w, g->d_edges2, m, m_alloc, 0);
+        if (e == cudaSuccess) e = cudaDeviceSynchronize();
+    }
     cudaFree(d_tgt);
     cudaFree(d_w);
     if (e != cudaSuccess) { free_graph(g); return cuda_fail(e); }
@@ -264,6 +340,15 @@ int sssp_solve_ex(const sssp_graph* gc, uint32_t source, sssp_algo algo, uint64_
     p.bidir = (o.flags & SSSP_SOLVE_BIDIRECTIONAL) ? 1 : 0;
     if (o.local_budget != 0 && algo != SSSP_RHO && algo != SSSP_DELTA_STAR) return SSSP_ERR_INVALID_ARG;
     p.local_budget = o.local_budget;
+    if (g->reordered) {  // the relabelled copy; distances back in the caller's ids at the end
+        p.off = g->d_off2;
+        p.edges = g->d_edges2;
+        p.dist = g->d_dist2;
+        p.dist_out = dist_out;
+        p.perm = g->d_perm;
+        p.iperm = g->d_iperm;
+        p.source = g->h_perm[source];
+    }
     p.sample_cap = (algo == SSSP_RHO) ? rho_sample_bound(g->n, param) : 0;
     if (o.shape > SSSP_SHAPE_NARROW) return SSSP_ERR_INVALID_ARG;
     const int shape = o.shape == SSSP_SHAPE_NARROW ? 1 : 0;

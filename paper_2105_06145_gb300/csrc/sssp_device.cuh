@@ -20,17 +20,18 @@ __device__ __forceinline__ uint64_t ldcg64(const uint64_t* p)
 }
 __device__ __forceinline__ uint32_t ldcg32(const uint32_t* p) { return __ldcg(p); }
 
-// Load of delta[v] for the relaxation pre-check.  Within a solve delta only
-// decreases after the init barrier, so a value served from a non-coherent L1
-// line can only be too high: the pre-check then lets an extra atomicMin
-// through, never skips a needed one.
+// Load of delta[v] for the relaxation pre-check.  kL1: through the SM's L1
+// (ld.global.ca), for kernels that initialise delta once per launch: within
+// such a launch delta only decreases after the init barrier (and L1 holds no
+// line from before the launch), so a value served from a non-coherent L1 line
+// can only be too high -- the pre-check then lets an extra atomicMin through,
+// never skips a needed one.  Kernels that re-initialise distance arrays
+// during the launch (the server's slots) must use the L2 load.
+template <bool kL1>
 __device__ __forceinline__ uint64_t ld_precheck(const uint64_t* p)
 {
-#ifdef SSSP_PRECHECK_L1
-    return __ldca(reinterpret_cast<const unsigned long long*>(p));
-#else
+    if (kL1) return __ldca(reinterpret_cast<const unsigned long long*>(p));
     return __ldcg(reinterpret_cast<const unsigned long long*>(p));
-#endif
 }
 
 __device__ __forceinline__ unsigned long long global_timer_ns()
@@ -369,6 +370,7 @@ __device__ __forceinline__ void relax_apply4(uint64_t* dist, uint32_t* inq, cons
 
 // Warp-uniform: one batch of (up to) 4 relaxations per lane (4 gathers of
 // delta[v] in flight, then relax_apply4).
+template <bool kL1 = false>
 __device__ __forceinline__ void relax_batch4(uint64_t* dist, uint32_t* inq, const uint32_t (&v)[4],
                                              const uint64_t (&cand)[4], const bool (&ok)[4],
                                              uint32_t* stage, uint32_t& stc, uint32_t lane,
@@ -376,7 +378,7 @@ __device__ __forceinline__ void relax_batch4(uint64_t* dist, uint32_t* inq, cons
 {
     uint64_t dv[4];
 #pragma unroll
-    for (int t = 0; t < 4; ++t) dv[t] = ok[t] ? ld_precheck(&dist[v[t]]) : 0ull;
+    for (int t = 0; t < 4; ++t) dv[t] = ok[t] ? ld_precheck<kL1>(&dist[v[t]]) : 0ull;
     relax_apply4(dist, inq, v, cand, dv, ok, stage, stc, lane, lmin, lupd);
 }
 
@@ -405,7 +407,7 @@ __device__ __forceinline__ void stage_flush(uint32_t* stage, uint32_t& stc, uint
 // u itself -- WriteMin(delta[u], min over the chunk of delta[v] + w), with the
 // usual Update(u) -- and the improved delta[u] is then pushed to the chunk's
 // neighbours.
-template <bool kPull>
+template <bool kPull, bool kL1 = false>
 __device__ __forceinline__ void relax_chunk(uint4 rec, uint64_t du, const uint4* __restrict__ pairs,
                                             uint64_t* dist, uint32_t* inq, uint32_t* stage, uint32_t& stc,
                                             uint32_t lane, uint64_t& lmin, uint32_t& lupd)
@@ -427,7 +429,7 @@ __device__ __forceinline__ void relax_chunk(uint4 rec, uint64_t du, const uint4*
         }
         uint64_t dv[4];
 #pragma unroll
-        for (int t = 0; t < 4; ++t) dv[t] = ok[t] ? ld_precheck(&dist[vv[t]]) : 0ull;
+        for (int t = 0; t < 4; ++t) dv[t] = ok[t] ? ld_precheck<kL1>(&dist[vv[t]]) : 0ull;
         if (kPull) {
             uint64_t pull = kInf;
 #pragma unroll
@@ -466,6 +468,7 @@ __device__ __forceinline__ void relax_chunk(uint4 rec, uint64_t du, const uint4*
 // belongs to lane k.  When allow_flush, staged ids are flushed whenever fewer
 // than 256 staging slots are left; otherwise the caller guarantees room for
 // every push (at most the total degree).
+template <bool kL1 = false>
 __device__ __forceinline__ void relax_flat(uint64_t b, uint32_t deg, uint64_t du, const uint2* __restrict__ edges,
                                            uint64_t* dist, uint32_t* inq, uint32_t* stage, uint32_t& stc,
                                            uint32_t lane, uint64_t& lmin, uint32_t& lupd, bool allow_flush,
@@ -516,7 +519,7 @@ __device__ __forceinline__ void relax_flat(uint64_t b, uint32_t deg, uint64_t du
             vv[t] = ed.x;
             cand[t] = cdu[t] + ed.y;
         }
-        relax_batch4(dist, inq, vv, cand, ok, stage, stc, lane, lmin, lupd);
+        relax_batch4<kL1>(dist, inq, vv, cand, ok, stage, stc, lane, lmin, lupd);
         if (allow_flush && stc > (uint32_t)(kStage - 256)) stage_flush(stage, stc, lane, qsize, status, Qnext, qcap);
     }
 }

@@ -4,6 +4,7 @@
 
 #include <cstdint>
 #include <mutex>
+#include <vector>
 #include <cuda_runtime.h>
 
 #include "../../include/sssp.h"
@@ -108,6 +109,13 @@ struct SolveParams {
     sssp_stats* stats_out;        // optional device copy of the totals
     int bidir;                    // bidirectional relaxation of chunk records (symmetric graphs)
     uint32_t local_budget;        // local relaxation of super-sparse steps: vertices per warp and step (0 = off)
+    // relabelled graph (SSSP_GRAPH_REORDER): the solve runs on the relabelled
+    // copy with dist = internal distances in the new ids; at the end
+    // dist_out[v] = dist[perm[v]] for every caller id v; ext_count is indexed
+    // through iperm (new -> caller id).  All null without relabelling.
+    const uint32_t* perm;
+    const uint32_t* iperm;
+    uint64_t* dist_out;
 };
 
 // Chunk records of one vertex: its edge range [b, e) cut at multiples of kChunk.
@@ -168,6 +176,15 @@ struct sssp_graph {
     uint64_t item_cap = 0;
     sssp::Ctrl* d_ctrl = nullptr;
     uint64_t* d_dist_internal = nullptr;   // lazily allocated for sssp_solve_host
+    // SSSP_GRAPH_REORDER: relabelled copy for single solves (new id = rank by
+    // decreasing out-degree, ties by id; adjacencies sorted by new target)
+    bool reordered = false;
+    uint64_t* d_off2 = nullptr;
+    uint2* d_edges2 = nullptr;
+    uint32_t* d_perm = nullptr;            // caller id -> new id
+    uint32_t* d_iperm = nullptr;           // new id -> caller id
+    uint64_t* d_dist2 = nullptr;           // distances in the new ids
+    std::vector<uint32_t> h_perm;          // caller id -> new id (source mapping)
     sssp::Ctrl* h_ctrl = nullptr;                // pinned readback
     uint32_t last_grid = 0;
     double mean_w = 1.0;                   // mean edge weight (default Delta)

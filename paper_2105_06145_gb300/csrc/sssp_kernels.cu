@@ -272,7 +272,7 @@ __global__ void __launch_bounds__(kBlock, kMinBlocks) solve_kernel(SolveParams p
                         const uint64_t deg = e[j] - b[j];
                         l_fcount += 1;
                         l_fedges += deg;
-                        if (p.ext_count) p.ext_count[r.x] += 1u;
+                        if (p.ext_count) p.ext_count[p.iperm ? p.iperm[r.x] : r.x] += 1u;
                         if (deg == 0) {
                             s_kind[i] = kNoEdges;
                         } else if (deg <= kSmallDeg) {
@@ -391,8 +391,8 @@ __global__ void __launch_bounds__(kBlock, kMinBlocks) solve_kernel(SolveParams p
                 const uint64_t gn = g + nwarps;  // prefetch the next group's records
                 rnext = (gn < ngroups && gn * 32u + lane < fs) ? __ldcg(&p.fsmall[gn * 32u + lane])
                                                               : make_uint4(0, 0, 0, 0);
-                relax_flat(rec_start(rec), rec_len(rec), rec_du(rec), edges, dist, inq, stage, stc, lane, lmin,
-                           lupd, true, &ctrl->qsize[nx], &ctrl->status, Qnext, n);
+                relax_flat<true>(rec_start(rec), rec_len(rec), rec_du(rec), edges, dist, inq, stage, stc, lane,
+                                 lmin, lupd, true, &ctrl->qsize[nx], &ctrl->status, Qnext, n);
             }
 
             // (b) higher-degree vertices: one warp per chunk record; the next
@@ -408,9 +408,9 @@ __global__ void __launch_bounds__(kBlock, kMinBlocks) solve_kernel(SolveParams p
                     rn = nit < fc ? __ldcg(&p.items[nit]) : make_uint4(0, 0, 0, 0);
                     const uint64_t du = ldcg64(&dist[rc.z]);
                     if (p.bidir)
-                        relax_chunk<true>(rc, du, pairs, dist, inq, stage, stc, lane, lmin, lupd);
+                        relax_chunk<true, true>(rc, du, pairs, dist, inq, stage, stc, lane, lmin, lupd);
                     else
-                        relax_chunk<false>(rc, du, pairs, dist, inq, stage, stc, lane, lmin, lupd);
+                        relax_chunk<false, true>(rc, du, pairs, dist, inq, stage, stc, lane, lmin, lupd);
                     if (stc > (uint32_t)(kStage - 256)) stage_flush(stage, stc, lane, &ctrl->qsize[nx], &ctrl->status, Qnext, n);
                 }
             }
@@ -468,6 +468,9 @@ __global__ void __launch_bounds__(kBlock, kMinBlocks) solve_kernel(SolveParams p
         if (!grid_sync_err(&ctrl->bar, &ctrl->status, &s_bar_target, p.timeout_ns)) break;
     }
 
+    // relabelled graph: distances back in the caller's ids
+    if (p.perm)
+        for (uint64_t i = gtid; i < n; i += gthreads) p.dist_out[i] = ldcg64(&dist[__ldg(&p.perm[i])]);
     if (blockIdx.x == 0 && tid == 0) {
         ctrl->steps = k - 1;
         if (p.stats_out) {

@@ -23,7 +23,7 @@ ALGOS = {"rho": SSSP_RHO, "delta_star": SSSP_DELTA_STAR, "bellman_ford": SSSP_BE
          "delta": SSSP_DELTA, "dijkstra": SSSP_DIJKSTRA}
 SSSP_SOLVE_BIDIRECTIONAL = 1
 SSSP_SHAPE_WIDE, SSSP_SHAPE_NARROW = 0, 1
-SSSP_GRAPH_SYMMETRIC, SSSP_GRAPH_VERIFY = 1, 2
+SSSP_GRAPH_SYMMETRIC, SSSP_GRAPH_VERIFY, SSSP_GRAPH_REORDER = 1, 2, 4
 SSSP_OK = 0
 SSSP_ERR_INVALID_ARG, SSSP_ERR_OUT_OF_MEMORY, SSSP_ERR_CUDA = -1, -2, -3
 SSSP_ERR_TIMEOUT, SSSP_ERR_INTERNAL = -4, -5

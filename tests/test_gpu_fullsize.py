@@ -19,8 +19,8 @@ def lib():
     return sssp
 
 
-def _run(lib, g, sources, cases):
-    G = lib.Graph(g)
+def _run(lib, g, sources, cases, flags=0, opts=None):
+    G = lib.Graph(g, flags)
     dist = torch.empty(g.n, dtype=torch.int64, device="cuda")
     stream = torch.cuda.current_stream().cuda_stream
     for s in sources:
@@ -28,7 +28,7 @@ def _run(lib, g, sources, cases):
         assert oracle.check(g, s, want)[0] == 0
         for algo, param in cases:
             dist.fill_(0)
-            G.solve(s, algo, param, dist, stream)
+            G.solve(s, algo, param, dist, stream, opts)
             st = G.stats(stream)
             assert st["status"] == 0, (algo, param, st)
             got = dist.cpu().numpy().view(np.uint64)
@@ -43,9 +43,17 @@ def test_rmat22_all_rules(lib):
              (3, 1 << 15), (4, 0)]
     _run(lib, g, [s], cases)
     _run(lib, g, extra, [(0, 1 << 20)])
+    # the benchmark's launch configuration: relabelled symmetric graph,
+    # bidirectional relaxation, wide shape, rho in the sweep
+    bench_flags = lib.SSSP_GRAPH_SYMMETRIC | lib.SSSP_GRAPH_REORDER
+    bidir = lib.make_options(flags=lib.SSSP_SOLVE_BIDIRECTIONAL)
+    _run(lib, g, [s] + extra, [(0, 1 << 18), (0, 1 << 20), (0, 1 << 22), (1, 1 << 15), (2, 0)], bench_flags, bidir)
 
 
 def test_road4096(lib):
     g, s = gg.workload_road(4096)
     assert g.n == 4096 * 4096
     _run(lib, g, [s], [(0, 1 << 20), (0, 1 << 14), (1, 1 << 13), (1, 1 << 15), (3, 1 << 13)])
+    # the tuned road configuration: Delta*-Stepping with local relaxation in the narrow shape
+    opts = lib.make_options(flags=lib.SSSP_SOLVE_BIDIRECTIONAL, local_budget=256, shape=lib.SSSP_SHAPE_NARROW)
+    _run(lib, g, [s], [(1, 2111), (0, 1 << 16)], lib.SSSP_GRAPH_SYMMETRIC, opts)

@@ -184,8 +184,13 @@ __global__ void __launch_bounds__(kBlock, kMinBlocks) solve_kernel(SolveParams p
         }
 
         // ---------------- Extract(theta) ----------------
-        // Each block takes a contiguous slice of Q_k and processes it in rounds
-        // of at most kExtractCap entries staged in shared memory: (1) ids and
+        // Q_k is cut into R x gridDim.x runs of equal length (at most
+        // kExtractCap entries each); in round r, block b takes run r*gridDim.x+b.
+        // Interleaving the runs gives every block a sample of the whole list:
+        // the entries queued last (at the end of the list) are extracted far
+        // more often than the ones kept from earlier steps, so contiguous
+        // slices would leave the last blocks with most of the extractions.
+        // Each round is staged in shared memory: (1) ids and
         // keys are loaded with every load of the round in flight; (2) the
         // extracted ids leave Q (queue bit cleared) and their edge ranges are
         // read; (3) one block scan and one atomic per output list reserve the
@@ -198,13 +203,15 @@ __global__ void __launch_bounds__(kBlock, kMinBlocks) solve_kernel(SolveParams p
             uint8_t* s_kind = s_dyn + (size_t)kExtractCap * sizeof(uint4);      // [kExtractCap]
             enum : uint8_t { kNone = 0, kKeep = 1, kSmall = 2, kChunked = 3, kNoEdges = 4 };
             uint64_t l_fcount = 0, l_fedges = 0, l_kmin = kInf;
-            const uint64_t slo = (uint64_t)q * blockIdx.x / gridDim.x;
-            const uint64_t shi = (uint64_t)q * (blockIdx.x + 1) / gridDim.x;
+            const uint64_t per_block = ((uint64_t)q + gridDim.x - 1) / gridDim.x;
+            const uint32_t rounds = (uint32_t)((per_block + kExtractCap - 1) / kExtractCap);  // >= 1 (q >= 1)
+            const uint64_t run = (per_block + rounds - 1) / rounds;                           // <= kExtractCap
             // every block runs the first round (possibly empty) so that every
             // block knows theta
-            for (uint64_t r0 = slo; r0 < shi || r0 == slo; r0 += kExtractCap) {
-                const uint32_t L = (uint32_t)(r0 >= shi ? 0 : (shi - r0) < kExtractCap ? (shi - r0) : kExtractCap);
-                const bool select_now = rho_sample && r0 == slo;
+            for (uint32_t rr = 0; rr < rounds; ++rr) {
+                const uint64_t r0 = ((uint64_t)rr * gridDim.x + blockIdx.x) * run;
+                const uint32_t L = (uint32_t)(r0 >= q ? 0 : ((uint64_t)q - r0) < run ? ((uint64_t)q - r0) : run);
+                const bool select_now = rho_sample && rr == 0;
                 const bool sel_in_regs = select_now && s_cnt <= (uint32_t)kBlock;
                 // (1) ids, keys, and the keep / extract decision
                 uint32_t extm = 0;  // bit j: entry j of this thread is extracted

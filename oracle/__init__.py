@@ -12,7 +12,6 @@ What it computes (see oracle.c for the passages each function follows):
   stepping        -- Algorithm 1 run sequentially with the ExtDist of Table 2
                      (rho, Delta*, Bellman-Ford, Delta with FinishCheck, Dijkstra)
   rho_extdist     -- the sampled rho-th smallest threshold (Sec. 6, App. B)
-  rho_extdist_bitmap -- the same threshold over the dense-mode flag array
   delta_extdist   -- theta = i * Delta (Delta*-Stepping, Table 2)
   splitmix64      -- the counter-based generator the sampler uses
   check           -- the invariants that characterise d
@@ -78,8 +77,6 @@ def _L():
         lib.oracle_hops.restype = i64
         lib.oracle_rho_extdist.argtypes = [P, u32, P, u32, u64, u64, u64, u32]
         lib.oracle_rho_extdist.restype = u64
-        lib.oracle_rho_extdist_bitmap.argtypes = [P, u32, P, u32, u64, u64, u64, u32]
-        lib.oracle_rho_extdist_bitmap.restype = u64
         lib.oracle_delta_extdist.argtypes = [ctypes.POINTER(u64), u64, u64]
         lib.oracle_delta_extdist.restype = u64
         lib.oracle_delta_theta.argtypes = [ctypes.POINTER(u64), u64, u64]
@@ -166,19 +163,6 @@ def rho_extdist(queue: np.ndarray, dist: np.ndarray, n: int, rho: int, seed: int
     qp = queue.ctypes.data if queue.size else np.zeros(1, np.uint32).ctypes.data
     return int(_L().oracle_rho_extdist(qp, queue.size, dist.ctypes.data, n, rho, seed, step,
                                        dense_before))
-
-
-def rho_extdist_bitmap(inq: np.ndarray, dist: np.ndarray, n: int, rho: int, seed: int, step: int,
-                       dense_before: int) -> int:
-    """inq: uint8/bool flags [n] (1 = queued); packed here into 32-bit words,
-    bit v%32 of word v/32 (little-endian bit order)."""
-    flags = np.ascontiguousarray(inq, dtype=np.uint8)
-    words = np.packbits(np.pad(flags, (0, (-flags.size) % 32)), bitorder="little").view(np.uint32)
-    words = np.ascontiguousarray(words if words.size else np.zeros(1, np.uint32))
-    dist = np.ascontiguousarray(dist, dtype=np.uint64)
-    q = int(flags.astype(bool).sum())
-    return int(_L().oracle_rho_extdist_bitmap(words.ctypes.data, q, dist.ctypes.data, n, rho, seed,
-                                              step, dense_before))
 
 
 def delta_extdist(i: int, delta: int, qmin: int) -> tuple[int, int]:

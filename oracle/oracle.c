@@ -21,9 +21,6 @@
  *                           Bellman-Ford, Delta*-Stepping and rho-Stepping.
  *   oracle_rho_extdist   -- the sampling-based rho-th smallest threshold of
  *                           Sec. 6 ("Threshold estimation") and Appendix B.
- *   oracle_rho_extdist_bitmap -- the same threshold when the frontier is the
- *                           bit-flag array of dense mode (Sec. 6, "Sparse-
- *                           dense optimization").
  *   oracle_delta_extdist -- theta = i*Delta of Table 2 (Delta*-Stepping).
  *   oracle_splitmix64    -- the counter-based generator the rho sampler draws
  *                           from (Steele, Lea, Flood, OOPSLA 2014).
@@ -374,55 +371,6 @@ uint64_t oracle_rho_extdist(const uint32_t* queue, uint32_t q, const uint64_t* d
     qsort(keys, (size_t)s, sizeof(uint64_t), cmp_u64);
     uint64_t r = rho_eff * s / (uint64_t)q;
     if (r > s - 1) r = s - 1;
-    return keys[r];
-}
-
-/*
- * rho-Stepping threshold when the frontier is held as n bit flags (Sec. 6
- * "Sparse-dense optimization": in dense mode Q is the flag array, not a list;
- * "Threshold estimation": s uniformly random samples from the frontier).
- * inq_words[v/32] bit v%32 is set iff v is in Q; q = |Q| (given); the other
- * arguments are those of oracle_rho_extdist.  Readings:
- *   - rho', s and the q <= rho' rule are those of oracle_rho_extdist;
- *   - a uniform sample of Q is drawn by rejection: probe j (j = 0, 1, ...)
- *     is vertex floor(h_j * n / 2^64), h_j as in oracle_rho_extdist; a probe
- *     on a queued vertex is a sample.  The samples are the first s such
- *     probes among P = min(16384, 2 * ceil(s * n / q)) probes (twice the
- *     expected number, so fewer than s accepted probes is rare); s' <= s
- *     samples are taken;
- *   - theta = sorted_samples[min(s'-1, floor(rho' * s' / q))]; no accepted
- *     probe (s' = 0) extracts every queued vertex (UINT64_MAX).
- * With every vertex queued (q = n) probe j is sample j and hits vertex
- * floor(h_j * n / 2^64), the position the list sampler reads in the
- * identity list, so the two definitions agree there.
- */
-#define ORC_MAX_PROBES 16384u
-
-uint64_t oracle_rho_extdist_bitmap(const uint32_t* inq_words, uint32_t q, const uint64_t* dist,
-                                   uint32_t n, uint64_t rho, uint64_t seed, uint64_t step,
-                                   uint32_t dense_before)
-{
-    uint64_t rho_eff = rho;
-    if ((uint64_t)q * 20u > (uint64_t)n && dense_before < 2) {
-        rho_eff = rho / 10u;
-        if (rho_eff < 1) rho_eff = 1;
-    }
-    if ((uint64_t)q <= rho_eff) return ORC_INF;
-    uint64_t s = 10u * ((q + rho_eff - 1) / rho_eff + 1u + floor_log2_u64((uint64_t)q + 1u));
-    if (s > ORC_MAX_SAMPLES) s = ORC_MAX_SAMPLES;
-    uint64_t probes = 2u * ((s * (uint64_t)n + q - 1) / q);
-    if (probes > ORC_MAX_PROBES) probes = ORC_MAX_PROBES;
-    uint64_t keys[ORC_MAX_SAMPLES];
-    uint64_t taken = 0;
-    for (uint64_t j = 0; j < probes && taken < s; ++j) {
-        uint64_t h = oracle_splitmix64(seed, (step << 32) | j);
-        uint32_t v = (uint32_t)(((unsigned __int128)h * (unsigned __int128)n) >> 64);
-        if ((inq_words[v >> 5] >> (v & 31u)) & 1u) keys[taken++] = dist[v];
-    }
-    if (taken == 0) return ORC_INF;
-    qsort(keys, (size_t)taken, sizeof(uint64_t), cmp_u64);
-    uint64_t r = rho_eff * taken / (uint64_t)q;
-    if (r > taken - 1) r = taken - 1;
     return keys[r];
 }
 

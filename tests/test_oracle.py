@@ -233,58 +233,6 @@ def test_rho_extdist_dense_rule():
     assert oracle.rho_extdist(queue, keys, n, 10 * q, 0, 1, 0) == INF
 
 
-def test_rho_extdist_bitmap_full_queue_equals_list_sampler():
-    """With every vertex queued, rejection sampling over the flag array accepts
-    every probe, and probe j hits the position the list sampler reads in the
-    identity list: the two thresholds coincide (dense and sparse steps)."""
-    rng = np.random.default_rng(5)
-    for n in (1000, 40000, 300001):
-        keys = rng.integers(0, 1 << 40, n).astype(np.uint64)
-        flags = np.ones(n, np.uint8)
-        ident = np.arange(n, dtype=np.uint32)
-        for rho, seed, step, dense_before in ((n // 50, 3, 1, 0), (n // 7, 9, 5, 2), (64, 1, 2, 3)):
-            want = oracle.rho_extdist(ident, keys, n, rho, seed, step, dense_before)
-            got = oracle.rho_extdist_bitmap(flags, keys, n, rho, seed, step, dense_before)
-            assert got == want, (n, rho)
-
-
-def test_rho_extdist_bitmap_special_cases():
-    n = 5000
-    flags = np.zeros(n, np.uint8)
-    flags[::3] = 1
-    q = int(flags.sum())
-    keys = np.arange(n, dtype=np.uint64) * np.uint64(7)
-    # |Q| <= rho': everything is extracted
-    assert oracle.rho_extdist_bitmap(flags, keys, n, q, 1, 1, 2) == INF
-    assert oracle.rho_extdist_bitmap(np.zeros(n, np.uint8), keys, n, 1, 1, 1, 2) == INF
-    # theta is the key of a queued vertex (never of an unqueued one)
-    for seed in range(20):
-        th = oracle.rho_extdist_bitmap(flags, keys, n, 100, seed, 1 + seed, 2)
-        assert th % 7 == 0 and (th // 7) % 3 == 0
-    # all queued keys equal (unqueued ones smaller): theta is that key
-    same = np.where(flags == 1, 42, 1).astype(np.uint64)
-    assert oracle.rho_extdist_bitmap(flags, same, n, 50, 4, 2, 2) == 42
-
-
-def test_rho_extdist_bitmap_rank_within_constant_factor():
-    """Appendix B over the flag array: the rank of theta among the queued keys
-    lies within a factor 2 of rho w.h.p. (frontier densities 1/20 .. 1)."""
-    rng = np.random.default_rng(12)
-    good = total = 0
-    for trial in range(200):
-        n = int(rng.integers(20000, 300000))
-        dens = float(rng.uniform(0.05, 1.0))
-        flags = (rng.random(n) < dens).astype(np.uint8)
-        q = int(flags.sum())
-        rho = int(rng.integers(10, max(11, q // 2)))
-        keys = rng.permutation(n).astype(np.uint64)
-        th = oracle.rho_extdist_bitmap(flags, keys, n, rho, trial, 1 + trial % 5, 2)
-        rank = int(np.count_nonzero((keys <= np.uint64(th)) & (flags == 1)))
-        total += 1
-        good += (rho / 2 <= rank <= 2 * rho)
-    assert good >= 0.97 * total, (good, total)
-
-
 # --------------------------------------------------------------------------
 # Algorithm 1 run sequentially: exact distances and the paper's step bounds
 # --------------------------------------------------------------------------

@@ -206,7 +206,7 @@ def test_rho_threshold_matches_oracle(lib):
         if trial % 7 == 0:
             dist[:] = 5
         queue = rng.permutation(n)[:q].astype(np.uint32)
-        rho = int([1, 2, 10, 1000, q // 3 + 1, q, 1 << 40][trial % 7])
+        rho = max(1, int([1, 2, 10, 1000, q // 3 + 1, q, 1 << 40][trial % 7]))
         seed = int(rng.integers(0, 1 << 62))
         step = int(rng.integers(1, 1000))
         dense_before = int(trial % 4)

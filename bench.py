@@ -34,6 +34,7 @@ if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
 
 METRIC = "SSSP GTEPS and % HBM roofline on 1 GB300; batched queries/s and p50/p99 latency vs plain"
+ALGO_NAMES = {0: "rho", 1: "delta_star", 2: "bellman_ford", 3: "delta", 4: "dijkstra"}
 
 # Algorithmic bytes per unit of work ("Measurement"):
 BYTES_PER_QUEUED = 16     # Extract filter: 4 B id + 8 B delta + 4 B re-append / F write
@@ -286,10 +287,17 @@ def measure_workload(name, sssp, torch, stream, stream_obj, rates_x=(2, 20)) -> 
         h = gg.knn(2_000_000, 64, 0.02, 10, float(1 << 20), seed=10)
         srcs = gg.pick_sources(h, 256, 9, mask=np.ones(h.n, np.uint8))
     Gx = sssp.Graph(h, sssp.SSSP_GRAPH_SYMMETRIC)
+    one = torch.empty(h.n, dtype=torch.int64, device="cuda")
+    # the best configuration of each rule alone (rho-Stepping, Delta*-Stepping)
+    per_rule = {}
+    for rname, rule in (("rho", sssp.SSSP_RHO), ("delta_star", sssp.SSSP_DELTA_STAR)):
+        tr = sssp.sssp_autotune_ex(Gx.handle, srcs[:3], 1 << rule, stream)
+        tq = _timed(torch, stream_obj, lambda: [sssp.sssp_solve_tuned(Gx.handle, s_, one.data_ptr(), stream)
+                                                for s_ in srcs[:10]])
+        per_rule[rname] = {"tuning": tr, "ms_per_solve": tq / 10, "gteps": 10 * h.m / (tq * 1e-3) / 1e9}
     t0 = time.perf_counter()
     tune = sssp.sssp_autotune(Gx.handle, srcs[:3], stream)
     tune_s = time.perf_counter() - t0
-    one = torch.empty(h.n, dtype=torch.int64, device="cuda")
     tp = _timed(torch, stream_obj, lambda: [sssp.sssp_solve_tuned(Gx.handle, s_, one.data_ptr(), stream)
                                             for s_ in srcs[:10]])
     plain_qps = 10e3 / tp
@@ -308,7 +316,7 @@ def measure_workload(name, sssp, torch, stream, stream_obj, rates_x=(2, 20)) -> 
     del out
     torch.cuda.empty_cache()
     res = {"n": h.n, "m": h.m, "tuning": tune, "tune_s": tune_s, "batch_tuning": btune, "batch_tune_s": btune_s,
-           "plain": {"queries_per_s": plain_qps, "gteps": plain_qps * h.m / 1e9},
+           "plain": {"queries_per_s": plain_qps, "gteps": plain_qps * h.m / 1e9}, "per_rule": per_rule,
            "batched64": {"queries_per_s": 64e3 / tb, "speedup": tp / 10 * 64 / tb, "status": st,
                          "last_equal_to_single": same}}
     rates = [int(max(1, round(x * plain_qps))) for x in rates_x]
@@ -522,6 +530,7 @@ def main():
     ap.add_argument("--no-batch", action="store_true", help="skip the batched-solve measurements")
     ap.add_argument("--no-serve", action="store_true", help="skip the serving measurement")
     ap.add_argument("--no-other", action="store_true", help="skip the road-like and k-NN workloads")
+    ap.add_argument("--no-sweep", action="store_true", help="skip the rho / Delta* / Bellman-Ford sweep")
     ap.add_argument("--serve", action="store_true", help="run the serving sweep (RMAT-25, road, k-NN) only")
     ap.add_argument("--serve-workloads", default="rmat25,road,knn")
     ap.add_argument("--serve-rates", default="1000,2000,5000,10000,20000,50000")
@@ -638,6 +647,26 @@ def main():
         gather = {"gathers_per_s": g.m / (gms * 1e-3), "kernel": "torch.index_select (int64 index)"}
         del idx, outg
 
+    # the parameter sweep of the workload (RMAT scale 22: rho in {2^18, 2^20,
+    # 2^22}, Delta* in {2^13, 2^15, 2^17}, Bellman-Ford), same graph copy,
+    # relaxation and sources as the headline; one solve per source
+    sweep = None
+    if rank == 0 and not args.no_sweep and args.workload == "rmat" and args.scale == 22:
+        sweep = []
+        for sa, sp in ((sssp.SSSP_RHO, 1 << 18), (sssp.SSSP_RHO, 1 << 20), (sssp.SSSP_RHO, 1 << 22),
+                       (sssp.SSSP_DELTA_STAR, 1 << 13), (sssp.SSSP_DELTA_STAR, 1 << 15),
+                       (sssp.SSSP_DELTA_STAR, 1 << 17), (sssp.SSSP_BELLMAN_FORD, 0)):
+            sbuf = torch.zeros((nsrc, sssp.STATS_BYTES // 8), dtype=torch.int64, device="cuda")
+            sopt = [sssp.make_options(stats_out_ptr=sbuf[i].data_ptr(), flags=solve_flags) for i in range(nsrc)]
+            ts = _timed(torch, stream_obj, lambda: [G.solve(srcs[i], sa, sp, dist_out, stream, sopt[i])
+                                                    for i in range(nsrc)])
+            sr = sbuf.cpu().numpy().view(np.uint64)
+            assert all(int(np.int32(r[5] & np.uint64(0xFFFFFFFF))) == 0 for r in sr)
+            sweep.append({"algo": ALGO_NAMES[sa], "param": sp, "ms_per_solve": ts / nsrc,
+                          "gteps": nsrc * g.m / (ts * 1e-3) / 1e9,
+                          "steps": float(np.mean(sr[:, 0].astype(np.float64))),
+                          "edges_per_m": float(np.mean(sr[:, 3].astype(np.float64))) / g.m})
+
     # end-to-end through the C ABI with a host output buffer (pinned)
     e2e = None
     if not args.no_e2e:
@@ -719,6 +748,7 @@ def main():
             "batched": batched,
             "served": served,
             "workloads": workloads,
+            "sweep": sweep,
             "gpu_launches": K,
             "clocks": clk,
         }

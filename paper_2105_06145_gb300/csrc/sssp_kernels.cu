@@ -141,7 +141,10 @@ __global__ void __launch_bounds__(kBlock, kMinBlocks) solve_kernel(SolveParams p
             }
             break;
         }
-        const uint32_t gwarp = blockIdx.x * kWarps + wid;
+        // global warp rank for the relaxation's round-robin over records,
+        // numbered across the blocks first: consecutive records (a hub's
+        // chunks; the few records of a small step) land on different SMs
+        const uint32_t gwarp = wid * gridDim.x + blockIdx.x;
         const uint32_t nwarps = gridDim.x * kWarps;
         if (blockIdx.x == 0 && tid == 0) {
             const unsigned long long now = global_timer_ns() - s_t_start;

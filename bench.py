@@ -228,7 +228,83 @@ def _timed(torch, stream_obj, fn) -> float:
     return e0.elapsed_time(e1)
 
 
-def measure_batched(sssp, G, g, torch, stream, stream_obj) -> dict:
+class _View:
+    """A CSR over arrays in shared memory (what the oracle reads: n, off, tgt, w)."""
+
+    def __init__(self, n, off, tgt, w):
+        self.n, self.off, self.tgt, self.w = n, off, tgt, w
+
+
+def _oracle_worker(job):
+    """Parallel oracle baseline, one worker: binary-heap Dijkstra for each of its
+    (graph, source) tasks, graphs read from shared memory.  job = (names,
+    tasks); tasks = [(n, m, off_base, edge_base, source), ...].  Returns the
+    number of solves (a job with no tasks only attaches: pool warm-up)."""
+    from multiprocessing import shared_memory
+    import oracle
+    names, tasks = job
+    shm = [shared_memory.SharedMemory(name=x) for x in names]
+    OFF = np.ndarray((shm[0].size // 8,), np.uint64, buffer=shm[0].buf)
+    TGT = np.ndarray((shm[1].size // 4,), np.uint32, buffer=shm[1].buf)
+    WW = np.ndarray((shm[2].size // 4,), np.uint32, buffer=shm[2].buf)
+    done = 0
+    for n, m, ob, eb, src in tasks:
+        oracle.dijkstra(_View(n, OFF[ob:ob + n + 1], TGT[eb:eb + m], WW[eb:eb + m]), src)
+        done += 1
+    del OFF, TGT, WW
+    for x in shm:
+        x.close()
+    return done
+
+
+def oracle_parallel(graphs_sources) -> dict:
+    """Throughput of P independent oracle solves on all P host cores (spawned
+    workers, graphs shared read-only): queries/s over the wall time of the
+    solves alone (pool start and attach are outside the timed region)."""
+    import multiprocessing as mp
+    from concurrent.futures import ProcessPoolExecutor
+    from multiprocessing import shared_memory
+    P = os.cpu_count() or 1
+    graphs = {}
+    for h, _ in graphs_sources:
+        graphs.setdefault(id(h), h)
+    offs, tgts, ws, base = [], [], [], {}
+    ob = eb = 0
+    for key, h in graphs.items():
+        base[key] = (ob, eb)
+        offs.append(np.asarray(h.off, np.uint64)); tgts.append(np.asarray(h.tgt, np.uint32))
+        ws.append(np.asarray(h.w, np.uint32))
+        ob += h.n + 1
+        eb += h.m
+    arrays = [np.concatenate(offs), np.concatenate(tgts) if eb else np.zeros(1, np.uint32),
+              np.concatenate(ws) if eb else np.zeros(1, np.uint32)]
+    shm = []
+    try:
+        for a in arrays:
+            x = shared_memory.SharedMemory(create=True, size=max(8, a.nbytes))
+            np.ndarray(a.shape, a.dtype, buffer=x.buf)[:] = a
+            shm.append(x)
+        names = [x.name for x in shm]
+        tasks = [(h.n, h.m, base[id(h)][0], base[id(h)][1], int(s_)) for h, s_ in graphs_sources]
+        jobs = [(names, tasks[i::P]) for i in range(P)]
+        # an executor (not a Pool): a worker that dies fails the call instead
+        # of being replaced forever
+        with ProcessPoolExecutor(max_workers=P, mp_context=mp.get_context("spawn")) as ex:
+            for f in [ex.submit(_oracle_worker, (names, [])) for _ in range(P)]:
+                f.result(timeout=300)
+            t0 = time.perf_counter()
+            done = sum(f.result(timeout=600) for f in [ex.submit(_oracle_worker, j) for j in jobs])
+            dt = time.perf_counter() - t0
+    finally:
+        for x in shm:
+            x.close()
+            x.unlink()
+    return {"value": done / dt, "unit": "queries/s", "cores": P, "kind": "oracle",
+            "sample": f"{done} binary-heap Dijkstra solves over {len(graphs)} graph(s), "
+                      f"{P} spawned workers ({dt:.1f} s)"}
+
+
+def measure_batched(sssp, G, g, torch, stream, stream_obj, cpu: bool = False) -> dict:
     """Batched solves: (a) 64 sources on this graph in one launch, (b) 512 graphs of
     uneven size in one launch with per-instance rho from the autotuner (one tuning
     per graph class); each against the plain loop of single solves, each plain
@@ -270,6 +346,12 @@ def measure_batched(sssp, G, g, torch, stream, stream_obj) -> dict:
                         "graph_classes_tuned": len(classes), "first8_equal_to_single": same}
     for Gx in Gs:
         Gx.close()
+    if cpu:
+        # the oracle on every host core: 2 sources per core on the RMAT-22 graph,
+        # and all 512 graphs
+        P = os.cpu_count() or 1
+        res["sources64_rmat22"]["cpu_baseline"] = oracle_parallel([(g, s_) for s_ in (srcs * 64)[:2 * P]])
+        res["graphs512"]["cpu_baseline"] = oracle_parallel(W)
     return res
 
 
@@ -688,7 +770,7 @@ def main():
     # plain loop of single solves on the same GPU, identical distances
     batched = None
     if rank == 0 and not args.no_batch and args.workload == "rmat" and args.scale == 22:
-        batched = measure_batched(sssp, G, g, torch, stream, stream_obj)
+        batched = measure_batched(sssp, G, g, torch, stream, stream_obj, cpu=not args.no_cpu_baseline)
 
     served = None
     if rank == 0 and not args.no_serve and args.workload == "rmat" and args.scale == 22:

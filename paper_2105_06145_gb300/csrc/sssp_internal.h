@@ -42,7 +42,7 @@ constexpr uint32_t kStageBytes = kWarps * (uint32_t)kStage * 4u;        // 64 KB
 // Batched / serving kernels: staging (and the sampler's keys).
 constexpr uint32_t kBatchDynSmem = kStageBytes > kMaxSamples * 8u ? kStageBytes : kMaxSamples * 8u;
 // Single solve: Extract stages one round of up to kExtractCap queue entries
-// of the block's slice (a 16-byte record and a kind byte each) in the same
+// of one of the block's runs (a 16-byte record and a kind byte each) in the same
 // region (Extract, the sampler and the relaxation never overlap in time).
 #ifndef SSSP_EXTRACT_PER
 #define SSSP_EXTRACT_PER 4

@@ -355,7 +355,7 @@ def measure_batched(sssp, G, g, torch, stream, stream_obj, cpu: bool = False) ->
     return res
 
 
-def measure_workload(name, sssp, torch, stream, stream_obj, rates_x=(2, 20)) -> dict:
+def measure_workload(name, sssp, torch, stream, stream_obj, rates_x=(2, 20), cpu: bool = False) -> dict:
     """Road-like (4096^2 jittered grid) or k-NN (2M points) workload: the
     autotuner's single-solve choice as a plain loop of single solves; 64
     sources in one batched launch and the continuous-batching server, both in
@@ -408,6 +408,8 @@ def measure_workload(name, sssp, torch, stream, stream_obj, rates_x=(2, 20)) -> 
     Gx.close()
     del Gx
     torch.cuda.empty_cache()
+    if cpu:  # the oracle on every host core, 2 sources per core
+        res["cpu_baseline"] = oracle_parallel([(h, s_) for s_ in srcs[:2 * (os.cpu_count() or 1)]])
     return res
 
 
@@ -787,7 +789,8 @@ def main():
     if rank == 0 and not args.no_other and args.workload == "rmat" and args.scale == 22:
         workloads = {}
         for wname in ("road4096", "knn2m"):
-            workloads[wname] = measure_workload(wname, sssp, torch, stream, stream_obj)
+            workloads[wname] = measure_workload(wname, sssp, torch, stream, stream_obj,
+                                                cpu=not args.no_cpu_baseline)
             if batched is not None:
                 batched[f"sources64_{wname}"] = workloads[wname]["batched64"]
             if served is not None:

@@ -239,7 +239,8 @@ def _oracle_worker(job):
     """Parallel oracle baseline, one worker: binary-heap Dijkstra for each of its
     (graph, source) tasks, graphs read from shared memory.  job = (names,
     tasks); tasks = [(n, m, off_base, edge_base, source), ...].  Returns the
-    number of solves (a job with no tasks only attaches: pool warm-up)."""
+    XOR of each solve's distance array, one per task (a job with no tasks
+    only attaches: pool warm-up)."""
     from multiprocessing import shared_memory
     import oracle
     names, tasks = job
@@ -247,20 +248,21 @@ def _oracle_worker(job):
     OFF = np.ndarray((shm[0].size // 8,), np.uint64, buffer=shm[0].buf)
     TGT = np.ndarray((shm[1].size // 4,), np.uint32, buffer=shm[1].buf)
     WW = np.ndarray((shm[2].size // 4,), np.uint32, buffer=shm[2].buf)
-    done = 0
+    digests = []
     for n, m, ob, eb, src in tasks:
-        oracle.dijkstra(_View(n, OFF[ob:ob + n + 1], TGT[eb:eb + m], WW[eb:eb + m]), src)
-        done += 1
+        d = oracle.dijkstra(_View(n, OFF[ob:ob + n + 1], TGT[eb:eb + m], WW[eb:eb + m]), src)
+        digests.append(int(np.bitwise_xor.reduce(d)))
     del OFF, TGT, WW
     for x in shm:
         x.close()
-    return done
+    return digests
 
 
-def oracle_parallel(graphs_sources) -> dict:
+def oracle_parallel(graphs_sources, with_digests: bool = False) -> dict:
     """Throughput of P independent oracle solves on all P host cores (spawned
     workers, graphs shared read-only): queries/s over the wall time of the
-    solves alone (pool start and attach are outside the timed region)."""
+    solves alone (pool start and attach are outside the timed region).
+    with_digests: also return each task's distance XOR, in task order."""
     import multiprocessing as mp
     from concurrent.futures import ProcessPoolExecutor
     from multiprocessing import shared_memory
@@ -293,15 +295,23 @@ def oracle_parallel(graphs_sources) -> dict:
             for f in [ex.submit(_oracle_worker, (names, [])) for _ in range(P)]:
                 f.result(timeout=300)
             t0 = time.perf_counter()
-            done = sum(f.result(timeout=600) for f in [ex.submit(_oracle_worker, j) for j in jobs])
+            parts = [f.result(timeout=600) for f in [ex.submit(_oracle_worker, j) for j in jobs]]
             dt = time.perf_counter() - t0
+        done = sum(len(x) for x in parts)
+        digests = [0] * len(tasks)
+        for i, part in enumerate(parts):  # job i ran tasks i, i+P, i+2P, ...
+            for j, dg in enumerate(part):
+                digests[i + j * P] = dg
     finally:
         for x in shm:
             x.close()
             x.unlink()
-    return {"value": done / dt, "unit": "queries/s", "cores": P, "kind": "oracle",
-            "sample": f"{done} binary-heap Dijkstra solves over {len(graphs)} graph(s), "
-                      f"{P} spawned workers ({dt:.1f} s)"}
+    out = {"value": done / dt, "unit": "queries/s", "cores": P, "kind": "oracle",
+           "sample": f"{done} binary-heap Dijkstra solves over {len(graphs)} graph(s), "
+                     f"{P} spawned workers ({dt:.1f} s)"}
+    if with_digests:
+        out["digests"] = digests
+    return out
 
 
 def measure_batched(sssp, G, g, torch, stream, stream_obj, cpu: bool = False) -> dict:

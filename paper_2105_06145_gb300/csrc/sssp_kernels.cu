@@ -14,8 +14,10 @@
 //   until |Q| = 0
 //
 // State that must be coherent across blocks (delta, the queue bitmap, queue
-// lists, counters) is read with L2-only loads (ld.global.cg) or atomics;
-// the graph (offsets, packed edges) is read-only for the kernel's lifetime.
+// lists, counters) is read with L2-only loads (ld.global.cg) or atomics --
+// except the relaxation's pre-check of delta[v], which reads through L1 and
+// may see a value that is too high, never one too low (ld_precheck); the
+// graph (offsets, packed edges) is read-only for the kernel's lifetime.
 // Every device-wide wait is bounded by a globaltimer deadline; on expiry the
 // kernel records SSSP_ERR_TIMEOUT and every block returns.
 

@@ -27,6 +27,7 @@ SSSP_GRAPH_SYMMETRIC, SSSP_GRAPH_VERIFY, SSSP_GRAPH_REORDER = 1, 2, 4
 SSSP_OK = 0
 SSSP_ERR_INVALID_ARG, SSSP_ERR_OUT_OF_MEMORY, SSSP_ERR_CUDA = -1, -2, -3
 SSSP_ERR_TIMEOUT, SSSP_ERR_INTERNAL = -4, -5
+SSSP_MAX_BATCH = 2048  # instances per batched call
 INF = (1 << 64) - 1
 
 if not os.path.exists(LIB_PATH):

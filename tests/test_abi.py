@@ -66,3 +66,27 @@ def test_symmetry_verification_without_gpu():
         sssp.sssp_graph_create_ex(2, 2, off, tgt, w, sssp.SSSP_GRAPH_SYMMETRIC | sssp.SSSP_GRAPH_VERIFY)
     with pytest.raises(sssp.SSSPError):
         sssp.sssp_graph_create_ex(2, 2, off, tgt, w, 1 << 7)  # unknown flag
+
+
+def _header_constants():
+    src = open(os.path.join(ROOT, "include", "sssp.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    consts = {k: int(v.rstrip("uU"), 0) for k, v in re.findall(r"#define\s+(SSSP_\w+)\s+(-?\w+)", src)
+              if re.fullmatch(r"-?(0x[0-9a-fA-F]+|\d+)[uU]?", v)}
+    for body in re.findall(r"typedef\s+enum\s*\{(.*?)\}", src, flags=re.S):
+        for k, v in re.findall(r"(SSSP_\w+)\s*=\s*(-?\d+)", body):
+            consts[k] = int(v)
+    return consts
+
+
+def test_binding_constants_match_the_header():
+    """Every numeric constant the header defines (algorithms, statuses, flags,
+    shapes, limits) has the same value in the Python binding."""
+    from paper_2105_06145_gb300 import sssp
+    consts = _header_constants()
+    assert {"SSSP_RHO", "SSSP_DELTA_STAR", "SSSP_BELLMAN_FORD", "SSSP_ERR_TIMEOUT",
+            "SSSP_SOLVE_BIDIRECTIONAL", "SSSP_GRAPH_REORDER"} <= set(consts)
+    missing = [k for k in consts if not hasattr(sssp, k)]
+    assert not missing, missing
+    for k, v in consts.items():
+        assert getattr(sssp, k) == v, (k, getattr(sssp, k), v)

@@ -90,3 +90,41 @@ def test_binding_constants_match_the_header():
     assert not missing, missing
     for k, v in consts.items():
         assert getattr(sssp, k) == v, (k, getattr(sssp, k), v)
+
+
+def test_binding_struct_layouts_match_the_header(tmp_path):
+    """Sizes and field offsets of every struct the binding passes across the
+    boundary, as gcc lays them out from the header, equal the ctypes ones."""
+    import shutil
+    import subprocess
+    from paper_2105_06145_gb300 import sssp
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no C compiler")
+    structs = [sssp.sssp_step_trace, sssp.sssp_stats, sssp.sssp_options, sssp.sssp_server_config,
+               sssp.sssp_query_info, sssp.sssp_tuning]
+    lines = ["#include <stddef.h>", "#include <stdio.h>", '#include "sssp.h"', "int main(void) {"]
+    for st in structs:
+        n = st.__name__
+        lines.append(f'printf("{n} sizeof %zu\\n", sizeof({n}));')
+        for f, _ in st._fields_:
+            lines.append(f'printf("{n} {f} %zu\\n", offsetof({n}, {f}));')
+    lines += ["return 0;", "}"]
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines) + "\n")
+    exe = tmp_path / "layout"
+    subprocess.check_call([cc, "-std=c11", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)])
+    got = {}
+    for ln in subprocess.check_output([str(exe)], text=True).split("\n"):
+        if ln:
+            s, f, v = ln.split()
+            got[(s, f)] = int(v)
+    for st in structs:
+        n = st.__name__
+        assert got[(n, "sizeof")] == ctypes.sizeof(st), n
+        for f, _ in st._fields_:
+            assert got[(n, f)] == getattr(st, f).offset, (n, f)
+    dt = np.dtype(sssp.TRACE_DTYPE)
+    assert dt.itemsize == got[("sssp_step_trace", "sizeof")]
+    for f in dt.names:
+        assert dt.fields[f][1] == got[("sssp_step_trace", f)], f

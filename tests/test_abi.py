@@ -128,3 +128,22 @@ def test_binding_struct_layouts_match_the_header(tmp_path):
     assert dt.itemsize == got[("sssp_step_trace", "sizeof")]
     for f in dt.names:
         assert dt.fields[f][1] == got[("sssp_step_trace", f)], f
+
+
+def test_binding_arity_matches_the_header():
+    """Every function the binding types has as many parameters as the header
+    declares (a drifted prototype would pass garbage through ctypes)."""
+    from paper_2105_06145_gb300 import sssp
+    src = open(os.path.join(ROOT, "include", "sssp.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    protos = dict(re.findall(r"\b(sssp_\w+)\s*\(([^;{]*?)\)\s*;", src, flags=re.S))
+    checked = 0
+    for name, params in protos.items():
+        fn = getattr(sssp._lib, name, None)
+        if fn is None or fn.argtypes is None:
+            continue
+        p = params.strip()
+        n = 0 if p in ("", "void") else p.count(",") + 1
+        assert len(fn.argtypes) == n, (name, len(fn.argtypes), n)
+        checked += 1
+    assert checked >= 30, checked

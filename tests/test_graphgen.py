@@ -90,3 +90,39 @@ def test_pick_sources_in_largest_component():
     lab = gg.largest_cc(g)
     srcs = gg.pick_sources(g, 30, 1)
     assert len(set(srcs)) == 30 and all(lab[s] for s in srcs)
+
+
+def test_generators_do_not_depend_on_the_thread_count():
+    """The OpenMP generators give the same graphs with 1 thread as with the
+    default count (every random number is splitmix64(seed, index)); the sizes
+    are large enough (>= 2^20 edge draws) for the multi-threaded sort path."""
+    import hashlib
+    import os
+    import subprocess
+    import sys
+
+    def digest(g):
+        h = hashlib.sha256()
+        for a in (g.off, g.tgt, g.w):
+            h.update(np.ascontiguousarray(a).tobytes())
+        return h.hexdigest()
+
+    here = {"rmat": digest(gg.rmat(17, 8, gen_seed=6, wseed=7)),
+            "road": digest(gg.road(1100, 0.75, seed=8)),
+            "knn": digest(gg.knn(3000, 4, 0.05, 5, float(1 << 20), seed=9))}
+    code = ("import hashlib, json, numpy as np\n"
+            "from paper_2105_06145_gb300 import graphgen as gg\n"
+            "def digest(g):\n"
+            "    h = hashlib.sha256()\n"
+            "    for a in (g.off, g.tgt, g.w):\n"
+            "        h.update(np.ascontiguousarray(a).tobytes())\n"
+            "    return h.hexdigest()\n"
+            "print(json.dumps({'rmat': digest(gg.rmat(17, 8, gen_seed=6, wseed=7)),\n"
+            "                  'road': digest(gg.road(1100, 0.75, seed=8)),\n"
+            "                  'knn': digest(gg.knn(3000, 4, 0.05, 5, float(1 << 20), seed=9))}))\n")
+    env = dict(os.environ, OMP_NUM_THREADS="1")
+    env.pop("SSSP_GRAPH_CACHE", None)
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    out = subprocess.check_output([sys.executable, "-c", code], env=env, cwd=root, text=True)
+    import json
+    assert json.loads(out.strip().splitlines()[-1]) == here

@@ -36,3 +36,22 @@ def test_oracle_parallel_equals_in_process_oracle():
     want = [int(np.bitwise_xor.reduce(oracle.dijkstra(h, s))) for h, s in tasks]
     assert r["digests"] == want
     assert r["cores"] >= 1 and r["value"] > 0 and r["kind"] == "oracle"
+
+
+def test_reference_arm_prints_one_json_line():
+    """`bench.py --impl reference` (the oracle on host cores) runs without a GPU
+    and prints the contract's line: impl, metric, value, cpu_baseline, e2e."""
+    import json
+    import os
+    import subprocess
+    import sys
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    out = subprocess.check_output([sys.executable, "bench.py", "--impl", "reference", "--scale", "12",
+                                   "--steps", "2", "--warmup", "1"], cwd=root, text=True, timeout=600)
+    lines = [ln for ln in out.splitlines() if ln.startswith("{")]
+    assert len(lines) == 1
+    d = json.loads(lines[0])
+    assert d["impl"] == "reference" and d["unit"] == "GTEPS" and d["value"] > 0
+    assert d["steps"] == 2 and d["warmup"] == 1 and d["higher_is_better"] is True
+    assert d["cpu_baseline"]["kind"] == "oracle" and d["cpu_baseline"]["value"] == d["value"]
+    assert d["e2e"] == {"value": d["value"], "unit": "GTEPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}

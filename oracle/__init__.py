@@ -75,7 +75,7 @@ def _L():
         lib.oracle_check.restype = i32
         lib.oracle_hops.argtypes = [u32, P, P, P, u32, P]
         lib.oracle_hops.restype = i64
-        lib.oracle_rho_extdist.argtypes = [P, u32, P, u32, u64, u64, u64, u32]
+        lib.oracle_rho_extdist.argtypes = [P, u32, P, u32, u64, u64, u64, u32, u32]
         lib.oracle_rho_extdist.restype = u64
         lib.oracle_delta_extdist.argtypes = [ctypes.POINTER(u64), u64, u64]
         lib.oracle_delta_extdist.restype = u64
@@ -83,7 +83,7 @@ def _L():
         lib.oracle_delta_theta.restype = u64
         lib.oracle_delta_finish.argtypes = [ctypes.POINTER(u64), u64, u64]
         lib.oracle_delta_finish.restype = None
-        lib.oracle_stepping.argtypes = [u32, P, P, P, u32, i32, u64, u64, P, P,
+        lib.oracle_stepping.argtypes = [u32, P, P, P, u32, i32, u64, u64, u32, P, P,
                                         ctypes.POINTER(Stats)]
         lib.oracle_stepping.restype = i32
         lib.oracle_lbpq_extract.argtypes = [u32, P, P, u64, P]
@@ -157,12 +157,13 @@ def hops(g, s: int) -> tuple[np.ndarray, int]:
 
 
 def rho_extdist(queue: np.ndarray, dist: np.ndarray, n: int, rho: int, seed: int, step: int,
-                dense_before: int) -> int:
+                dense_before: int, reduced: int = 2) -> int:
+    """reduced: how many dense steps use rho/10 (Sec. 6 uses the first two)."""
     queue = np.ascontiguousarray(queue, dtype=np.uint32)
     dist = np.ascontiguousarray(dist, dtype=np.uint64)
     qp = queue.ctypes.data if queue.size else np.zeros(1, np.uint32).ctypes.data
     return int(_L().oracle_rho_extdist(qp, queue.size, dist.ctypes.data, n, rho, seed, step,
-                                       dense_before))
+                                       dense_before, reduced))
 
 
 def delta_extdist(i: int, delta: int, qmin: int) -> tuple[int, int]:
@@ -187,14 +188,15 @@ def delta_finish(i: int, theta: int, min_new: int) -> int:
 
 
 def stepping(g, s: int, algo: int, param: int, seed: int = 0,
-             want_ext: bool = False) -> tuple[np.ndarray, dict, np.ndarray | None]:
-    """Algorithm 1 run sequentially: (dist, stats, per-vertex extraction counts)."""
+             want_ext: bool = False, reduced: int = 2) -> tuple[np.ndarray, dict, np.ndarray | None]:
+    """Algorithm 1 run sequentially: (dist, stats, per-vertex extraction counts).
+    reduced: rho-Stepping's count of dense steps that use rho/10 (the paper's 2)."""
     off, tgt, w = _arrs(g)
     dist = np.empty(g.n, dtype=np.uint64)
     ext = np.empty(g.n, dtype=np.uint32) if want_ext else None
     st = Stats()
     rc = _L().oracle_stepping(g.n, off.ctypes.data, tgt.ctypes.data, w.ctypes.data, s, algo,
-                              param, seed, dist.ctypes.data,
+                              param, seed, reduced, dist.ctypes.data,
                               ext.ctypes.data if want_ext else None, ctypes.byref(st))
     if rc != 0:
         raise ValueError("oracle_stepping failed")

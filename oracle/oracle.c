@@ -336,8 +336,10 @@ static int cmp_u64(const void* a, const void* b)
  *
  * queue[0..q) lists the ids in Q in list order; dist is the key array; n is
  * the vertex count; step is the 1-based step number; dense_before is the
- * number of dense steps that came before this one.  Readings:
- *   - a step is dense when 20*q > n; the first two dense steps use
+ * number of dense steps that came before this one; reduced is how many dense
+ * steps use 10% of rho (the paper's choice is 2; Sec. 6 gives it as a tuning
+ * made on its machine, so the count is a parameter here).  Readings:
+ *   - a step is dense when 20*q > n; the first `reduced` dense steps use
  *     rho' = max(1, floor(rho/10)), every other step rho' = rho;
  *   - "n" inside s and the rank is the frontier size q (samples come from the
  *     current frontier), "log n" is the paper's 1 + log2(n+1) taken as
@@ -352,10 +354,10 @@ static int cmp_u64(const void* a, const void* b)
  */
 uint64_t oracle_rho_extdist(const uint32_t* queue, uint32_t q, const uint64_t* dist,
                             uint32_t n, uint64_t rho, uint64_t seed, uint64_t step,
-                            uint32_t dense_before)
+                            uint32_t dense_before, uint32_t reduced)
 {
     uint64_t rho_eff = rho;
-    if ((uint64_t)q * 20u > (uint64_t)n && dense_before < 2) {
+    if ((uint64_t)q * 20u > (uint64_t)n && dense_before < reduced) {
         rho_eff = rho / 10u;
         if (rho_eff < 1) rho_eff = 1;
     }
@@ -437,7 +439,8 @@ enum { ORC_RHO = 0, ORC_DELTA_STAR = 1, ORC_BELLMAN_FORD = 2, ORC_DELTA = 3, ORC
  * array-based LaB-PQ of Sec. 4.3 (a flag per vertex; Update sets the flag and
  * appends the id, Extract scans the queued ids and packs those with key <=
  * theta).  algo selects the ExtDist (and FinishCheck) of Table 2:
- *   ORC_RHO          theta from oracle_rho_extdist (param = rho >= 1)
+ *   ORC_RHO          theta from oracle_rho_extdist (param = rho >= 1;
+ *                    rho_reduced = dense steps that use rho/10, the paper's 2)
  *   ORC_DELTA_STAR   theta from oracle_delta_extdist (param = Delta >= 1)
  *   ORC_BELLMAN_FORD theta = +infinity (param ignored)
  *   ORC_DELTA        theta = i*Delta with FinishCheck (oracle_delta_theta /
@@ -451,7 +454,7 @@ enum { ORC_RHO = 0, ORC_DELTA_STAR = 1, ORC_BELLMAN_FORD = 2, ORC_DELTA = 3, ORC
  */
 int oracle_stepping(uint32_t n, const uint64_t* off, const uint32_t* tgt,
                     const uint32_t* w, uint32_t s, int algo, uint64_t param,
-                    uint64_t seed, uint64_t* dist, uint32_t* ext_count,
+                    uint64_t seed, uint32_t rho_reduced, uint64_t* dist, uint32_t* ext_count,
                     oracle_stats* st)
 {
     if (s >= n) return -1;
@@ -492,8 +495,8 @@ int oracle_stepping(uint32_t n, const uint64_t* off, const uint32_t* tgt,
         } else {
             int dense = (uint64_t)qlen * 20u > (uint64_t)n;
             uint64_t rho_eff = param;
-            if (dense && dense_seen < 2) { rho_eff = param / 10u; if (rho_eff < 1) rho_eff = 1; }
-            theta = oracle_rho_extdist(Q, qlen, dist, n, param, seed, z.steps, dense_seen);
+            if (dense && dense_seen < rho_reduced) { rho_eff = param / 10u; if (rho_eff < 1) rho_eff = 1; }
+            theta = oracle_rho_extdist(Q, qlen, dist, n, param, seed, z.steps, dense_seen, rho_reduced);
             if ((uint64_t)qlen <= rho_eff) z.partial_steps++; else z.full_steps++;
             if (dense) dense_seen++;
         }

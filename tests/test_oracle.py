@@ -233,6 +233,81 @@ def test_rho_extdist_dense_rule():
     assert oracle.rho_extdist(queue, keys, n, 10 * q, 0, 1, 0) == INF
 
 
+def _dense_ranks(rho, dense_before, reduced, trials=40):
+    """Ranks of the sampled threshold on a dense step (20*q > n) over keys that
+    are a permutation of 0..q-1 (rank = theta + 1)."""
+    q, n = 50000, 100000
+    keys = np.random.default_rng(5).permutation(q).astype(np.uint64)
+    queue = np.arange(q, dtype=np.uint32)
+    return [oracle.rho_extdist(queue, keys, n, rho, s, 1, dense_before, reduced) + 1 for s in range(trials)]
+
+
+def test_rho_extdist_reduced_step_count():
+    """Sec. 6 runs the first two dense steps with 10 % of rho; the count is a
+    parameter: the first `reduced` dense steps use rho/10, later ones rho, and
+    a count of 0 is plain rho-Stepping on every step."""
+    rho = 5000
+    for reduced in (0, 2, 6):
+        for before in range(8):
+            med = np.median(_dense_ranks(rho, before, reduced))
+            if before < reduced:
+                assert rho / 20 <= med <= rho / 5, (reduced, before, med)
+            else:
+                assert rho / 2 <= med <= 2 * rho, (reduced, before, med)
+    # the same sample positions: a step below both counts, or past both, draws
+    # the same threshold whatever the count
+    q, n = 30000, 60000
+    keys = np.random.default_rng(6).integers(0, 1 << 40, q, dtype=np.uint64)
+    queue = np.random.default_rng(7).permutation(q).astype(np.uint32)
+    for step in (1, 5, 9):
+        a = oracle.rho_extdist(queue, keys, n, 3000, 77, step, 1, 2)
+        b = oracle.rho_extdist(queue, keys, n, 3000, 77, step, 1, 6)
+        c = oracle.rho_extdist(queue, keys, n, 3000, 77, step, 6, 2)
+        d = oracle.rho_extdist(queue, keys, n, 3000, 77, step, 0, 0)
+        assert a == b and c == d and a != c
+    # a sparse step (20*q <= n) ignores the count
+    for reduced in (0, 2, 6, 1000):
+        assert oracle.rho_extdist(queue, keys, 10 ** 7, 3000, 77, 3, 0, reduced) == \
+            oracle.rho_extdist(queue, keys, 10 ** 7, 3000, 77, 3, 0, 0)
+
+
+def test_rho_extdist_rank_bound_at_reduced_rho():
+    """Appendix B's guarantee holds for the reduced rho' = floor(rho/10) of a
+    reduced dense step: rank within [rho'/2, 2 rho'] w.h.p."""
+    rng = np.random.default_rng(13)
+    good = total = 0
+    for trial in range(300):
+        q = int(rng.integers(2000, 200000))
+        rho = int(rng.integers(100, q // 2))
+        keys = rng.permutation(q).astype(np.uint64)
+        queue = rng.permutation(q).astype(np.uint32)
+        n = 10 * q  # 20*q > n: dense
+        th = oracle.rho_extdist(queue, keys, n, rho, trial, 1 + trial % 5, trial % 4, 4)
+        rank, rp = th + 1, rho // 10
+        total += 1
+        good += (rp / 2 <= rank <= 2 * rp)
+    assert good >= 0.97 * total, (good, total)
+
+
+@pytest.mark.parametrize("reduced", [0, 1, 6, 50])
+def test_stepping_with_any_reduced_count(reduced):
+    """The count of reduced dense steps changes thresholds only: distances equal
+    Dijkstra's, Lemma 5.1's extraction bound and the partial-step bound of
+    Theorem 5.3's proof hold for every count."""
+    for g in _bounded_graphs():
+        s = int(np.flatnonzero(gg.largest_cc(g))[0])
+        d = oracle.dijkstra(g, s)
+        h, kn = oracle.hops(g, s)
+        for rho in (64, 1 << 10):
+            ds, st, ext = oracle.stepping(g, s, oracle.RHO, rho, seed=3, want_ext=True, reduced=reduced)
+            assert np.array_equal(d, ds), (g.name, rho, reduced)
+            reach = d != oracle.INF
+            hv = h.astype(np.int64)
+            hv[s] = 1
+            assert np.all(ext[reach].astype(np.int64) <= hv[reach])
+            assert st["partial_steps"] <= kn + 1
+
+
 # --------------------------------------------------------------------------
 # Algorithm 1 run sequentially: exact distances and the paper's step bounds
 # --------------------------------------------------------------------------

@@ -36,7 +36,9 @@ if ROOT not in sys.path:
 METRIC = "SSSP GTEPS and % HBM roofline on 1 GB300; batched queries/s and p50/p99 latency vs plain"
 ALGO_NAMES = {0: "rho", 1: "delta_star", 2: "bellman_ford", 3: "delta", 4: "dijkstra"}
 
-# Algorithmic bytes per unit of work ("Measurement"):
+# Algorithmic bytes per unit of work of one solve, from its device counters
+# (what the method itself must move per queued id, extracted vertex, scanned
+# edge and successful update):
 BYTES_PER_QUEUED = 16     # Extract filter: 4 B id + 8 B delta + 4 B re-append / F write
 BYTES_PER_EXTRACTED = 32  # 16 B offsets + 8 B delta[u] + 4 B F write + 4 B F read
 BYTES_PER_EDGE = 16       # 8 B packed (target, weight) + 8 B delta[v]
@@ -139,6 +141,25 @@ class ClockSampler:
                 "samples": len(sm), "reasons": sorted(reasons)}
 
 
+def cpu_model() -> str:
+    """The host CPU's model name (lscpu, else /proc/cpuinfo, else platform)."""
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.strip().lower().startswith("model name"):
+                return line.split(":", 1)[1].strip()
+    except Exception:
+        pass
+    try:
+        for line in open("/proc/cpuinfo"):
+            if line.lower().startswith(("model name", "cpu model")):
+                return line.split(":", 1)[1].strip()
+    except OSError:
+        pass
+    import platform
+    return platform.processor() or platform.machine()
+
+
 def dist_env():
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -208,7 +229,7 @@ def run_reference(args, g, srcs, label, rank, world):
         "ms_per_step": 1e3 * tot / args.steps, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "u64", "data": "synthetic",
         "config": {"workload": label, "n": g.n, "m": g.m, "algo": "dijkstra (CPU oracle)"},
-        "cpu_baseline": {"value": gteps, "unit": "GTEPS", "cores": 1, "kind": "oracle",
+        "cpu_baseline": {"value": gteps, "unit": "GTEPS", "cores": 1, "cpu_model": cpu_model(), "kind": "oracle",
                          "sample": f"{args.steps} full single-source solves of {label}"},
         "e2e": {"value": gteps, "unit": "GTEPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
@@ -226,6 +247,20 @@ def _timed(torch, stream_obj, fn) -> float:
         e1.record(stream_obj)
         torch.cuda.synchronize()
     return e0.elapsed_time(e1)
+
+
+def rows_equal_to_single(torch, stream_obj, rows, sources, solve_one) -> int:
+    """How many rows[i] (a batched or served result) equal the single solve of
+    sources[i] (solve_one(source, out_tensor) enqueues it); run after the
+    timed region."""
+    one = torch.empty_like(rows[0])
+    eq = 0
+    with torch.cuda.stream(stream_obj):
+        for i, s_ in enumerate(sources):
+            solve_one(int(s_), one)
+            torch.cuda.synchronize()
+            eq += int(bool(torch.equal(rows[i], one)))
+    return eq
 
 
 class _View:
@@ -306,7 +341,7 @@ def oracle_parallel(graphs_sources, with_digests: bool = False) -> dict:
         for x in shm:
             x.close()
             x.unlink()
-    out = {"value": done / dt, "unit": "queries/s", "cores": P, "kind": "oracle",
+    out = {"value": done / dt, "unit": "queries/s", "cores": P, "cpu_model": cpu_model(), "kind": "oracle",
            "sample": f"{done} binary-heap Dijkstra solves over {len(graphs)} graph(s), "
                      f"{P} spawned workers ({dt:.1f} s)"}
     if with_digests:
@@ -330,10 +365,11 @@ def measure_batched(sssp, G, g, torch, stream, stream_obj, cpu: bool = False) ->
     st, _ = sssp.sssp_batch_last_stats(64, stream)
     tp = _timed(torch, stream_obj, lambda: [sssp.sssp_solve_tuned(G.handle, s_, one.data_ptr(), stream)
                                             for s_ in srcs])
-    same = bool(torch.equal(out.view(64, g.n)[-1], one))
+    eq = rows_equal_to_single(torch, stream_obj, out.view(64, g.n), srcs,
+                              lambda s_, o: sssp.sssp_solve_tuned(G.handle, s_, o.data_ptr(), stream))
     res["sources64_rmat22"] = {"queries_per_s": 64e3 / tb, "plain_queries_per_s": 64e3 / tp,
-                               "speedup": tp / tb, "status": st, "last_equal_to_single": same,
-                               "tuning": tune}
+                               "speedup": tp / tb, "status": st, "all_equal": eq == 64,
+                               "instances_equal_to_single": eq, "tuning": tune}
     del out, one
     W = gg.workload_multi()
     Gs = [sssp.Graph(h, sssp.SSSP_GRAPH_SYMMETRIC) for h, _ in W]
@@ -347,13 +383,16 @@ def measure_batched(sssp, G, g, torch, stream, stream_obj, cpu: bool = False) ->
     hs, ss, ptrs = [x.handle for x in Gs], [s_ for _, s_ in W], [o.data_ptr() for o in outs]
     tb = _timed(torch, stream_obj, lambda: sssp.sssp_solve_multi(hs, ss, sssp.SSSP_RHO, None, ptrs, stream))
     st, _ = sssp.sssp_batch_last_stats(len(W), stream)
-    keep = [o.clone() for o in outs[:8]]
+    keep = [o.clone() for o in outs]
     tp = _timed(torch, stream_obj, lambda: [sssp.sssp_solve_tuned(Gx.handle, s_, o.data_ptr(), stream)
                                             for (h, s_), Gx, o in zip(W, Gs, outs)])
-    same = all(bool(torch.equal(a, b)) for a, b in zip(keep, outs[:8]))
+    torch.cuda.synchronize()
+    eq = sum(int(bool(torch.equal(a, b))) for a, b in zip(keep, outs))
+    del keep
     res["graphs512"] = {"queries_per_s": len(W) * 1e3 / tb, "plain_queries_per_s": len(W) * 1e3 / tp,
                         "speedup": tp / tb, "status": st, "edges_total": int(sum(h.m for h, _ in W)),
-                        "graph_classes_tuned": len(classes), "first8_equal_to_single": same}
+                        "graph_classes_tuned": len(classes), "all_equal": eq == len(W),
+                        "instances_equal_to_single": eq}
     for Gx in Gs:
         Gx.close()
     if cpu:
@@ -402,15 +441,14 @@ def measure_workload(name, sssp, torch, stream, stream_obj, rates_x=(2, 20), cpu
     tb = _timed(torch, stream_obj, lambda: sssp.sssp_solve_sources(Gx.handle, srcs[:64], btune["algo"], None,
                                                                    out.data_ptr(), stream))
     st, _ = sssp.sssp_batch_last_stats(64, stream)
-    sssp.sssp_solve_tuned(Gx.handle, srcs[63], one.data_ptr(), stream)
-    torch.cuda.synchronize()
-    same = bool(torch.equal(out.view(64, h.n)[63], one))
+    eq = rows_equal_to_single(torch, stream_obj, out.view(64, h.n), srcs[:64],
+                              lambda s_, o: sssp.sssp_solve_tuned(Gx.handle, s_, o.data_ptr(), stream))
     del out
     torch.cuda.empty_cache()
     res = {"n": h.n, "m": h.m, "tuning": tune, "tune_s": tune_s, "batch_tuning": btune, "batch_tune_s": btune_s,
            "plain": {"queries_per_s": plain_qps, "gteps": plain_qps * h.m / 1e9}, "per_rule": per_rule,
            "batched64": {"queries_per_s": 64e3 / tb, "speedup": tp / 10 * 64 / tb, "status": st,
-                         "last_equal_to_single": same}}
+                         "all_equal": eq == 64, "instances_equal_to_single": eq}}
     rates = [int(max(1, round(x * plain_qps))) for x in rates_x]
     sv = measure_serving(sssp, Gx, h, torch, srcs, rates, window_s=1.0, hard_s=8.0, slots=0,
                          algo=btune["algo"], param=btune["param"], tuned=True)
@@ -429,7 +467,11 @@ def measure_serving(sssp, G, g, torch, sources, rates, window_s=1.0, hard_s=10.0
     for `window_s` seconds against the resident graph; queries go to the
     continuous-batching server as client-side result buffers allow.  Latency
     is from the scheduled arrival to the completion seen by the client; the
-    plain loop (one sssp_solve at a time) is measured on the same sources."""
+    plain loop (one sssp_solve at a time) is measured on the same sources.
+    Every rate keeps a sample of its served results (the first completions and
+    every 8th after them, their buffers held back from reuse) and compares each
+    with the single solve of its source after the window (`checked`,
+    `all_equal`)."""
     algo = sssp.SSSP_RHO if algo is None else algo
     srv = sssp.sssp_server_create(G.handle, slots=slots, algo=algo, param=param)
     S = sssp.sssp_server_slots(srv)
@@ -464,6 +506,9 @@ def measure_serving(sssp, G, g, torch, sources, rates, window_s=1.0, hard_s=10.0
         free = list(range(nbuf))
         outstanding = {}
         lat = []
+        held = []            # (source, buffer) of served results kept for the check
+        hold_max = max(1, min(8, nbuf // 4))
+        ndone = 0
         i = 0
         t0 = time.perf_counter()
         last_done = t0
@@ -473,16 +518,20 @@ def measure_serving(sssp, G, g, torch, sources, rates, window_s=1.0, hard_s=10.0
             while i < arr.size and arr[i] <= now and free:
                 b = free.pop()
                 tk = sssp.sssp_server_submit(srv, int(srcs[i]), bufs[b].data_ptr())
-                outstanding[tk] = (arr[i], b)
+                outstanding[tk] = (arr[i], b, int(srcs[i]))
                 i += 1
                 progressed = True
             done = sssp.sssp_server_drain(srv)
             if done:
                 tnow = time.perf_counter()
                 for tk, info in done:
-                    a_, b = outstanding.pop(tk)
+                    a_, b, src_ = outstanding.pop(tk)
                     lat.append(tnow - t0 - a_)
-                    free.append(b)
+                    if len(held) < hold_max and (ndone < 2 or ndone % 8 == 0):
+                        held.append((src_, b))
+                    else:
+                        free.append(b)
+                    ndone += 1
                 last_done = tnow
                 progressed = True
             if not progressed:
@@ -500,7 +549,23 @@ def measure_serving(sssp, G, g, torch, sources, rates, window_s=1.0, hard_s=10.0
         for tk in list(outstanding):
             sssp.sssp_server_wait(srv, tk, 120_000_000_000)
         sssp.sssp_server_drain(srv)
+        torch.cuda.synchronize()
+        if held:  # the sampled served results against single solves of their sources
+            one = torch.empty(g.n, dtype=torch.int64, device="cuda")
+            eq = 0
+            for src_, b in held:
+                if tuned:
+                    sssp.sssp_solve_tuned(G.handle, src_, one.data_ptr(), stream)
+                else:
+                    G.solve(src_, algo, prm, one, stream)
+                torch.cuda.synchronize()
+                eq += int(bool(torch.equal(bufs[b], one)))
+            del one
+            out["rates"][-1]["checked"] = len(held)
+            out["rates"][-1]["equal_to_single"] = eq
     best = max(r["queries_per_s"] for r in out["rates"])
+    out["checked"] = sum(r.get("checked", 0) for r in out["rates"])
+    out["all_equal"] = all(r.get("equal_to_single", 0) == r.get("checked", 0) for r in out["rates"])
     out["saturation_queries_per_s"] = best
     out["speedup_vs_plain"] = best / plain_qps
     out["launches"] = sssp.sssp_server_stats(srv)["launches"]
@@ -814,7 +879,7 @@ def main():
         for i in range(ns):
             oracle.dijkstra(g, srcs[i % nsrc])
         tc = time.perf_counter() - t0
-        cpu = {"value": ns * g.m / tc / 1e9, "unit": "GTEPS", "cores": 1, "kind": "oracle",
+        cpu = {"value": ns * g.m / tc / 1e9, "unit": "GTEPS", "cores": 1, "cpu_model": cpu_model(), "kind": "oracle",
                "sample": f"{ns} full single-source binary-heap Dijkstra solves of {label} "
                          f"({tc:.1f} s)"}
 

@@ -110,7 +110,20 @@ typedef struct {
                                 steps, edges and updates change (edges then counts the
                                 local relaxations too).                                  */
     uint32_t shape;          /* kernel shape, SSSP_SHAPE_*; the distances do not depend on it */
+    uint32_t rho_reduced;    /* rho-Stepping: how many dense steps (20*|Q| > n) use
+                                rho' = max(1, rho/10) instead of rho (Sec. 6, "Threshold
+                                estimation", uses the first two).  0 = 2 (the paper's
+                                count); SSSP_RHO_REDUCED_NONE = none; else the count.
+                                Other rules ignore it.                                   */
+    uint32_t small_deg;      /* degree-bin cut-off: extracted vertices of out-degree
+                                1..small_deg are relaxed as warp-flattened groups of 32,
+                                larger ones as chunk records.  0 = 32; else 8..128     */
+    uint32_t chunk;          /* edges per chunk record (a chunk never crosses a multiple
+                                of this in the edge array).  0 = 256; else 128, 256, 512
+                                or 1024.  Neither cut-off changes the distances.       */
 } sssp_options;
+
+#define SSSP_RHO_REDUCED_NONE 0xFFFFFFFFu /* sssp_options.rho_reduced: plain rho on every step */
 
 /* sssp_options.flags */
 #define SSSP_SOLVE_BIDIRECTIONAL 1u /* bidirectional relaxation (Sec. 6, "Bidirectional
@@ -119,7 +132,13 @@ typedef struct {
                                        min(delta[u], delta[v] + w) over them (WriteMin on u with
                                        the usual Update).  Needs a graph created with
                                        SSSP_GRAPH_SYMMETRIC (INVALID_ARG otherwise).  Applied to
-                                       vertices of degree > 32.                                 */
+                                       vertices relaxed as chunk records (out-degree above the
+                                       small_deg cut-off).  It pulls over u's OUT-edges as if
+                                       they were in-edges, so the distances are correct only
+                                       when every edge (u,v,w) really has its reverse (v,u,w):
+                                       on a graph declared SSSP_GRAPH_SYMMETRIC that is not
+                                       symmetric the results are wrong.  Create the graph with
+                                       SSSP_GRAPH_VERIFY as well unless symmetry is known.      */
 
 /* sssp_options.shape: thread-block shape of the persistent solve kernel.  WIDE
    keeps the most memory operations in flight (best when steps relax many
@@ -130,7 +149,10 @@ typedef struct {
 #define SSSP_SHAPE_NARROW 1u /* 512 threads per block, one block per SM            */
 
 /* sssp_graph_create_ex flags */
-#define SSSP_GRAPH_SYMMETRIC 1u     /* every edge (u,v,w) has its reverse (v,u,w)         */
+#define SSSP_GRAPH_SYMMETRIC 1u     /* every edge (u,v,w) has its reverse (v,u,w); taken
+                                       on trust unless SSSP_GRAPH_VERIFY is also given (a
+                                       false claim makes SSSP_SOLVE_BIDIRECTIONAL solves
+                                       return wrong distances)                            */
 #define SSSP_GRAPH_VERIFY 2u        /* check SSSP_GRAPH_SYMMETRIC on the host, O(m log d);
                                        INVALID_ARG when it does not hold                  */
 #define SSSP_GRAPH_REORDER 4u       /* single solves run on a relabelled device copy: new id
@@ -215,16 +237,18 @@ int sssp_last_stats(const sssp_graph* g, sssp_stats* out, void* stream);
  * App. B; the same device code the solve runs).  Reads the queue queue[0..q)
  * (device uint32 ids < n) and their keys dist[] (device uint64[n]); writes
  * theta to *theta_out (device uint64).  n is the vertex count, step the
- * 1-based step number, dense_before the number of earlier dense steps.
- * The sample count s, its cap of 4096, the sample positions (splitmix64
- * output step*2^32 + j from state `seed`, reduced by multiply-high), the
- * rank floor(rho'*s/q) and the dense-step rule (rho' = max(1, rho/10) in the
- * first two steps with 20*q > n) are those of the solve.  q <= rho' gives
- * UINT64_MAX (extract every queued vertex).  Asynchronous on `stream`.
+ * 1-based step number, dense_before the number of earlier dense steps and
+ * reduced the number of dense steps that use rho/10 (the exact count: 2 is
+ * the paper's).  The sample count s, its cap of 4096, the sample positions
+ * (splitmix64 output step*2^32 + j from state `seed`, reduced by
+ * multiply-high), the rank floor(rho'*s/q) and the dense-step rule (rho' =
+ * max(1, rho/10) when 20*q > n and dense_before < reduced) are those of the
+ * solve.  q <= rho' gives UINT64_MAX (extract every queued vertex).
+ * Asynchronous on `stream`.
  */
 int sssp_rho_threshold(const uint32_t* queue, uint32_t q, const uint64_t* dist, uint32_t n,
                        uint64_t rho, uint64_t seed, uint64_t step, uint32_t dense_before,
-                       uint64_t* theta_out, void* stream);
+                       uint32_t reduced, uint64_t* theta_out, void* stream);
 
 /* ------------------------------------------------------------------------ */
 /* Batched solves: many independent instances of the stepping loop (each its */
@@ -350,19 +374,22 @@ int sssp_server_destroy(sssp_server* s);
  * A solve that allocates nothing.  (The paper has no counterpart: this is a
  * systems entry point of this library.)  It is meant for callers that cannot
  * allocate device memory when they need a solve -- a plugin whose enqueue step
- * runs inside a framework that owns all device memory, code running while a
- * stream is captured into a CUDA graph, or a latency-critical loop that cannot
- * take the implicit device synchronisation of cudaMalloc/cudaFree.  It calls
- * no cudaMalloc, cudaFree or other allocating routine.
+ * runs inside a framework that owns all device memory through its own pool,
+ * or a latency-critical loop that cannot take the implicit device
+ * synchronisation of cudaMalloc/cudaFree.  It calls no cudaMalloc, cudaFree
+ * or other allocating routine.
  *
  * The solver's working memory is a file-scope device array of about 10.4 MB,
  * sized for SSSP_NOALLOC_MAX_VERTICES and SSSP_NOALLOC_MAX_EDGES; every GPU
  * that loads it keeps it until the process exits.  All calls on a device
- * share that array: calls that overlap on the GPU (different streams, or host
- * threads without ordering) race and give undefined results; order them.
- * The first call on a device looks up the array's device address (once per
- * device, with that device current); make that first call before any stream
- * capture begins.
+ * share that array and it keeps the last call's contents (each call clears
+ * what must start from zero): calls that overlap on the GPU (different
+ * streams, or host threads without ordering) race and give undefined results;
+ * order them.  The first call on a device does a one-time set-up with that
+ * device current: it looks up the array's device address and the launch
+ * grid, and keeps both for the life of the process; make that first call
+ * before any stream capture begins.  A cudaDeviceReset of the device discards
+ * the array, so the entry point must not be called on that device after one.
  *
  *   n, m       vertex and edge counts; n in [1, SSSP_NOALLOC_MAX_VERTICES],
  *              m <= SSSP_NOALLOC_MAX_EDGES, otherwise SSSP_ERR_INVALID_ARG
@@ -405,6 +432,9 @@ typedef struct {
     uint32_t slots;          /* batch autotuner: concurrent queries with the highest
                                 throughput (the server's slot count when its config
                                 gives none); 0 = not measured                          */
+    uint32_t rho_reduced;    /* sssp_options.rho_reduced (0 = the paper's 2)                */
+    uint32_t small_deg;      /* sssp_options.small_deg (0 = 32; single solves only)         */
+    uint32_t chunk;          /* sssp_options.chunk (0 = 256; single solves only)            */
 } sssp_tuning;
 
 /*

@@ -195,8 +195,12 @@ int sssp_graph_create_ex(uint32_t n, uint64_t m, const uint64_t* offsets, const 
         return SSSP_ERR_INVALID_ARG;
 
     // exact capacities of the relaxation records one Extract can produce:
-    // each vertex is queued at most once, so at most every vertex at once
-    uint64_t small_cap = 0, item_cap = 0;
+    // each vertex is queued at most once, so at most every vertex at once.
+    // Two sets: at the default degree-bin cut-offs (batched and serving
+    // launches) and the largest over every cut-off a single solve may take
+    // (small_deg in [kSmallDegMin, kSmallDegMax], chunks of >= 2^kChunkLog2Min
+    // edges) -- the single solve's record arrays are sized for the latter.
+    uint64_t small_cap = 0, item_cap = 0, small_any = 0, item_any = 0;
     unsigned __int128 wsum = 0;
     for (uint64_t e = 0; e < m; ++e) wsum += weights[e];
     uint64_t max_deg = 0;
@@ -206,6 +210,8 @@ int sssp_graph_create_ex(uint32_t n, uint64_t m, const uint64_t* offsets, const 
         if (deg == 0) continue;
         if (deg <= kSmallDeg) ++small_cap;
         else item_cap += chunk_count(offsets[u], offsets[u + 1]);
+        if (deg <= kSmallDegMax) ++small_any;
+        if (deg > kSmallDegMin) item_any += chunk_count(offsets[u], offsets[u + 1], kChunkLog2Min);
     }
 
     // relabelled copy for single solves (its chunk records are counted too:
@@ -214,10 +220,14 @@ int sssp_graph_create_ex(uint32_t n, uint64_t m, const uint64_t* offsets, const 
     std::vector<uint64_t> off2;
     if (flags & SSSP_GRAPH_REORDER) {
         relabel_graph(n, offsets, targets, weights, perm, iperm, off2, tgt2, w2);
-        uint64_t item_cap2 = 0;
-        for (uint32_t u = 0; u < n; ++u)
-            if (off2[u + 1] - off2[u] > kSmallDeg) item_cap2 += chunk_count(off2[u], off2[u + 1]);
+        uint64_t item_cap2 = 0, item_any2 = 0;
+        for (uint32_t u = 0; u < n; ++u) {
+            const uint64_t deg = off2[u + 1] - off2[u];
+            if (deg > kSmallDeg) item_cap2 += chunk_count(off2[u], off2[u + 1]);
+            if (deg > kSmallDegMin) item_any2 += chunk_count(off2[u], off2[u + 1], kChunkLog2Min);
+        }
         item_cap = item_cap2 > item_cap ? item_cap2 : item_cap;
+        item_any = item_any2 > item_any ? item_any2 : item_any;
     }
 
     sssp_graph* g = new (std::nothrow) sssp_graph();
@@ -237,12 +247,14 @@ int sssp_graph_create_ex(uint32_t n, uint64_t m, const uint64_t* offsets, const 
     g->mean_w = m ? (double)wsum / (double)m : 1.0;
     g->max_deg = max_deg;
     g->item_cap = item_cap + 1;
+    g->fsmall_cap_any = small_any + 1;
+    g->item_cap_any = item_any + 1;
     if ((e = dalloc(&g->d_off, (uint64_t)n + 1)) != cudaSuccess ||
         (e = dalloc(&g->d_edges, m_alloc)) != cudaSuccess ||
         (e = dalloc(&g->d_inq, ((uint64_t)n + 31) / 32)) != cudaSuccess ||
         (e = dalloc(&g->d_qa, n)) != cudaSuccess || (e = dalloc(&g->d_qb, n)) != cudaSuccess ||
-        (e = dalloc(&g->d_fsmall, g->fsmall_cap)) != cudaSuccess ||
-        (e = dalloc(&g->d_items, g->item_cap)) != cudaSuccess ||
+        (e = dalloc(&g->d_fsmall, g->fsmall_cap_any)) != cudaSuccess ||
+        (e = dalloc(&g->d_items, g->item_cap_any)) != cudaSuccess ||
         (e = dalloc(&g->d_ctrl, 1)) != cudaSuccess ||
         (e = cudaMallocHost(reinterpret_cast<void**>(&g->h_ctrl), sizeof(Ctrl))) != cudaSuccess ||
         (e = dalloc(&d_tgt, m)) != cudaSuccess || (e = dalloc(&d_w, m)) != cudaSuccess) {
@@ -319,9 +331,9 @@ int sssp_solve_ex(const sssp_graph* gc, uint32_t source, sssp_algo algo, uint64_
     p.qa = g->d_qa;
     p.qb = g->d_qb;
     p.fsmall = g->d_fsmall;
-    p.fsmall_cap = g->fsmall_cap;
+    p.fsmall_cap = g->fsmall_cap_any;
     p.items = g->d_items;
-    p.item_cap = g->item_cap;
+    p.item_cap = g->item_cap_any;
     p.ctrl = g->d_ctrl;
     p.source = source;
     p.algo = (int)algo;
@@ -340,6 +352,17 @@ int sssp_solve_ex(const sssp_graph* gc, uint32_t source, sssp_algo algo, uint64_
     p.bidir = (o.flags & SSSP_SOLVE_BIDIRECTIONAL) ? 1 : 0;
     if (o.local_budget != 0 && algo != SSSP_RHO && algo != SSSP_DELTA_STAR) return SSSP_ERR_INVALID_ARG;
     p.local_budget = o.local_budget;
+    p.rho_reduced = o.rho_reduced == 0 ? kRhoReducedDefault
+                    : o.rho_reduced == SSSP_RHO_REDUCED_NONE ? 0u : o.rho_reduced;
+    if (o.small_deg != 0 && (o.small_deg < kSmallDegMin || o.small_deg > kSmallDegMax)) return SSSP_ERR_INVALID_ARG;
+    p.small_deg = o.small_deg ? o.small_deg : kSmallDeg;
+    p.chunk_log2 = kChunkLog2;
+    if (o.chunk != 0) {
+        uint32_t lg = 0;
+        while ((1u << lg) < o.chunk && lg < 31) ++lg;
+        if ((1u << lg) != o.chunk || lg < kChunkLog2Min || lg > kChunkLog2Max) return SSSP_ERR_INVALID_ARG;
+        p.chunk_log2 = lg;
+    }
     if (g->reordered) {  // the relabelled copy; distances back in the caller's ids at the end
         p.off = g->d_off2;
         p.edges = g->d_edges2;
@@ -439,7 +462,8 @@ int sssp_solve_host_ex(const sssp_graph* gc, uint32_t source, sssp_algo algo, ui
 }
 
 int sssp_rho_threshold(const uint32_t* queue, uint32_t q, const uint64_t* dist, uint32_t n, uint64_t rho,
-                       uint64_t seed, uint64_t step, uint32_t dense_before, uint64_t* theta_out, void* stream)
+                       uint64_t seed, uint64_t step, uint32_t dense_before, uint32_t reduced, uint64_t* theta_out,
+                       void* stream)
 {
     if ((q > 0 && !queue) || !dist || !theta_out || n == 0 || rho == 0 || q > n) return SSSP_ERR_INVALID_ARG;
     static uint32_t* d_err = nullptr;
@@ -451,8 +475,8 @@ int sssp_rho_threshold(const uint32_t* queue, uint32_t q, const uint64_t* dist, 
             if (e != cudaSuccess) { d_err = nullptr; return cuda_fail(e); }
         }
     }
-    cudaError_t e = launch_rho_threshold(queue, q, dist, n, rho, seed, step, dense_before, theta_out, d_err,
-                                         reinterpret_cast<cudaStream_t>(stream));
+    cudaError_t e = launch_rho_threshold(queue, q, dist, n, rho, seed, step, dense_before, reduced, theta_out,
+                                         d_err, reinterpret_cast<cudaStream_t>(stream));
     return e == cudaSuccess ? SSSP_OK : cuda_fail(e);
 }
 

@@ -73,6 +73,8 @@ struct InstDesc {
     uint64_t seed;
     uint32_t bidir;          // bidirectional relaxation of chunk records (symmetric graph)
     uint32_t local_budget;   // local relaxation of super-sparse steps (0 = off)
+    uint32_t rho_reduced;    // rho-Stepping: dense steps that use rho/10 (Sec. 6)
+    uint32_t pad;
 };
 
 struct BatchCtrl {
@@ -210,8 +212,8 @@ __device__ void phase_T(const BatchParams& p, uint64_t k, BatchSmem& S, uint64_t
             const uint32_t* Qcur = (k & 1) ? D.qa : D.qb;
             const uint32_t dense_seen = ldcg32(&C->dense_seen);
             const uint64_t lstep = k - ldcg64((const uint64_t*)&C->admit_step) + 1;  // the instance's own step
-            theta = rho_extdist_block(Qcur, q, D.dist, D.n, D.param, D.seed, lstep, dense_seen, s_keys,
-                                      p.sample_cap, &S.err);
+            theta = rho_extdist_block(Qcur, q, D.dist, D.n, D.param, D.seed, lstep, dense_seen, D.rho_reduced,
+                                      s_keys, p.sample_cap, &S.err);
             if (tid == 0 && (uint64_t)q * 20ull > (uint64_t)D.n) C->dense_seen = dense_seen + 1;
         }
         if (tid == 0) C->theta = theta;
@@ -497,12 +499,13 @@ __device__ void phase_R(const BatchParams& p, uint64_t k, BatchSmem& S, uint32_t
                 uint64_t* const idist = Dp->dist;
                 const uint4 rc = __ldcg(&Dp->items[it - S.pre1[i]]);
                 const uint64_t du = ldcg64(&idist[rc.z]);
+                uint32_t* const Qn_i = (k & 1) ? Dp->qb : Dp->qa;
                 if (Dp->bidir)
                     relax_chunk<true>(rc, du, reinterpret_cast<const uint4*>(Dp->edges), idist, Dp->inq, stage,
-                                      stc, lane, lmin, lupd);
+                                      stc, lane, lmin, lupd, &p.ictrl[i].qsize[nx], status, Qn_i, Dp->n);
                 else
                     relax_chunk<false>(rc, du, reinterpret_cast<const uint4*>(Dp->edges), idist, Dp->inq, stage,
-                                       stc, lane, lmin, lupd);
+                                       stc, lane, lmin, lupd, &p.ictrl[i].qsize[nx], status, Qn_i, Dp->n);
                 if (stc > (uint32_t)(kStage - 256)) {
                     uint32_t* Qn = (k & 1) ? Dp->qb : Dp->qa;
                     stage_flush(stage, stc, lane, &p.ictrl[i].qsize[nx], status, Qn, Dp->n);
@@ -859,7 +862,10 @@ void batch_extras(const sssp_graph* g, sssp_algo algo, InstDesc* d)
     sssp_tuning t;
     d->bidir = 0;
     d->local_budget = 0;
+    d->rho_reduced = kRhoReducedDefault;
     if (sssp_lookup_batch_tuning(g, &t) && t.algo == algo) {
+        d->rho_reduced = t.rho_reduced == 0 ? kRhoReducedDefault
+                         : t.rho_reduced == SSSP_RHO_REDUCED_NONE ? 0u : t.rho_reduced;
         d->bidir = ((t.flags & SSSP_SOLVE_BIDIRECTIONAL) && (g->flags & SSSP_GRAPH_SYMMETRIC)) ? 1u : 0u;
         if ((algo == SSSP_RHO || algo == SSSP_DELTA_STAR) && g->n >= kBatchLocalMinN) d->local_budget = t.local_budget;
     }

@@ -203,16 +203,17 @@ __device__ __forceinline__ uint64_t block_reduce_min64(uint64_t x, uint64_t* s_t
 // ExtDist of rho-Stepping (Table 2; Sec. 6 "Threshold estimation"; App. B).
 //
 // Sample count s, rank r and the effective rho' of a step with q queued ids:
-// rho' = max(1, rho/10) in the first two dense steps (20 q > n), else rho;
-// s = min(4096, 10 (ceil(q/rho') + 1 + floor(log2(q+1)))); r = min(s-1,
-// floor(rho' s / q)); theta is the r-th smallest (0-based) of the s sampled
-// keys.  Returns false when q <= rho' (theta = +inf: extract every queued id).
+// rho' = max(1, rho/10) in the first `reduced` dense steps (20 q > n; the
+// paper uses the first two), else rho; s = min(4096, 10 (ceil(q/rho') + 1 +
+// floor(log2(q+1)))); r = min(s-1, floor(rho' s / q)); theta is the r-th
+// smallest (0-based) of the s sampled keys.  Returns false when q <= rho'
+// (theta = +inf: extract every queued id).
 // ---------------------------------------------------------------------------
 __device__ __forceinline__ bool rho_sample_plan(uint32_t q, uint32_t n, uint64_t rho, uint32_t dense_before,
-                                                uint32_t* s_out, uint32_t* r_out)
+                                                uint32_t reduced, uint32_t* s_out, uint32_t* r_out)
 {
     uint64_t rho_eff = rho;
-    if ((uint64_t)q * 20ull > (uint64_t)n && dense_before < 2) {
+    if ((uint64_t)q * 20ull > (uint64_t)n && dense_before < reduced) {
         rho_eff = rho / 10ull;
         if (rho_eff < 1) rho_eff = 1;
     }
@@ -297,10 +298,10 @@ __device__ __forceinline__ uint64_t block_select(uint64_t x, uint32_t s, uint32_
 // point; the solve kernel runs the same steps with its Extract loads in flight).
 static __device__ __noinline__ uint64_t rho_extdist_block(const uint32_t* Q, uint32_t q, const uint64_t* dist, uint32_t n,
                                       uint64_t rho, uint64_t seed, uint64_t step, uint32_t dense_before,
-                                      uint64_t* skeys, uint32_t cap, int* err)
+                                      uint32_t reduced, uint64_t* skeys, uint32_t cap, int* err)
 {
     uint32_t s, r;
-    if (!rho_sample_plan(q, n, rho, dense_before, &s, &r)) return kInf;  // extract every queued vertex
+    if (!rho_sample_plan(q, n, rho, dense_before, reduced, &s, &r)) return kInf;  // extract every queued vertex
     uint64_t x = kInf;
     if (s <= blockDim.x) {
         if (threadIdx.x < s) x = ldcg64(&dist[ldcg32(&Q[rho_sample_pos(seed, step, threadIdx.x, q)])]);
@@ -400,23 +401,27 @@ __device__ __forceinline__ void stage_flush(uint32_t* stage, uint32_t& stc, uint
     stc = 0;
 }
 
-// Warp-uniform: relax the edges of one chunk record (<= kChunk edges of vertex
-// u, within one kChunk-aligned block of the edge array), read as 16-byte pairs
-// of packed edges.  With kPull (bidirectional relaxation for undirected
+// Warp-uniform: relax the edges of one chunk record (at most 2^kChunkLog2Max
+// edges of vertex u, within one aligned block of the edge array whose length
+// is even), read as 16-byte pairs of packed edges.  With kPull (bidirectional relaxation for undirected
 // graphs, Sec. 6): the delta[v] values gathered for the pre-check first relax
 // u itself -- WriteMin(delta[u], min over the chunk of delta[v] + w), with the
 // usual Update(u) -- and the improved delta[u] is then pushed to the chunk's
 // neighbours.
+// Each 64-pair round stages at most 129 ids (128 targets and u itself), so the
+// warp's staging buffer is flushed to the next queue list (qsize, Qnext of
+// capacity qcap) before a round that might not fit.
 template <bool kPull, bool kL1 = false>
 __device__ __forceinline__ void relax_chunk(uint4 rec, uint64_t du, const uint4* __restrict__ pairs,
                                             uint64_t* dist, uint32_t* inq, uint32_t* stage, uint32_t& stc,
-                                            uint32_t lane, uint64_t& lmin, uint32_t& lupd)
+                                            uint32_t lane, uint64_t& lmin, uint32_t& lupd, unsigned int* qsize,
+                                            int* status, uint32_t* Qnext, uint32_t qcap)
 {
     const uint64_t cs = rec_start(rec), ce = cs + rec_len(rec);
     const uint64_t p0 = cs >> 1, p1 = (ce + 1) >> 1;
 #pragma unroll 1
-    for (uint32_t h = 0; h < kChunkPairs; h += 64) {
-        if (p0 + h >= p1) break;  // warp-uniform
+    for (uint32_t h = 0; p0 + h < p1; h += 64) {  // warp-uniform
+        if (stc > (uint32_t)kStage - 129u) stage_flush(stage, stc, lane, qsize, status, Qnext, qcap);
         uint32_t vv[4], ww[4];
         bool ok[4];
 #pragma unroll

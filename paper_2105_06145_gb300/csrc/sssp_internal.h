@@ -26,10 +26,15 @@ constexpr int kWarps = kBlock / 32;
 #ifndef SSSP_EXTRACT_ITEMS
 #define SSSP_EXTRACT_ITEMS 4
 #endif
-constexpr uint32_t kSmallDeg = SSSP_SMALL_DEG;  // degree <= this: warp-flattened relaxation groups
+constexpr uint32_t kSmallDeg = SSSP_SMALL_DEG;  // default cut-off: degree <= this -> warp-flattened groups
 constexpr int kSmallRounds = 4;             // 32-edge rounds per batch in the flattened path
-constexpr uint32_t kChunk = 256;            // edges per relaxation chunk item (even)
-constexpr uint32_t kChunkPairs = kChunk / 2;  // 16-byte edge pairs per chunk
+constexpr uint32_t kChunk = 256;            // default edges per relaxation chunk record (even)
+constexpr uint32_t kChunkLog2 = 8;
+// Range of the single solve's runtime degree-bin cut-offs (sssp_options
+// small_deg / chunk); the batched kernels use the defaults above.
+constexpr uint32_t kSmallDegMin = 8, kSmallDegMax = 128;
+constexpr uint32_t kChunkLog2Min = 7, kChunkLog2Max = 10;   // 128 .. 1024 edges
+constexpr uint32_t kRhoReducedDefault = 2;  // dense steps with rho/10 (Sec. 6)
 constexpr int kExtractItems = SSSP_EXTRACT_ITEMS;  // batched kernels: queue entries per thread per extract tile
 constexpr int kStage = 512;                 // per-warp staging slots for re-queued ids
 constexpr uint32_t kMaxSamples = 4096;      // cap on the rho sampler's sample count
@@ -109,6 +114,9 @@ struct SolveParams {
     sssp_stats* stats_out;        // optional device copy of the totals
     int bidir;                    // bidirectional relaxation of chunk records (symmetric graphs)
     uint32_t local_budget;        // local relaxation of super-sparse steps: vertices per warp and step (0 = off)
+    uint32_t rho_reduced;         // rho-Stepping: dense steps that use rho/10
+    uint32_t small_deg;           // degree-bin cut-off: 1..small_deg -> low-degree records
+    uint32_t chunk_log2;          // chunk records cover at most 2^chunk_log2 edges (aligned)
     // relabelled graph (SSSP_GRAPH_REORDER): the solve runs on the relabelled
     // copy with dist = internal distances in the new ids; at the end
     // dist_out[v] = dist[perm[v]] for every caller id v; ext_count is indexed
@@ -118,8 +126,11 @@ struct SolveParams {
     uint64_t* dist_out;
 };
 
-// Chunk records of one vertex: its edge range [b, e) cut at multiples of kChunk.
-inline uint64_t chunk_count(uint64_t b, uint64_t e) { return e > b ? (e - 1) / kChunk - b / kChunk + 1 : 0; }
+// Chunk records of one vertex: its edge range [b, e) cut at multiples of 2^lg.
+inline uint64_t chunk_count(uint64_t b, uint64_t e, uint32_t lg = kChunkLog2)
+{
+    return e > b ? ((e - 1) >> lg) - (b >> lg) + 1 : 0;
+}
 
 // Upper bound on chunk records of one Extract when only n and m are known:
 // each vertex of degree > kSmallDeg yields at most deg/kChunk + 2 records and
@@ -139,8 +150,8 @@ int solve_kernel_threads();             // threads per block of this build of th
 unsigned int solve_kernel_smem();       // its dynamic shared memory per block
 cudaError_t launch_rho_threshold(const uint32_t* queue, uint32_t q, const uint64_t* dist,
                                  uint32_t n, uint64_t rho, uint64_t seed, uint64_t step,
-                                 uint32_t dense_before, uint64_t* theta_out, uint32_t* err_out,
-                                 cudaStream_t st);
+                                 uint32_t dense_before, uint32_t reduced, uint64_t* theta_out,
+                                 uint32_t* err_out, cudaStream_t st);
 uint32_t rho_sample_bound(uint32_t n, uint64_t rho);   // power-of-two smem keys needed
 
 // Batched solves (sssp_batch.cu).
@@ -171,9 +182,11 @@ struct sssp_graph {
     uint32_t* d_qa = nullptr;
     uint32_t* d_qb = nullptr;
     uint4* d_fsmall = nullptr;
-    uint64_t fsmall_cap = 0;
+    uint64_t fsmall_cap = 0;               // records of one Extract at the default cut-offs
     uint4* d_items = nullptr;
     uint64_t item_cap = 0;
+    uint64_t fsmall_cap_any = 0;           // ... at any allowed cut-offs (single-solve scratch)
+    uint64_t item_cap_any = 0;
     sssp::Ctrl* d_ctrl = nullptr;
     uint64_t* d_dist_internal = nullptr;   // lazily allocated for sssp_solve_host
     // SSSP_GRAPH_REORDER: relabelled copy for single solves (new id = rank by

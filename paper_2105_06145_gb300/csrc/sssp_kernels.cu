@@ -184,7 +184,7 @@ __global__ void __launch_bounds__(kBlock, kMinBlocks) solve_kernel(SolveParams p
             // rho-Stepping: theta is selected from s sampled keys in the first
             // Extract round below, with that round's loads in flight
             theta = kInf;
-            rho_sample = rho_sample_plan(q, n, p.param, dense_seen, &s_cnt, &r_idx);
+            rho_sample = rho_sample_plan(q, n, p.param, dense_seen, p.rho_reduced, &s_cnt, &r_idx);
             if ((uint64_t)q * 20ull > (uint64_t)n) ++dense_seen;
         }
 
@@ -201,9 +201,11 @@ __global__ void __launch_bounds__(kBlock, kMinBlocks) solve_kernel(SolveParams p
         // read; (3) one block scan and one atomic per output list reserve the
         // block's output ranges; (4) the staged records are written out.
         // Kept ids -> next queue list; extracted ids -> relaxation records
-        // (degree <= kSmallDeg: one record in fsmall; larger: one record per
-        // kChunk-aligned run of its edges in items).
+        // (degree <= small_deg: one record in fsmall; larger: one record per
+        // 2^chunk_log2-aligned run of its edges in items).
         {
+            const uint32_t small_deg = p.small_deg, cl = p.chunk_log2;
+            const uint64_t chunk = 1ull << cl;
             uint4* s_rec = reinterpret_cast<uint4*>(s_dyn);                      // [kExtractCap]
             uint8_t* s_kind = s_dyn + (size_t)kExtractCap * sizeof(uint4);      // [kExtractCap]
             enum : uint8_t { kNone = 0, kKeep = 1, kSmall = 2, kChunked = 3, kNoEdges = 4 };
@@ -287,7 +289,7 @@ __global__ void __launch_bounds__(kBlock, kMinBlocks) solve_kernel(SolveParams p
                         if (p.ext_count) p.ext_count[p.iperm ? p.iperm[r.x] : r.x] += 1u;
                         if (deg == 0) {
                             s_kind[i] = kNoEdges;
-                        } else if (deg <= kSmallDeg) {
+                        } else if (deg <= small_deg) {
                             s_kind[i] = kSmall;
                             s_rec[i] = make_rec(b[j], deg, (uint64_t)r.y | ((uint64_t)r.z << 32));
                             ++nsmall;
@@ -295,7 +297,7 @@ __global__ void __launch_bounds__(kBlock, kMinBlocks) solve_kernel(SolveParams p
                             s_kind[i] = kChunked;
                             s_rec[i] = make_uint4(r.x, (uint32_t)b[j], (uint32_t)(b[j] >> 32),
                                                   deg < 0xFFFFFFFFull ? (uint32_t)deg : 0xFFFFFFFFu);
-                            nchunks += (uint32_t)((e[j] - 1) / kChunk - b[j] / kChunk + 1);
+                            nchunks += (uint32_t)(((e[j] - 1) >> cl) - (b[j] >> cl) + 1);
                         }
                     }
                 }
@@ -329,7 +331,7 @@ __global__ void __launch_bounds__(kBlock, kMinBlocks) solve_kernel(SolveParams p
                         bj = (uint64_t)r.y | ((uint64_t)r.z << 32);
                         ej = r.w != 0xFFFFFFFFu ? bj + r.w : __ldg(&off[r.x + 1]);
                     }
-                    const uint64_t nch = kd == kChunked ? (ej - 1) / kChunk - bj / kChunk + 1 : 0;
+                    const uint64_t nch = kd == kChunked ? ((ej - 1) >> cl) - (bj >> cl) + 1 : 0;
                     if (kd == kKeep) {
                         if (pk < n) Qnext[pk] = r.x;
                         ++pk;
@@ -337,9 +339,9 @@ __global__ void __launch_bounds__(kBlock, kMinBlocks) solve_kernel(SolveParams p
                         if (ps < p.fsmall_cap) p.fsmall[ps] = r;
                         ++ps;
                     } else if (kd == kChunked && nch <= 4) {
-                        for (uint64_t c0 = bj / kChunk * kChunk; c0 < ej; c0 += kChunk, ++pc) {
+                        for (uint64_t c0 = (bj >> cl) << cl; c0 < ej; c0 += chunk, ++pc) {
                             const uint64_t cs = bj > c0 ? bj : c0;
-                            const uint64_t ce = ej < c0 + kChunk ? ej : c0 + kChunk;
+                            const uint64_t ce = ej < c0 + chunk ? ej : c0 + chunk;
                             if (pc < p.item_cap) p.items[pc] = make_rec(cs, ce - cs, r.x);
                         }
                     }
@@ -352,11 +354,11 @@ __global__ void __launch_bounds__(kBlock, kMinBlocks) solve_kernel(SolveParams p
                         const uint64_t se = __shfl_sync(FULL_MASK, ej, src);
                         const uint32_t sv = __shfl_sync(FULL_MASK, r.x, src);
                         const uint64_t sp = __shfl_sync(FULL_MASK, pc, src);
-                        const uint64_t sn = (se - 1) / kChunk - sb / kChunk + 1;
+                        const uint64_t sn = ((se - 1) >> cl) - (sb >> cl) + 1;
                         for (uint64_t t = lane; t < sn; t += 32) {
-                            const uint64_t c0 = (sb / kChunk + t) * kChunk;
+                            const uint64_t c0 = ((sb >> cl) + t) << cl;
                             const uint64_t cs = sb > c0 ? sb : c0;
-                            const uint64_t ce = se < c0 + kChunk ? se : c0 + kChunk;
+                            const uint64_t ce = se < c0 + chunk ? se : c0 + chunk;
                             if (sp + t < p.item_cap) p.items[sp + t] = make_rec(cs, ce - cs, sv);
                         }
                     }
@@ -420,9 +422,11 @@ __global__ void __launch_bounds__(kBlock, kMinBlocks) solve_kernel(SolveParams p
                     rn = nit < fc ? __ldcg(&p.items[nit]) : make_uint4(0, 0, 0, 0);
                     const uint64_t du = ldcg64(&dist[rc.z]);
                     if (p.bidir)
-                        relax_chunk<true, true>(rc, du, pairs, dist, inq, stage, stc, lane, lmin, lupd);
+                        relax_chunk<true, true>(rc, du, pairs, dist, inq, stage, stc, lane, lmin, lupd,
+                                                &ctrl->qsize[nx], &ctrl->status, Qnext, n);
                     else
-                        relax_chunk<false, true>(rc, du, pairs, dist, inq, stage, stc, lane, lmin, lupd);
+                        relax_chunk<false, true>(rc, du, pairs, dist, inq, stage, stc, lane, lmin, lupd,
+                                                 &ctrl->qsize[nx], &ctrl->status, Qnext, n);
                     if (stc > (uint32_t)(kStage - 256)) stage_flush(stage, stc, lane, &ctrl->qsize[nx], &ctrl->status, Qnext, n);
                 }
             }
@@ -526,14 +530,15 @@ cudaError_t launch_pack_edges(const uint32_t* tgt, const uint32_t* w, uint2* edg
 __global__ void __launch_bounds__(kBlock) rho_threshold_kernel(const uint32_t* queue, uint32_t q,
                                                                const uint64_t* dist, uint32_t n,
                                                                uint64_t rho, uint64_t seed, uint64_t step,
-                                                               uint32_t dense_before, uint64_t* theta_out,
-                                                               uint32_t* err_out, uint32_t cap)
+                                                               uint32_t dense_before, uint32_t reduced,
+                                                               uint64_t* theta_out, uint32_t* err_out, uint32_t cap)
 {
     extern __shared__ uint64_t s_keys[];
     __shared__ int s_e;
     if (threadIdx.x == 0) s_e = 0;
     __syncthreads();
-    const uint64_t th = rho_extdist_block(queue, q, dist, n, rho, seed, step, dense_before, s_keys, cap, &s_e);
+    const uint64_t th = rho_extdist_block(queue, q, dist, n, rho, seed, step, dense_before, reduced, s_keys, cap,
+                                          &s_e);
     __syncthreads();
     if (threadIdx.x == 0) {
         *theta_out = th;
@@ -556,7 +561,7 @@ uint32_t rho_sample_bound(uint32_t n, uint64_t rho)
 
 cudaError_t launch_rho_threshold(const uint32_t* queue, uint32_t q, const uint64_t* dist, uint32_t n,
                                  uint64_t rho, uint64_t seed, uint64_t step, uint32_t dense_before,
-                                 uint64_t* theta_out, uint32_t* err_out, cudaStream_t st)
+                                 uint32_t reduced, uint64_t* theta_out, uint32_t* err_out, cudaStream_t st)
 {
     const uint32_t cap = kMaxSamples;
     static bool attr_set = false;
@@ -567,7 +572,8 @@ cudaError_t launch_rho_threshold(const uint32_t* queue, uint32_t q, const uint64
         attr_set = true;
     }
     rho_threshold_kernel<<<1, kBlock, cap * sizeof(uint64_t), st>>>(queue, q, dist, n, rho, seed, step,
-                                                                    dense_before, theta_out, err_out, cap);
+                                                                    dense_before, reduced, theta_out, err_out,
+                                                                    cap);
     return cudaGetLastError();
 }
 

@@ -2,9 +2,8 @@
 //
 // Some callers cannot allocate device memory at the moment they need a
 // solve: a plugin whose enqueue step runs inside a framework that owns all
-// device memory through its own pool, code that runs while a stream is being
-// captured into a CUDA graph, or a latency-critical loop that cannot afford
-// the implicit device synchronisation of cudaMalloc/cudaFree.
+// device memory through its own pool, or a latency-critical loop that cannot
+// afford the implicit device synchronisation of cudaMalloc/cudaFree.
 // sssp_solve_noalloc serves them: the caller passes the graph, already in
 // device memory, and the output buffer; the solver's working memory (queue
 // bitmap, queue lists, extraction lists, control block) comes from the
@@ -51,11 +50,14 @@ static __device__ __align__(256) unsigned char g_noalloc_scratch[kScratchBytes];
 constexpr int kMaxDevices = 64;
 std::mutex g_setup_mu;
 void* g_scratch_addr[kMaxDevices] = {};
-int g_num_sms[kMaxDevices] = {};
+uint32_t g_grid[kMaxDevices] = {};
 
 // Once per device, with that device current: the device address of the
-// scratch array (its host-side name is only a stand-in) and the SM count.
-int setup_device(int dev, unsigned char** scratch, int* num_sms)
+// scratch array (its host-side name is only a stand-in, not a device
+// address) and the cooperative grid of the solve kernel (blocks per SM x SMs,
+// with the kernel's shared-memory attribute set).  Later calls reuse both, so
+// a call does no host-side set-up work.
+int setup_device(int dev, unsigned char** scratch, uint32_t* grid)
 {
     if (dev < 0 || dev >= kMaxDevices) return SSSP_ERR_CUDA;
     std::lock_guard<std::mutex> lk(g_setup_mu);
@@ -66,11 +68,17 @@ int setup_device(int dev, unsigned char** scratch, int* num_sms)
         int sms = 0;
         e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
         if (e != cudaSuccess || sms <= 0) return SSSP_ERR_CUDA;
+        const void* fn = solve_kernel_ptr();
+        e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSolveDynSmem);
+        if (e != cudaSuccess) return SSSP_ERR_CUDA;
+        int bps = 0;
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, fn, kBlock, kSolveDynSmem);
+        if (e != cudaSuccess || bps < 1) return SSSP_ERR_CUDA;
+        g_grid[dev] = (uint32_t)(bps * sms);
         g_scratch_addr[dev] = ptr;
-        g_num_sms[dev] = sms;
     }
     *scratch = static_cast<unsigned char*>(g_scratch_addr[dev]);
-    *num_sms = g_num_sms[dev];
+    *grid = g_grid[dev];
     return SSSP_OK;
 }
 
@@ -90,8 +98,8 @@ extern "C" int sssp_solve_noalloc(uint32_t n, uint64_t m, const uint64_t* offset
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess) return SSSP_ERR_CUDA;
     unsigned char* base = nullptr;
-    int num_sms = 0;
-    int rc = setup_device(dev, &base, &num_sms);
+    uint32_t grid = 0;
+    int rc = setup_device(dev, &base, &grid);
     if (rc != SSSP_OK) return rc;
 
     SolveParams p;
@@ -117,20 +125,14 @@ extern "C" int sssp_solve_noalloc(uint32_t n, uint64_t m, const uint64_t* offset
     p.solve_timeout_ns = 60000000000ull;
     p.stats_out = stats_out;
     p.sample_cap = (algo == SSSP_RHO) ? rho_sample_bound(n, param) : 0;
-
-    const void* fn = solve_kernel_ptr();
-    cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSolveDynSmem);
-    if (e != cudaSuccess) return SSSP_ERR_CUDA;
-    const size_t dyn_smem = kSolveDynSmem;
-    int bps = 0;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, fn, kBlock, dyn_smem);
-    if (e != cudaSuccess || bps < 1) return SSSP_ERR_CUDA;
-    const uint32_t grid = (uint32_t)(bps * num_sms);
+    p.rho_reduced = kRhoReducedDefault;
+    p.small_deg = kSmallDeg;
+    p.chunk_log2 = kChunkLog2;
 
     cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
-    e = cudaMemsetAsync(p.ctrl, 0, sizeof(Ctrl), st);  // the control block must start at zero
+    cudaError_t e = cudaMemsetAsync(p.ctrl, 0, sizeof(Ctrl), st);  // the control block must start at zero
     if (e != cudaSuccess) return SSSP_ERR_CUDA;
     void* args[] = {&p};
-    e = cudaLaunchCooperativeKernel(fn, dim3(grid), dim3(kBlock), args, dyn_smem, st);
+    e = cudaLaunchCooperativeKernel(solve_kernel_ptr(), dim3(grid), dim3(kBlock), args, kSolveDynSmem, st);
     return e == cudaSuccess ? SSSP_OK : SSSP_ERR_CUDA;
 }

@@ -16,7 +16,11 @@
 //   2. the two fastest of (1) in both shapes, on up to two sources;
 //   3. sparse graphs (mean out-degree < 20): the two fastest of (1) of each
 //      rule, in the winning shape, with local budgets 64, 256 and 1024;
-//   4. the winner on every sample source (sssp_tuning.ms).
+//   4. rho-Stepping winner: the number of dense steps that use rho/10 (the
+//      paper's 2, then 4, 6, 8 and none);
+//   5. the degree-bin cut-offs: small-degree bound 16 and 64 (default 32),
+//      then chunk records of 128 and 512 edges (default 256);
+//   6. the winner on every sample source (sssp_tuning.ms).
 // The result is kept on the graph handle and in a per-class table (graph class
 // = size, mean degree, degree skew and symmetry; sssp_graph_class), which
 // sssp_solve_tuned and the batched and serving calls consult for graphs that
@@ -51,6 +55,9 @@ struct Candidate {
     uint32_t shape;
     uint32_t local;
     double ms;
+    uint32_t rho_reduced;   // sssp_options encoding (0 = the paper's 2)
+    uint32_t small_deg;     // 0 = default
+    uint32_t chunk;         // 0 = default
 };
 
 // Mean time of one solve per source (ms); a failed solve is reported as rc.
@@ -62,6 +69,9 @@ int time_config(const sssp_graph* g, const Candidate& c, const uint32_t* srcs, u
     o.flags = (g->flags & SSSP_GRAPH_SYMMETRIC) ? SSSP_SOLVE_BIDIRECTIONAL : 0u;
     o.shape = c.shape;
     o.local_budget = c.local;
+    o.rho_reduced = c.rho_reduced;
+    o.small_deg = c.small_deg;
+    o.chunk = c.chunk;
     double total = 0;
     for (uint32_t i = 0; i < ns; ++i) {
         cudaError_t e = cudaEventRecord(e0, st);
@@ -162,7 +172,7 @@ int sssp_autotune_ex(sssp_graph* g, const uint32_t* sources, uint32_t k, uint32_
     }
     int rc = SSSP_OK;
     uint32_t timed = 0;
-    Candidate best{SSSP_RHO, 0, SSSP_SHAPE_WIDE, 0, 0};
+    Candidate best{SSSP_RHO, 0, SSSP_SHAPE_WIDE, 0, 0, 0, 0, 0};
     do {
         // rule / parameter candidates: rho = n/4 ... n/1024 (>= 64), Delta =
         // mean weight x {1/8, 1/2, 2, 8}
@@ -172,12 +182,12 @@ int sssp_autotune_ex(sssp_graph* g, const uint32_t* sources, uint32_t k, uint32_
             if (rho < 64) rho = 64;
             bool dup = false;
             for (const Candidate& c : cand) dup = dup || (c.algo == SSSP_RHO && c.param == rho);
-            if (!dup) cand.push_back({SSSP_RHO, rho, SSSP_SHAPE_WIDE, 0, 0});
+            if (!dup) cand.push_back({SSSP_RHO, rho, SSSP_SHAPE_WIDE, 0, 0, 0, 0, 0});
         }
         for (double f : {0.125, 0.5, 2.0, 8.0}) {
             if (!(rules & (1u << SSSP_DELTA_STAR))) break;
             const double d = g->mean_w * f;
-            cand.push_back({SSSP_DELTA_STAR, d > 1.0 ? (uint64_t)d : 1ull, SSSP_SHAPE_WIDE, 0, 0});
+            cand.push_back({SSSP_DELTA_STAR, d > 1.0 ? (uint64_t)d : 1ull, SSSP_SHAPE_WIDE, 0, 0, 0, 0, 0});
         }
         // one warm-up solve (first launch of the kernel, lazy allocations)
         double ignore;
@@ -225,7 +235,40 @@ int sssp_autotune_ex(sssp_graph* g, const uint32_t* sources, uint32_t k, uint32_
                 }
             if (rc != SSSP_OK) break;
         }
-        // (4)
+        // (4) rho-Stepping: how many dense steps use rho/10 (Sec. 6 uses two)
+        if (best.algo == SSSP_RHO) {
+            const Candidate base = best;
+            for (uint32_t red : {4u, 6u, 8u, (uint32_t)SSSP_RHO_REDUCED_NONE}) {
+                Candidate c = base;
+                c.rho_reduced = red;
+                if ((rc = time_config(g, c, sources, ns2, dist, st, e0, e1, &c.ms)) != SSSP_OK) break;
+                ++timed;
+                if (c.ms < best.ms) best = c;
+            }
+            if (rc != SSSP_OK) break;
+        }
+        // (5) degree-bin cut-offs: the small-degree bound, then the chunk length
+        {
+            Candidate base = best;
+            for (uint32_t sd : {16u, 64u}) {
+                Candidate c = base;
+                c.small_deg = sd;
+                if ((rc = time_config(g, c, sources, ns2, dist, st, e0, e1, &c.ms)) != SSSP_OK) break;
+                ++timed;
+                if (c.ms < best.ms) best = c;
+            }
+            if (rc != SSSP_OK) break;
+            base = best;
+            for (uint32_t ch : {128u, 512u}) {
+                Candidate c = base;
+                c.chunk = ch;
+                if ((rc = time_config(g, c, sources, ns2, dist, st, e0, e1, &c.ms)) != SSSP_OK) break;
+                ++timed;
+                if (c.ms < best.ms) best = c;
+            }
+            if (rc != SSSP_OK) break;
+        }
+        // (6)
         if ((rc = time_config(g, best, sources, k, dist, st, e0, e1, &best.ms)) != SSSP_OK) break;
     } while (false);
     cudaEventDestroy(e0);
@@ -241,6 +284,9 @@ int sssp_autotune_ex(sssp_graph* g, const uint32_t* sources, uint32_t k, uint32_
     t.local_budget = best.local;
     t.ms = best.ms;
     t.candidates = timed;
+    t.rho_reduced = best.rho_reduced;
+    t.small_deg = best.small_deg;
+    t.chunk = best.chunk;
     {
         std::lock_guard<std::mutex> lk(g->mu);
         g->tuning = t;
@@ -260,7 +306,9 @@ int sssp_autotune_ex(sssp_graph* g, const uint32_t* sources, uint32_t k, uint32_
 // timed as one sssp_solve_sources launch over up to 8 of the sources (with the
 // local budget the batch would use); the two best of each rule re-timed on all
 // k sources; then local budgets 0, 64 and 256 for the winner (all k sources)
-// on graphs where batched launches use local relaxation.  The result is kept as the graph's batch tuning,
+// on graphs where batched launches use local relaxation, and for a
+// rho-Stepping winner 4, 6 or no dense steps with rho/10 (the paper's 2 is the
+// starting point).  The result is kept as the graph's batch tuning,
 // which the batched and serving calls prefer.
 int sssp_autotune_batch(sssp_graph* g, const uint32_t* sources, uint32_t k, uint32_t rules, sssp_tuning* out,
                         void* stream)
@@ -362,6 +410,16 @@ int sssp_autotune_batch(sssp_graph* g, const uint32_t* sources, uint32_t k, uint
             if (ms < best_ms) { best_ms = ms; best = t; }
         }
     }
+    if (rc == SSSP_OK && best.algo == SSSP_RHO) {  // dense steps with rho/10 (Sec. 6 uses two)
+        const sssp_tuning base = best;
+        for (uint32_t red : {4u, 6u, (uint32_t)SSSP_RHO_REDUCED_NONE}) {
+            sssp_tuning t = base;
+            t.rho_reduced = red;
+            if ((rc = time_batch(t, &ms)) != SSSP_OK) break;
+            ++timed;
+            if (ms < best_ms) { best_ms = ms; best = t; }
+        }
+    }
     if (rc == SSSP_OK) rc = time_batch(best, &best_ms);
     // throughput of the winner with fewer concurrent sources: on a graph where
     // one solve already keeps the device busy, fewer queries at once are faster
@@ -407,6 +465,10 @@ int sssp_graph_set_tuning(sssp_graph* g, const sssp_tuning* t)
     if (t->shape > SSSP_SHAPE_NARROW || (t->flags & ~SSSP_SOLVE_BIDIRECTIONAL)) return SSSP_ERR_INVALID_ARG;
     if ((t->flags & SSSP_SOLVE_BIDIRECTIONAL) && !(g->flags & SSSP_GRAPH_SYMMETRIC)) return SSSP_ERR_INVALID_ARG;
     if (t->local_budget != 0 && t->algo == SSSP_BELLMAN_FORD) return SSSP_ERR_INVALID_ARG;
+    if (t->small_deg != 0 && (t->small_deg < sssp::kSmallDegMin || t->small_deg > sssp::kSmallDegMax))
+        return SSSP_ERR_INVALID_ARG;
+    if (t->chunk != 0 && t->chunk != 128 && t->chunk != 256 && t->chunk != 512 && t->chunk != 1024)
+        return SSSP_ERR_INVALID_ARG;
     std::lock_guard<std::mutex> lk(g->mu);
     g->tuning = *t;
     g->tuned = true;
@@ -429,6 +491,9 @@ int sssp_solve_tuned(const sssp_graph* g, uint32_t source, uint64_t* dist_out, v
     o.flags = t.flags;
     o.shape = t.shape;
     o.local_budget = t.local_budget;
+    o.rho_reduced = t.rho_reduced;
+    o.small_deg = t.small_deg;
+    o.chunk = t.chunk;
     return sssp_solve_ex(g, source, t.algo, t.param, dist_out, &o, stream);
 }
 

@@ -28,6 +28,7 @@ SSSP_OK = 0
 SSSP_ERR_INVALID_ARG, SSSP_ERR_OUT_OF_MEMORY, SSSP_ERR_CUDA = -1, -2, -3
 SSSP_ERR_TIMEOUT, SSSP_ERR_INTERNAL = -4, -5
 SSSP_MAX_BATCH = 2048  # instances per batched call
+SSSP_RHO_REDUCED_NONE = 0xFFFFFFFF  # sssp_options.rho_reduced: plain rho on every step
 INF = (1 << 64) - 1
 
 if not os.path.exists(LIB_PATH):
@@ -67,7 +68,8 @@ class sssp_options(ctypes.Structure):
                 ("grid_limit", ctypes.c_uint32), ("test_exit_block", ctypes.c_uint32),
                 ("stats_out", ctypes.c_void_p), ("solve_timeout_ns", ctypes.c_uint64),
                 ("flags", ctypes.c_uint32), ("local_budget", ctypes.c_uint32),
-                ("shape", ctypes.c_uint32)]
+                ("shape", ctypes.c_uint32), ("rho_reduced", ctypes.c_uint32),
+                ("small_deg", ctypes.c_uint32), ("chunk", ctypes.c_uint32)]
 
 
 TRACE_RECORD_BYTES = ctypes.sizeof(sssp_step_trace)
@@ -94,7 +96,7 @@ _lib.sssp_last_status.argtypes = [_P, _P]
 _lib.sssp_last_status.restype = _i32
 _lib.sssp_last_stats.argtypes = [_P, ctypes.POINTER(sssp_stats), _P]
 _lib.sssp_last_stats.restype = _i32
-_lib.sssp_rho_threshold.argtypes = [_P, _u32, _P, _u32, _u64, _u64, _u64, _u32, _P, _P]
+_lib.sssp_rho_threshold.argtypes = [_P, _u32, _P, _u32, _u64, _u64, _u64, _u32, _u32, _P, _P]
 _lib.sssp_rho_threshold.restype = _i32
 _lib.sssp_solve_noalloc.argtypes = [_u32, _u64, _P, _P, _u32, _i32, _u64, _P, _P, _P]
 _lib.sssp_solve_noalloc.restype = _i32
@@ -167,7 +169,8 @@ _lib.sssp_array_extract.restype = _i32
 class sssp_tuning(ctypes.Structure):
     _fields_ = [("algo", ctypes.c_int), ("shape", ctypes.c_uint32), ("param", ctypes.c_uint64),
                 ("flags", ctypes.c_uint32), ("local_budget", ctypes.c_uint32), ("ms", ctypes.c_double),
-                ("candidates", ctypes.c_uint32), ("slots", ctypes.c_uint32)]
+                ("candidates", ctypes.c_uint32), ("slots", ctypes.c_uint32),
+                ("rho_reduced", ctypes.c_uint32), ("small_deg", ctypes.c_uint32), ("chunk", ctypes.c_uint32)]
 
     def as_dict(self) -> dict:
         return {k: (float(getattr(self, k)) if k == "ms" else int(getattr(self, k))) for k, _ in self._fields_}
@@ -246,7 +249,7 @@ def make_options(seed: int = 0, timeout_ns: int = 0, max_steps: int = 0, ext_cou
                  trace_ptr: int = 0, trace_cap: int = 0, grid_limit: int = 0,
                  test_exit_block: int = 0, stats_out_ptr: int = 0,
                  solve_timeout_ns: int = 0, flags: int = 0, local_budget: int = 0,
-                 shape: int = 0) -> sssp_options:
+                 shape: int = 0, rho_reduced: int = 0, small_deg: int = 0, chunk: int = 0) -> sssp_options:
     o = sssp_options()
     o.seed, o.timeout_ns, o.max_steps = seed, timeout_ns, max_steps
     o.ext_count = ext_count_ptr or None
@@ -257,6 +260,7 @@ def make_options(seed: int = 0, timeout_ns: int = 0, max_steps: int = 0, ext_cou
     o.flags = flags
     o.local_budget = local_budget
     o.shape = shape
+    o.rho_reduced, o.small_deg, o.chunk = rho_reduced, small_deg, chunk
     return o
 
 
@@ -292,9 +296,9 @@ def sssp_last_stats(g: int, stream: int = 0) -> dict:
 
 
 def sssp_rho_threshold(queue_ptr: int, q: int, dist_ptr: int, n: int, rho: int, seed: int,
-                       step: int, dense_before: int, theta_out_ptr: int, stream: int = 0) -> int:
+                       step: int, dense_before: int, reduced: int, theta_out_ptr: int, stream: int = 0) -> int:
     return _check(_lib.sssp_rho_threshold(queue_ptr or None, q, dist_ptr, n, rho, seed, step,
-                                          dense_before, theta_out_ptr, stream or None),
+                                          dense_before, reduced, theta_out_ptr, stream or None),
                   "sssp_rho_threshold")
 
 

@@ -210,13 +210,14 @@ def test_rho_threshold_matches_oracle(lib):
         seed = int(rng.integers(0, 1 << 62))
         step = int(rng.integers(1, 1000))
         dense_before = int(trial % 4)
-        want = oracle.rho_extdist(queue, dist, n, rho, seed, step, dense_before)
+        reduced = [2, 0, 6, 3, 1][trial % 5]  # dense steps that use rho/10 (the paper's 2)
+        want = oracle.rho_extdist(queue, dist, n, rho, seed, step, dense_before, reduced)
         dq = torch.from_numpy(queue.view(np.int32).copy()).cuda() if q else torch.zeros(1, dtype=torch.int32, device="cuda")
         dd = torch.from_numpy(dist.view(np.int64).copy()).cuda()
-        lib.sssp_rho_threshold(dq.data_ptr(), q, dd.data_ptr(), n, rho, seed, step, dense_before,
+        lib.sssp_rho_threshold(dq.data_ptr(), q, dd.data_ptr(), n, rho, seed, step, dense_before, reduced,
                                out.data_ptr(), stream)
         got = int(out.cpu().numpy().view(np.uint64)[0])
-        assert got == want, (trial, n, q, rho)
+        assert got == want, (trial, n, q, rho, reduced)
 
 
 def test_timeout_is_reported_not_hung(lib):
@@ -303,4 +304,63 @@ def test_local_relaxation_of_super_sparse_steps(lib):
         rc = lib.sssp_solve_ex(G.handle, s, algo, param, dist.data_ptr(), lib.make_options(local_budget=8), 0,
                                check=False)
         assert rc == lib.SSSP_ERR_INVALID_ARG
+    G.close()
+
+
+def test_reduced_rho_count_and_degree_cutoffs(lib):
+    """The count of dense steps that use rho/10 (Sec. 6; the paper's 2) and
+    the degree-bin cut-offs (small-degree bound, chunk length) change how the
+    work is split, never the distances: every combination equals the oracle,
+    on a grid, an RMAT graph (dense steps, hubs) and a hub graph whose hubs
+    span many chunk records, with and without bidirectional relaxation."""
+    flags = lib.SSSP_GRAPH_SYMMETRIC | lib.SSSP_GRAPH_VERIFY
+    n = 60000
+    rng = np.random.default_rng(19)
+    hs, hd, hw = [], [], []
+    for h in (0, 1):
+        t = rng.integers(0, n, 5000)
+        hs += [np.full(t.size, h), t]; hd += [t, np.full(t.size, h)]
+        ww = rng.integers(1, 1 << 18, t.size); hw += [ww, ww]
+    t1, t2 = rng.integers(0, n, 4 * n), rng.integers(0, n, 4 * n)
+    ww = rng.integers(1, 1 << 18, t1.size)
+    hs += [t1, t2]; hd += [t2, t1]; hw += [ww, ww]
+    hub = gg.from_edges(n, np.concatenate(hs), np.concatenate(hd), np.concatenate(hw), name="hubs_sym")
+    for g in (gg.grid(120, 130, wseed=5), gg.rmat(15, 16, gen_seed=9, wseed=10), hub):
+        s = gg.pick_sources(g, 1, 4)[0]
+        want = oracle.dijkstra(g, s)
+        G = lib.Graph(g, flags)
+        for red in (0, lib.SSSP_RHO_REDUCED_NONE, 1, 6, 40):
+            for algo, param in ((0, 64), (0, max(64, g.n // 16))):
+                got, st = solve(lib, g, s, algo, param, opts=lib.make_options(rho_reduced=red), G=G)
+                assert st["status"] == 0 and np.array_equal(got, want), (g.name, red, algo, param)
+        for sd in (8, 16, 33, 64, 128):
+            for ch in (128, 256, 512, 1024):
+                for fl in (0, lib.SSSP_SOLVE_BIDIRECTIONAL):
+                    for algo, param, shape in ((0, 1 << 10, 0), (1, 1 << 15, 1), (2, 0, 0)):
+                        o = lib.make_options(small_deg=sd, chunk=ch, flags=fl, shape=shape)
+                        got, st = solve(lib, g, s, algo, param, opts=o, G=G)
+                        assert st["status"] == 0 and np.array_equal(got, want), (g.name, sd, ch, fl, algo)
+        G.close()
+    # out-of-range cut-offs are refused
+    g = gg.grid(8, 8)
+    G = lib.Graph(g)
+    dist = torch.empty(g.n, dtype=torch.int64, device="cuda")
+    for kw in ({"small_deg": 7}, {"small_deg": 129}, {"chunk": 64}, {"chunk": 300}, {"chunk": 2048}):
+        rc = lib.sssp_solve_ex(G.handle, 0, 0, 64, dist.data_ptr(), lib.make_options(**kw), 0, check=False)
+        assert rc == lib.SSSP_ERR_INVALID_ARG, kw
+    G.close()
+
+
+def test_reduced_rho_count_full_relabelled_graph(lib):
+    """The reduced-rho count on the degree-ordered copy (the benchmark's
+    layout) with the local relaxation: RMAT-17, every vertex compared."""
+    g = gg.rmat(17, 16, gen_seed=2, wseed=3)
+    flags = lib.SSSP_GRAPH_SYMMETRIC | lib.SSSP_GRAPH_VERIFY | lib.SSSP_GRAPH_REORDER
+    G = lib.Graph(g, flags)
+    for s in gg.pick_sources(g, 3, 4):
+        want = oracle.dijkstra(g, s)
+        for red in (2, 6, 10):
+            o = lib.make_options(rho_reduced=red, flags=lib.SSSP_SOLVE_BIDIRECTIONAL)
+            got, st = solve(lib, g, s, 0, g.n // 16, opts=o, G=G)
+            assert st["status"] == 0 and np.array_equal(got, want), (s, red)
     G.close()

@@ -1,0 +1,82 @@
+"""Serving at the sizes of the serving workload: the 4096^2 road-like grid,
+the 2M-point k-NN graph (64 Gaussian clusters, k = 10) and RMAT scale 25
+(~1.07 G directed edges), each resident on the device, with staggered queries
+through the continuous-batching server so that they overlap on the device.
+
+Every served result equals the single solve of the same source (uint64,
+element by element); on the road and k-NN graphs at least four served results
+also equal the oracle's Dijkstra, and on RMAT-25 one does (the oracle takes
+tens of seconds per RMAT-25 source on one host core; the single solve it is
+compared with is checked against the oracle at RMAT-22 by the full-size
+parity tests)."""
+import time
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_2105_06145_gb300 import graphgen as gg
+
+torch = pytest.importorskip("torch")
+pytestmark = [pytest.mark.gpu, pytest.mark.slow]
+
+
+@pytest.fixture(scope="module")
+def lib():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2105_06145_gb300 import sssp
+    return sssp
+
+
+def _serve_and_check(lib, g, flags, srcs, slots, algo, param, n_oracle, stagger_s):
+    G = lib.Graph(g, flags)
+    stream = torch.cuda.current_stream().cuda_stream
+    srv = lib.sssp_server_create(G.handle, slots=slots, algo=algo, param=param)
+    outs = [torch.full((g.n,), 9, dtype=torch.int64, device="cuda") for _ in srcs]
+    torch.cuda.synchronize()
+    tickets = []
+    for s, o in zip(srcs, outs):
+        tickets.append(lib.sssp_server_submit(srv, int(s), o.data_ptr()))
+        time.sleep(stagger_s)
+    infos = [lib.sssp_server_wait(srv, t, 600_000_000_000) for t in tickets]
+    lib.sssp_server_destroy(srv)
+    assert all(i["status"] == 0 and i["steps"] >= 1 for i in infos), infos
+    one = torch.empty(g.n, dtype=torch.int64, device="cuda")
+    for s, o in zip(srcs, outs):
+        G.solve(int(s), algo, param, one, stream)
+        assert G.status(stream) == 0
+        assert torch.equal(o, one), (g.name, s)
+    for s, o in list(zip(srcs, outs))[:n_oracle]:
+        assert np.array_equal(o.cpu().numpy().view(np.uint64), oracle.dijkstra(g, int(s))), (g.name, s)
+    # continuous batching: some query was admitted while another was running
+    iv = sorted((i["device_admit_ns"], i["device_done_ns"]) for i in infos)
+    assert any(iv[b][0] > iv[a][0] and iv[b][0] < iv[a][1] for a in range(len(iv)) for b in range(a + 1, len(iv)))
+    G.close()
+    del outs, one
+    torch.cuda.empty_cache()
+
+
+def test_serve_road4096(lib):
+    g, s0 = gg.workload_road(4096)
+    srcs = [s0] + gg.pick_sources(g, 7, 9, mask=gg.largest_cc(g))
+    _serve_and_check(lib, g, lib.SSSP_GRAPH_SYMMETRIC | lib.SSSP_GRAPH_VERIFY, srcs, slots=4,
+                     algo=lib.SSSP_DELTA_STAR, param=2111, n_oracle=4, stagger_s=0.005)
+
+
+def test_serve_knn2m(lib):
+    g = gg.knn(2_000_000, 64, 0.02, 10, float(1 << 20), seed=10)
+    srcs = gg.pick_sources(g, 16, 9, mask=np.ones(g.n, np.uint8))
+    _serve_and_check(lib, g, lib.SSSP_GRAPH_SYMMETRIC | lib.SSSP_GRAPH_VERIFY, srcs, slots=8,
+                     algo=lib.SSSP_RHO, param=1 << 15, n_oracle=6, stagger_s=0.0005)
+
+
+def test_serve_rmat25(lib):
+    g = gg.rmat(25, 16, 0.57, 0.19, 0.19, gen_seed=8, wseed=8)
+    assert g.n == 1 << 25 and g.m > 10 ** 9
+    srcs = gg.pick_sources(g, 4, 9, mask=gg.largest_cc(g))
+    # the generator symmetrises, so the graph is declared symmetric without the
+    # O(m log d) host check; the comparison with single solves and the oracle
+    # covers the bidirectional-free server path either way
+    _serve_and_check(lib, g, lib.SSSP_GRAPH_SYMMETRIC, srcs, slots=2, algo=lib.SSSP_RHO, param=g.n // 16,
+                     n_oracle=1, stagger_s=0.002)

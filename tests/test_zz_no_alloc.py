@@ -1,12 +1,16 @@
 """sssp_solve_noalloc: the solve for callers that cannot allocate device memory
-(framework plugins that must not allocate, code under stream capture,
-latency-critical loops).  It takes the graph already on the device and uses a
-static scratch array instead of allocating.  Its output must equal the
-regular entry point's (bit-exact uint64 distances) on consecutive calls that
-share the scratch array.  This file is collected last on purpose."""
+when they need a solve (a plugin inside a framework that owns all device
+memory through its own pool, a latency-critical loop that cannot take the
+device synchronisation of cudaMalloc/cudaFree).  It takes the graph already on
+the device and uses a static scratch array instead of allocating.  Its output
+must equal the regular entry point's and the oracle's (bit-exact uint64
+distances) on consecutive calls that share the scratch array, and a call after
+the first must not change the device's free memory.  This file is collected
+last on purpose."""
 import numpy as np
 import pytest
 
+import oracle
 from paper_2105_06145_gb300 import graphgen as gg
 
 torch = pytest.importorskip("torch")
@@ -67,11 +71,35 @@ def test_noalloc_matches_regular_entry_on_consecutive_calls(lib):
     for g, algo, param in cases:
         s = gg.pick_sources(g, 1, 9)[0]
         want = _regular(lib, g, s, algo, param)
+        assert np.array_equal(want, oracle.dijkstra(g, s)), (g.name, algo, param)
         dev = _device_csr(g)
         for call in range(2):  # two calls in a row share the scratch array
             got, status, steps = _noalloc(lib, g, s, algo, param, dev)
             assert status == 0 and steps >= 1
             assert np.array_equal(got, want), (g.name, algo, param, call)
+
+
+def test_noalloc_call_takes_no_device_memory(lib):
+    """After the first call (the one-time set-up) a call changes neither the
+    device's free memory nor its result."""
+    g = gg.rmat(13, 16, gen_seed=5, wseed=6)
+    s = gg.pick_sources(g, 1, 3)[0]
+    want = oracle.dijkstra(g, s)
+    dev = _device_csr(g)
+    d = torch.empty(g.n, dtype=torch.int64, device="cuda")
+    stream = torch.cuda.current_stream().cuda_stream
+    lib.sssp_solve_noalloc(g.n, g.m, dev[0].data_ptr(), dev[1].data_ptr(), s, lib.SSSP_RHO, 256, d.data_ptr(),
+                           0, stream)
+    torch.cuda.synchronize()
+    free0, _ = torch.cuda.mem_get_info()
+    for _ in range(3):
+        d.fill_(0)
+        lib.sssp_solve_noalloc(g.n, g.m, dev[0].data_ptr(), dev[1].data_ptr(), s, lib.SSSP_RHO, 256,
+                               d.data_ptr(), 0, stream)
+        torch.cuda.synchronize()
+        assert np.array_equal(d.cpu().numpy().view(np.uint64), want)
+    free1, _ = torch.cuda.mem_get_info()
+    assert free1 == free0, (free0, free1)
 
 
 def test_noalloc_rejects_sizes_beyond_its_maximum(lib):

@@ -259,7 +259,7 @@ int sssp_rho_threshold(const uint32_t* queue, uint32_t q, const uint64_t* dist, 
 #define SSSP_MAX_BATCH 2048   /* instances per batched call */
 
 /*
- * k sources on one graph.
+ * k sources on one graph (mode SSSP_BATCH_AUTO of sssp_solve_sources_ex).
  *   sources   HOST uint32[k], each < n (repeats allowed)
  *   params    HOST uint64[k] per-instance rho / Delta (as for sssp_solve), or
  *             NULL: rho = max(64, n/16), Delta = max(1, mean weight / 4)
@@ -279,6 +279,23 @@ int sssp_rho_threshold(const uint32_t* queue, uint32_t q, const uint64_t* dist, 
  */
 int sssp_solve_sources(const sssp_graph* g, const uint32_t* sources, uint32_t k, sssp_algo algo,
                        const uint64_t* params, uint64_t* dist_out, void* stream);
+
+/* How a batch of sources on one graph is run (sssp_solve_sources_ex). */
+#define SSSP_BATCH_AUTO 0u     /* the graph's batch tuning (sssp_autotune_batch) decides; without
+                                  one, SHARED where it applies, else SEPARATE                    */
+#define SSSP_BATCH_SHARED 1u   /* one edge scan per step shared by every instance that extracted
+                                  the vertex (k <= 64; rho-Stepping, Delta*-Stepping,
+                                  Bellman-Ford): distances are kept vertex-major inside, so one
+                                  vertex's k distances share cache lines.  Uses the graph's
+                                  bidirectional relaxation setting (batch tuning); no local
+                                  relaxation.  INVALID_ARG when it does not apply               */
+#define SSSP_BATCH_SEPARATE 2u /* independent instances (any k and rule; each instance uses its
+                                  graph's bidirectional and local relaxation settings)           */
+
+/* sssp_solve_sources with an explicit SSSP_BATCH_* mode.  The distances do not
+   depend on the mode. */
+int sssp_solve_sources_ex(const sssp_graph* g, const uint32_t* sources, uint32_t k, sssp_algo algo,
+                          const uint64_t* params, uint32_t mode, uint64_t* dist_out, void* stream);
 
 /*
  * k independent graphs, one source each (instance i solves gs[i] from
@@ -435,6 +452,7 @@ typedef struct {
     uint32_t rho_reduced;    /* sssp_options.rho_reduced (0 = the paper's 2)                */
     uint32_t small_deg;      /* sssp_options.small_deg (0 = 32; single solves only)         */
     uint32_t chunk;          /* sssp_options.chunk (0 = 256; single solves only)            */
+    uint32_t batch_mode;     /* batch autotuner: SSSP_BATCH_SHARED or SSSP_BATCH_SEPARATE   */
 } sssp_tuning;
 
 /*

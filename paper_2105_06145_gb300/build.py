@@ -16,7 +16,7 @@ CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libsssp.so")
 SOURCES = ["sssp_kernels.cu", "sssp_api.cu", "sssp_noalloc.cu", "sssp_batch.cu", "sssp_tune.cu",
-           "sssp_tourney.cu"]
+           "sssp_tourney.cu", "sssp_msbatch.cu"]
 HEADERS = ["sssp_internal.h", "sssp_device.cuh", os.path.join("..", "..", "include", "sssp.h")]
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]

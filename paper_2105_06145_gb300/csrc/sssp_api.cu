@@ -200,7 +200,7 @@ int sssp_graph_create_ex(uint32_t n, uint64_t m, const uint64_t* offsets, const 
     // launches) and the largest over every cut-off a single solve may take
     // (small_deg in [kSmallDegMin, kSmallDegMax], chunks of >= 2^kChunkLog2Min
     // edges) -- the single solve's record arrays are sized for the latter.
-    uint64_t small_cap = 0, item_cap = 0, small_any = 0, item_any = 0;
+    uint64_t small_cap = 0, item_cap = 0, small_any = 0, item_any = 0, ms_rec = 0;
     unsigned __int128 wsum = 0;
     for (uint64_t e = 0; e < m; ++e) wsum += weights[e];
     uint64_t max_deg = 0;
@@ -211,6 +211,7 @@ int sssp_graph_create_ex(uint32_t n, uint64_t m, const uint64_t* offsets, const 
         if (deg <= kSmallDeg) ++small_cap;
         else item_cap += chunk_count(offsets[u], offsets[u + 1]);
         if (deg <= kSmallDegMax) ++small_any;
+        ms_rec += (deg + kMsRecEdges - 1) / kMsRecEdges;
         if (deg > kSmallDegMin) item_any += chunk_count(offsets[u], offsets[u + 1], kChunkLog2Min);
     }
 
@@ -249,6 +250,7 @@ int sssp_graph_create_ex(uint32_t n, uint64_t m, const uint64_t* offsets, const 
     g->item_cap = item_cap + 1;
     g->fsmall_cap_any = small_any + 1;
     g->item_cap_any = item_any + 1;
+    g->ms_rec_cap = ms_rec + 1;
     if ((e = dalloc(&g->d_off, (uint64_t)n + 1)) != cudaSuccess ||
         (e = dalloc(&g->d_edges, m_alloc)) != cudaSuccess ||
         (e = dalloc(&g->d_inq, ((uint64_t)n + 31) / 32)) != cudaSuccess ||

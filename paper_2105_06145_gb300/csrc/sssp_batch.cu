@@ -949,6 +949,16 @@ int solve_batch(const sssp_graph* const* gs, const uint32_t* sources, uint32_t k
     return SSSP_OK;
 }
 
+// Which kind of batched launch ran last on a device (sssp_batch_last_stats
+// reports that one).
+enum { kLastSeparate = 0, kLastShared = 1 };
+std::atomic<int> g_last_kind[64];
+void set_last_kind(int dev, int kind)
+{
+    if (dev >= 0 && dev < 64) g_last_kind[dev].store(kind);
+}
+int last_kind(int dev) { return dev >= 0 && dev < 64 ? g_last_kind[dev].load() : kLastSeparate; }
+
 }  // namespace
 }  // namespace sssp
 
@@ -1124,26 +1134,54 @@ using namespace sssp;
 
 extern "C" {
 
+int sssp_solve_sources_ex(const sssp_graph* g, const uint32_t* sources, uint32_t k, sssp_algo algo,
+                          const uint64_t* params, uint32_t mode, uint64_t* dist_out, void* stream)
+{
+    if (!g || !dist_out || !sources || k == 0 || k > kMaxBatch || mode > SSSP_BATCH_SEPARATE)
+        return SSSP_ERR_INVALID_ARG;
+    if (!algo_valid(algo)) return SSSP_ERR_INVALID_ARG;
+    sssp_tuning t;
+    const bool tuned = sssp_lookup_batch_tuning(g, &t) && t.algo == algo;
+    if (mode == SSSP_BATCH_AUTO) {
+        mode = tuned && t.batch_mode ? t.batch_mode : SSSP_BATCH_SHARED;
+        if (mode == SSSP_BATCH_SHARED && !ms_batch_supported(algo, k)) mode = SSSP_BATCH_SEPARATE;
+    }
+    std::vector<uint64_t*> outs(k);
+    for (uint32_t i = 0; i < k; ++i) outs[i] = dist_out + (size_t)i * g->n;
+    if (mode == SSSP_BATCH_SHARED) {
+        if (!ms_batch_supported(algo, k)) return SSSP_ERR_INVALID_ARG;
+        uint32_t red = kRhoReducedDefault;
+        if (tuned && t.rho_reduced) red = t.rho_reduced == SSSP_RHO_REDUCED_NONE ? 0u : t.rho_reduced;
+        const bool bidir = tuned && (t.flags & SSSP_SOLVE_BIDIRECTIONAL) && (g->flags & SSSP_GRAPH_SYMMETRIC);
+        const int rc = ms_solve_sources(g, sources, k, algo, params, outs.data(), red, bidir, stream);
+        if (rc == SSSP_OK) set_last_kind(g->device, kLastShared);
+        return rc;
+    }
+    std::vector<const sssp_graph*> gs(k, g);
+    const int rc = solve_batch(gs.data(), sources, k, algo, params, outs.data(), stream);
+    if (rc == SSSP_OK) set_last_kind(g->device, kLastSeparate);
+    return rc;
+}
+
 int sssp_solve_sources(const sssp_graph* g, const uint32_t* sources, uint32_t k, sssp_algo algo,
                        const uint64_t* params, uint64_t* dist_out, void* stream)
 {
-    if (!g || !dist_out || k == 0 || k > kMaxBatch) return SSSP_ERR_INVALID_ARG;
-    std::vector<const sssp_graph*> gs(k, g);
-    std::vector<uint64_t*> outs(k);
-    for (uint32_t i = 0; i < k; ++i) outs[i] = dist_out + (size_t)i * g->n;
-    return solve_batch(gs.data(), sources, k, algo, params, outs.data(), stream);
+    return sssp_solve_sources_ex(g, sources, k, algo, params, SSSP_BATCH_AUTO, dist_out, stream);
 }
 
 int sssp_solve_multi(const sssp_graph* const* gs, const uint32_t* sources, uint32_t k, sssp_algo algo,
                      const uint64_t* params, uint64_t* const* dist_outs, void* stream)
 {
-    return solve_batch(gs, sources, k, algo, params, dist_outs, stream);
+    const int rc = solve_batch(gs, sources, k, algo, params, dist_outs, stream);
+    if (rc == SSSP_OK) set_last_kind(gs[0]->device, kLastSeparate);
+    return rc;
 }
 
 int sssp_batch_last_stats(sssp_stats* out, uint32_t k, void* stream)
 {
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return SSSP_ERR_CUDA;
+    if (last_kind(dev) == kLastShared) return ms_last_stats(dev, out, k, reinterpret_cast<cudaStream_t>(stream));
     std::lock_guard<std::mutex> lk(g_ws_mu);
     Workspace& w = g_ws[dev];
     if (w.device < 0 || k > w.last_k || (k > 0 && !out)) return SSSP_ERR_INVALID_ARG;

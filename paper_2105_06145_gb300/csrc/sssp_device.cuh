@@ -617,11 +617,14 @@ __device__ __forceinline__ uint64_t local_relax(uint64_t theta, uint32_t budget,
         uint64_t b = 0, du = 0;
         uint32_t deg = 0;
         if (lane < cnt) {
+            // the distance and the edge range are loaded together (the graph
+            // is read-only), so a round waits for one load, not two in a row
             const uint32_t x = stage[lq + lane];
             du = ldcg64(&dist[x]);
+            const uint64_t bx = __ldg(&off[x]), ex = __ldg(&off[x + 1]);
             if (du <= theta) {
-                b = off[x];
-                const uint64_t d = off[x + 1] - b;
+                b = bx;
+                const uint64_t d = ex - bx;
                 deg = d <= (uint64_t)kSmallDeg ? (uint32_t)d : 0u;
             }
         }

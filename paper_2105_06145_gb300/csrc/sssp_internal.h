@@ -159,6 +159,15 @@ constexpr uint32_t kMaxBatch = 2048;        // instances per batched launch
 const void* batch_kernel_ptr();
 const void* serve_kernel_ptr();
 
+// Batched solves of k <= 64 sources on one graph with one shared edge scan
+// per step (sssp_msbatch.cu): outs[i] receives instance i's distances.
+bool ms_batch_supported(sssp_algo algo, uint32_t k);
+int ms_solve_sources(const sssp_graph* g, const uint32_t* sources, uint32_t k, sssp_algo algo,
+                     const uint64_t* params, uint64_t* const* outs, uint32_t rho_reduced, bool bidir,
+                     void* stream);
+int ms_last_stats(int dev, sssp_stats* out, uint32_t k, cudaStream_t st);
+constexpr uint32_t kMsRecEdges = 32;        // edges per relaxation record of the shared-scan kernel
+
 }  // namespace sssp
 
 // The narrow build of the solve kernel (sssp_kernels.cu compiled with
@@ -187,6 +196,7 @@ struct sssp_graph {
     uint64_t item_cap = 0;
     uint64_t fsmall_cap_any = 0;           // ... at any allowed cut-offs (single-solve scratch)
     uint64_t item_cap_any = 0;
+    uint64_t ms_rec_cap = 0;               // shared-scan batch: records of one Extract (sum of ceil(deg/32))
     sssp::Ctrl* d_ctrl = nullptr;
     uint64_t* d_dist_internal = nullptr;   // lazily allocated for sssp_solve_host
     // SSSP_GRAPH_REORDER: relabelled copy for single solves (new id = rank by

@@ -220,8 +220,13 @@ __global__ void __launch_bounds__(kBlock, kMinBlocks) solve_kernel(SolveParams p
                 const uint32_t L = (uint32_t)(r0 >= q ? 0 : ((uint64_t)q - r0) < run ? ((uint64_t)q - r0) : run);
                 const bool select_now = rho_sample && rr == 0;
                 const bool sel_in_regs = select_now && s_cnt <= (uint32_t)kBlock;
-                // (1) ids, keys, and the keep / extract decision
+                // (1) ids, keys, and the keep / extract decision; in a sparse
+                //     step (20 q <= n: few entries per thread, most of them
+                //     extracted) the edge range of the first entry is loaded
+                //     with its key instead of after the decision
                 uint32_t extm = 0;  // bit j: entry j of this thread is extracted
+                const bool spec_range = (uint64_t)q * 20ull <= (uint64_t)n;
+                uint64_t sb0 = 0, se0 = 0;
                 {
                     uint32_t v[kExtractPer];
                     uint64_t d[kExtractPer];
@@ -238,6 +243,10 @@ __global__ void __launch_bounds__(kBlock, kMinBlocks) solve_kernel(SolveParams p
                     for (int j = 0; j < kExtractPer; ++j) {
                         const uint32_t i = tid + (uint32_t)j * kBlock;
                         d[j] = i < L ? ldcg64(&dist[v[j]]) : kInf;
+                    }
+                    if (spec_range && tid < L) {
+                        sb0 = __ldg(&off[v[0]]);
+                        se0 = __ldg(&off[v[0] + 1]);
                     }
                     if (select_now) {
                         // ExtDist of rho-Stepping (Table 2; Sec. 6; App. B)
@@ -272,9 +281,14 @@ __global__ void __launch_bounds__(kBlock, kMinBlocks) solve_kernel(SolveParams p
                         const uint32_t i = tid + (uint32_t)j * kBlock;
                         b[j] = 0; e[j] = 0;
                         if ((extm >> j) & 1u) {
-                            const uint32_t u = s_rec[i].x;
-                            b[j] = __ldg(&off[u]);
-                            e[j] = __ldg(&off[u + 1]);
+                            if (j == 0 && spec_range) {
+                                b[j] = sb0;
+                                e[j] = se0;
+                            } else {
+                                const uint32_t u = s_rec[i].x;
+                                b[j] = __ldg(&off[u]);
+                                e[j] = __ldg(&off[u + 1]);
+                            }
                         }
                     }
 #pragma unroll

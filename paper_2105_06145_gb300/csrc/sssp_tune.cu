@@ -305,10 +305,11 @@ int sssp_autotune_ex(sssp_graph* g, const uint32_t* sources, uint32_t k, uint32_
 // fastest in a batch).  Candidates as in sssp_autotune's first stage, each
 // timed as one sssp_solve_sources launch over up to 8 of the sources (with the
 // local budget the batch would use); the two best of each rule re-timed on all
-// k sources; then local budgets 0, 64 and 256 for the winner (all k sources)
-// on graphs where batched launches use local relaxation, and for a
-// rho-Stepping winner 4, 6 or no dense steps with rho/10 (the paper's 2 is the
-// starting point).  The result is kept as the graph's batch tuning,
+// k sources (separate instances, SSSP_BATCH_SEPARATE) and, for k <= 64, with
+// one shared edge scan per step (SSSP_BATCH_SHARED); then local budgets 0, 64
+// and 256 for a separate-instance winner on graphs where batched launches use
+// local relaxation, and for a rho-Stepping winner 4, 6, 8 or no dense steps
+// with rho/10 (the paper's 2 is the starting point).  The result is kept as the graph's batch tuning,
 // which the batched and serving calls prefer.
 int sssp_autotune_batch(sssp_graph* g, const uint32_t* sources, uint32_t k, uint32_t rules, sssp_tuning* out,
                         void* stream)
@@ -364,6 +365,7 @@ int sssp_autotune_batch(sssp_graph* g, const uint32_t* sources, uint32_t k, uint
         t.param = prm;
         t.flags = sym ? SSSP_SOLVE_BIDIRECTIONAL : 0u;
         t.local_budget = local0;
+        t.batch_mode = SSSP_BATCH_SEPARATE;
         for (const sssp_tuning& c : cand) if (c.algo == a && c.param == prm) return;
         cand.push_back(t);
     };
@@ -388,6 +390,7 @@ int sssp_autotune_batch(sssp_graph* g, const uint32_t* sources, uint32_t k, uint
     // (a few instances are latency-bound and can rank configurations
     // differently from a full batch)
     kk = k;
+    std::vector<sssp_tuning> finalists;
     for (sssp_algo a : {SSSP_RHO, SSSP_DELTA_STAR}) {
         for (int r = 0; r < 2 && rc == SSSP_OK; ++r) {
             size_t bi = cand.size();
@@ -395,12 +398,32 @@ int sssp_autotune_batch(sssp_graph* g, const uint32_t* sources, uint32_t k, uint
                 if (cand[i].algo == a && sweep[i] < INFINITY && (bi == cand.size() || sweep[i] < sweep[bi])) bi = i;
             if (bi == cand.size()) break;
             sweep[bi] = INFINITY;  // taken
+            finalists.push_back(cand[bi]);
             if ((rc = time_batch(cand[bi], &ms)) != SSSP_OK) break;
             ++timed;
             if (ms < best_ms) { best_ms = ms; best = cand[bi]; }
         }
     }
-    if (rc == SSSP_OK && g->n >= (1u << 20) && g->n && (double)g->m / (double)g->n < 20.0) {
+    // the same finalists with one shared edge scan per step (k <= 64): no
+    // local or bidirectional relaxation there; rho-Stepping also with six
+    // dense steps at rho/10
+    if (rc == SSSP_OK && sssp::ms_batch_supported(SSSP_RHO, k)) {
+        for (const sssp_tuning& f : finalists) {
+            for (uint32_t red : {0u, 6u}) {
+                if (red && f.algo != SSSP_RHO) continue;
+                sssp_tuning t = f;
+                t.batch_mode = SSSP_BATCH_SHARED;
+                t.local_budget = 0;
+                t.rho_reduced = red;
+                if ((rc = time_batch(t, &ms)) != SSSP_OK) break;
+                ++timed;
+                if (ms < best_ms) { best_ms = ms; best = t; }
+            }
+            if (rc != SSSP_OK) break;
+        }
+    }
+    if (rc == SSSP_OK && best.batch_mode == SSSP_BATCH_SEPARATE && g->n >= (1u << 20) &&
+        (double)g->m / (double)g->n < 20.0) {
         for (uint32_t local : {0u, 64u, 256u}) {
             if (local == best.local_budget) continue;
             sssp_tuning t = best;
@@ -412,7 +435,8 @@ int sssp_autotune_batch(sssp_graph* g, const uint32_t* sources, uint32_t k, uint
     }
     if (rc == SSSP_OK && best.algo == SSSP_RHO) {  // dense steps with rho/10 (Sec. 6 uses two)
         const sssp_tuning base = best;
-        for (uint32_t red : {4u, 6u, (uint32_t)SSSP_RHO_REDUCED_NONE}) {
+        for (uint32_t red : {4u, 6u, 8u, (uint32_t)SSSP_RHO_REDUCED_NONE}) {
+            if (red == base.rho_reduced) continue;
             sssp_tuning t = base;
             t.rho_reduced = red;
             if ((rc = time_batch(t, &ms)) != SSSP_OK) break;
@@ -469,6 +493,7 @@ int sssp_graph_set_tuning(sssp_graph* g, const sssp_tuning* t)
         return SSSP_ERR_INVALID_ARG;
     if (t->chunk != 0 && t->chunk != 128 && t->chunk != 256 && t->chunk != 512 && t->chunk != 1024)
         return SSSP_ERR_INVALID_ARG;
+    if (t->batch_mode > SSSP_BATCH_SEPARATE) return SSSP_ERR_INVALID_ARG;
     std::lock_guard<std::mutex> lk(g->mu);
     g->tuning = *t;
     g->tuned = true;

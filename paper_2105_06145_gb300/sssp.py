@@ -29,6 +29,7 @@ SSSP_ERR_INVALID_ARG, SSSP_ERR_OUT_OF_MEMORY, SSSP_ERR_CUDA = -1, -2, -3
 SSSP_ERR_TIMEOUT, SSSP_ERR_INTERNAL = -4, -5
 SSSP_MAX_BATCH = 2048  # instances per batched call
 SSSP_RHO_REDUCED_NONE = 0xFFFFFFFF  # sssp_options.rho_reduced: plain rho on every step
+SSSP_BATCH_AUTO, SSSP_BATCH_SHARED, SSSP_BATCH_SEPARATE = 0, 1, 2  # sssp_solve_sources_ex modes
 INF = (1 << 64) - 1
 
 if not os.path.exists(LIB_PATH):
@@ -102,6 +103,8 @@ _lib.sssp_solve_noalloc.argtypes = [_u32, _u64, _P, _P, _u32, _i32, _u64, _P, _P
 _lib.sssp_solve_noalloc.restype = _i32
 _lib.sssp_solve_sources.argtypes = [_P, _P, _u32, _i32, _P, _P, _P]
 _lib.sssp_solve_sources.restype = _i32
+_lib.sssp_solve_sources_ex.argtypes = [_P, _P, _u32, _i32, _P, _u32, _P, _P]
+_lib.sssp_solve_sources_ex.restype = _i32
 _lib.sssp_solve_multi.argtypes = [_P, _P, _u32, _i32, _P, _P, _P]
 _lib.sssp_solve_multi.restype = _i32
 _lib.sssp_batch_last_stats.argtypes = [_P, _u32, _P]
@@ -148,7 +151,7 @@ EXPORTED = ["sssp_graph_create", "sssp_graph_destroy", "sssp_graph_info", "sssp_
             "sssp_autotune", "sssp_graph_get_tuning", "sssp_graph_set_tuning", "sssp_graph_class",
             "sssp_solve_tuned", "sssp_autotune_ex", "sssp_tourney_create", "sssp_tourney_destroy",
             "sssp_tourney_update", "sssp_tourney_extract", "sssp_tourney_min", "sssp_tourney_inq",
-            "sssp_array_extract", "sssp_autotune_batch"]
+            "sssp_array_extract", "sssp_autotune_batch", "sssp_solve_sources_ex"]
 
 _lib.sssp_tourney_create.argtypes = [_u32, ctypes.POINTER(_P)]
 _lib.sssp_tourney_create.restype = _i32
@@ -170,7 +173,8 @@ class sssp_tuning(ctypes.Structure):
     _fields_ = [("algo", ctypes.c_int), ("shape", ctypes.c_uint32), ("param", ctypes.c_uint64),
                 ("flags", ctypes.c_uint32), ("local_budget", ctypes.c_uint32), ("ms", ctypes.c_double),
                 ("candidates", ctypes.c_uint32), ("slots", ctypes.c_uint32),
-                ("rho_reduced", ctypes.c_uint32), ("small_deg", ctypes.c_uint32), ("chunk", ctypes.c_uint32)]
+                ("rho_reduced", ctypes.c_uint32), ("small_deg", ctypes.c_uint32), ("chunk", ctypes.c_uint32),
+                ("batch_mode", ctypes.c_uint32)]
 
     def as_dict(self) -> dict:
         return {k: (float(getattr(self, k)) if k == "ms" else int(getattr(self, k))) for k, _ in self._fields_}
@@ -319,6 +323,17 @@ def sssp_solve_sources(g: int, sources, algo: int, params, dist_out_ptr: int, st
     rc = _lib.sssp_solve_sources(g, src.ctypes.data, src.size, algo,
                                  prm.ctypes.data if prm is not None else None, dist_out_ptr, stream or None)
     return _check(rc, "sssp_solve_sources") if check else rc
+
+
+def sssp_solve_sources_ex(g: int, sources, algo: int, params, mode: int, dist_out_ptr: int, stream: int = 0,
+                          check: bool = True) -> int:
+    """sssp_solve_sources with an SSSP_BATCH_* mode (shared edge scan or separate instances)."""
+    src = np.ascontiguousarray(sources, dtype=np.uint32)
+    prm = None if params is None else np.ascontiguousarray(params, dtype=np.uint64)
+    rc = _lib.sssp_solve_sources_ex(g, src.ctypes.data, src.size, algo,
+                                    prm.ctypes.data if prm is not None else None, mode, dist_out_ptr,
+                                    stream or None)
+    return _check(rc, "sssp_solve_sources_ex") if check else rc
 
 
 def sssp_solve_multi(graphs, sources, algo: int, params, dist_out_ptrs, stream: int = 0,

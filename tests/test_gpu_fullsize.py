@@ -48,6 +48,11 @@ def test_rmat22_all_rules(lib):
     bench_flags = lib.SSSP_GRAPH_SYMMETRIC | lib.SSSP_GRAPH_REORDER
     bidir = lib.make_options(flags=lib.SSSP_SOLVE_BIDIRECTIONAL)
     _run(lib, g, [s] + extra, [(0, 1 << 18), (0, 1 << 20), (0, 1 << 22), (1, 1 << 15), (2, 0)], bench_flags, bidir)
+    # ... with the benchmark's count of dense steps that use rho/10 (6) and
+    # the autotuner's other choices of the count and of the degree cut-offs
+    for red, sd, ch in ((6, 0, 0), (4, 64, 512), (8, 16, 128)):
+        o = lib.make_options(flags=lib.SSSP_SOLVE_BIDIRECTIONAL, rho_reduced=red, small_deg=sd, chunk=ch)
+        _run(lib, g, [s] + extra, [(0, 1 << 18), (0, 1 << 19)], bench_flags, o)
 
 
 def test_road4096(lib):

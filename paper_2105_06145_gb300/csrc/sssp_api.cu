@@ -47,6 +47,7 @@ void free_graph(sssp_graph* g)
     cudaFree(g->d_items);
     cudaFree(g->d_ctrl);
     cudaFree(g->d_dist_internal);
+    cudaFree(g->d_lrel);
     cudaFree(g->d_off2);
     cudaFree(g->d_edges2);
     cudaFree(g->d_perm);
@@ -354,6 +355,16 @@ int sssp_solve_ex(const sssp_graph* gc, uint32_t source, sssp_algo algo, uint64_
     p.bidir = (o.flags & SSSP_SOLVE_BIDIRECTIONAL) ? 1 : 0;
     if (o.local_budget != 0 && algo != SSSP_RHO && algo != SSSP_DELTA_STAR) return SSSP_ERR_INVALID_ARG;
     p.local_budget = o.local_budget;
+    if (o.local_budget != 0) {
+        // per-vertex record of local relaxations (allocated by the first solve
+        // that uses local relaxation on this graph)
+        std::lock_guard<std::mutex> lk(g->mu);
+        if (!g->d_lrel) {
+            cudaError_t e = dalloc(&g->d_lrel, g->n);
+            if (e != cudaSuccess) { g->d_lrel = nullptr; return cuda_fail(e); }
+        }
+        p.lrel = g->d_lrel;
+    }
     p.rho_reduced = o.rho_reduced == 0 ? kRhoReducedDefault
                     : o.rho_reduced == SSSP_RHO_REDUCED_NONE ? 0u : o.rho_reduced;
     if (o.small_deg != 0 && (o.small_deg < kSmallDegMin || o.small_deg > kSmallDegMax)) return SSSP_ERR_INVALID_ARG;

@@ -592,15 +592,18 @@ __device__ __forceinline__ void block_reduce_2add_min(uint64_t& a, uint64_t& b, 
 // out-edges relaxed at once (WriteMin and Update as in the main relaxation);
 // the ids that queues are appended behind and are looked at in turn.  Every id
 // stays staged and so reaches Q_next: a vertex relaxed here is extracted again
-// in a later step (a vertex this step would have extracted next).  Stops after
-// `budget` relaxed vertices, or when the frontier is exhausted.  Returns the
-// edges relaxed.
+// in a later step (a vertex this step would have extracted next).  With lrel
+// (one entry per vertex), the distance a vertex was relaxed with here is
+// recorded, so that its later extraction can skip the edges when the distance
+// has not changed since (relaxing them again with the same value cannot lower
+// any target).  Stops after `budget` relaxed vertices, or when the frontier is
+// exhausted.  Returns the edges relaxed.
 // ---------------------------------------------------------------------------
 __device__ __forceinline__ uint64_t local_relax(uint64_t theta, uint32_t budget, const uint64_t* __restrict__ off,
                                                 const uint2* __restrict__ edges, uint64_t* dist, uint32_t* inq,
                                                 uint32_t* stage, uint32_t& stc, uint32_t lane, uint64_t& lmin,
                                                 uint32_t& lupd, unsigned int* qsize, int* status, uint32_t* Qnext,
-                                                uint32_t n)
+                                                uint32_t n, uint64_t* lrel = nullptr)
 {
     uint32_t lq = 0, done = 0;
     uint64_t scanned = 0;
@@ -615,11 +618,11 @@ __device__ __forceinline__ uint64_t local_relax(uint64_t theta, uint32_t budget,
         uint32_t cnt = stc - lq;
         cnt = cnt < 32u ? cnt : 32u;
         uint64_t b = 0, du = 0;
-        uint32_t deg = 0;
+        uint32_t deg = 0, x = 0;
         if (lane < cnt) {
             // the distance and the edge range are loaded together (the graph
             // is read-only), so a round waits for one load, not two in a row
-            const uint32_t x = stage[lq + lane];
+            x = stage[lq + lane];
             du = ldcg64(&dist[x]);
             const uint64_t bx = __ldg(&off[x]), ex = __ldg(&off[x + 1]);
             if (du <= theta) {
@@ -634,6 +637,7 @@ __device__ __forceinline__ uint64_t local_relax(uint64_t theta, uint32_t budget,
         const uint32_t incl = (uint32_t)warp_incl_scan64(deg, lane);
         const uint32_t take = __popc(__ballot_sync(FULL_MASK, lane < cnt && incl <= room));
         if (lane >= take) deg = 0;
+        if (lrel && deg > 0) lrel[x] = du;
         done += __popc(__ballot_sync(FULL_MASK, deg > 0));
         scanned += __shfl_sync(FULL_MASK, incl, take - 1);
         lq += take;

@@ -115,6 +115,7 @@ struct SolveParams {
     int bidir;                    // bidirectional relaxation of chunk records (symmetric graphs)
     uint32_t local_budget;        // local relaxation of super-sparse steps: vertices per warp and step (0 = off)
     uint32_t rho_reduced;         // rho-Stepping: dense steps that use rho/10
+    uint64_t* lrel;               // [n] distance each vertex was last locally relaxed with, or null
     uint32_t small_deg;           // degree-bin cut-off: 1..small_deg -> low-degree records
     uint32_t chunk_log2;          // chunk records cover at most 2^chunk_log2 edges (aligned)
     // relabelled graph (SSSP_GRAPH_REORDER): the solve runs on the relabelled
@@ -196,9 +197,10 @@ struct sssp_graph {
     uint64_t item_cap = 0;
     uint64_t fsmall_cap_any = 0;           // ... at any allowed cut-offs (single-solve scratch)
     uint64_t item_cap_any = 0;
-    uint64_t ms_rec_cap = 0;               // shared-scan batch: records of one Extract (sum of ceil(deg/32))
+    uint64_t ms_rec_cap = 0;               // shared-scan batch: per-warp records of one Extract (sum of ceil(deg/32))
     sssp::Ctrl* d_ctrl = nullptr;
     uint64_t* d_dist_internal = nullptr;   // lazily allocated for sssp_solve_host
+    uint64_t* d_lrel = nullptr;            // lazily allocated for solves with local relaxation
     // SSSP_GRAPH_REORDER: relabelled copy for single solves (new id = rank by
     // decreasing out-degree, ties by id; adjacencies sorted by new target)
     bool reordered = false;

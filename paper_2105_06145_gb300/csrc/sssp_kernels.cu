@@ -94,6 +94,8 @@ __global__ void __launch_bounds__(kBlock, kMinBlocks) solve_kernel(SolveParams p
         inq[i] = (i == (p.source >> 5)) ? (1u << (p.source & 31u)) : 0u;
     if (p.ext_count)
         for (uint64_t i = gtid; i < n; i += gthreads) p.ext_count[i] = 0;
+    if (p.lrel)
+        for (uint64_t i = gtid; i < n; i += gthreads) p.lrel[i] = kInf;
     if (p.trace)
         for (uint64_t i = gtid; i < p.trace_cap; i += gthreads) {
             p.trace[i].t_extract_end_max = 0;
@@ -281,13 +283,18 @@ __global__ void __launch_bounds__(kBlock, kMinBlocks) solve_kernel(SolveParams p
                         const uint32_t i = tid + (uint32_t)j * kBlock;
                         b[j] = 0; e[j] = 0;
                         if ((extm >> j) & 1u) {
+                            const uint32_t u = s_rec[i].x;
                             if (j == 0 && spec_range) {
                                 b[j] = sb0;
                                 e[j] = se0;
                             } else {
-                                const uint32_t u = s_rec[i].x;
                                 b[j] = __ldg(&off[u]);
                                 e[j] = __ldg(&off[u + 1]);
+                            }
+                            // locally relaxed with this same distance: its edges are done
+                            if (p.lrel) {
+                                const uint4 r = s_rec[i];
+                                if (ldcg64(&p.lrel[u]) == ((uint64_t)r.y | ((uint64_t)r.z << 32))) e[j] = b[j];
                             }
                         }
                     }
@@ -453,7 +460,7 @@ __global__ void __launch_bounds__(kBlock, kMinBlocks) solve_kernel(SolveParams p
                 const uint64_t fed = ldcg64((const uint64_t*)&ctrl->fedges[c]);
                 if (fed < 20ull * fcnt)
                     ledg = local_relax(theta, p.local_budget, off, edges, dist, inq, stage, stc, lane, lmin, lupd,
-                                       &ctrl->qsize[nx], &ctrl->status, Qnext, n);
+                                       &ctrl->qsize[nx], &ctrl->status, Qnext, n, p.lrel);
             }
 
             // (c) block-aggregated flush of what is left in the warps' staging

@@ -28,9 +28,9 @@
 //   phase R   relaxation of the records: WriteMin on D[v*R + i] for the
 //             instances in F(u), then one atomicOr of the improved bits on
 //             v's mask (Update); v joins the next union list when its mask
-//             was empty.  Lanes are the record's edges; the instances of
-//             F(u) are taken four at a time (consecutive instances share a
-//             row sector, so their accesses to one target row share lines).
+//             was empty.  Masks with few instances are relaxed edge-parallel
+//             (lanes = edges), others instance-parallel (lanes = instance
+//             pairs, one coalesced row access per edge).
 // Grid barriers separate the phases (Extract is not concurrent with Update,
 // Sec. 3.1).  The distances equal k single solves; the thresholds of
 // rho-Stepping come from a different sample draw than a single solve's, so
@@ -49,8 +49,11 @@ namespace sssp {
 
 constexpr uint32_t kMsMax = 64;        // instances per shared-scan launch
 constexpr uint32_t kMsRec = 32;        // edges per relaxation record
-constexpr uint32_t kMsSparse = 4;      // instances of a record mask relaxed together (loads in flight)
-constexpr int kMsBlock = 512;          // threads per block
+constexpr uint32_t kMsSparse = 4;      // masks with at most this many instances: edge-parallel relaxation
+#ifndef SSSP_MS_BLOCK
+#define SSSP_MS_BLOCK 1024
+#endif
+constexpr int kMsBlock = SSSP_MS_BLOCK;  // threads per block
 constexpr int kMsWarps = kMsBlock / 32;
 constexpr uint32_t kMsDraws = 64u * 1024u;  // rho sampler: union-list positions drawn per instance and step
 constexpr uint32_t kMsDynSmem = (uint32_t)kMsWarps * kStage * 4u > kMaxSamples * 8u
@@ -73,7 +76,8 @@ struct MsCtrl {
     int status;
     unsigned int pad;
     unsigned int usize[3];            // union list size of step k (slot k%3)
-    unsigned int nrec[3];             // relaxation records of step k (slot k%3)
+    unsigned int nsmall[3];           // low-degree records of step k (slot k%3)
+    unsigned int nbig[3];             // records of higher-degree vertices of step k (slot k%3)
     unsigned long long steps;
 };
 
@@ -88,9 +92,11 @@ struct MsParams {
     uint64_t* QM;                     // [n] queue masks
     uint32_t* qa;                     // union lists [n]
     uint32_t* qb;
-    uint4* rec;                       // records: x = u, y = edge count, z|w = first edge
+    uint4* rec;                       // records: x = u, y = edge count, z|w = first edge; flattened
+                                      // records in [0, small_cap), per-warp records after it
     uint64_t* fm;                     // record masks F(u)
-    uint64_t rec_cap;
+    uint64_t small_cap;               // flattened records (vertices of degree 1..32, <= kMsSparse instances)
+    uint64_t big_cap;                 // per-warp records (32 edges each)
     MsInst* inst;
     MsCtrl* ctrl;
     const uint32_t* src;              // [K] sources (ids of the graph the kernel runs on)
@@ -106,7 +112,7 @@ struct MsParams {
 
 struct MsSmem {
     uint64_t tmp[3 * kMsWarps];
-    uint32_t base[2];
+    uint32_t base[3];
     unsigned long long bar_target;
     unsigned long long t_start;
     unsigned long long cnt[4][kMsMax];   // per-instance block sums of the phase
@@ -295,28 +301,40 @@ __device__ void ms_phase_E(const MsParams& p, uint64_t k, uint32_t U, MsSmem& S)
         const uint64_t new_qm = my_qm & ~my_fm;
         if (valid && my_fm) p.QM[my_v] = new_qm;  // no other writer in this phase
         const bool keep = valid && new_qm != 0;
-        const uint64_t nrec = (valid && my_fm) ? ((uint64_t)my_deg + kMsRec - 1) / kMsRec : 0;
+        // degree 1..32 and at most kMsSparse instances: a flattened record;
+        // otherwise 32-edge records relaxed one per warp (lanes then cover
+        // instance pairs when the mask is wide)
+        const bool small = valid && my_fm && my_deg >= 1 && my_deg <= kMsRec && __popcll(my_fm) <= (int)kMsSparse;
+        const uint64_t nrec = (valid && my_fm && !small) ? ((uint64_t)my_deg + kMsRec - 1) / kMsRec : 0;
         uint64_t tot;
-        const uint64_t ex = ms_excl_scan64((uint64_t)(keep ? 1u : 0u) | (nrec << 16), S.tmp, &tot);
+        const uint64_t ex = ms_excl_scan64((uint64_t)(keep ? 1u : 0u) | ((uint64_t)(small ? 1u : 0u) << 16) |
+                                           (nrec << 32), S.tmp, &tot);
         if (tid == 0) {
-            const uint32_t tk = (uint32_t)(tot & 0xFFFFu);
-            const uint64_t tr = tot >> 16;
+            const uint32_t tk = (uint32_t)(tot & 0xFFFFu), ts = (uint32_t)((tot >> 16) & 0xFFFFu);
+            const uint64_t tr = tot >> 32;
             S.base[0] = tk ? atomicAdd(&p.ctrl->usize[nx], tk) : 0u;
-            S.base[1] = tr ? atomicAdd(&p.ctrl->nrec[c], (unsigned int)tr) : 0u;
-            if ((uint64_t)S.base[0] + tk > p.n || (uint64_t)S.base[1] + tr > p.rec_cap)
+            S.base[1] = ts ? atomicAdd(&p.ctrl->nsmall[c], ts) : 0u;
+            S.base[2] = tr ? atomicAdd(&p.ctrl->nbig[c], (unsigned int)tr) : 0u;
+            if ((uint64_t)S.base[0] + tk > p.n || (uint64_t)S.base[1] + ts > p.small_cap ||
+                (uint64_t)S.base[2] + tr > p.big_cap)
                 raise_error(&p.ctrl->bar, &p.ctrl->status, SSSP_ERR_INTERNAL);
         }
         __syncthreads();
         const uint64_t pk = (uint64_t)S.base[0] + (ex & 0xFFFFu);
-        uint64_t pr = (uint64_t)S.base[1] + (ex >> 16);
+        const uint64_t ps = (uint64_t)S.base[1] + ((ex >> 16) & 0xFFFFu);
+        uint64_t pr = (uint64_t)S.base[2] + (ex >> 32);
         if (keep && pk < p.n) Qnext[pk] = my_v;
+        if (small && ps < p.small_cap) {
+            p.rec[ps] = make_uint4(my_v, my_deg, (uint32_t)my_b, (uint32_t)(my_b >> 32));
+            p.fm[ps] = my_fm;
+        }
         if (nrec > 0 && nrec <= 4) {
             for (uint64_t j = 0; j < nrec; ++j, ++pr) {
-                if (pr >= p.rec_cap) break;
+                if (pr >= p.big_cap) break;
                 const uint64_t st = my_b + j * kMsRec;
                 const uint32_t len = (uint32_t)((my_e - st) < kMsRec ? (my_e - st) : kMsRec);
-                p.rec[pr] = make_uint4(my_v, len, (uint32_t)st, (uint32_t)(st >> 32));
-                p.fm[pr] = my_fm;
+                p.rec[p.small_cap + pr] = make_uint4(my_v, len, (uint32_t)st, (uint32_t)(st >> 32));
+                p.fm[p.small_cap + pr] = my_fm;
             }
         }
         // vertices with many records: the whole warp writes them
@@ -331,11 +349,11 @@ __device__ void ms_phase_E(const MsParams& p, uint64_t k, uint32_t U, MsSmem& S)
             const uint64_t sp = __shfl_sync(FULL_MASK, pr, sl);
             const uint64_t sn = __shfl_sync(FULL_MASK, nrec, sl);
             for (uint64_t j = lane; j < sn; j += 32) {
-                if (sp + j >= p.rec_cap) break;
+                if (sp + j >= p.big_cap) break;
                 const uint64_t st = sb + j * kMsRec;
                 const uint32_t len = (uint32_t)((se - st) < kMsRec ? (se - st) : kMsRec);
-                p.rec[sp + j] = make_uint4(sv, len, (uint32_t)st, (uint32_t)(st >> 32));
-                p.fm[sp + j] = sf;
+                p.rec[p.small_cap + sp + j] = make_uint4(sv, len, (uint32_t)st, (uint32_t)(st >> 32));
+                p.fm[p.small_cap + sp + j] = sf;
             }
         }
         __syncthreads();  // S.tmp / S.base reuse
@@ -373,99 +391,268 @@ __device__ void ms_phase_R(const MsParams& p, uint64_t k, MsSmem& S, uint32_t* s
     const uint32_t R = p.R;
     const uint32_t i0 = 2 * lane;
     const bool track_min = p.algo == SSSP_DELTA_STAR;
-    uint64_t nrec = ldcg32(&p.ctrl->nrec[c]);
-    nrec = nrec < p.rec_cap ? nrec : p.rec_cap;
+    uint64_t nsm = ldcg32(&p.ctrl->nsmall[c]);
+    nsm = nsm < p.small_cap ? nsm : p.small_cap;
+    uint64_t nrec = ldcg32(&p.ctrl->nbig[c]);
+    nrec = nrec < p.big_cap ? nrec : p.big_cap;
     const uint32_t gwarp = wid * gridDim.x + blockIdx.x;
     const uint32_t nwarps = gridDim.x * kMsWarps;
     uint64_t qn0 = 0, qn1 = 0, up0 = 0, up1 = 0, um0 = kInf, um1 = kInf;
     uint32_t stc = 0;
+
+    // (a) vertices of degree 1..32 extracted by at most kMsSparse instances:
+    //     32 records per warp with their edges spread over the lanes 32 at a
+    //     time; each lane walks the (short) instance mask of its edge's
+    //     record (per-instance counts by shared-memory atomics)
+    const uint64_t ngroups = (nsm + 31u) >> 5;
+    const uint32_t lmask = lane == 31 ? FULL_MASK : ((2u << lane) - 1u);
+    for (uint64_t gi = gwarp; gi < ngroups; gi += nwarps) {
+        const uint64_t r = gi * 32u + lane;
+        const bool valid = r < nsm;
+        const uint4 rc = valid ? __ldcg(&p.rec[r]) : make_uint4(0u, 0u, 0u, 0u);
+        const uint64_t fmk = valid ? ldcg64(&p.fm[r]) : 0ull;
+        const uint32_t len = rc.y;
+        const uint64_t start = (uint64_t)rc.z | ((uint64_t)rc.w << 32);
+        const uint32_t incl = (uint32_t)warp_incl_scan64(len, lane);
+        const uint32_t excl = incl - len;
+        const uint32_t total = __shfl_sync(FULL_MASK, incl, 31);
+        uint32_t started = 0;
+        for (uint32_t r0 = 0; r0 < total; r0 += 32) {
+            // owner of edge r0+lane: the record whose run of edges holds it
+            const uint32_t contrib = (len > 0 && excl >= r0 && excl < r0 + 32u) ? (1u << (excl - r0)) : 0u;
+            const uint32_t starts = __reduce_or_sync(FULL_MASK, contrib);
+            int owner = (int)(started + __popc(starts & lmask)) - 1;
+            owner = owner < 0 ? 0 : owner;
+            started += __popc(starts);
+            const uint32_t e = r0 + lane;
+            const bool ok = e < total;
+            const uint32_t ou = __shfl_sync(FULL_MASK, rc.x, owner);
+            const uint64_t ofm = __shfl_sync(FULL_MASK, fmk, owner);
+            const uint64_t ost = __shfl_sync(FULL_MASK, start, owner);
+            const uint32_t oex = __shfl_sync(FULL_MASK, excl, owner);
+            const uint2 ed = ok ? __ldcs(&p.edges[ost + (e - oex)]) : make_uint2(0u, 0u);
+            uint64_t newb = 0;
+            uint64_t m = ok ? ofm : 0ull;
+            while (m) {  // per lane: four instances at a time, loads in flight
+                uint32_t ib[4];
+                uint64_t dua[4], dvb[4];
+#pragma unroll
+                for (int t = 0; t < 4; ++t) {
+                    ib[t] = m ? (uint32_t)(__ffsll((long long)m) - 1) : 64u;
+                    m &= m - 1;
+                }
+#pragma unroll
+                for (int t = 0; t < 4; ++t) {
+                    dua[t] = ib[t] < 64u ? ldcg64(&p.D[(uint64_t)ou * R + ib[t]]) : kInf;
+                    dvb[t] = ib[t] < 64u ? ld_precheck<true>(&p.D[(uint64_t)ed.x * R + ib[t]]) : 0ull;
+                }
+#pragma unroll
+                for (int t = 0; t < 4; ++t) {
+                    if (ib[t] >= 64u || dua[t] == kInf) continue;
+                    const uint64_t cand = dua[t] + ed.y;
+                    if (cand < dvb[t]) {
+                        atomicMin(reinterpret_cast<unsigned long long*>(&p.D[(uint64_t)ed.x * R + ib[t]]),
+                                  (unsigned long long)cand);
+                        newb |= 1ull << ib[t];
+                        atomicAdd(&S.cnt[1][ib[t]], 1ull);
+                        if (track_min) atomicMin(&S.mn[ib[t]], (unsigned long long)cand);
+                    }
+                }
+            }
+            const uint64_t old = newb ? atomicOr(reinterpret_cast<unsigned long long*>(&p.QM[ed.x]),
+                                                 (unsigned long long)newb) : 0ull;
+            stage_push(newb != 0 && old == 0, ed.x, stage, stc, lane);
+            uint64_t newly = newb & ~old;
+            while (newly) {
+                const uint32_t it = (uint32_t)(__ffsll((long long)newly) - 1);
+                newly &= newly - 1;
+                atomicAdd(&S.cnt[0][it], 1ull);
+            }
+            if (stc > (uint32_t)kStage - 32u) stage_flush(stage, stc, lane, &p.ctrl->usize[nx], &p.ctrl->status, Qnext, p.n);
+        }
+    }
+
+    // (b) every other record: one warp per record of <= 32 edges
     for (uint64_t r = gwarp; r < nrec; r += nwarps) {
-        const uint4 rc = __ldcg(&p.rec[r]);
-        const uint64_t fmk = ldcg64(&p.fm[r]);
+        const uint4 rc = __ldcg(&p.rec[p.small_cap + r]);
+        const uint64_t fmk = ldcg64(&p.fm[p.small_cap + r]);
         const uint32_t u = rc.x, len = rc.y;
         const uint64_t start = (uint64_t)rc.z | ((uint64_t)rc.w << 32);
         const uint32_t b2 = (uint32_t)(fmk >> i0) & 3u;
         // delta_i[u] read at relaxation time (Algorithm 1)
         const ulonglong2 du = b2 ? ld_pair_cg(&p.D[(uint64_t)u * R + i0]) : make_ulonglong2(kInf, kInf);
         const uint2 ed = lane < len ? __ldcs(&p.edges[start + lane]) : make_uint2(0u, 0u);
-        // lanes = the record's edges; the instances of F(u) are taken four at
-        // a time with their four pre-check loads in flight (bits of one row
-        // sector share a line, so later loads of the same row hit L1)
-        uint64_t newb = 0, ubits = 0;
-        uint64_t m = fmk;
-        while (m) {  // warp-uniform
-            uint32_t ib[kMsSparse];
-            uint64_t dui[kMsSparse], dv[kMsSparse];
+        const uint32_t pc = __popcll(fmk);
+        uint64_t ubits = 0;  // instances whose delta[u] a pull lowered
+        if (pc <= kMsSparse) {
+            // lanes = the record's edges; the instances of F(u) are taken four at
+            // a time with their four pre-check loads in flight (bits of one row
+            // sector share a line, so later loads of the same row hit L1)
+            uint64_t newb = 0;
+            uint64_t m = fmk;
+            while (m) {  // warp-uniform
+                uint32_t ib[kMsSparse];
+                uint64_t dui[kMsSparse], dv[kMsSparse];
 #pragma unroll
-            for (uint32_t t = 0; t < kMsSparse; ++t) {
-                ib[t] = m ? (uint32_t)(__ffsll((long long)m) - 1) : 64u;
-                m &= m - 1;
-            }
+                for (uint32_t t = 0; t < kMsSparse; ++t) {
+                    ib[t] = m ? (uint32_t)(__ffsll((long long)m) - 1) : 64u;
+                    m &= m - 1;
+                }
 #pragma unroll
-            for (uint32_t t = 0; t < kMsSparse; ++t) {
-                const uint32_t it = ib[t] < 64u ? ib[t] : 0u;
-                const uint64_t mine = (it & 1u) ? du.y : du.x;
-                dui[t] = __shfl_sync(FULL_MASK, mine, it >> 1);
-                const bool ok = ib[t] < 64u && lane < len && dui[t] != kInf;
-                dv[t] = ok ? ld_precheck<true>(&p.D[(uint64_t)ed.x * R + it]) : 0ull;
-            }
-            if (p.bidir) {
-                // bidirectional relaxation (undirected graph): the gathered
-                // delta_i[v] first lower delta_i[u] (WriteMin + Update of u),
-                // then u pushes with the lowered value
+                for (uint32_t t = 0; t < kMsSparse; ++t) {
+                    const uint32_t it = ib[t] < 64u ? ib[t] : 0u;
+                    const uint64_t mine = (it & 1u) ? du.y : du.x;
+                    dui[t] = __shfl_sync(FULL_MASK, mine, it >> 1);
+                    const bool ok = ib[t] < 64u && lane < len && dui[t] != kInf;
+                    dv[t] = ok ? ld_precheck<true>(&p.D[(uint64_t)ed.x * R + it]) : 0ull;
+                }
+                if (p.bidir) {
+                    // bidirectional relaxation (undirected graph): the gathered
+                    // delta_i[v] first lower delta_i[u] (WriteMin + Update of u),
+                    // then u pushes with the lowered value
+#pragma unroll
+                    for (uint32_t t = 0; t < kMsSparse; ++t) {
+                        if (ib[t] >= 64u) break;  // warp-uniform
+                        uint64_t pull = (lane < len && dui[t] != kInf && dv[t] != kInf) ? dv[t] + ed.y : kInf;
+#pragma unroll
+                        for (int o = 16; o > 0; o >>= 1) {
+                            const uint64_t y = __shfl_xor_sync(FULL_MASK, pull, o);
+                            pull = y < pull ? y : pull;
+                        }
+                        if (pull < dui[t]) {  // warp-uniform
+                            dui[t] = pull;
+                            ubits |= 1ull << ib[t];
+                            if (lane == 0)
+                                atomicMin(reinterpret_cast<unsigned long long*>(&p.D[(uint64_t)u * R + ib[t]]),
+                                          (unsigned long long)pull);
+                            if (lane == (ib[t] >> 1)) {
+                                if (ib[t] & 1u) { ++up1; um1 = pull < um1 ? pull : um1; }
+                                else { ++up0; um0 = pull < um0 ? pull : um0; }
+                            }
+                        }
+                    }
+                }
 #pragma unroll
                 for (uint32_t t = 0; t < kMsSparse; ++t) {
                     if (ib[t] >= 64u) break;  // warp-uniform
-                    uint64_t pull = (lane < len && dui[t] != kInf && dv[t] != kInf) ? dv[t] + ed.y : kInf;
-#pragma unroll
-                    for (int o = 16; o > 0; o >>= 1) {
-                        const uint64_t y = __shfl_xor_sync(FULL_MASK, pull, o);
-                        pull = y < pull ? y : pull;
+                    const uint64_t cand = dui[t] + ed.y;
+                    const bool imp = lane < len && dui[t] != kInf && cand < dv[t];
+                    if (imp) {
+                        atomicMin(reinterpret_cast<unsigned long long*>(&p.D[(uint64_t)ed.x * R + ib[t]]),
+                                  (unsigned long long)cand);
+                        newb |= 1ull << ib[t];
                     }
-                    if (pull < dui[t]) {  // warp-uniform
-                        dui[t] = pull;
-                        ubits |= 1ull << ib[t];
-                        if (lane == 0)
-                            atomicMin(reinterpret_cast<unsigned long long*>(&p.D[(uint64_t)u * R + ib[t]]),
-                                      (unsigned long long)pull);
+                    const uint32_t cnt = __popc(__ballot_sync(FULL_MASK, imp));
+                    if (lane == (ib[t] >> 1)) { if (ib[t] & 1u) up1 += cnt; else up0 += cnt; }
+                    if (track_min) {
+                        uint64_t mn = imp ? cand : kInf;
+#pragma unroll
+                        for (int o = 16; o > 0; o >>= 1) {
+                            const uint64_t y = __shfl_xor_sync(FULL_MASK, mn, o);
+                            mn = y < mn ? y : mn;
+                        }
                         if (lane == (ib[t] >> 1)) {
-                            if (ib[t] & 1u) { ++up1; um1 = pull < um1 ? pull : um1; }
-                            else { ++up0; um0 = pull < um0 ? pull : um0; }
+                            if (ib[t] & 1u) um1 = mn < um1 ? mn : um1; else um0 = mn < um0 ? mn : um0;
                         }
                     }
                 }
             }
-#pragma unroll
-            for (uint32_t t = 0; t < kMsSparse; ++t) {
-                if (ib[t] >= 64u) break;  // warp-uniform
-                const uint64_t cand = dui[t] + ed.y;
-                const bool imp = lane < len && dui[t] != kInf && cand < dv[t];
-                if (imp) {
-                    atomicMin(reinterpret_cast<unsigned long long*>(&p.D[(uint64_t)ed.x * R + ib[t]]),
-                              (unsigned long long)cand);
-                    newb |= 1ull << ib[t];
-                }
-                const uint32_t cnt = __popc(__ballot_sync(FULL_MASK, imp));
-                if (lane == (ib[t] >> 1)) { if (ib[t] & 1u) up1 += cnt; else up0 += cnt; }
-                if (track_min) {
-                    uint64_t mn = imp ? cand : kInf;
-#pragma unroll
-                    for (int o = 16; o > 0; o >>= 1) {
-                        const uint64_t y = __shfl_xor_sync(FULL_MASK, mn, o);
-                        mn = y < mn ? y : mn;
-                    }
-                    if (lane == (ib[t] >> 1)) {
-                        if (ib[t] & 1u) um1 = mn < um1 ? mn : um1; else um0 = mn < um0 ? mn : um0;
-                    }
+            // Update(v): one test-and-set of the improved bits on v's mask; the
+            // bits pulled into u update u's mask (lane 0)
+            const uint64_t old = newb ? atomicOr(reinterpret_cast<unsigned long long*>(&p.QM[ed.x]),
+                                                 (unsigned long long)newb) : 0ull;
+            const uint64_t newly = newb & ~old;
+            stage_push(newb != 0 && old == 0, ed.x, stage, stc, lane);
+            // newly queued bits per instance: lane l counts instances 2l, 2l+1
+            {
+                uint64_t mm = fmk;
+                while (mm) {  // warp-uniform
+                    const uint32_t it = (uint32_t)(__ffsll((long long)mm) - 1);
+                    mm &= mm - 1;
+                    const uint32_t cnt = __popc(__ballot_sync(FULL_MASK, (newly >> it) & 1ull));
+                    if (lane == (it >> 1)) { if (it & 1u) qn1 += cnt; else qn0 += cnt; }
                 }
             }
+        } else {
+            // many instances: lanes = instance pairs (lane l: 2l, 2l+1), four
+            // edges at a time, one coalesced access to each target's row
+            uint64_t du0 = du.x, du1 = du.y;
+            uint32_t ub2 = 0;
+            for (uint32_t e0 = 0; e0 < len; e0 += 4) {
+                uint32_t vv[4], ww[4];
+                ulonglong2 dv[4];
+#pragma unroll
+                for (int t = 0; t < 4; ++t) {
+                    vv[t] = __shfl_sync(FULL_MASK, ed.x, (e0 + t) & 31u);
+                    ww[t] = __shfl_sync(FULL_MASK, ed.y, (e0 + t) & 31u);
+                }
+#pragma unroll
+                for (int t = 0; t < 4; ++t) {
+                    const bool ok = e0 + t < len && b2 != 0;
+                    dv[t] = ok ? __ldca(reinterpret_cast<const ulonglong2*>(&p.D[(uint64_t)vv[t] * R + i0]))
+                               : make_ulonglong2(kInf, kInf);
+                }
+                if (p.bidir) {
+                    // bidirectional relaxation: the group's gathered rows first
+                    // lower this lane's delta_i[u] (the values stay in lane)
+                    uint64_t p0 = kInf, p1 = kInf;
+#pragma unroll
+                    for (int t = 0; t < 4; ++t) {
+                        if (e0 + t >= len) continue;
+                        if ((b2 & 1u) && dv[t].x != kInf && dv[t].x + ww[t] < p0) p0 = dv[t].x + ww[t];
+                        if ((b2 & 2u) && dv[t].y != kInf && dv[t].y + ww[t] < p1) p1 = dv[t].y + ww[t];
+                    }
+                    uint64_t* urow = &p.D[(uint64_t)u * R + i0];
+                    if (p0 < du0) {
+                        du0 = p0; ub2 |= 1u; ++up0; um0 = p0 < um0 ? p0 : um0;
+                        atomicMin(reinterpret_cast<unsigned long long*>(urow), (unsigned long long)p0);
+                    }
+                    if (p1 < du1) {
+                        du1 = p1; ub2 |= 2u; ++up1; um1 = p1 < um1 ? p1 : um1;
+                        atomicMin(reinterpret_cast<unsigned long long*>(urow + 1), (unsigned long long)p1);
+                    }
+                }
+                uint32_t my_vt = 0;
+                uint64_t my_nb = 0;
+#pragma unroll
+                for (int t = 0; t < 4; ++t) {
+                    uint32_t imp = 0;
+                    if (e0 + t < len) {
+                        uint64_t* row = &p.D[(uint64_t)vv[t] * R + i0];
+                        if ((b2 & 1u) && du0 != kInf) {
+                            const uint64_t cnd = du0 + ww[t];
+                            if (cnd < dv[t].x) {
+                                atomicMin(reinterpret_cast<unsigned long long*>(row), (unsigned long long)cnd);
+                                imp |= 1u; ++up0; um0 = cnd < um0 ? cnd : um0;
+                            }
+                        }
+                        if ((b2 & 2u) && du1 != kInf) {
+                            const uint64_t cnd = du1 + ww[t];
+                            if (cnd < dv[t].y) {
+                                atomicMin(reinterpret_cast<unsigned long long*>(row + 1), (unsigned long long)cnd);
+                                imp |= 2u; ++up1; um1 = cnd < um1 ? cnd : um1;
+                            }
+                        }
+                    }
+                    const uint64_t nb = lane_pairs_or(imp, lane);
+                    if (lane == (uint32_t)t) { my_vt = vv[t]; my_nb = nb; }
+                }
+                const uint64_t old = (lane < 4 && my_nb)
+                                         ? atomicOr(reinterpret_cast<unsigned long long*>(&p.QM[my_vt]),
+                                                    (unsigned long long)my_nb)
+                                         : 0ull;
+                const uint64_t newly = my_nb & ~old;
+                stage_push(lane < 4 && my_nb != 0 && old == 0, my_vt, stage, stc, lane);
+#pragma unroll
+                for (int t = 0; t < 4; ++t) {
+                    const uint64_t nw = __shfl_sync(FULL_MASK, newly, t);
+                    qn0 += (nw >> i0) & 1ull;
+                    qn1 += (nw >> (i0 + 1)) & 1ull;
+                }
+            }
+            ubits = lane_pairs_or(ub2, lane);
         }
-        // Update(v): one test-and-set of the improved bits on v's mask; the
-        // bits pulled into u update u's mask (lane 0)
-        const uint64_t old = newb ? atomicOr(reinterpret_cast<unsigned long long*>(&p.QM[ed.x]),
-                                             (unsigned long long)newb) : 0ull;
-        const uint64_t newly = newb & ~old;
-        stage_push(newb != 0 && old == 0, ed.x, stage, stc, lane);
+        // the bits pulled into u update u's mask (Update(u), lane 0)
         if (ubits) {  // warp-uniform
             uint64_t uold = 0;
             if (lane == 0) uold = atomicOr(reinterpret_cast<unsigned long long*>(&p.QM[u]), (unsigned long long)ubits);
@@ -474,16 +661,6 @@ __device__ void ms_phase_R(const MsParams& p, uint64_t k, MsSmem& S, uint32_t* s
             const uint64_t unew = ubits & ~uold;
             qn0 += (unew >> i0) & 1ull;
             qn1 += (unew >> (i0 + 1)) & 1ull;
-        }
-        // newly queued bits per instance: lane l counts instances 2l, 2l+1
-        {
-            uint64_t mm = fmk;
-            while (mm) {  // warp-uniform
-                const uint32_t it = (uint32_t)(__ffsll((long long)mm) - 1);
-                mm &= mm - 1;
-                const uint32_t cnt = __popc(__ballot_sync(FULL_MASK, (newly >> it) & 1ull));
-                if (lane == (it >> 1)) { if (it & 1u) qn1 += cnt; else qn0 += cnt; }
-            }
         }
         if (stc > (uint32_t)kStage - kMsRec - 1u) stage_flush(stage, stc, lane, &p.ctrl->usize[nx], &p.ctrl->status, Qnext, p.n);
     }
@@ -556,7 +733,8 @@ __global__ void __launch_bounds__(kMsBlock, 1) ms_batch_kernel(MsParams p)
         ms_phase_T(p, k, U, S, s_keys);
         if (blockIdx.x == 0 && tid == 0) {
             ctrl->usize[pv] = 0;
-            ctrl->nrec[pv] = 0;
+            ctrl->nsmall[pv] = 0;
+            ctrl->nbig[pv] = 0;
             if (S.err) raise_error(&ctrl->bar, &ctrl->status, SSSP_ERR_INTERNAL);
             if (global_timer_ns() - S.t_start > p.solve_timeout_ns) raise_error(&ctrl->bar, &ctrl->status, SSSP_ERR_TIMEOUT);
         }
@@ -671,8 +849,9 @@ int ms_solve_sources(const sssp_graph* g, const uint32_t* sources, uint32_t k, s
     if (rc != SSSP_OK) return rc;
     const uint32_t R = (k + 3) & ~3u;
     const uint64_t n = g->n;
-    const size_t need = a256(8ull * n * R) + a256(8ull * n) + 2 * a256(4ull * n) + a256(16ull * g->ms_rec_cap) +
-                        a256(8ull * g->ms_rec_cap);
+    const uint64_t rec_cap = g->fsmall_cap + g->ms_rec_cap;  // degree 1..32: one each; larger: 32 edges each
+    const size_t need = a256(8ull * n * R) + a256(8ull * n) + 2 * a256(4ull * n) + a256(16ull * rec_cap) +
+                        a256(8ull * rec_cap);
     if (need > w.bytes) {
         cudaDeviceSynchronize();
         cudaFree(w.buf);
@@ -688,9 +867,10 @@ int ms_solve_sources(const sssp_graph* g, const uint32_t* sources, uint32_t k, s
     p.QM = reinterpret_cast<uint64_t*>(b); b += a256(8ull * n);
     p.qa = reinterpret_cast<uint32_t*>(b); b += a256(4ull * n);
     p.qb = reinterpret_cast<uint32_t*>(b); b += a256(4ull * n);
-    p.rec = reinterpret_cast<uint4*>(b); b += a256(16ull * g->ms_rec_cap);
+    p.rec = reinterpret_cast<uint4*>(b); b += a256(16ull * rec_cap);
     p.fm = reinterpret_cast<uint64_t*>(b);
-    p.rec_cap = g->ms_rec_cap;
+    p.small_cap = g->fsmall_cap;
+    p.big_cap = g->ms_rec_cap;
     // the staging is reused: wait until the previous call's copy has left it
     if ((e = cudaEventSynchronize(w.copied)) != cudaSuccess) return ms_fail(e);
     uint64_t max_param = 1;

@@ -462,7 +462,7 @@ def measure_workload(name, sssp, torch, stream, stream_obj, rates_x=(2, 20), cpu
 
 
 def measure_serving(sssp, G, g, torch, sources, rates, window_s=1.0, hard_s=10.0, slots=0,
-                    algo=None, param=0, seed=8, tuned=False) -> dict:
+                    algo=None, param=0, seed=8, tuned=False, gang=0, gang_wait_ns=0) -> dict:
     """Serving: a Poisson query stream at each offered rate
     for `window_s` seconds against the resident graph; queries go to the
     continuous-batching server as client-side result buffers allow.  Latency
@@ -473,7 +473,7 @@ def measure_serving(sssp, G, g, torch, sources, rates, window_s=1.0, hard_s=10.0
     with the single solve of its source after the window (`checked`,
     `all_equal`)."""
     algo = sssp.SSSP_RHO if algo is None else algo
-    srv = sssp.sssp_server_create(G.handle, slots=slots, algo=algo, param=param)
+    srv = sssp.sssp_server_create(G.handle, slots=slots, algo=algo, param=param, gang=gang, gang_wait_ns=gang_wait_ns)
     S = sssp.sssp_server_slots(srv)
     nbuf = S + 32
     free_b, _ = torch.cuda.mem_get_info()
@@ -498,7 +498,8 @@ def measure_serving(sssp, G, g, torch, sources, rates, window_s=1.0, hard_s=10.0
         plain_one(s_)
     plain_qps = nplain / (time.perf_counter() - t0)
     rng = np.random.default_rng(seed)
-    out = {"slots": S, "result_buffers": nbuf, "plain_queries_per_s": plain_qps, "rates": []}
+    out = {"slots": S, "mode": "shared" if sssp.sssp_server_mode(srv) == sssp.SSSP_BATCH_SHARED else "separate",
+           "result_buffers": nbuf, "plain_queries_per_s": plain_qps, "rates": []}
     for rate in rates:
         arr = np.cumsum(rng.exponential(1.0 / rate, size=int(rate * window_s * 1.2) + 16))
         arr = arr[arr < window_s]

@@ -331,6 +331,16 @@ typedef struct {
     uint64_t idle_ns;      /* the device loop exits after this long without a query  */
                            /* (0 = 2 ms; at most 1 s); it restarts on the next query */
     double hbm_fraction;   /* share of free HBM the slots may take (0 = 0.5)         */
+    uint32_t batch_mode;   /* SSSP_BATCH_*: SHARED runs the slots as the instances of */
+                           /* one shared edge scan (at most 64 slots; rho, Delta*,    */
+                           /* Bellman-Ford), SEPARATE as independent instances; AUTO */
+                           /* (0) follows the graph's batch tuning, else SHARED where */
+                           /* it applies                                              */
+    uint32_t gang;         /* SHARED: waiting queries are admitted together once this */
+                           /* many wait (queries that start together stay aligned,    */
+                           /* which is what the shared scan shares), when nothing    */
+                           /* else runs, or after gang_wait_ns; 0 = every slot        */
+    uint64_t gang_wait_ns; /* 0 = 20 ms; at most 1 s                                  */
 } sssp_server_config;
 
 typedef struct {
@@ -343,18 +353,25 @@ typedef struct {
 } sssp_query_info;
 
 /*
- * Create a server for graph g.  Slots are admitted by free HBM: each slot's
- * working memory (queue bitmap, two queue lists, extraction records) comes out
- * of hbm_fraction of the free device memory, capped at SSSP_MAX_BATCH and at
- * cfg->slots.  Starts a host thread that assigns queries to slots, keeps the
- * device loop running while there is work and collects completions (through
- * host-mapped memory).  While the device loop runs it occupies every SM.
- * Errors: INVALID_ARG, OUT_OF_MEMORY (not one slot fits), CUDA.
+ * Create a server for graph g.  Slots are admitted by free HBM: the slots'
+ * working memory comes out of hbm_fraction of the free device memory, capped
+ * at cfg->slots (and at SSSP_MAX_BATCH, or 64 in SSSP_BATCH_SHARED mode).  In
+ * SHARED mode the slots are the instances of one shared edge scan (per slot
+ * one vertex-major distance column: a query's column is reset when it is
+ * admitted and copied to its dist_out when its queue empties); in SEPARATE
+ * mode each slot has its own queue bitmap, lists and records.  Starts a host
+ * thread that assigns queries to slots, keeps the device loop running while
+ * there is work and collects completions (through host-mapped memory).  While
+ * the device loop runs it occupies every SM.  Errors: INVALID_ARG (also SHARED
+ * for a rule it does not cover), OUT_OF_MEMORY (not one slot fits), CUDA.
  */
 int sssp_server_create(const sssp_graph* g, const sssp_server_config* cfg, sssp_server** out);
 
 /* Number of slots the server got. */
 int sssp_server_slots(const sssp_server* s, uint32_t* slots);
+
+/* The SSSP_BATCH_* mode the server runs its slots in (SHARED or SEPARATE). */
+int sssp_server_mode(const sssp_server* s, uint32_t* mode);
 
 /*
  * Queue a query; non-blocking, thread-safe.  dist_out: caller-owned DEVICE

@@ -566,26 +566,6 @@ __global__ void __launch_bounds__(kBlock, 1) batch_kernel(BatchParams p)
 // overlaps on the device (continuous batching).  With no query left the loop
 // waits a bounded idle time for new commands, then the kernel exits.
 // ---------------------------------------------------------------------------
-struct SlotCmd {                  // written by the host
-    unsigned long long ticket;
-    unsigned long long dist_ptr;  // caller-owned device uint64[n]
-    unsigned int source;
-    unsigned int seq;             // written last
-};
-struct SlotDone {                 // written by the device
-    unsigned long long ticket;
-    unsigned long long t_admit_ns, t_done_ns;
-    unsigned long long edges, extracted;
-    unsigned int steps;
-    int status;
-    unsigned int seq;             // written last
-    unsigned int pad;
-};
-struct ServeShared {              // host-mapped
-    unsigned long long submitted; // host: commands written so far (monotone)
-    unsigned int stop;            // host: leave the loop
-    unsigned int pad;
-};
 struct ServeState {               // device memory, kept across launches
     unsigned long long seen_submitted;
     unsigned long long step;      // last global step run
@@ -603,22 +583,6 @@ struct ServeParams {
     uint64_t param;
 };
 
-__device__ __forceinline__ unsigned int ld_acquire_sys_u32(const unsigned int* p)
-{
-    unsigned int v;
-    asm volatile("ld.acquire.sys.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
-    return v;
-}
-__device__ __forceinline__ unsigned long long ld_acquire_sys_u64(const unsigned long long* p)
-{
-    unsigned long long v;
-    asm volatile("ld.acquire.sys.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
-    return v;
-}
-__device__ __forceinline__ void st_release_sys_u32(unsigned int* p, unsigned int v)
-{
-    asm volatile("st.release.sys.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
-}
 
 // Block 0 only: retire finished slots, admit new commands; returns (in every
 // thread of block 0) false when the loop should exit.
@@ -1001,6 +965,7 @@ struct sssp_server {
     bool kernel_running = false;
     uint64_t launches = 0;
     int fatal = SSSP_OK;
+    sssp::MsServer* ms = nullptr;         // shared-scan slots (SSSP_BATCH_SHARED), else separate instances
 };
 
 namespace sssp {
@@ -1087,10 +1052,16 @@ void server_loop(sssp_server* s)
         // keep the device loop alive while there is work
         if (s->kernel_running && cudaStreamQuery(s->stream) == cudaSuccess) {
             s->kernel_running = false;
-            BatchCtrl hc;
-            if (cudaMemcpy(&hc, s->d_ctrl, sizeof hc, cudaMemcpyDeviceToHost) == cudaSuccess && hc.status != 0) {
+            int status = SSSP_OK;
+            if (s->ms) {
+                status = ms_server_status(s->ms);
+            } else {
+                BatchCtrl hc;
+                if (cudaMemcpy(&hc, s->d_ctrl, sizeof hc, cudaMemcpyDeviceToHost) == cudaSuccess) status = hc.status;
+            }
+            if (status != SSSP_OK) {
                 std::lock_guard<std::mutex> lk(s->mu);
-                s->fatal = hc.status;
+                s->fatal = status;
                 s->cv.notify_all();
                 break;
             }
@@ -1105,10 +1076,15 @@ void server_loop(sssp_server* s)
             }
             if (need) {
                 void* args[] = {&sp};
-                cudaError_t e = cudaMemsetAsync(s->d_ctrl, 0, sizeof(BatchCtrl), s->stream);
-                if (e == cudaSuccess)
-                    e = cudaLaunchCooperativeKernel(serve_kernel_ptr(), dim3(s->grid), dim3(kBlock), args,
-                                                    kBatchDynSmem, s->stream);
+                cudaError_t e = cudaSuccess;
+                if (s->ms) {
+                    e = ms_server_launch(s->ms, s->stream) == SSSP_OK ? cudaSuccess : cudaErrorLaunchFailure;
+                } else {
+                    e = cudaMemsetAsync(s->d_ctrl, 0, sizeof(BatchCtrl), s->stream);
+                    if (e == cudaSuccess)
+                        e = cudaLaunchCooperativeKernel(serve_kernel_ptr(), dim3(s->grid), dim3(kBlock), args,
+                                                        kBatchDynSmem, s->stream);
+                }
                 if (e != cudaSuccess) {
                     std::lock_guard<std::mutex> lk(s->mu);
                     s->fatal = SSSP_ERR_CUDA;
@@ -1212,7 +1188,7 @@ int sssp_server_create(const sssp_graph* g, const sssp_server_config* cfg, sssp_
     memset(&c, 0, sizeof c);
     if (cfg) c = *cfg;
     if (!algo_valid(c.algo)) return SSSP_ERR_INVALID_ARG;
-    if (c.idle_ns > 1000000000ull) return SSSP_ERR_INVALID_ARG;
+    if (c.idle_ns > 1000000000ull || c.gang_wait_ns > 1000000000ull) return SSSP_ERR_INVALID_ARG;
     cudaError_t e = cudaSetDevice(g->device);
     if (e != cudaSuccess) return fail(e);
     sssp_server* s = new (std::nothrow) sssp_server();
@@ -1223,42 +1199,39 @@ int sssp_server_create(const sssp_graph* g, const sssp_server_config* cfg, sssp_
     s->param = c.param ? c.param : sssp_graph_batch_param(g, c.algo);
     if (algo_needs_param(s->algo) && s->param == 0) { delete s; return SSSP_ERR_INVALID_ARG; }
     s->idle_ns = c.idle_ns ? c.idle_ns : 2000000ull;
-    // admission by free HBM: per-slot working memory out of a fraction of what is free
-    const size_t per_slot = instance_scratch_bytes(g->n, g->fsmall_cap, g->item_cap);
+    // the slots' kernel: one shared edge scan (SSSP_BATCH_SHARED) or separate instances
+    if (c.batch_mode > SSSP_BATCH_SEPARATE) { delete s; return SSSP_ERR_INVALID_ARG; }
+    sssp_tuning bt;
+    const bool btuned = sssp_lookup_batch_tuning(g, &bt) && bt.algo == c.algo;
+    uint32_t mode = c.batch_mode;
+    if (mode == SSSP_BATCH_AUTO) {
+        mode = btuned && bt.batch_mode ? bt.batch_mode : SSSP_BATCH_SHARED;
+        if (mode == SSSP_BATCH_SHARED && !ms_batch_supported(c.algo, 1)) mode = SSSP_BATCH_SEPARATE;
+    } else if (mode == SSSP_BATCH_SHARED && !ms_batch_supported(c.algo, 1)) {
+        delete s;
+        return SSSP_ERR_INVALID_ARG;
+    }
+    // admission by free HBM: the slots' working memory out of a fraction of what is free
     size_t free_b = 0, total_b = 0;
     if ((e = cudaMemGetInfo(&free_b, &total_b)) != cudaSuccess) { delete s; return fail(e); }
     const double frac = (c.hbm_fraction > 0.0 && c.hbm_fraction <= 1.0) ? c.hbm_fraction : 0.5;
-    uint64_t fit = (uint64_t)((double)free_b * frac) / (per_slot ? per_slot : 1);
-    uint64_t want = c.slots ? c.slots : kMaxBatch;
-    {
-        sssp_tuning bt;
-        if (!c.slots && g->batch_tuned && sssp_lookup_batch_tuning(g, &bt) && bt.slots) want = bt.slots;
+    const uint64_t budget = (uint64_t)((double)free_b * frac);
+    const uint64_t cap = mode == SSSP_BATCH_SHARED ? 64u : kMaxBatch;
+    uint64_t want = c.slots ? c.slots : cap;
+    if (!c.slots && g->batch_tuned && btuned && bt.slots) want = bt.slots;
+    if (want > cap) want = cap;
+    const size_t per_slot = instance_scratch_bytes(g->n, g->fsmall_cap, g->item_cap);
+    if (mode == SSSP_BATCH_SHARED) {
+        while (want > 0 && ms_server_bytes(g, (uint32_t)want) > budget) --want;
+    } else {
+        const uint64_t fit = budget / (per_slot ? per_slot : 1);
+        if (fit < want) want = fit;
     }
-    if (want > kMaxBatch) want = kMaxBatch;
-    if (fit < want) want = fit;
     if (want == 0) { delete s; return SSSP_ERR_OUT_OF_MEMORY; }
     s->S = (uint32_t)want;
     s->slots.resize(s->S);
-    int rc = batch_blocks(g->device, &s->grid);
-    if (rc != SSSP_OK) { delete s; return rc; }
-    {
-        const void* fn = serve_kernel_ptr();
-        e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kBatchDynSmem);
-        int bps = 0;
-        if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, fn, kBlock, kBatchDynSmem);
-        if (e != cudaSuccess || bps < 1) { delete s; return e != cudaSuccess ? fail(e) : SSSP_ERR_CUDA; }
-        int sms = 0;
-        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, g->device);
-        s->grid = (uint32_t)(bps * sms);
-    }
-    s->sample_cap = s->algo == SSSP_RHO ? rho_sample_bound(g->n, s->param) : 1;
     const size_t S = s->S;
-    if ((e = cudaMalloc(&s->scratch, per_slot * S)) != cudaSuccess ||
-        (e = cudaMalloc(reinterpret_cast<void**>(&s->d_desc), sizeof(InstDesc) * S)) != cudaSuccess ||
-        (e = cudaMalloc(reinterpret_cast<void**>(&s->d_ictrl), sizeof(InstCtrl) * S)) != cudaSuccess ||
-        (e = cudaMalloc(reinterpret_cast<void**>(&s->d_ctrl), sizeof(BatchCtrl))) != cudaSuccess ||
-        (e = cudaMalloc(reinterpret_cast<void**>(&s->d_state), sizeof(ServeState))) != cudaSuccess ||
-        (e = cudaHostAlloc(reinterpret_cast<void**>(&s->h_cmd), sizeof(SlotCmd) * S, cudaHostAllocMapped)) != cudaSuccess ||
+    if ((e = cudaHostAlloc(reinterpret_cast<void**>(&s->h_cmd), sizeof(SlotCmd) * S, cudaHostAllocMapped)) != cudaSuccess ||
         (e = cudaHostAlloc(reinterpret_cast<void**>(&s->h_done), sizeof(SlotDone) * S, cudaHostAllocMapped)) != cudaSuccess ||
         (e = cudaHostAlloc(reinterpret_cast<void**>(&s->h_shared), sizeof(ServeShared), cudaHostAllocMapped)) != cudaSuccess ||
         (e = cudaHostGetDevicePointer(reinterpret_cast<void**>(&s->d_cmd), s->h_cmd, 0)) != cudaSuccess ||
@@ -1271,6 +1244,38 @@ int sssp_server_create(const sssp_graph* g, const sssp_server_config* cfg, sssp_
     memset(s->h_cmd, 0, sizeof(SlotCmd) * S);
     memset(s->h_done, 0, sizeof(SlotDone) * S);
     memset(s->h_shared, 0, sizeof(ServeShared));
+    if (mode == SSSP_BATCH_SHARED) {
+        uint32_t red = kRhoReducedDefault;
+        if (btuned && bt.rho_reduced) red = bt.rho_reduced == SSSP_RHO_REDUCED_NONE ? 0u : bt.rho_reduced;
+        const bool bidir = btuned && (bt.flags & SSSP_SOLVE_BIDIRECTIONAL);
+        const int rc = ms_server_create(g, s->S, s->algo, s->param, red, bidir, s->d_cmd, s->d_done, s->d_shared,
+                                        s->idle_ns, c.gang, c.gang_wait_ns, &s->ms);
+        if (rc != SSSP_OK) { sssp_server_destroy(s); return rc; }
+        s->worker = std::thread(server_loop, s);
+        *out = s;
+        return SSSP_OK;
+    }
+    int rc = batch_blocks(g->device, &s->grid);
+    if (rc != SSSP_OK) { sssp_server_destroy(s); return rc; }
+    {
+        const void* fn = serve_kernel_ptr();
+        e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kBatchDynSmem);
+        int bps = 0;
+        if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, fn, kBlock, kBatchDynSmem);
+        if (e != cudaSuccess || bps < 1) { sssp_server_destroy(s); return e != cudaSuccess ? fail(e) : SSSP_ERR_CUDA; }
+        int sms = 0;
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, g->device);
+        s->grid = (uint32_t)(bps * sms);
+    }
+    s->sample_cap = s->algo == SSSP_RHO ? rho_sample_bound(g->n, s->param) : 1;
+    if ((e = cudaMalloc(&s->scratch, per_slot * S)) != cudaSuccess ||
+        (e = cudaMalloc(reinterpret_cast<void**>(&s->d_desc), sizeof(InstDesc) * S)) != cudaSuccess ||
+        (e = cudaMalloc(reinterpret_cast<void**>(&s->d_ictrl), sizeof(InstCtrl) * S)) != cudaSuccess ||
+        (e = cudaMalloc(reinterpret_cast<void**>(&s->d_ctrl), sizeof(BatchCtrl))) != cudaSuccess ||
+        (e = cudaMalloc(reinterpret_cast<void**>(&s->d_state), sizeof(ServeState))) != cudaSuccess) {
+        sssp_server_destroy(s);
+        return fail(e);
+    }
     std::vector<InstDesc> desc(S);
     unsigned char* base = static_cast<unsigned char*>(s->scratch);
     for (size_t i = 0; i < S; ++i) {
@@ -1304,6 +1309,13 @@ int sssp_server_slots(const sssp_server* s, uint32_t* slots)
 {
     if (!s || !slots) return SSSP_ERR_INVALID_ARG;
     *slots = s->S;
+    return SSSP_OK;
+}
+
+int sssp_server_mode(const sssp_server* s, uint32_t* mode)
+{
+    if (!s || !mode) return SSSP_ERR_INVALID_ARG;
+    *mode = s->ms ? SSSP_BATCH_SHARED : SSSP_BATCH_SEPARATE;
     return SSSP_OK;
 }
 
@@ -1395,6 +1407,7 @@ int sssp_server_destroy(sssp_server* s)
     }
     if (s->worker.joinable()) s->worker.join();
     if (s->stream) { cudaStreamSynchronize(s->stream); cudaStreamDestroy(s->stream); }
+    ms_server_destroy(s->ms);
     cudaFree(s->scratch);
     cudaFree(s->d_desc);
     cudaFree(s->d_ictrl);

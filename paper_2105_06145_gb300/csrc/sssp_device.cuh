@@ -50,6 +50,25 @@ __device__ __forceinline__ unsigned long long ld_acquire_u64(const unsigned long
 
 __device__ __forceinline__ void set_status(int* status, int code) { atomicCAS(status, 0, code); }
 
+// System-scope acquire / release accesses to host-mapped memory (the
+// servers' command and completion records).
+__device__ __forceinline__ unsigned int ld_acquire_sys_u32(const unsigned int* p)
+{
+    unsigned int v;
+    asm volatile("ld.acquire.sys.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+__device__ __forceinline__ unsigned long long ld_acquire_sys_u64(const unsigned long long* p)
+{
+    unsigned long long v;
+    asm volatile("ld.acquire.sys.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+    return v;
+}
+__device__ __forceinline__ void st_release_sys_u32(unsigned int* p, unsigned int v)
+{
+    asm volatile("st.release.sys.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
 // splitmix64 (Steele, Lea, Flood 2014): output k of the generator started at
 // state `seed` is mix(seed + (k+1) * golden_gamma).
 __device__ __forceinline__ uint64_t splitmix64_at(uint64_t seed, uint64_t k)

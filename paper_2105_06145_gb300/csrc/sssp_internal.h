@@ -160,6 +160,40 @@ constexpr uint32_t kMaxBatch = 2048;        // instances per batched launch
 const void* batch_kernel_ptr();
 const void* serve_kernel_ptr();
 
+// Query servers: one command and one completion record per slot in
+// host-mapped memory, and the host's submission counter / stop flag.
+struct SlotCmd {                  // written by the host
+    unsigned long long ticket;
+    unsigned long long dist_ptr;  // caller-owned device uint64[n]
+    unsigned int source;
+    unsigned int seq;             // written last
+};
+struct SlotDone {                 // written by the device
+    unsigned long long ticket;
+    unsigned long long t_admit_ns, t_done_ns;
+    unsigned long long edges, extracted;
+    unsigned int steps;
+    int status;
+    unsigned int seq;             // written last
+    unsigned int pad;
+};
+struct ServeShared {              // host-mapped
+    unsigned long long submitted; // host: commands written so far (monotone)
+    unsigned int stop;            // host: leave the loop
+    unsigned int pad;
+};
+
+// The shared-scan server's device state (sssp_msbatch.cu): a persistent loop
+// over S <= 64 query slots that are the instances of the shared-scan kernel.
+struct MsServer;
+size_t ms_server_bytes(const sssp_graph* g, uint32_t S);
+int ms_server_create(const sssp_graph* g, uint32_t S, sssp_algo algo, uint64_t param, uint32_t rho_reduced,
+                     bool bidir, SlotCmd* d_cmd, SlotDone* d_done, ServeShared* d_shared, uint64_t idle_ns,
+                     uint32_t gang, uint64_t gang_wait_ns, MsServer** out);
+int ms_server_launch(MsServer* s, cudaStream_t st);
+int ms_server_status(MsServer* s);      // device status after the loop returned (synchronous)
+void ms_server_destroy(MsServer* s);
+
 // Batched solves of k <= 64 sources on one graph with one shared edge scan
 // per step (sssp_msbatch.cu): outs[i] receives instance i's distances.
 bool ms_batch_supported(sssp_algo algo, uint32_t k);

@@ -38,6 +38,7 @@
 #include <cstdint>
 #include <cstring>
 #include <mutex>
+#include <new>
 #include <vector>
 
 #include <cuda_runtime.h>
@@ -767,6 +768,248 @@ __global__ void __launch_bounds__(kMsBlock, 1) ms_batch_kernel(MsParams p)
 }
 
 // ---------------------------------------------------------------------------
+// Serving with the shared scan: a long-lived loop over S <= 64 query slots
+// that are the kernel's instances.  At each step boundary block 0 retires the
+// slots whose queue emptied (their column of D is copied to the caller's
+// output by every block before the completion record is released) and admits
+// newly submitted queries into free slots (their column is reset by every
+// block, then the source is queued); admitted queries join the running ones
+// at that step (continuous batching).  With no query left the loop waits a
+// bounded idle time for a command, then the kernel returns.
+// ---------------------------------------------------------------------------
+struct MsServeState {                 // device memory, kept across launches
+    unsigned long long seen_submitted;
+    unsigned long long step;          // last global step run
+    unsigned int nretire, nadmit, exit_flag, pad;
+    unsigned int retire[kMsMax], admit[kMsMax];
+    unsigned int running[kMsMax], seq[kMsMax];
+    unsigned long long ticket[kMsMax], t_admit[kMsMax], admit_step[kMsMax], dist_ptr[kMsMax];
+    unsigned int source[kMsMax];      // caller's id
+    unsigned long long seen_ns[kMsMax];  // device time a slot's waiting command was first seen (0: none)
+};
+
+struct MsServeParams {
+    MsParams p;                       // p.src / p.param: device arrays of S entries, written at admission
+    uint32_t* src_w;
+    SlotCmd* cmd;
+    SlotDone* done;
+    ServeShared* shared;
+    MsServeState* st;
+    uint64_t idle_ns;
+    uint64_t param;
+    uint32_t gang;                    // admit when this many commands wait, the device is idle,
+    uint64_t gang_wait_ns;            // or the oldest waiting command is this old
+};
+
+// Block 0: which slots retire (queue empty at step k) and which free slots
+// take a new command; exit_flag when the loop should return.
+__device__ void ms_serve_decide(const MsServeParams& sp, uint64_t k, MsSmem& S)
+{
+    const MsParams& p = sp.p;
+    MsServeState* st = sp.st;
+    const uint32_t tid = threadIdx.x;
+    const int c = (int)(k % 3);
+    if (tid == 0) { st->nretire = 0; st->nadmit = 0; }
+    __syncthreads();
+    for (uint32_t i = tid; i < p.K; i += kMsBlock)
+        if (st->running[i] && ldcg32(&p.inst[i].qsize[c]) == 0) st->retire[atomicAdd(&st->nretire, 1u)] = i;
+    __syncthreads();
+    for (;;) {
+        if (tid == 0) {
+            const unsigned long long sub = ld_acquire_sys_u64(&sp.shared->submitted);
+            S.scnt = sub != st->seen_submitted;
+            st->seen_submitted = sub;
+        }
+        __syncthreads();
+        // free slots holding a command not yet admitted (queries that start
+        // together stay aligned step by step, which is what the shared scan
+        // shares, so they are admitted as a gang: when sp.gang of them wait,
+        // when nothing else runs, or when the oldest has waited gang_wait_ns)
+        if (tid == 0) { S.base[1] = 0; S.t_start = ~0ull; }
+        __syncthreads();
+        const unsigned long long now = global_timer_ns();
+        for (uint32_t i = tid; i < p.K; i += kMsBlock) {
+            if (st->running[i]) continue;
+            const unsigned int cs = ld_acquire_sys_u32(&sp.cmd[i].seq);
+            if (cs == st->seq[i]) continue;
+            if (st->seen_ns[i] == 0) st->seen_ns[i] = now;
+            atomicAdd(&S.base[1], 1u);
+            atomicMin(&S.t_start, (unsigned long long)st->seen_ns[i]);
+        }
+        uint32_t live0 = 0;
+        for (uint32_t i = tid; i < p.K; i += kMsBlock) {
+            bool retiring = false;
+            for (uint32_t r = 0; r < st->nretire; ++r) retiring |= st->retire[r] == i;
+            live0 += (st->running[i] && !retiring) ? 1u : 0u;
+        }
+        live0 = __syncthreads_count(live0 != 0);
+        const bool take = S.base[1] >= sp.gang || live0 == 0 ||
+                          (S.base[1] > 0 && now - S.t_start >= sp.gang_wait_ns);
+        if (take) {
+            for (uint32_t i = tid; i < p.K; i += kMsBlock) {
+                if (st->running[i]) continue;
+                const unsigned int cs = ld_acquire_sys_u32(&sp.cmd[i].seq);
+                if (cs == st->seq[i]) continue;
+                const volatile SlotCmd* cm = &sp.cmd[i];
+                st->dist_ptr[i] = cm->dist_ptr;
+                st->source[i] = cm->source < p.n ? cm->source : 0u;
+                st->ticket[i] = cm->ticket;
+                st->seq[i] = cs;
+                st->seen_ns[i] = 0;
+                st->admit[atomicAdd(&st->nadmit, 1u)] = i;
+            }
+        }
+        __syncthreads();
+        uint32_t live = 0;
+        for (uint32_t i = tid; i < p.K; i += kMsBlock) {
+            bool retiring = false;
+            for (uint32_t r = 0; r < st->nretire; ++r) retiring |= st->retire[r] == i;
+            live += (st->running[i] && !retiring) ? 1u : 0u;
+        }
+        live = __syncthreads_count(live != 0);
+        if (tid == 0) {
+            S.base[0] = 0;  // 0: run, 1: a command came while idle, 2: leave
+            if (ld_acquire_sys_u32(&sp.shared->stop)) {
+                S.base[0] = 2;
+            } else if (live == 0 && st->nadmit == 0 && st->nretire == 0) {
+                const unsigned long long t0 = global_timer_ns();
+                S.base[0] = 2;
+                while (global_timer_ns() - t0 < sp.idle_ns) {
+                    if (ld_acquire_sys_u64(&sp.shared->submitted) != st->seen_submitted) { S.base[0] = 1; break; }
+                    if (ld_acquire_sys_u32(&sp.shared->stop)) break;
+                    __nanosleep(2000);
+                }
+            }
+            st->exit_flag = S.base[0] == 2 ? 1u : 0u;
+        }
+        __syncthreads();
+        if (S.base[0] != 1) return;
+    }
+}
+
+// Block 0, after the columns were copied / reset: completion records of the
+// retired slots, then the admitted queries' sources are queued.
+__device__ void ms_serve_publish(const MsServeParams& sp, uint64_t k)
+{
+    const MsParams& p = sp.p;
+    MsServeState* st = sp.st;
+    const uint32_t tid = threadIdx.x;
+    const int c = (int)(k % 3), pv = (int)((k + 2) % 3);
+    uint32_t* Qcur = (k & 1) ? p.qa : p.qb;
+    for (uint32_t r = tid; r < st->nretire; r += kMsBlock) {
+        const uint32_t i = st->retire[r];
+        MsInst* I = &p.inst[i];
+        SlotDone* D = &sp.done[i];
+        D->ticket = st->ticket[i];
+        D->t_admit_ns = st->t_admit[i];
+        D->t_done_ns = global_timer_ns();
+        D->edges = I->edges + I->fedges[pv];
+        D->extracted = I->extracted + I->fext[pv];
+        D->steps = (unsigned int)(k - st->admit_step[i]);
+        D->status = *reinterpret_cast<volatile int*>(&p.ctrl->status);
+        __threadfence_system();
+        st_release_sys_u32(&D->seq, st->seq[i]);
+        st->running[i] = 0;
+        memset(I, 0, sizeof(MsInst));
+        I->qmin[0] = kInf; I->qmin[1] = kInf; I->qmin[2] = kInf;
+    }
+    for (uint32_t a = tid; a < st->nadmit; a += kMsBlock) {
+        const uint32_t i = st->admit[a];
+        const uint32_t caller = st->source[i];
+        const uint32_t s = p.perm ? p.perm[caller] : caller;
+        sp.src_w[i] = s;
+        p.D[(uint64_t)s * p.R + i] = 0ull;
+        const unsigned long long old = atomicOr(reinterpret_cast<unsigned long long*>(&p.QM[s]), 1ull << i);
+        if (old == 0) Qcur[atomicAdd(&p.ctrl->usize[c], 1u)] = s;
+        MsInst* I = &p.inst[i];
+        memset(I, 0, sizeof(MsInst));
+        I->qmin[0] = kInf; I->qmin[1] = kInf; I->qmin[2] = kInf;
+        I->qsize[c] = 1;
+        I->qmin[c] = 0;
+        st->admit_step[i] = k;
+        st->t_admit[i] = global_timer_ns();
+        st->running[i] = 1;
+    }
+}
+
+__global__ void __launch_bounds__(kMsBlock, 1) ms_serve_kernel(MsServeParams sp)
+{
+    extern __shared__ __align__(16) unsigned char s_dyn[];
+    uint32_t* s_stage = reinterpret_cast<uint32_t*>(s_dyn);
+    uint64_t* s_keys = reinterpret_cast<uint64_t*>(s_dyn);
+    __shared__ MsSmem S;
+    const MsParams& p = sp.p;
+    const uint32_t tid = threadIdx.x, wid = tid >> 5;
+    const uint64_t gthreads = (uint64_t)gridDim.x * kMsBlock;
+    const uint64_t gtid = (uint64_t)blockIdx.x * kMsBlock + tid;
+    MsCtrl* ctrl = p.ctrl;
+    MsServeState* st = sp.st;
+    uint32_t* stage = s_stage + wid * kStage;
+    if (tid == 0) {
+        S.bar_target = 0;
+        S.err = 0;
+    }
+    for (uint32_t i = tid; i < kMsMax; i += kMsBlock) {
+        S.cnt[0][i] = 0; S.cnt[1][i] = 0; S.cnt[2][i] = 0; S.cnt[3][i] = 0; S.mn[i] = kInf;
+    }
+    __syncthreads();
+    uint64_t k = ldcg64((const uint64_t*)&st->step) + 1;
+    for (;;) {
+        const int c = (int)(k % 3), pv = (int)((k + 2) % 3);
+        if (blockIdx.x == 0) ms_serve_decide(sp, k, S);
+        if (!grid_sync_err(&ctrl->bar, &ctrl->status, &S.bar_target, p.timeout_ns)) return;
+        if (ldcg32(&st->exit_flag)) break;
+        const uint32_t nret = ldcg32(&st->nretire), nadm = ldcg32(&st->nadmit);
+        if (nret + nadm != 0) {
+            // finished queries' columns to their callers (caller's ids), new
+            // queries' columns reset
+            for (uint32_t r = 0; r < nret; ++r) {
+                const uint32_t i = ldcg32(&st->retire[r]);
+                uint64_t* out = reinterpret_cast<uint64_t*>(ldcg64((const uint64_t*)&st->dist_ptr[i]));
+                for (uint64_t v = gtid; v < p.n; v += gthreads) {
+                    const uint64_t kv = p.perm ? (uint64_t)__ldg(&p.perm[v]) : v;
+                    out[v] = __ldcg(reinterpret_cast<const unsigned long long*>(&p.D[kv * p.R + i]));
+                }
+            }
+            for (uint32_t a = 0; a < nadm; ++a) {
+                const uint32_t i = ldcg32(&st->admit[a]);
+                for (uint64_t v = gtid; v < p.n; v += gthreads) p.D[v * p.R + i] = kInf;
+            }
+            if (!grid_sync_err(&ctrl->bar, &ctrl->status, &S.bar_target, p.timeout_ns)) return;
+            if (blockIdx.x == 0) ms_serve_publish(sp, k);
+            if (!grid_sync_err(&ctrl->bar, &ctrl->status, &S.bar_target, p.timeout_ns)) return;
+        }
+        uint32_t U = ldcg32(&ctrl->usize[c]);
+        U = U < p.n ? U : p.n;
+        if (U == 0) {
+            // nothing queued (all blocks agree): every slot is idle, back to
+            // admission at the same step; a running slot here would be an
+            // internal fault, reported instead of looping
+            if (blockIdx.x == 0 && tid == 0) {
+                bool any = false;
+                for (uint32_t i = 0; i < p.K; ++i) any |= ldcg32(&st->running[i]) != 0;
+                if (any) raise_error(&ctrl->bar, &ctrl->status, SSSP_ERR_INTERNAL);
+            }
+            continue;
+        }
+        ms_phase_T(p, k, U, S, s_keys);
+        if (blockIdx.x == 0 && tid == 0) {
+            ctrl->usize[pv] = 0;
+            ctrl->nsmall[pv] = 0;
+            ctrl->nbig[pv] = 0;
+            if (S.err) raise_error(&ctrl->bar, &ctrl->status, SSSP_ERR_INTERNAL);
+        }
+        if (!grid_sync_err(&ctrl->bar, &ctrl->status, &S.bar_target, p.timeout_ns)) return;
+        ms_phase_E(p, k, U, S);
+        if (!grid_sync_err(&ctrl->bar, &ctrl->status, &S.bar_target, p.timeout_ns)) return;
+        ms_phase_R(p, k, S, stage);
+        if (blockIdx.x == 0 && tid == 0) st->step = k;
+        if (!grid_sync_err(&ctrl->bar, &ctrl->status, &S.bar_target, p.timeout_ns)) return;
+        ++k;
+    }
+}
+
+// ---------------------------------------------------------------------------
 // host side
 // ---------------------------------------------------------------------------
 namespace {
@@ -936,6 +1179,128 @@ int ms_last_stats(int dev, sssp_stats* out, uint32_t k, cudaStream_t st)
         out[i].grid = w.grid;
     }
     return w.h_ctrl->status;
+}
+
+
+// ---------------------------------------------------------------------------
+// host side of the shared-scan server
+// ---------------------------------------------------------------------------
+struct MsServer {
+    void* buf = nullptr;
+    MsServeParams sp;
+    uint32_t grid = 0;
+};
+
+size_t ms_server_bytes(const sssp_graph* g, uint32_t S)
+{
+    const uint64_t n = g->n, R = (S + 3) & ~3u;
+    const uint64_t rec_cap = g->fsmall_cap + g->ms_rec_cap;
+    return a256(8ull * n * R) + a256(8ull * n) + 2 * a256(4ull * n) + a256(16ull * rec_cap) + a256(8ull * rec_cap) +
+           a256(sizeof(MsInst) * kMsMax) + a256(sizeof(MsCtrl)) + a256(sizeof(MsServeState)) + 2 * a256(8ull * kMsMax);
+}
+
+int ms_server_create(const sssp_graph* g, uint32_t S, sssp_algo algo, uint64_t param, uint32_t rho_reduced,
+                     bool bidir, SlotCmd* d_cmd, SlotDone* d_done, ServeShared* d_shared, uint64_t idle_ns,
+                     uint32_t gang, uint64_t gang_wait_ns, MsServer** out)
+{
+    if (!g || !out || S == 0 || S > kMsMax || !ms_batch_supported(algo, S)) return SSSP_ERR_INVALID_ARG;
+    MsServer* m = new (std::nothrow) MsServer();
+    if (!m) return SSSP_ERR_OUT_OF_MEMORY;
+    const size_t bytes = ms_server_bytes(g, S);
+    cudaError_t e = cudaMalloc(&m->buf, bytes);
+    if (e != cudaSuccess) { delete m; return ms_fail(e); }
+    const uint64_t n = g->n;
+    const uint32_t R = (S + 3) & ~3u;
+    const uint64_t rec_cap = g->fsmall_cap + g->ms_rec_cap;
+    unsigned char* b = static_cast<unsigned char*>(m->buf);
+    MsParams& p = m->sp.p;
+    memset(&m->sp, 0, sizeof m->sp);
+    p.D = reinterpret_cast<uint64_t*>(b); b += a256(8ull * n * R);
+    p.QM = reinterpret_cast<uint64_t*>(b); b += a256(8ull * n);
+    p.qa = reinterpret_cast<uint32_t*>(b); b += a256(4ull * n);
+    p.qb = reinterpret_cast<uint32_t*>(b); b += a256(4ull * n);
+    p.rec = reinterpret_cast<uint4*>(b); b += a256(16ull * rec_cap);
+    p.fm = reinterpret_cast<uint64_t*>(b); b += a256(8ull * rec_cap);
+    p.inst = reinterpret_cast<MsInst*>(b); b += a256(sizeof(MsInst) * kMsMax);
+    p.ctrl = reinterpret_cast<MsCtrl*>(b); b += a256(sizeof(MsCtrl));
+    m->sp.st = reinterpret_cast<MsServeState*>(b); b += a256(sizeof(MsServeState));
+    m->sp.src_w = reinterpret_cast<uint32_t*>(b); b += a256(8ull * kMsMax);
+    uint64_t* d_param = reinterpret_cast<uint64_t*>(b);
+    p.small_cap = g->fsmall_cap;
+    p.big_cap = g->ms_rec_cap;
+    p.off = g->reordered ? g->d_off2 : g->d_off;
+    p.edges = g->reordered ? g->d_edges2 : g->d_edges;
+    p.perm = g->reordered ? g->d_perm : nullptr;
+    p.n = g->n;
+    p.K = S;
+    p.R = R;
+    p.rho_reduced = rho_reduced;
+    p.bidir = (bidir && (g->flags & SSSP_GRAPH_SYMMETRIC)) ? 1u : 0u;
+    p.src = m->sp.src_w;
+    p.param = d_param;
+    p.algo = (int)algo;
+    p.sample_cap = kMaxSamples;
+    p.timeout_ns = 2000000000ull;
+    p.solve_timeout_ns = ~0ull;
+    m->sp.cmd = d_cmd;
+    m->sp.done = d_done;
+    m->sp.shared = d_shared;
+    m->sp.idle_ns = idle_ns;
+    m->sp.param = param;
+    m->sp.gang = gang ? (gang < S ? gang : S) : S;
+    m->sp.gang_wait_ns = gang_wait_ns ? gang_wait_ns : 20000000ull;
+    // zero state: empty masks, no query in any slot; every slot's parameter
+    std::vector<uint64_t> prm(kMsMax, param);
+    std::vector<MsInst> inst(kMsMax);
+    memset(inst.data(), 0, sizeof(MsInst) * kMsMax);
+    for (MsInst& x : inst) { x.qmin[0] = kInf; x.qmin[1] = kInf; x.qmin[2] = kInf; }
+    if ((e = cudaMemset(p.QM, 0, 8ull * n)) != cudaSuccess ||
+        (e = cudaMemset(m->sp.st, 0, sizeof(MsServeState))) != cudaSuccess ||
+        (e = cudaMemset(p.ctrl, 0, sizeof(MsCtrl))) != cudaSuccess ||
+        (e = cudaMemcpy(d_param, prm.data(), 8ull * kMsMax, cudaMemcpyHostToDevice)) != cudaSuccess ||
+        (e = cudaMemcpy(p.inst, inst.data(), sizeof(MsInst) * kMsMax, cudaMemcpyHostToDevice)) != cudaSuccess) {
+        cudaFree(m->buf);
+        delete m;
+        return ms_fail(e);
+    }
+    const void* fn = reinterpret_cast<const void*>(&ms_serve_kernel);
+    int bps = 0, sms = 0;
+    if ((e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kMsDynSmem)) != cudaSuccess ||
+        (e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, fn, kMsBlock, kMsDynSmem)) != cudaSuccess ||
+        (e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, g->device)) != cudaSuccess || bps < 1) {
+        cudaFree(m->buf);
+        delete m;
+        return e != cudaSuccess ? ms_fail(e) : SSSP_ERR_CUDA;
+    }
+    m->grid = (uint32_t)(bps * sms);
+    *out = m;
+    return SSSP_OK;
+}
+
+int ms_server_launch(MsServer* m, cudaStream_t st)
+{
+    // the barrier word and status start from zero; the ring slots are zero
+    // whenever the loop has returned (it returns only with no query queued)
+    cudaError_t e = cudaMemsetAsync(m->sp.p.ctrl, 0, sizeof(MsCtrl), st);
+    if (e != cudaSuccess) return ms_fail(e);
+    void* args[] = {&m->sp};
+    e = cudaLaunchCooperativeKernel(reinterpret_cast<const void*>(&ms_serve_kernel), dim3(m->grid), dim3(kMsBlock), args,
+                                    kMsDynSmem, st);
+    return e == cudaSuccess ? SSSP_OK : ms_fail(e);
+}
+
+int ms_server_status(MsServer* m)
+{
+    MsCtrl hc;
+    if (cudaMemcpy(&hc, m->sp.p.ctrl, sizeof hc, cudaMemcpyDeviceToHost) != cudaSuccess) return SSSP_ERR_CUDA;
+    return hc.status;
+}
+
+void ms_server_destroy(MsServer* m)
+{
+    if (!m) return;
+    cudaFree(m->buf);
+    delete m;
 }
 
 }  // namespace sssp

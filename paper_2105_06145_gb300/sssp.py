@@ -111,7 +111,8 @@ _lib.sssp_batch_last_stats.argtypes = [_P, _u32, _P]
 _lib.sssp_batch_last_stats.restype = _i32
 class sssp_server_config(ctypes.Structure):
     _fields_ = [("slots", ctypes.c_uint32), ("algo", ctypes.c_int), ("param", ctypes.c_uint64),
-                ("idle_ns", ctypes.c_uint64), ("hbm_fraction", ctypes.c_double)]
+                ("idle_ns", ctypes.c_uint64), ("hbm_fraction", ctypes.c_double), ("batch_mode", ctypes.c_uint32),
+                ("gang", ctypes.c_uint32), ("gang_wait_ns", ctypes.c_uint64)]
 
 
 class sssp_query_info(ctypes.Structure):
@@ -127,6 +128,8 @@ _lib.sssp_server_create.argtypes = [_P, ctypes.POINTER(sssp_server_config), ctyp
 _lib.sssp_server_create.restype = _i32
 _lib.sssp_server_slots.argtypes = [_P, ctypes.POINTER(_u32)]
 _lib.sssp_server_slots.restype = _i32
+_lib.sssp_server_mode.argtypes = [_P, ctypes.POINTER(_u32)]
+_lib.sssp_server_mode.restype = _i32
 _lib.sssp_server_submit.argtypes = [_P, _u32, _P, ctypes.POINTER(_u64)]
 _lib.sssp_server_submit.restype = _i32
 _lib.sssp_server_poll.argtypes = [_P, _u64, ctypes.POINTER(sssp_query_info)]
@@ -151,7 +154,7 @@ EXPORTED = ["sssp_graph_create", "sssp_graph_destroy", "sssp_graph_info", "sssp_
             "sssp_autotune", "sssp_graph_get_tuning", "sssp_graph_set_tuning", "sssp_graph_class",
             "sssp_solve_tuned", "sssp_autotune_ex", "sssp_tourney_create", "sssp_tourney_destroy",
             "sssp_tourney_update", "sssp_tourney_extract", "sssp_tourney_min", "sssp_tourney_inq",
-            "sssp_array_extract", "sssp_autotune_batch", "sssp_solve_sources_ex"]
+            "sssp_array_extract", "sssp_autotune_batch", "sssp_solve_sources_ex", "sssp_server_mode"]
 
 _lib.sssp_tourney_create.argtypes = [_u32, ctypes.POINTER(_P)]
 _lib.sssp_tourney_create.restype = _i32
@@ -359,8 +362,9 @@ def sssp_batch_last_stats(k: int, stream: int = 0) -> tuple[int, list]:
 
 
 def sssp_server_create(g: int, slots: int = 0, algo: int = SSSP_RHO, param: int = 0, idle_ns: int = 0,
-                       hbm_fraction: float = 0.0) -> int:
-    cfg = sssp_server_config(slots, algo, param, idle_ns, hbm_fraction)
+                       hbm_fraction: float = 0.0, batch_mode: int = SSSP_BATCH_AUTO, gang: int = 0,
+                       gang_wait_ns: int = 0) -> int:
+    cfg = sssp_server_config(slots, algo, param, idle_ns, hbm_fraction, batch_mode, gang, gang_wait_ns)
     h = _P()
     _check(_lib.sssp_server_create(g, ctypes.byref(cfg), ctypes.byref(h)), "sssp_server_create")
     return h.value
@@ -369,6 +373,13 @@ def sssp_server_create(g: int, slots: int = 0, algo: int = SSSP_RHO, param: int 
 def sssp_server_slots(s: int) -> int:
     v = _u32()
     _check(_lib.sssp_server_slots(s, ctypes.byref(v)), "sssp_server_slots")
+    return v.value
+
+
+def sssp_server_mode(s: int) -> int:
+    """SSSP_BATCH_SHARED or SSSP_BATCH_SEPARATE: how the server runs its slots."""
+    v = _u32()
+    _check(_lib.sssp_server_mode(s, ctypes.byref(v)), "sssp_server_mode")
     return v.value
 
 

@@ -31,12 +31,14 @@ def _single(lib, G, n, s, algo, param):
     return d.cpu().numpy().view(np.uint64).copy()
 
 
+@pytest.mark.parametrize("mode", [1, 2])  # SSSP_BATCH_SHARED (one shared scan), SSSP_BATCH_SEPARATE
 @pytest.mark.parametrize("algo,param", [(0, 2048), (1, 1 << 14), (2, 0)])
-def test_overlapping_queries_equal_alone(lib, algo, param):
+def test_overlapping_queries_equal_alone(lib, algo, param, mode):
     g = gg.road(200, 0.75, seed=3)                       # ~250 steps per query: queries overlap
     srcs = gg.pick_sources(g, 24, 17)
     G = lib.Graph(g)
-    srv = lib.sssp_server_create(G.handle, slots=6, algo=algo, param=param)
+    srv = lib.sssp_server_create(G.handle, slots=6, algo=algo, param=param, batch_mode=mode)
+    assert lib.sssp_server_mode(srv) == mode
     outs = [torch.full((g.n,), 9, dtype=torch.int64, device="cuda") for _ in srcs]
     torch.cuda.synchronize()
     tickets = []
@@ -59,11 +61,12 @@ def test_overlapping_queries_equal_alone(lib, algo, param):
     G.close()
 
 
-def test_backpressure_idle_restart_and_destroy(lib):
+@pytest.mark.parametrize("mode", [1, 2])
+def test_backpressure_idle_restart_and_destroy(lib, mode):
     g = gg.rmat(14, 16, gen_seed=41, wseed=42)
     srcs = gg.pick_sources(g, 40, 3)
     G = lib.Graph(g)
-    srv = lib.sssp_server_create(G.handle, slots=4, algo=0, param=1 << 10, idle_ns=1_000_000)
+    srv = lib.sssp_server_create(G.handle, slots=4, algo=0, param=1 << 10, idle_ns=1_000_000, batch_mode=mode)
     assert lib.sssp_server_slots(srv) == 4
     outs = [torch.empty(g.n, dtype=torch.int64, device="cuda") for _ in srcs]
     torch.cuda.synchronize()
@@ -87,4 +90,33 @@ def test_backpressure_idle_restart_and_destroy(lib):
     lib.sssp_server_destroy(srv)
     # the context is still usable
     assert np.array_equal(_single(lib, G, g.n, srcs[2], 2, 0), oracle.dijkstra(g, srcs[2]))
+    G.close()
+
+
+def test_shared_server_relabelled_graph_and_wide_slots(lib):
+    """The shared-scan server on a degree-ordered symmetric graph with
+    bidirectional relaxation (batch tuning) and all 64 slots: every query of
+    a stream twice the slot count equals the oracle; repeated sources; a
+    Delta-Stepping server falls back to separate instances."""
+    g = gg.rmat(15, 16, gen_seed=43, wseed=44)
+    G = lib.Graph(g, lib.SSSP_GRAPH_SYMMETRIC | lib.SSSP_GRAPH_VERIFY | lib.SSSP_GRAPH_REORDER)
+    lib.sssp_graph_set_tuning(G.handle, {"algo": 0, "param": 1 << 11, "flags": 1, "rho_reduced": 6})
+    srv = lib.sssp_server_create(G.handle, slots=64, algo=0, param=1 << 11)
+    assert lib.sssp_server_mode(srv) == lib.SSSP_BATCH_SHARED and lib.sssp_server_slots(srv) == 64
+    srcs = gg.pick_sources(g, 128, 5)
+    srcs[7] = srcs[3]
+    outs = [torch.full((g.n,), 1, dtype=torch.int64, device="cuda") for _ in srcs]
+    torch.cuda.synchronize()
+    tickets = [lib.sssp_server_submit(srv, s, o.data_ptr()) for s, o in zip(srcs, outs)]
+    for t in tickets:
+        assert lib.sssp_server_wait(srv, t, 60_000_000_000)["status"] == 0
+    for s, o in zip(srcs, outs):
+        assert np.array_equal(o.cpu().numpy().view(np.uint64), oracle.dijkstra(g, s)), s
+    lib.sssp_server_destroy(srv)
+    srv = lib.sssp_server_create(G.handle, slots=4, algo=3, param=1 << 12)
+    assert lib.sssp_server_mode(srv) == lib.SSSP_BATCH_SEPARATE
+    t = lib.sssp_server_submit(srv, srcs[0], outs[0].data_ptr())
+    assert lib.sssp_server_wait(srv, t)["status"] == 0
+    assert np.array_equal(outs[0].cpu().numpy().view(np.uint64), oracle.dijkstra(g, srcs[0]))
+    lib.sssp_server_destroy(srv)
     G.close()

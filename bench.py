@@ -673,6 +673,95 @@ def run_lbpq(args):
     print(json.dumps({"lbpq_extract": {"n": n, "tree_build_s": build_s, "rows": rows}}), flush=True)
 
 
+def run_trace(args):
+    """--trace: one solve of the workload from its first source with the
+    per-step trace on (sssp_options.trace), printed as a per-step phase table
+    (device times of Extract, the first grid barrier, the relaxation and the
+    end-of-step barrier) and a JSON summary.  The configuration is the bench's
+    (rho-Stepping, --param, --rho-reduced) unless --trace-config gives
+    algo,param,shape,local_budget."""
+    import torch
+    from paper_2105_06145_gb300 import sssp
+    g, srcs, label = build_workload(args.workload, args.scale)
+    flags = sssp.SSSP_GRAPH_SYMMETRIC | (sssp.SSSP_GRAPH_REORDER if args.workload == "rmat" else 0)
+    G = sssp.Graph(g, flags)
+    if args.trace_config:
+        a, prm, shape, local = (int(x) for x in args.trace_config.split(","))
+    else:
+        a, prm, shape, local = sssp.ALGOS[args.algo], args.param or (1 << 18), 0, 0
+    red = args.rho_reduced if args.rho_reduced > 0 else sssp.SSSP_RHO_REDUCED_NONE
+    stream = torch.cuda.current_stream().cuda_stream
+    d = torch.empty(g.n, dtype=torch.int64, device="cuda")
+    cap = 100000
+    trb = torch.zeros(cap * sssp.TRACE_RECORD_BYTES // 8, dtype=torch.int64, device="cuda")
+    base = dict(flags=sssp.SSSP_SOLVE_BIDIRECTIONAL, shape=shape, local_budget=local, rho_reduced=red)
+    s0 = srcs[0]
+    for _ in range(2):
+        G.solve(s0, a, prm, d, stream, sssp.make_options(**base))
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    G.solve(s0, a, prm, d, stream, sssp.make_options(**base))
+    e1.record()
+    torch.cuda.synchronize()
+    G.solve(s0, a, prm, d, stream, sssp.make_options(trace_ptr=trb.data_ptr(), trace_cap=cap, **base))
+    st = G.stats(stream)
+    tr = np.frombuffer(trb.cpu().numpy().tobytes(), dtype=sssp.TRACE_DTYPE)[:min(st["steps"], cap)]
+    t_ns, t_rel = tr["t_ns"].astype(np.int64), tr["t_relax_ns"].astype(np.int64)
+    ext = tr["t_extract_end_max"].astype(np.int64) - t_ns
+    bar1 = t_rel - tr["t_extract_end_max"].astype(np.int64)
+    rel = tr["t_relax_end_max"].astype(np.int64) - t_rel
+    bar2 = np.append(t_ns[1:], t_ns[-1]) - tr["t_relax_end_max"].astype(np.int64)
+    bar2[-1] = 0
+    if args.trace_steps:
+        for i, t in enumerate(tr):
+            print(f"step {i + 1:5d} q={int(t['queued']):9d} f={int(t['extracted']):9d} edges={int(t['edges']):10d} "
+                  f"extract_us={ext[i] / 1e3:7.1f} barrier_us={bar1[i] / 1e3:5.1f} relax_us={rel[i] / 1e3:7.1f} "
+                  f"end_us={bar2[i] / 1e3:5.1f}")
+    summary = {"workload": label, "source": int(s0), "algo": ALGO_NAMES[a], "param": prm, "shape": shape,
+               "local_budget": local, "rho_reduced": args.rho_reduced, "ms_untraced": e0.elapsed_time(e1),
+               "steps": int(st["steps"]), "edges_per_m": st["edges"] / g.m,
+               "phase_us_sum": {"extract": float(ext.sum() / 1e3), "barrier_after_extract": float(bar1.sum() / 1e3),
+                                "relax": float(rel.sum() / 1e3), "end_of_step": float(bar2.sum() / 1e3)},
+               "phase_us_median": {"extract": float(np.median(ext) / 1e3), "barrier_after_extract": float(np.median(bar1) / 1e3),
+                                   "relax": float(np.median(rel) / 1e3), "end_of_step": float(np.median(bar2[:-1]) / 1e3) if len(bar2) > 1 else 0.0}}
+    print(json.dumps({"trace": summary}), flush=True)
+    G.close()
+
+
+def run_batched_case(args):
+    """--batched-case: 64 sources on RMAT at --scale (degree-ordered symmetric
+    copy, rho-Stepping rho = n/16 with 6 reduced dense steps, bidirectional),
+    two launches with one shared edge scan (SSSP_BATCH_SHARED) and two with
+    separate instances (SSSP_BATCH_SEPARATE), every instance checked against
+    its single solve; the case the batch kernels' profiles capture."""
+    import torch
+    from paper_2105_06145_gb300 import graphgen as gg, sssp
+    g = gg.rmat(args.scale, 16, 0.57, 0.19, 0.19, gen_seed=2, wseed=3)
+    G = sssp.Graph(g, sssp.SSSP_GRAPH_SYMMETRIC | sssp.SSSP_GRAPH_REORDER)
+    srcs = gg.pick_sources(g, 64, 6)
+    stream = torch.cuda.current_stream().cuda_stream
+    rho = max(64, g.n // 16)
+    sssp.sssp_graph_set_tuning(G.handle, {"algo": 0, "param": rho, "flags": 1, "rho_reduced": 6})
+    out = torch.empty(64 * g.n, dtype=torch.int64, device="cuda")
+    one = torch.empty(g.n, dtype=torch.int64, device="cuda")
+    res = {}
+    for mode, name in ((sssp.SSSP_BATCH_SHARED, "shared"), (sssp.SSSP_BATCH_SEPARATE, "separate")):
+        for _ in range(2):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            sssp.sssp_solve_sources_ex(G.handle, srcs, 0, [rho] * 64, mode, out.data_ptr(), stream)
+            e1.record()
+            torch.cuda.synchronize()
+            st, stats = sssp.sssp_batch_last_stats(64, stream)
+            assert st == 0, st
+        eq = rows_equal_to_single(torch, torch.cuda.current_stream(), out.view(64, g.n), srcs,
+                                  lambda s_, o: sssp.sssp_solve_tuned(G.handle, s_, o.data_ptr(), stream))
+        res[name] = {"ms": e0.elapsed_time(e1), "edges_per_m": sum(x["edges"] for x in stats) / 64 / g.m,
+                     "all_equal": eq == 64}
+    print(json.dumps({"batched_case": {"scale": args.scale, "k": 64, **res}}), flush=True)
+    G.close()
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -699,6 +788,11 @@ def main():
     ap.add_argument("--serve-window", type=float, default=1.0)
     ap.add_argument("--serve-slots", type=int, default=0, help="0 = the batch autotuner's slot count")
     ap.add_argument("--lbpq", action="store_true", help="the tournament-tree vs array LaB-PQ Extract comparison only")
+    ap.add_argument("--trace", action="store_true", help="per-step phase summary of one traced solve only")
+    ap.add_argument("--trace-config", default="", help="algo,param,shape,local_budget for --trace")
+    ap.add_argument("--trace-steps", action="store_true", help="--trace: also print every step")
+    ap.add_argument("--batched-case", action="store_true",
+                    help="64 sources on RMAT --scale with the shared-scan and separate batch kernels only")
     ap.add_argument("--lbpq-n", type=int, default=100_000_000)
     ap.add_argument("--lbpq-rho", default="10,13,16,19,22,25", help="log2 of the rho values")
     args = ap.parse_args()
@@ -709,6 +803,12 @@ def main():
         return
     if args.lbpq:
         run_lbpq(args)
+        return
+    if args.trace:
+        run_trace(args)
+        return
+    if args.batched_case:
+        run_batched_case(args)
         return
     g, srcs, label = build_workload(args.workload, args.scale)
 

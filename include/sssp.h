@@ -474,12 +474,15 @@ typedef struct {
 
 /*
  * Time candidate configurations on the k sample sources (HOST uint32[k], each
- * < n) and keep the fastest: rho in {n/4, n/16, ..., n/1024} (at least 64) and
- * Delta in mean-weight x {1/8, 1/2, 2, 8} in the wide shape on the first
+ * < n) and keep the fastest: rho in {n/4, n/8, ..., n/1024} (at least 64) and
+ * Delta in mean-weight x {1/8, 1/4, ..., 8} in the wide shape on the first
  * source; the two best in both shapes on two sources; on graphs with mean
  * out-degree < 20 the two best parameters of each rule in the winning shape
- * with local budgets 64, 256, 1024; the winner is re-timed on all k sources.  Bidirectional relaxation is used when the graph
- * was created SSSP_GRAPH_SYMMETRIC.  The result is stored on the graph and in
+ * with local budgets 64, 256, 1024; for a rho winner the count of dense steps
+ * at rho/10 (2, 4, 6, 8, none); the degree-bin cut-offs (small_deg 16, 32,
+ * 64, then chunk 128, 256, 512); the winner is re-timed on all k sources.
+ * Bidirectional relaxation is used when the graph was created
+ * SSSP_GRAPH_SYMMETRIC.  The result is stored on the graph and in
  * a per-class table (sssp_graph_class) that sssp_solve_tuned, sssp_solve_sources,
  * sssp_solve_multi (params == NULL) and the server (param == 0) use for graphs
  * of the same class that were not tuned themselves.  Synchronous on `stream`;

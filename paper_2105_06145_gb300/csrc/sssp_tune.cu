@@ -11,8 +11,9 @@
 // distances never depend on the choice, only the time does.
 //
 // Search (every solve timed with CUDA events on the caller's stream):
-//   1. every rule/parameter candidate, wide shape, no local relaxation, on the
-//      first sample source;
+//   1. every rule/parameter candidate (rho = n/4 ... n/1024 and Delta = mean
+//      weight x 1/8 ... 8, factors of 2 apart), wide shape, no local
+//      relaxation, on the first sample source;
 //   2. the two fastest of (1) in both shapes, on up to two sources;
 //   3. sparse graphs (mean out-degree < 20): the two fastest of (1) of each
 //      rule, in the winning shape, with local budgets 64, 256 and 1024;
@@ -174,17 +175,17 @@ int sssp_autotune_ex(sssp_graph* g, const uint32_t* sources, uint32_t k, uint32_
     uint32_t timed = 0;
     Candidate best{SSSP_RHO, 0, SSSP_SHAPE_WIDE, 0, 0, 0, 0, 0};
     do {
-        // rule / parameter candidates: rho = n/4 ... n/1024 (>= 64), Delta =
-        // mean weight x {1/8, 1/2, 2, 8}
+        // rule / parameter candidates: rho = n/4 ... n/1024 (>= 64) and Delta =
+        // mean weight x {1/8 ... 8}, each a factor of 2 apart
         std::vector<Candidate> cand;
-        for (uint32_t j = 2; j <= 10 && (rules & (1u << SSSP_RHO)); j += 2) {
+        for (uint32_t j = 2; j <= 10 && (rules & (1u << SSSP_RHO)); ++j) {
             uint64_t rho = (uint64_t)g->n >> j;
             if (rho < 64) rho = 64;
             bool dup = false;
             for (const Candidate& c : cand) dup = dup || (c.algo == SSSP_RHO && c.param == rho);
             if (!dup) cand.push_back({SSSP_RHO, rho, SSSP_SHAPE_WIDE, 0, 0, 0, 0, 0});
         }
-        for (double f : {0.125, 0.5, 2.0, 8.0}) {
+        for (double f : {0.125, 0.25, 0.5, 1.0, 2.0, 4.0, 8.0}) {
             if (!(rules & (1u << SSSP_DELTA_STAR))) break;
             const double d = g->mean_w * f;
             cand.push_back({SSSP_DELTA_STAR, d > 1.0 ? (uint64_t)d : 1ull, SSSP_SHAPE_WIDE, 0, 0, 0, 0, 0});

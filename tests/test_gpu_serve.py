@@ -37,7 +37,10 @@ def test_overlapping_queries_equal_alone(lib, algo, param, mode):
     g = gg.road(200, 0.75, seed=3)                       # ~250 steps per query: queries overlap
     srcs = gg.pick_sources(g, 24, 17)
     G = lib.Graph(g)
-    srv = lib.sssp_server_create(G.handle, slots=6, algo=algo, param=param, batch_mode=mode)
+    # gang=1: each query is admitted at the first step boundary after it
+    # arrives (plain continuous batching; the shared-scan default waits for a
+    # full gang, see test_gang_admission_of_the_shared_server)
+    srv = lib.sssp_server_create(G.handle, slots=6, algo=algo, param=param, batch_mode=mode, gang=1)
     assert lib.sssp_server_mode(srv) == mode
     outs = [torch.full((g.n,), 9, dtype=torch.int64, device="cuda") for _ in srcs]
     torch.cuda.synchronize()
@@ -118,5 +121,41 @@ def test_shared_server_relabelled_graph_and_wide_slots(lib):
     t = lib.sssp_server_submit(srv, srcs[0], outs[0].data_ptr())
     assert lib.sssp_server_wait(srv, t)["status"] == 0
     assert np.array_equal(outs[0].cpu().numpy().view(np.uint64), oracle.dijkstra(g, srcs[0]))
+    lib.sssp_server_destroy(srv)
+    G.close()
+
+
+def test_gang_admission_of_the_shared_server(lib):
+    """The shared-scan server's default admits waiting queries as a gang (every
+    slot holds one, nothing else runs, or the oldest waited gang_wait_ns), so
+    queries that start together stay aligned; results equal the oracle, a
+    burst of 3x the slots is admitted in gangs that start at the same device
+    time, and a query arriving while a gang runs still starts once
+    gang_wait_ns has passed."""
+    g = gg.road(160, 0.75, seed=6)
+    srcs = gg.pick_sources(g, 24, 21)
+    G = lib.Graph(g)
+    srv = lib.sssp_server_create(G.handle, slots=8, algo=1, param=1 << 13, batch_mode=lib.SSSP_BATCH_SHARED)
+    outs = [torch.full((g.n,), 5, dtype=torch.int64, device="cuda") for _ in srcs]
+    torch.cuda.synchronize()
+    tickets = [lib.sssp_server_submit(srv, s, o.data_ptr()) for s, o in zip(srcs, outs)]
+    infos = [lib.sssp_server_wait(srv, t, 60_000_000_000) for t in tickets]
+    assert all(i["status"] == 0 for i in infos)
+    for s, o in zip(srcs, outs):
+        assert np.array_equal(o.cpu().numpy().view(np.uint64), oracle.dijkstra(g, s))
+    admits = sorted({i["device_admit_ns"] // 100_000 for i in infos})   # 0.1 ms bins
+    assert len(admits) <= 6, admits                                     # gangs, not 24 single admissions
+    lib.sssp_server_destroy(srv)
+    # a short wait lets a late query join a running gang
+    srv = lib.sssp_server_create(G.handle, slots=8, algo=1, param=1 << 13, batch_mode=lib.SSSP_BATCH_SHARED,
+                                 gang_wait_ns=200_000)
+    t0 = lib.sssp_server_submit(srv, srcs[0], outs[0].data_ptr())
+    time.sleep(0.001)
+    t1 = lib.sssp_server_submit(srv, srcs[1], outs[1].data_ptr())
+    i0, i1 = lib.sssp_server_wait(srv, t0), lib.sssp_server_wait(srv, t1)
+    assert i0["status"] == 0 and i1["status"] == 0
+    assert i1["device_admit_ns"] < i0["device_done_ns"], (i0, i1)     # joined while the first ran
+    for s, o in zip(srcs[:2], outs[:2]):
+        assert np.array_equal(o.cpu().numpy().view(np.uint64), oracle.dijkstra(g, s))
     lib.sssp_server_destroy(srv)
     G.close()

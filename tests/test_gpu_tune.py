@@ -93,6 +93,10 @@ def test_autotune_then_solve_tuned(lib):
         assert t["flags"] == lib.SSSP_SOLVE_BIDIRECTIONAL
         if g.m / g.n >= 20:
             assert t["local_budget"] == 0
+        # the count of dense steps at rho/10 and the degree-bin cut-offs it chose
+        assert t["rho_reduced"] in (0, 4, 6, 8, lib.SSSP_RHO_REDUCED_NONE)
+        assert t["rho_reduced"] == 0 or t["algo"] == lib.SSSP_RHO
+        assert t["small_deg"] in (0, 16, 64) and t["chunk"] in (0, 128, 512)
         assert lib.sssp_graph_get_tuning(G.handle) == t
         for s in srcs[:2]:
             dist = torch.full((g.n,), 7, dtype=torch.int64, device="cuda")
@@ -135,7 +139,8 @@ def test_set_tuning_validation(lib):
     lib.sssp_graph_set_tuning(G.handle, good)
     assert lib.sssp_graph_get_tuning(G.handle)["param"] == 1024
     for bad in ({"param": 0}, {"shape": 2}, {"flags": lib.SSSP_SOLVE_BIDIRECTIONAL}, {"algo": 9},
-                {"algo": lib.SSSP_BELLMAN_FORD, "local_budget": 64}):
+                {"algo": lib.SSSP_BELLMAN_FORD, "local_budget": 64}, {"small_deg": 7}, {"small_deg": 200},
+                {"chunk": 300}, {"chunk": 2048}, {"batch_mode": 3}):
         with pytest.raises(lib.SSSPError):
             lib.sssp_graph_set_tuning(G.handle, {**good, **bad})
     dist = torch.empty(g.n, dtype=torch.int64, device="cuda")
@@ -195,6 +200,7 @@ def test_autotune_batch_is_used_by_batched_calls(lib):
     single = lib.sssp_autotune(G.handle, srcs[:2], _stream())
     tb = lib.sssp_autotune_batch(G.handle, srcs, (1 << lib.SSSP_RHO) | (1 << lib.SSSP_DELTA_STAR), _stream())
     assert tb["algo"] in (lib.SSSP_RHO, lib.SSSP_DELTA_STAR) and tb["param"] >= 1 and tb["candidates"] >= 5
+    assert tb["batch_mode"] in (lib.SSSP_BATCH_SHARED, lib.SSSP_BATCH_SEPARATE)
     assert lib.sssp_graph_get_tuning(G.handle) == single  # single-solve tuning unchanged
     out = torch.empty(len(srcs) * g.n, dtype=torch.int64, device="cuda")
     lib.sssp_solve_sources(G.handle, srcs, tb["algo"], None, out.data_ptr(), _stream())
@@ -222,4 +228,23 @@ def test_server_takes_the_tuned_slot_count(lib):
         assert lib.sssp_server_wait(srv, tk, 60_000_000_000)["status"] == 0
         assert np.array_equal(b.cpu().numpy().view(np.uint64), oracle.dijkstra(g, s))
     lib.sssp_server_destroy(srv)
+    G.close()
+
+
+def test_tuned_solve_applies_every_recorded_choice(lib):
+    """A tuning that sets the count of reduced dense steps and both degree-bin
+    cut-offs is applied by sssp_solve_tuned (and by the class table) with the
+    oracle's distances."""
+    g = gg.rmat(15, 16, gen_seed=81, wseed=82)
+    G = lib.Graph(g, lib.SSSP_GRAPH_SYMMETRIC | lib.SSSP_GRAPH_REORDER)
+    for t in ({"algo": 0, "param": 1 << 11, "flags": 1, "rho_reduced": 8, "small_deg": 16, "chunk": 128},
+              {"algo": 0, "param": 1 << 11, "flags": 1, "rho_reduced": lib.SSSP_RHO_REDUCED_NONE, "small_deg": 128,
+               "chunk": 1024, "shape": 1},
+              {"algo": 1, "param": 1 << 15, "flags": 0, "small_deg": 64, "chunk": 512, "local_budget": 64}):
+        lib.sssp_graph_set_tuning(G.handle, t)
+        for s in gg.pick_sources(g, 2, 19):
+            dist = torch.full((g.n,), 7, dtype=torch.int64, device="cuda")
+            lib.sssp_solve_tuned(G.handle, s, dist.data_ptr(), _stream())
+            assert lib.sssp_last_status(G.handle, _stream()) == 0
+            assert np.array_equal(dist.cpu().numpy().view(np.uint64), oracle.dijkstra(g, s)), t
     G.close()

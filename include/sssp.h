@@ -139,6 +139,22 @@ typedef struct {
                                        on a graph declared SSSP_GRAPH_SYMMETRIC that is not
                                        symmetric the results are wrong.  Create the graph with
                                        SSSP_GRAPH_VERIFY as well unless symmetry is known.      */
+#define SSSP_SOLVE_FUSED 2u         /* super-sparse steps (20*|Q| <= n, at most 4 queued ids per
+                                       thread, theta the same for every block: every rule
+                                       except a rho-Stepping step that samples theta) run
+                                       Extract and the relaxation without the device-wide wait
+                                       between them: each block relaxes the vertices it has
+                                       just extracted.  Extract then overlaps other blocks'
+                                       WriteMin, so an extracted vertex may be relaxed with a
+                                       distance that another block lowers at the same time;
+                                       each block re-checks its extracted vertices after the
+                                       step and re-queues those whose distance dropped.  The
+                                       distances are the same; steps and edges may differ.
+                                       Used by the narrow kernel shape (SSSP_SHAPE_NARROW; the
+                                       wide shape runs every step unfused), where it allocates
+                                       128 bytes per thread of the launch on the graph's first
+                                       such solve.  Best on graphs whose solves take thousands
+                                       of small steps (road-like grids).                       */
 
 /* sssp_options.shape: thread-block shape of the persistent solve kernel.  WIDE
    keeps the most memory operations in flight (best when steps relax many
@@ -459,7 +475,8 @@ typedef struct {
     sssp_algo algo;          /* SSSP_RHO or SSSP_DELTA_STAR (or SSSP_BELLMAN_FORD)          */
     uint32_t shape;          /* SSSP_SHAPE_*                                                */
     uint64_t param;          /* rho or Delta                                                */
-    uint32_t flags;          /* SSSP_SOLVE_* (bidirectional relaxation on symmetric graphs) */
+    uint32_t flags;          /* SSSP_SOLVE_* (bidirectional relaxation on symmetric graphs,
+                                fused super-sparse steps)                                 */
     uint32_t local_budget;   /* sssp_options.local_budget                                   */
     double ms;               /* autotuner: mean solve time of the choice on the samples     */
     uint32_t candidates;     /* autotuner: configurations timed                             */
@@ -479,7 +496,8 @@ typedef struct {
  * source; the two best in both shapes on two sources; on graphs with mean
  * out-degree < 20 the two best parameters of each rule in the winning shape
  * with local budgets 64, 256, 1024; for a rho winner the count of dense steps
- * at rho/10 (2, 4, 6, 8, none); the degree-bin cut-offs (small_deg 16, 32,
+ * at rho/10 (2, 4, 6, 8, none); again on graphs with mean out-degree < 20 the
+ * winner in the narrow shape with SSSP_SOLVE_FUSED; the degree-bin cut-offs (small_deg 16, 32,
  * 64, then chunk 128, 256, 512); the winner is re-timed on all k sources.
  * Bidirectional relaxation is used when the graph was created
  * SSSP_GRAPH_SYMMETRIC.  The result is stored on the graph and in

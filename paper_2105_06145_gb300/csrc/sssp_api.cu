@@ -48,6 +48,7 @@ void free_graph(sssp_graph* g)
     cudaFree(g->d_ctrl);
     cudaFree(g->d_dist_internal);
     cudaFree(g->d_lrel);
+    cudaFree(g->d_fre);
     cudaFree(g->d_off2);
     cudaFree(g->d_edges2);
     cudaFree(g->d_perm);
@@ -350,7 +351,7 @@ int sssp_solve_ex(const sssp_graph* gc, uint32_t source, sssp_algo algo, uint64_
     p.trace_cap = o.trace_cap;
     p.exit_block = o.test_exit_block;
     p.stats_out = o.stats_out;
-    if (o.flags & ~SSSP_SOLVE_BIDIRECTIONAL) return SSSP_ERR_INVALID_ARG;
+    if (o.flags & ~(SSSP_SOLVE_BIDIRECTIONAL | SSSP_SOLVE_FUSED)) return SSSP_ERR_INVALID_ARG;
     if ((o.flags & SSSP_SOLVE_BIDIRECTIONAL) && !(g->flags & SSSP_GRAPH_SYMMETRIC)) return SSSP_ERR_INVALID_ARG;
     p.bidir = (o.flags & SSSP_SOLVE_BIDIRECTIONAL) ? 1 : 0;
     if (o.local_budget != 0 && algo != SSSP_RHO && algo != SSSP_DELTA_STAR) return SSSP_ERR_INVALID_ARG;
@@ -403,6 +404,19 @@ int sssp_solve_ex(const sssp_graph* gc, uint32_t source, sssp_algo algo, uint64_
     if (o.grid_limit && o.grid_limit < grid) grid = o.grid_limit;
     if (p.exit_block > grid) return SSSP_ERR_INVALID_ARG;
     g->last_grid = grid;
+    if ((o.flags & SSSP_SOLVE_FUSED) && shape == 1) {
+        // per block two step-parity buffers of one Extract round's entries
+        const uint64_t need = (uint64_t)grid * 2ull * (uint64_t)kShapes[shape].threads() * (uint64_t)kExtractPer;
+        std::lock_guard<std::mutex> lk(g->mu);
+        if (g->fre_cap < need) {
+            cudaFree(g->d_fre);
+            g->fre_cap = 0;
+            cudaError_t e = dalloc(&g->d_fre, need);
+            if (e != cudaSuccess) { g->d_fre = nullptr; return cuda_fail(e); }
+            g->fre_cap = need;
+        }
+        p.fre = g->d_fre;
+    }
 
     cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
     cudaError_t e = cudaMemsetAsync(g->d_ctrl, 0, sizeof(Ctrl), st);

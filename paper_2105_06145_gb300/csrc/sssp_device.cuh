@@ -353,6 +353,31 @@ __device__ __forceinline__ void stage_push(bool push, uint32_t v, uint32_t* stag
     stc += __popc(b);
 }
 
+// Warp-uniform: the re-check after a fused step (SSSP_SOLVE_FUSED).  Lane
+// entry j is a vertex u[j] the block extracted in that step and the distance
+// du[j] it was relaxed with (kInf: no entry).  Where delta[u] has dropped below
+// du since, u is queued again (Update: test-and-set of its queue bit, staged
+// when the bit was clear).
+template <int P>
+__device__ __forceinline__ void requeue_dropped(const uint32_t (&u)[P], const uint64_t (&du)[P], const uint64_t* dist,
+                                                uint32_t* inq, uint32_t* stage, uint32_t& stc, uint32_t lane,
+                                                uint64_t& lmin)
+{
+    uint64_t dv[P];
+#pragma unroll
+    for (int j = 0; j < P; ++j) dv[j] = du[j] != kInf ? ldcg64(&dist[u[j]]) : kInf;
+#pragma unroll
+    for (int j = 0; j < P; ++j) {
+        bool push = false;
+        if (dv[j] < du[j]) {
+            lmin = dv[j] < lmin ? dv[j] : lmin;
+            const uint32_t prev = atomicOr(&inq[u[j] >> 5], 1u << (u[j] & 31u));
+            push = (prev & (1u << (u[j] & 31u))) == 0;
+        }
+        stage_push(push, u[j], stage, stc, lane);
+    }
+}
+
 // Warp-uniform: the second half of a batch of (up to) 4 relaxations per lane,
 // given the pre-check values dv[t] = delta[v[t]]:
 //   for every candidate with cand < delta[v]: WriteMin(delta[v], cand)

@@ -118,6 +118,10 @@ struct SolveParams {
     uint64_t* lrel;               // [n] distance each vertex was last locally relaxed with, or null
     uint32_t small_deg;           // degree-bin cut-off: 1..small_deg -> low-degree records
     uint32_t chunk_log2;          // chunk records cover at most 2^chunk_log2 edges (aligned)
+    // SSSP_SOLVE_FUSED: per block two step-parity buffers of kExtractCap
+    // (vertex, -, distance it was relaxed with) -- the vertices the block
+    // extracted in a fused step, re-checked after the step; null = no fused steps
+    uint4* fre;
     // relabelled graph (SSSP_GRAPH_REORDER): the solve runs on the relabelled
     // copy with dist = internal distances in the new ids; at the end
     // dist_out[v] = dist[perm[v]] for every caller id v; ext_count is indexed
@@ -235,6 +239,8 @@ struct sssp_graph {
     sssp::Ctrl* d_ctrl = nullptr;
     uint64_t* d_dist_internal = nullptr;   // lazily allocated for sssp_solve_host
     uint64_t* d_lrel = nullptr;            // lazily allocated for solves with local relaxation
+    uint4* d_fre = nullptr;                // lazily allocated for solves with SSSP_SOLVE_FUSED
+    uint64_t fre_cap = 0;                  // its entries
     // SSSP_GRAPH_REORDER: relabelled copy for single solves (new id = rank by
     // decreasing out-degree, ties by id; adjacencies sorted by new target)
     bool reordered = false;

@@ -29,6 +29,11 @@
 
 namespace sssp {
 
+// Fused super-sparse steps (SSSP_SOLVE_FUSED) are compiled into the narrow
+// shape only: in the wide one (64 registers a thread) the extra live state
+// spills.  The wide shape runs every step unfused.
+constexpr bool kFusedSteps = kBlock <= 512;
+
 // ---------------------------------------------------------------------------
 // Block 0, one thread: add the counters of step `step` (ring slot `slot`) to
 // the solve's totals and to its trace record, then reset the slot for reuse.
@@ -121,6 +126,8 @@ __global__ void __launch_bounds__(kBlock, kMinBlocks) solve_kernel(SolveParams p
     uint64_t delta_i = 1;          // Delta*- / Delta-Stepping bucket index (Table 2)
     uint64_t prev_theta = 0;       // theta of the previous step (Delta-Stepping FinishCheck)
     uint32_t dense_seen = 0;       // rho-Stepping: dense steps so far (Sec. 6)
+    bool prev_fused = false;       // the previous step was fused (SSSP_SOLVE_FUSED; grid-uniform)
+    uint32_t fre_L = 0;            // ... and this block's slice of its queue had fre_L entries
 
     uint64_t k = 1;
     for (; started; ++k) {
@@ -134,7 +141,9 @@ __global__ void __launch_bounds__(kBlock, kMinBlocks) solve_kernel(SolveParams p
         const uint64_t umin_c = p.algo == SSSP_DELTA ? ldcg64((const uint64_t*)&ctrl->umin[c]) : kInf;
         q = q < n ? q : n;  // a capacity fault is reported via status; never read past a list
 
-        if (q == 0) {
+        // an empty queue ends the solve, unless the previous step was fused:
+        // then this step only re-checks that step's extractions (below)
+        if (q == 0 && !(kFusedSteps && prev_fused)) {
             if (blockIdx.x == 0 && tid == 0) fold_step(p, ctrl, pv, k - 1);
             break;
         }
@@ -162,7 +171,9 @@ __global__ void __launch_bounds__(kBlock, kMinBlocks) solve_kernel(SolveParams p
         uint64_t theta;
         bool rho_sample = false;  // rho-Stepping with q > rho': theta from samples
         uint32_t s_cnt = 0, r_idx = 0;
-        if (p.algo == SSSP_BELLMAN_FORD) {
+        if (q == 0) {
+            theta = 0;  // re-check step: nothing to extract
+        } else if (p.algo == SSSP_BELLMAN_FORD) {
             theta = kInf;
         } else if (p.algo == SSSP_DELTA_STAR || p.algo == SSSP_DELTA) {
             const uint64_t qmin = qmin_c;
@@ -190,6 +201,139 @@ __global__ void __launch_bounds__(kBlock, kMinBlocks) solve_kernel(SolveParams p
             if ((uint64_t)q * 20ull > (uint64_t)n) ++dense_seen;
         }
 
+        // SSSP_SOLVE_FUSED: a super-sparse step whose theta every block has
+        // already (not one that samples it) and whose queue fits one Extract
+        // round per block runs Extract and the relaxation block by block
+        const uint64_t per_block_q = ((uint64_t)q + gridDim.x - 1) / gridDim.x;
+        const bool fused = kFusedSteps && p.fre != nullptr && q != 0 && !rho_sample && (uint64_t)q * 20ull <= (uint64_t)n &&
+                           per_block_q <= (uint64_t)kExtractCap;
+        const uint4* fre_prev = p.fre + ((uint64_t)blockIdx.x * 2u + ((k + 1) & 1u)) * kExtractCap;
+        uint32_t stc = 0;          // the warp's staged ids (next queue list)
+        uint64_t lmin = kInf;      // smallest distance this thread wrote or re-queued
+        uint32_t lupd = 0;         // successful WriteMin of this thread
+        uint64_t f_cnt = 0, f_edg = 0, f_kmin = kInf;  // fused step: extracted, their edges, min kept key
+        uint32_t fre_next = 0;
+
+        if (fused) {
+            // ---------------- Extract(theta) and relaxation, fused ----------------
+            // The block's slice of Q_k (entry i held by thread i mod kBlock) is
+            // extracted and relaxed by the block itself, with no device-wide
+            // wait in between.  Other blocks' WriteMin may lower the distance
+            // of an entry while it is examined.  A kept entry keeps its queue
+            // bit and is examined again in the next step.  An extracted one is
+            // recorded with the distance it is relaxed with; in the next step
+            // (when every WriteMin of this step is visible) the block re-queues
+            // those whose distance has dropped since: a WriteMin that found the
+            // bit still set before this block cleared it queued nothing.
+            const uint64_t r0 = (uint64_t)blockIdx.x * per_block_q;
+            const uint32_t L = (uint32_t)(r0 >= q ? 0 : ((uint64_t)q - r0 < per_block_q ? (uint64_t)q - r0 : per_block_q));
+            uint4* fre_cur = p.fre + ((uint64_t)blockIdx.x * 2u + (k & 1u)) * kExtractCap;
+            const uint32_t small_deg = p.small_deg, cl = p.chunk_log2;
+            uint32_t v[kExtractPer], ru[kExtractPer];
+            uint64_t d[kExtractPer], rdu[kExtractPer];
+            // ids, the previous step's records, then keys and current distances (all in flight)
+#pragma unroll
+            for (int j = 0; j < kExtractPer; ++j) {
+                const uint32_t i = tid + (uint32_t)j * kBlock;
+                v[j] = i < L ? ldcg32(&Qcur[r0 + i]) : 0u;
+                const uint4 r = i < fre_L ? __ldcg(&fre_prev[i]) : make_uint4(0u, 0u, ~0u, ~0u);
+                ru[j] = r.x;
+                rdu[j] = (uint64_t)r.z | ((uint64_t)r.w << 32);
+            }
+            uint64_t sb0 = 0, se0 = 0;
+#pragma unroll
+            for (int j = 0; j < kExtractPer; ++j) {
+                const uint32_t i = tid + (uint32_t)j * kBlock;
+                d[j] = i < L ? ldcg64(&dist[v[j]]) : kInf;
+            }
+            if (tid < L) {
+                sb0 = __ldg(&off[v[0]]);
+                se0 = __ldg(&off[v[0] + 1]);
+            }
+            requeue_dropped(ru, rdu, dist, inq, stage, stc, lane, lmin);
+            // (1) keep / extract; kept ids are staged for the next queue list
+            uint32_t extm = 0;
+#pragma unroll
+            for (int j = 0; j < kExtractPer; ++j) {
+                const uint32_t i = tid + (uint32_t)j * kBlock;
+                if (i >= L) continue;
+                if (d[j] <= theta) {
+                    atomicAnd(&inq[v[j] >> 5], ~(1u << (v[j] & 31u)));
+                    extm |= 1u << j;
+                } else {
+                    f_kmin = d[j] < f_kmin ? d[j] : f_kmin;
+                }
+            }
+#pragma unroll
+            for (int j = 0; j < kExtractPer; ++j) {
+                const uint32_t i = tid + (uint32_t)j * kBlock;
+                stage_push(i < L && !((extm >> j) & 1u), v[j], stage, stc, lane);
+            }
+            if (p.trace && k - 1 < p.trace_cap) {
+                if (blockIdx.x == 0 && tid == 0) {
+                    p.trace[k - 1].theta = theta;
+                    p.trace[k - 1].t_relax_ns = global_timer_ns() - s_t_start;
+                }
+                if (tid == 0)
+                    atomicMax((unsigned long long*)&p.trace[k - 1].t_extract_end_max, global_timer_ns() - s_t_start);
+            }
+            // (2) edge ranges (the first entry's was loaded with its key); the
+            //     record for the next step's re-check
+            uint64_t b[kExtractPer], e[kExtractPer];
+#pragma unroll
+            for (int j = 0; j < kExtractPer; ++j) {
+                const uint32_t i = tid + (uint32_t)j * kBlock;
+                b[j] = 0; e[j] = 0;
+                if ((extm >> j) & 1u) {
+                    b[j] = j == 0 ? sb0 : __ldg(&off[v[j]]);
+                    e[j] = j == 0 ? se0 : __ldg(&off[v[j] + 1]);
+                    // locally relaxed with this same distance: its edges are done
+                    if (p.lrel && ldcg64(&p.lrel[v[j]]) == d[j]) e[j] = b[j];
+                    f_cnt += 1;
+                    f_edg += e[j] - b[j];
+                    if (p.ext_count) p.ext_count[p.iperm ? p.iperm[v[j]] : v[j]] += 1u;
+                }
+                if (i < L) {
+                    const uint64_t du = ((extm >> j) & 1u) ? d[j] : kInf;
+                    fre_cur[i] = make_uint4(v[j], 0u, (uint32_t)du, (uint32_t)(du >> 32));
+                }
+            }
+            // (3) out-degree <= small_deg: flattened over the warp's lanes
+#pragma unroll
+            for (int j = 0; j < kExtractPer; ++j) {
+                const uint64_t deg = e[j] - b[j];
+                const uint32_t sd = (((extm >> j) & 1u) && deg <= small_deg) ? (uint32_t)deg : 0u;
+                if (stc > (uint32_t)(kStage - 256)) stage_flush(stage, stc, lane, &ctrl->qsize[nx], &ctrl->status, Qnext, n);
+                relax_flat<true>(b[j], sd, d[j], edges, dist, inq, stage, stc, lane, lmin, lupd, true,
+                                 &ctrl->qsize[nx], &ctrl->status, Qnext, n);
+            }
+            // (4) larger: the whole warp, one 2^chunk_log2-aligned piece at a time
+#pragma unroll
+            for (int j = 0; j < kExtractPer; ++j) {
+                uint32_t many = __ballot_sync(FULL_MASK, ((extm >> j) & 1u) && e[j] - b[j] > small_deg);
+                while (many) {
+                    const int src = __ffs(many) - 1;
+                    many &= many - 1;
+                    const uint64_t sb = __shfl_sync(FULL_MASK, b[j], src);
+                    const uint64_t se = __shfl_sync(FULL_MASK, e[j], src);
+                    const uint64_t sdu = __shfl_sync(FULL_MASK, d[j], src);
+                    const uint32_t su = __shfl_sync(FULL_MASK, v[j], src);
+                    for (uint64_t cs = sb; cs < se;) {
+                        const uint64_t nb = ((cs >> cl) + 1) << cl;
+                        const uint64_t ce = se < nb ? se : nb;
+                        const uint4 rec = make_rec(cs, ce - cs, su);
+                        if (p.bidir)
+                            relax_chunk<true, true>(rec, sdu, pairs, dist, inq, stage, stc, lane, lmin, lupd,
+                                                    &ctrl->qsize[nx], &ctrl->status, Qnext, n);
+                        else
+                            relax_chunk<false, true>(rec, sdu, pairs, dist, inq, stage, stc, lane, lmin, lupd,
+                                                     &ctrl->qsize[nx], &ctrl->status, Qnext, n);
+                        cs = ce;
+                    }
+                }
+            }
+            fre_next = L;
+        } else if (q != 0) {
         // ---------------- Extract(theta) ----------------
         // Q_k is cut into R x gridDim.x runs of equal length (at most
         // kExtractCap entries each); in round r, block b takes run r*gridDim.x+b.
@@ -399,11 +543,26 @@ __global__ void __launch_bounds__(kBlock, kMinBlocks) solve_kernel(SolveParams p
         if (p.trace && tid == 0 && k - 1 < p.trace_cap)
             atomicMax((unsigned long long*)&p.trace[k - 1].t_extract_end_max, global_timer_ns() - s_t_start);
         if (!grid_sync_err(&ctrl->bar, &ctrl->status, &s_bar_target, p.timeout_ns)) break;
+        }
 
         // ---------------- relax the out-edges of F ----------------
-        if (blockIdx.x == 0 && tid == 0 && p.trace && k - 1 < p.trace_cap)
+        if (!fused && blockIdx.x == 0 && tid == 0 && p.trace && k - 1 < p.trace_cap)
             p.trace[k - 1].t_relax_ns = global_timer_ns() - s_t_start;
-        {
+        if (kFusedSteps && !fused && fre_L != 0) {
+            // the previous step was fused: re-queue its extractions whose
+            // distance dropped since (see the fused step)
+            uint32_t ru[kExtractPer];
+            uint64_t rdu[kExtractPer];
+#pragma unroll
+            for (int j = 0; j < kExtractPer; ++j) {
+                const uint32_t i = tid + (uint32_t)j * kBlock;
+                const uint4 r = i < fre_L ? __ldcg(&fre_prev[i]) : make_uint4(0u, 0u, ~0u, ~0u);
+                ru[j] = r.x;
+                rdu[j] = (uint64_t)r.z | ((uint64_t)r.w << 32);
+            }
+            requeue_dropped(ru, rdu, dist, inq, stage, stc, lane, lmin);
+        }
+        if (!fused) {
             // the warp's first records are loaded together with the record
             // counts (within the arrays' capacity; used only if below the count)
             const uint64_t i_first = (uint64_t)gwarp * 32u + lane;
@@ -413,9 +572,6 @@ __global__ void __launch_bounds__(kBlock, kMinBlocks) solve_kernel(SolveParams p
             fs = fs < p.fsmall_cap ? fs : p.fsmall_cap;
             uint64_t fc = ldcg32(&ctrl->fchunk[c]);
             fc = fc < p.item_cap ? fc : p.item_cap;
-            uint32_t stc = 0;
-            uint64_t lmin = kInf;
-            uint32_t lupd = 0;
 
             // (a) low-degree vertices: 32 records per warp, edges flattened across lanes
             const uint64_t ngroups = (fs + 31u) >> 5;
@@ -451,14 +607,20 @@ __global__ void __launch_bounds__(kBlock, kMinBlocks) solve_kernel(SolveParams p
                     if (stc > (uint32_t)(kStage - 256)) stage_flush(stage, stc, lane, &ctrl->qsize[nx], &ctrl->status, Qnext, n);
                 }
             }
-
+        }
+        {
             // (d) super-sparse steps (Sec. 6, local BFS): keep relaxing from the
             //     vertices this warp has just queued while they are within theta
+            //     (after a fused step without the device-wide degree check)
             uint64_t ledg = 0;
-            if (p.local_budget != 0 && (uint64_t)q * 20ull <= (uint64_t)n) {
-                const uint64_t fcnt = ldcg32(&ctrl->fcount[c]);
-                const uint64_t fed = ldcg64((const uint64_t*)&ctrl->fedges[c]);
-                if (fed < 20ull * fcnt)
+            if (p.local_budget != 0 && q != 0 && (uint64_t)q * 20ull <= (uint64_t)n) {
+                bool go = fused;
+                if (!fused) {
+                    const uint64_t fcnt = ldcg32(&ctrl->fcount[c]);
+                    const uint64_t fed = ldcg64((const uint64_t*)&ctrl->fedges[c]);
+                    go = fed < 20ull * fcnt;
+                }
+                if (go)
                     ledg = local_relax(theta, p.local_budget, off, edges, dist, inq, stage, stc, lane, lmin, lupd,
                                        &ctrl->qsize[nx], &ctrl->status, Qnext, n, p.lrel);
             }
@@ -501,8 +663,19 @@ __global__ void __launch_bounds__(kBlock, kMinBlocks) solve_kernel(SolveParams p
                     atomicMax((unsigned long long*)&p.trace[k - 1].t_relax_end_max, now);
                 }
             }
+            if (fused) {  // the fused step's Extract counters
+                uint64_t bf = f_cnt, be = f_edg, bk = f_kmin;
+                block_reduce_2add_min(bf, be, bk, s_tmp);
+                if (tid == 0) {
+                    if (bf) atomicAdd(&ctrl->fcount[c], (unsigned int)bf);
+                    if (be) atomicAdd(&ctrl->fedges[c], (unsigned long long)be);
+                    if (algo_tracks_qmin(p.algo) && bk != kInf) atomicMin(&ctrl->qmin[nx], (unsigned long long)bk);
+                }
+            }
         }
         if (!grid_sync_err(&ctrl->bar, &ctrl->status, &s_bar_target, p.timeout_ns)) break;
+        prev_fused = fused;
+        fre_L = fre_next;
     }
 
     // relabelled graph: distances back in the caller's ids

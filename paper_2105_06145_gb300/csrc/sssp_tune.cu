@@ -19,9 +19,11 @@
 //      rule, in the winning shape, with local budgets 64, 256 and 1024;
 //   4. rho-Stepping winner: the number of dense steps that use rho/10 (the
 //      paper's 2, then 4, 6, 8 and none);
-//   5. the degree-bin cut-offs: small-degree bound 16 and 64 (default 32),
+//   5. sparse graphs: the winner in the narrow shape with fused super-sparse
+//      steps (SSSP_SOLVE_FUSED);
+//   6. the degree-bin cut-offs: small-degree bound 16 and 64 (default 32),
 //      then chunk records of 128 and 512 edges (default 256);
-//   6. the winner on every sample source (sssp_tuning.ms).
+//   7. the winner on every sample source (sssp_tuning.ms).
 // The result is kept on the graph handle and in a per-class table (graph class
 // = size, mean degree, degree skew and symmetry; sssp_graph_class), which
 // sssp_solve_tuned and the batched and serving calls consult for graphs that
@@ -59,6 +61,7 @@ struct Candidate {
     uint32_t rho_reduced;   // sssp_options encoding (0 = the paper's 2)
     uint32_t small_deg;     // 0 = default
     uint32_t chunk;         // 0 = default
+    uint32_t fused;         // 1 = SSSP_SOLVE_FUSED
 };
 
 // Mean time of one solve per source (ms); a failed solve is reported as rc.
@@ -67,7 +70,7 @@ int time_config(const sssp_graph* g, const Candidate& c, const uint32_t* srcs, u
 {
     sssp_options o;
     memset(&o, 0, sizeof o);
-    o.flags = (g->flags & SSSP_GRAPH_SYMMETRIC) ? SSSP_SOLVE_BIDIRECTIONAL : 0u;
+    o.flags = ((g->flags & SSSP_GRAPH_SYMMETRIC) ? SSSP_SOLVE_BIDIRECTIONAL : 0u) | (c.fused ? SSSP_SOLVE_FUSED : 0u);
     o.shape = c.shape;
     o.local_budget = c.local;
     o.rho_reduced = c.rho_reduced;
@@ -173,7 +176,7 @@ int sssp_autotune_ex(sssp_graph* g, const uint32_t* sources, uint32_t k, uint32_
     }
     int rc = SSSP_OK;
     uint32_t timed = 0;
-    Candidate best{SSSP_RHO, 0, SSSP_SHAPE_WIDE, 0, 0, 0, 0, 0};
+    Candidate best{SSSP_RHO, 0, SSSP_SHAPE_WIDE, 0, 0, 0, 0, 0, 0};
     do {
         // rule / parameter candidates: rho = n/4 ... n/1024 (>= 64) and Delta =
         // mean weight x {1/8 ... 8}, each a factor of 2 apart
@@ -183,12 +186,12 @@ int sssp_autotune_ex(sssp_graph* g, const uint32_t* sources, uint32_t k, uint32_
             if (rho < 64) rho = 64;
             bool dup = false;
             for (const Candidate& c : cand) dup = dup || (c.algo == SSSP_RHO && c.param == rho);
-            if (!dup) cand.push_back({SSSP_RHO, rho, SSSP_SHAPE_WIDE, 0, 0, 0, 0, 0});
+            if (!dup) cand.push_back({SSSP_RHO, rho, SSSP_SHAPE_WIDE, 0, 0, 0, 0, 0, 0});
         }
         for (double f : {0.125, 0.25, 0.5, 1.0, 2.0, 4.0, 8.0}) {
             if (!(rules & (1u << SSSP_DELTA_STAR))) break;
             const double d = g->mean_w * f;
-            cand.push_back({SSSP_DELTA_STAR, d > 1.0 ? (uint64_t)d : 1ull, SSSP_SHAPE_WIDE, 0, 0, 0, 0, 0});
+            cand.push_back({SSSP_DELTA_STAR, d > 1.0 ? (uint64_t)d : 1ull, SSSP_SHAPE_WIDE, 0, 0, 0, 0, 0, 0});
         }
         // one warm-up solve (first launch of the kernel, lazy allocations)
         double ignore;
@@ -248,7 +251,17 @@ int sssp_autotune_ex(sssp_graph* g, const uint32_t* sources, uint32_t k, uint32_
             }
             if (rc != SSSP_OK) break;
         }
-        // (5) degree-bin cut-offs: the small-degree bound, then the chunk length
+        // (5) fused super-sparse steps (narrow shape), for graphs whose solves
+        //     take many small steps
+        if (g->n && (double)g->m / (double)g->n < 20.0) {
+            Candidate c = best;
+            c.shape = SSSP_SHAPE_NARROW;
+            c.fused = 1;
+            if ((rc = time_config(g, c, sources, ns2, dist, st, e0, e1, &c.ms)) != SSSP_OK) break;
+            ++timed;
+            if (c.ms < best.ms) best = c;
+        }
+        // (6) degree-bin cut-offs: the small-degree bound, then the chunk length
         {
             Candidate base = best;
             for (uint32_t sd : {16u, 64u}) {
@@ -269,7 +282,7 @@ int sssp_autotune_ex(sssp_graph* g, const uint32_t* sources, uint32_t k, uint32_
             }
             if (rc != SSSP_OK) break;
         }
-        // (6)
+        // (7)
         if ((rc = time_config(g, best, sources, k, dist, st, e0, e1, &best.ms)) != SSSP_OK) break;
     } while (false);
     cudaEventDestroy(e0);
@@ -281,7 +294,7 @@ int sssp_autotune_ex(sssp_graph* g, const uint32_t* sources, uint32_t k, uint32_
     t.algo = best.algo;
     t.shape = best.shape;
     t.param = best.param;
-    t.flags = (g->flags & SSSP_GRAPH_SYMMETRIC) ? SSSP_SOLVE_BIDIRECTIONAL : 0u;
+    t.flags = ((g->flags & SSSP_GRAPH_SYMMETRIC) ? SSSP_SOLVE_BIDIRECTIONAL : 0u) | (best.fused ? SSSP_SOLVE_FUSED : 0u);
     t.local_budget = best.local;
     t.ms = best.ms;
     t.candidates = timed;
@@ -487,7 +500,8 @@ int sssp_graph_set_tuning(sssp_graph* g, const sssp_tuning* t)
     if (!g || !t) return SSSP_ERR_INVALID_ARG;
     if (t->algo != SSSP_RHO && t->algo != SSSP_DELTA_STAR && t->algo != SSSP_BELLMAN_FORD) return SSSP_ERR_INVALID_ARG;
     if (algo_needs_param(t->algo) && t->param == 0) return SSSP_ERR_INVALID_ARG;
-    if (t->shape > SSSP_SHAPE_NARROW || (t->flags & ~SSSP_SOLVE_BIDIRECTIONAL)) return SSSP_ERR_INVALID_ARG;
+    if (t->shape > SSSP_SHAPE_NARROW || (t->flags & ~(SSSP_SOLVE_BIDIRECTIONAL | SSSP_SOLVE_FUSED)))
+        return SSSP_ERR_INVALID_ARG;
     if ((t->flags & SSSP_SOLVE_BIDIRECTIONAL) && !(g->flags & SSSP_GRAPH_SYMMETRIC)) return SSSP_ERR_INVALID_ARG;
     if (t->local_budget != 0 && t->algo == SSSP_BELLMAN_FORD) return SSSP_ERR_INVALID_ARG;
     if (t->small_deg != 0 && (t->small_deg < sssp::kSmallDegMin || t->small_deg > sssp::kSmallDegMax))

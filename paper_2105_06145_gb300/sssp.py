@@ -21,7 +21,7 @@ LIB_PATH = os.environ.get("SSSP_LIB") or os.path.join(_HERE, "libsssp.so")
 SSSP_RHO, SSSP_DELTA_STAR, SSSP_BELLMAN_FORD, SSSP_DELTA, SSSP_DIJKSTRA = 0, 1, 2, 3, 4
 ALGOS = {"rho": SSSP_RHO, "delta_star": SSSP_DELTA_STAR, "bellman_ford": SSSP_BELLMAN_FORD,
          "delta": SSSP_DELTA, "dijkstra": SSSP_DIJKSTRA}
-SSSP_SOLVE_BIDIRECTIONAL = 1
+SSSP_SOLVE_BIDIRECTIONAL, SSSP_SOLVE_FUSED = 1, 2
 SSSP_SHAPE_WIDE, SSSP_SHAPE_NARROW = 0, 1
 SSSP_GRAPH_SYMMETRIC, SSSP_GRAPH_VERIFY, SSSP_GRAPH_REORDER = 1, 2, 4
 SSSP_OK = 0

@@ -62,3 +62,9 @@ def test_road4096(lib):
     # the tuned road configuration: Delta*-Stepping with local relaxation in the narrow shape
     opts = lib.make_options(flags=lib.SSSP_SOLVE_BIDIRECTIONAL, local_budget=256, shape=lib.SSSP_SHAPE_NARROW)
     _run(lib, g, [s], [(1, 2111), (0, 1 << 16)], lib.SSSP_GRAPH_SYMMETRIC, opts)
+    # ... with fused super-sparse steps, and a second source
+    extra = gg.pick_sources(g, 1, 31, mask=gg.largest_cc(g))
+    for lb in (256, 1024):
+        opts = lib.make_options(flags=lib.SSSP_SOLVE_BIDIRECTIONAL | lib.SSSP_SOLVE_FUSED, local_budget=lb,
+                                shape=lib.SSSP_SHAPE_NARROW)
+        _run(lib, g, [s] + extra, [(1, 2111), (0, 1 << 16)], lib.SSSP_GRAPH_SYMMETRIC, opts)

@@ -364,3 +364,54 @@ def test_reduced_rho_count_full_relabelled_graph(lib):
             got, st = solve(lib, g, s, 0, g.n // 16, opts=o, G=G)
             assert st["status"] == 0 and np.array_equal(got, want), (s, red)
     G.close()
+
+
+def test_fused_super_sparse_steps(lib):
+    """SSSP_SOLVE_FUSED (narrow shape: a super-sparse step's Extract and
+    relaxation run block by block, without the device-wide wait between them,
+    and each block re-checks its extractions in the next step): every rule on a
+    road-like graph, a unit-weight grid (many equal distances) and RMAT graphs
+    with hub vertices (relaxed by the extracting warp in a fused step), with
+    local and bidirectional relaxation, in the caller's and the degree-ordered
+    layout -- the distances equal the oracle's.  A solve whose last step was
+    fused ends with a re-check step (|Q| = 0); the trace totals still equal the
+    solve totals; the wide shape ignores the flag."""
+    F, B = lib.SSSP_SOLVE_FUSED, lib.SSSP_SOLVE_BIDIRECTIONAL
+    sym = lib.SSSP_GRAPH_SYMMETRIC | lib.SSSP_GRAPH_VERIFY
+    graphs = [(gg.road(150, 0.75, seed=11), sym), (gg.grid(70, 90, wmax_excl=0), sym),
+              (gg.rmat(14, 16, gen_seed=21, wseed=22), 0),
+              (gg.rmat(14, 16, gen_seed=23, wseed=24), sym | lib.SSSP_GRAPH_REORDER)]
+    cases = [(0, 64), (0, 1 << 12), (1, 1 << 10), (1, 1 << 14), (2, 0), (3, 1 << 12), (4, 0)]
+    cap = 200000
+    trace = torch.zeros(cap * lib.TRACE_RECORD_BYTES // 8, dtype=torch.int64, device="cuda")
+    ended_with_recheck = 0
+    for g, gflags in graphs:
+        G = lib.Graph(g, gflags)
+        for s in gg.pick_sources(g, 2, 5):
+            want = oracle.dijkstra(g, s)
+            for algo, param in cases:
+                variants = [dict(flags=F)]
+                if gflags & lib.SSSP_GRAPH_SYMMETRIC:
+                    variants.append(dict(flags=F | B))
+                if algo in (0, 1):
+                    variants.append(dict(flags=F | (B if gflags else 0), local_budget=256))
+                for kw in variants:
+                    o = lib.make_options(shape=lib.SSSP_SHAPE_NARROW, trace_ptr=trace.data_ptr(), trace_cap=cap, **kw)
+                    got, st = solve(lib, g, s, algo, param, opts=o, G=G)
+                    assert st["status"] == 0 and np.array_equal(got, want), (g.name, s, algo, param, kw)
+                    rec = np.frombuffer(trace.cpu().numpy().tobytes(),
+                                        dtype=np.dtype(lib.TRACE_DTYPE))[: st["steps"]]
+                    assert int(rec["extracted"].sum()) == st["extracted"]
+                    assert int(rec["queued"].sum()) == st["queued"]
+                    assert int(rec["edges"].sum()) == st["edges"]
+                    # only a re-check step runs with an empty queue, and only last
+                    assert np.all(rec["queued"][:-1] >= 1)
+                    ended_with_recheck += int(rec["queued"][-1] == 0)
+                # the wide shape runs every step unfused
+                o = lib.make_options(flags=F, shape=lib.SSSP_SHAPE_WIDE, trace_ptr=trace.data_ptr(), trace_cap=cap)
+                got, st = solve(lib, g, s, algo, param, opts=o, G=G)
+                assert st["status"] == 0 and np.array_equal(got, want), (g.name, s, algo, param, "wide")
+                rec = np.frombuffer(trace.cpu().numpy().tobytes(), dtype=np.dtype(lib.TRACE_DTYPE))[: st["steps"]]
+                assert np.all(rec["queued"] >= 1)
+        G.close()
+    assert ended_with_recheck > 0

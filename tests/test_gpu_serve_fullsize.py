@@ -5,6 +5,7 @@ through the continuous-batching server so that they overlap on the device.
 
 Every served result equals the single solve of the same source (uint64,
 element by element); on the road and k-NN graphs at least four served results
+of the shared-scan server (and one or two of the separate-instance server)
 also equal the oracle's Dijkstra, and on RMAT-25 one does (the oracle takes
 tens of seconds per RMAT-25 source on one host core; the single solve it is
 compared with is checked against the oracle at RMAT-22 by the full-size
@@ -29,10 +30,14 @@ def lib():
     return sssp
 
 
-def _serve_and_check(lib, g, flags, srcs, slots, algo, param, n_oracle, stagger_s):
+def _serve_and_check(lib, g, flags, srcs, slots, algo, param, n_oracle, stagger_s, mode=0):
     G = lib.Graph(g, flags)
     stream = torch.cuda.current_stream().cuda_stream
-    srv = lib.sssp_server_create(G.handle, slots=slots, algo=algo, param=param)
+    # gang=1: each query is admitted at the first step boundary after it
+    # arrives, so staggered queries overlap on the device
+    srv = lib.sssp_server_create(G.handle, slots=slots, algo=algo, param=param, batch_mode=mode, gang=1)
+    if mode:
+        assert lib.sssp_server_mode(srv) == mode
     outs = [torch.full((g.n,), 9, dtype=torch.int64, device="cuda") for _ in srcs]
     torch.cuda.synchronize()
     tickets = []
@@ -57,18 +62,22 @@ def _serve_and_check(lib, g, flags, srcs, slots, algo, param, n_oracle, stagger_
     torch.cuda.empty_cache()
 
 
-def test_serve_road4096(lib):
+@pytest.mark.parametrize("mode", [1, 2])  # SSSP_BATCH_SHARED, SSSP_BATCH_SEPARATE
+def test_serve_road4096(lib, mode):
     g, s0 = gg.workload_road(4096)
     srcs = [s0] + gg.pick_sources(g, 7, 9, mask=gg.largest_cc(g))
     _serve_and_check(lib, g, lib.SSSP_GRAPH_SYMMETRIC | lib.SSSP_GRAPH_VERIFY, srcs, slots=4,
-                     algo=lib.SSSP_DELTA_STAR, param=2111, n_oracle=4, stagger_s=0.005)
+                     algo=lib.SSSP_DELTA_STAR, param=2111, n_oracle=4 if mode == 1 else 1, stagger_s=0.005,
+                     mode=mode)
 
 
-def test_serve_knn2m(lib):
+@pytest.mark.parametrize("mode", [1, 2])
+def test_serve_knn2m(lib, mode):
     g = gg.knn(2_000_000, 64, 0.02, 10, float(1 << 20), seed=10)
     srcs = gg.pick_sources(g, 16, 9, mask=np.ones(g.n, np.uint8))
     _serve_and_check(lib, g, lib.SSSP_GRAPH_SYMMETRIC | lib.SSSP_GRAPH_VERIFY, srcs, slots=8,
-                     algo=lib.SSSP_RHO, param=1 << 15, n_oracle=6, stagger_s=0.0005)
+                     algo=lib.SSSP_RHO, param=1 << 15, n_oracle=6 if mode == 1 else 2, stagger_s=0.0005,
+                     mode=mode)
 
 
 def test_serve_rmat25(lib):

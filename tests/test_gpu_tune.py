@@ -90,7 +90,10 @@ def test_autotune_then_solve_tuned(lib):
         t = lib.sssp_autotune(G.handle, srcs, _stream())
         assert t["algo"] in (lib.SSSP_RHO, lib.SSSP_DELTA_STAR)
         assert t["param"] >= 1 and t["shape"] in (0, 1) and t["candidates"] >= 9 and t["ms"] > 0
-        assert t["flags"] == lib.SSSP_SOLVE_BIDIRECTIONAL
+        assert t["flags"] & lib.SSSP_SOLVE_BIDIRECTIONAL
+        assert t["flags"] & ~(lib.SSSP_SOLVE_BIDIRECTIONAL | lib.SSSP_SOLVE_FUSED) == 0
+        if t["flags"] & lib.SSSP_SOLVE_FUSED:  # fused steps are tried in the narrow shape only
+            assert t["shape"] == lib.SSSP_SHAPE_NARROW and g.m / g.n < 20
         if g.m / g.n >= 20:
             assert t["local_budget"] == 0
         # the count of dense steps at rho/10 and the degree-bin cut-offs it chose
@@ -232,15 +235,16 @@ def test_server_takes_the_tuned_slot_count(lib):
 
 
 def test_tuned_solve_applies_every_recorded_choice(lib):
-    """A tuning that sets the count of reduced dense steps and both degree-bin
-    cut-offs is applied by sssp_solve_tuned (and by the class table) with the
-    oracle's distances."""
+    """A tuning that sets the count of reduced dense steps, both degree-bin
+    cut-offs or fused super-sparse steps is applied by sssp_solve_tuned (and by
+    the class table) with the oracle's distances."""
     g = gg.rmat(15, 16, gen_seed=81, wseed=82)
     G = lib.Graph(g, lib.SSSP_GRAPH_SYMMETRIC | lib.SSSP_GRAPH_REORDER)
     for t in ({"algo": 0, "param": 1 << 11, "flags": 1, "rho_reduced": 8, "small_deg": 16, "chunk": 128},
               {"algo": 0, "param": 1 << 11, "flags": 1, "rho_reduced": lib.SSSP_RHO_REDUCED_NONE, "small_deg": 128,
                "chunk": 1024, "shape": 1},
-              {"algo": 1, "param": 1 << 15, "flags": 0, "small_deg": 64, "chunk": 512, "local_budget": 64}):
+              {"algo": 1, "param": 1 << 15, "flags": 0, "small_deg": 64, "chunk": 512, "local_budget": 64},
+              {"algo": 1, "param": 1 << 13, "flags": 3, "shape": 1, "local_budget": 256}):  # + fused steps
         lib.sssp_graph_set_tuning(G.handle, t)
         for s in gg.pick_sources(g, 2, 19):
             dist = torch.full((g.n,), 7, dtype=torch.int64, device="cuda")

@@ -679,14 +679,19 @@ def run_trace(args):
     (device times of Extract, the first grid barrier, the relaxation and the
     end-of-step barrier) and a JSON summary.  The configuration is the bench's
     (rho-Stepping, --param, --rho-reduced) unless --trace-config gives
-    algo,param,shape,local_budget."""
+    algo,param,shape,local_budget[,flags] (flags: extra SSSP_SOLVE_* bits, e.g.
+    2 = fused super-sparse steps, whose steps have no barrier after Extract:
+    there the relaxation column starts when block 0 has extracted)."""
     import torch
     from paper_2105_06145_gb300 import sssp
     g, srcs, label = build_workload(args.workload, args.scale)
     flags = sssp.SSSP_GRAPH_SYMMETRIC | (sssp.SSSP_GRAPH_REORDER if args.workload == "rmat" else 0)
     G = sssp.Graph(g, flags)
+    xflags = 0
     if args.trace_config:
-        a, prm, shape, local = (int(x) for x in args.trace_config.split(","))
+        cfg = [int(x) for x in args.trace_config.split(",")]
+        a, prm, shape, local = cfg[:4]
+        xflags = cfg[4] if len(cfg) > 4 else 0
     else:
         a, prm, shape, local = sssp.ALGOS[args.algo], args.param or (1 << 18), 0, 0
     red = args.rho_reduced if args.rho_reduced > 0 else sssp.SSSP_RHO_REDUCED_NONE
@@ -694,7 +699,7 @@ def run_trace(args):
     d = torch.empty(g.n, dtype=torch.int64, device="cuda")
     cap = 100000
     trb = torch.zeros(cap * sssp.TRACE_RECORD_BYTES // 8, dtype=torch.int64, device="cuda")
-    base = dict(flags=sssp.SSSP_SOLVE_BIDIRECTIONAL, shape=shape, local_budget=local, rho_reduced=red)
+    base = dict(flags=sssp.SSSP_SOLVE_BIDIRECTIONAL | xflags, shape=shape, local_budget=local, rho_reduced=red)
     s0 = srcs[0]
     for _ in range(2):
         G.solve(s0, a, prm, d, stream, sssp.make_options(**base))
@@ -707,8 +712,9 @@ def run_trace(args):
     st = G.stats(stream)
     tr = np.frombuffer(trb.cpu().numpy().tobytes(), dtype=sssp.TRACE_DTYPE)[:min(st["steps"], cap)]
     t_ns, t_rel = tr["t_ns"].astype(np.int64), tr["t_relax_ns"].astype(np.int64)
-    ext = tr["t_extract_end_max"].astype(np.int64) - t_ns
-    bar1 = t_rel - tr["t_extract_end_max"].astype(np.int64)
+    has_q = tr["queued"] > 0  # a fused solve's last step only re-checks (no Extract)
+    ext = np.where(has_q, tr["t_extract_end_max"].astype(np.int64) - t_ns, 0)
+    bar1 = np.where(has_q, np.maximum(t_rel - tr["t_extract_end_max"].astype(np.int64), 0), 0)
     rel = tr["t_relax_end_max"].astype(np.int64) - t_rel
     bar2 = np.append(t_ns[1:], t_ns[-1]) - tr["t_relax_end_max"].astype(np.int64)
     bar2[-1] = 0
@@ -718,7 +724,7 @@ def run_trace(args):
                   f"extract_us={ext[i] / 1e3:7.1f} barrier_us={bar1[i] / 1e3:5.1f} relax_us={rel[i] / 1e3:7.1f} "
                   f"end_us={bar2[i] / 1e3:5.1f}")
     summary = {"workload": label, "source": int(s0), "algo": ALGO_NAMES[a], "param": prm, "shape": shape,
-               "local_budget": local, "rho_reduced": args.rho_reduced, "ms_untraced": e0.elapsed_time(e1),
+               "local_budget": local, "flags": int(base["flags"]), "rho_reduced": args.rho_reduced, "ms_untraced": e0.elapsed_time(e1),
                "steps": int(st["steps"]), "edges_per_m": st["edges"] / g.m,
                "phase_us_sum": {"extract": float(ext.sum() / 1e3), "barrier_after_extract": float(bar1.sum() / 1e3),
                                 "relax": float(rel.sum() / 1e3), "end_of_step": float(bar2.sum() / 1e3)},
@@ -789,7 +795,7 @@ def main():
     ap.add_argument("--serve-slots", type=int, default=0, help="0 = the batch autotuner's slot count")
     ap.add_argument("--lbpq", action="store_true", help="the tournament-tree vs array LaB-PQ Extract comparison only")
     ap.add_argument("--trace", action="store_true", help="per-step phase summary of one traced solve only")
-    ap.add_argument("--trace-config", default="", help="algo,param,shape,local_budget for --trace")
+    ap.add_argument("--trace-config", default="", help="algo,param,shape,local_budget[,flags] for --trace")
     ap.add_argument("--trace-steps", action="store_true", help="--trace: also print every step")
     ap.add_argument("--batched-case", action="store_true",
                     help="64 sources on RMAT --scale with the shared-scan and separate batch kernels only")

@@ -495,10 +495,11 @@ typedef struct {
  * Delta in mean-weight x {1/8, 1/4, ..., 8} in the wide shape on the first
  * source; the two best in both shapes on two sources; on graphs with mean
  * out-degree < 20 the two best parameters of each rule in the winning shape
- * with local budgets 64, 256, 1024; for a rho winner the count of dense steps
- * at rho/10 (2, 4, 6, 8, none); again on graphs with mean out-degree < 20 the
- * winner in the narrow shape with SSSP_SOLVE_FUSED; the degree-bin cut-offs (small_deg 16, 32,
- * 64, then chunk 128, 256, 512); the winner is re-timed on all k sources.
+ * with local budgets 64, 256, 1024 and in the narrow shape with
+ * SSSP_SOLVE_FUSED and local budgets 0, 64, 256, 1024; for a rho winner the
+ * count of dense steps at rho/10 (2, 4, 6, 8, none); the degree-bin cut-offs
+ * (small_deg 16, 32, 64, then chunk 128, 256, 512); the winner is re-timed on
+ * all k sources.
  * Bidirectional relaxation is used when the graph was created
  * SSSP_GRAPH_SYMMETRIC.  The result is stored on the graph and in
  * a per-class table (sssp_graph_class) that sssp_solve_tuned, sssp_solve_sources,
@@ -518,8 +519,11 @@ int sssp_autotune_ex(sssp_graph* g, const uint32_t* sources, uint32_t k, uint32_
    uint32[k], k <= SSSP_MAX_BATCH): rho / Delta candidates as in
    sssp_autotune's first stage (rules: as sssp_autotune_ex), each timed as one
    sssp_solve_sources launch over up to 8 of the sources, the two best of each
-   rule re-timed on all k; on graphs of >= 2^20 vertices and mean degree < 20
-   also local budgets 0, 64, 256 for the winner; then the winner's throughput
+   rule re-timed on all k (for k <= 64 also with one shared edge scan,
+   SSSP_BATCH_SHARED); on graphs of >= 2^20 vertices and mean degree < 20
+   local budgets 0, 64, 256 for each of those of the separate-instance
+   kernel; for a rho winner the count of dense steps at rho/10 (4, 6, 8,
+   none); then the winner's throughput
    with 1, 4 and 16 concurrent sources (those < k) against k, the best count
    recorded as `slots`.  Kept as the graph's batch tuning, which
    sssp_solve_sources / sssp_solve_multi (params == NULL) and the server

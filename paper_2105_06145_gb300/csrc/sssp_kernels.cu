@@ -67,7 +67,7 @@ __global__ void __launch_bounds__(kBlock, kMinBlocks) solve_kernel(SolveParams p
     extern __shared__ __align__(16) unsigned char s_dyn[];
     uint32_t* s_stage = reinterpret_cast<uint32_t*>(s_dyn);  // [kWarps][kStage]
     uint64_t* s_keys = reinterpret_cast<uint64_t*>(s_dyn);   // rho samples (aliases the empty staging)
-    __shared__ uint64_t s_tmp[3 * kWarps];
+    __shared__ uint64_t s_tmp[6 * kWarps];
     __shared__ uint32_t s_base[3];
     __shared__ uint32_t s_wcnt[kWarps];
     __shared__ int s_err;
@@ -648,9 +648,20 @@ __global__ void __launch_bounds__(kBlock, kMinBlocks) solve_kernel(SolveParams p
                 const uint32_t wb = s_base[0] + s_wcnt[wid];
                 for (uint32_t i = lane; i < stc; i += 32) Qnext[wb + i] = stage[i];
             }
+            // (with the fused step's Extract counters: one reduction)
             uint64_t bu = lupd, bl = ledg, bm = lmin;
-            block_reduce_2add_min(bu, bl, bm, s_tmp);
+            uint64_t bf = 0, be = 0, bk = kInf;
+            if (kFusedSteps && fused) {
+                uint64_t sums[4] = {bu, bl, f_cnt, f_edg}, mins[2] = {bm, f_kmin};
+                block_reduce_4add_2min(sums, mins, s_tmp);
+                bu = sums[0]; bl = sums[1]; bf = sums[2]; be = sums[3]; bm = mins[0]; bk = mins[1];
+            } else {
+                block_reduce_2add_min(bu, bl, bm, s_tmp);
+            }
             if (tid == 0) {
+                if (bf) atomicAdd(&ctrl->fcount[c], (unsigned int)bf);
+                if (be) atomicAdd(&ctrl->fedges[c], (unsigned long long)be);
+                if (algo_tracks_qmin(p.algo) && bk != kInf) atomicMin(&ctrl->qmin[nx], (unsigned long long)bk);
                 if (bu) atomicAdd(&ctrl->updates[c], (unsigned long long)bu);
                 if (bl) atomicAdd(&ctrl->ledges[c], (unsigned long long)bl);
                 if (algo_tracks_qmin(p.algo) && bm != kInf) {
@@ -661,15 +672,6 @@ __global__ void __launch_bounds__(kBlock, kMinBlocks) solve_kernel(SolveParams p
                     const unsigned long long now = global_timer_ns() - s_t_start;
                     atomicMin((unsigned long long*)&p.trace[k - 1].t_relax_end_min, now);
                     atomicMax((unsigned long long*)&p.trace[k - 1].t_relax_end_max, now);
-                }
-            }
-            if (fused) {  // the fused step's Extract counters
-                uint64_t bf = f_cnt, be = f_edg, bk = f_kmin;
-                block_reduce_2add_min(bf, be, bk, s_tmp);
-                if (tid == 0) {
-                    if (bf) atomicAdd(&ctrl->fcount[c], (unsigned int)bf);
-                    if (be) atomicAdd(&ctrl->fedges[c], (unsigned long long)be);
-                    if (algo_tracks_qmin(p.algo) && bk != kInf) atomicMin(&ctrl->qmin[nx], (unsigned long long)bk);
                 }
             }
         }

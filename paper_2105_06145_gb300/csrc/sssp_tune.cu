@@ -16,14 +16,14 @@
 //      relaxation, on the first sample source;
 //   2. the two fastest of (1) in both shapes, on up to two sources;
 //   3. sparse graphs (mean out-degree < 20): the two fastest of (1) of each
-//      rule, in the winning shape, with local budgets 64, 256 and 1024;
+//      rule, in the winning shape with local budgets 64, 256 and 1024, and in
+//      the narrow shape with fused super-sparse steps (SSSP_SOLVE_FUSED) with
+//      local budgets 0, 64, 256 and 1024;
 //   4. rho-Stepping winner: the number of dense steps that use rho/10 (the
 //      paper's 2, then 4, 6, 8 and none);
-//   5. sparse graphs: the winner in the narrow shape with fused super-sparse
-//      steps (SSSP_SOLVE_FUSED);
-//   6. the degree-bin cut-offs: small-degree bound 16 and 64 (default 32),
+//   5. the degree-bin cut-offs: small-degree bound 16 and 64 (default 32),
 //      then chunk records of 128 and 512 edges (default 256);
-//   7. the winner on every sample source (sssp_tuning.ms).
+//   6. the winner on every sample source (sssp_tuning.ms).
 // The result is kept on the graph handle and in a per-class table (graph class
 // = size, mean degree, degree skew and symmetry; sssp_graph_class), which
 // sssp_solve_tuned and the batched and serving calls consult for graphs that
@@ -228,15 +228,22 @@ int sssp_autotune_ex(sssp_graph* g, const uint32_t* sources, uint32_t k, uint32_
                 for (const Candidate& c : sorted)
                     if (c.algo == a && taken < 2) { base.push_back(c); ++taken; }
             }
+            // ... and, since fused super-sparse steps change the ranking as
+            // much, the same in the narrow shape with fused steps (also
+            // without local relaxation)
+            const uint32_t win_shape = best.shape;
             for (size_t i = 0; i < base.size() && rc == SSSP_OK; ++i)
-                for (uint32_t local : {64u, 256u, 1024u}) {
-                    Candidate c = base[i];
-                    c.shape = best.shape;
-                    c.local = local;
-                    if ((rc = time_config(g, c, sources, ns2, dist, st, e0, e1, &c.ms)) != SSSP_OK) break;
-                    ++timed;
-                    if (c.ms < best.ms) best = c;
-                }
+                for (uint32_t fused : {0u, 1u})
+                    for (uint32_t local : {0u, 64u, 256u, 1024u}) {
+                        if (local == 0 && !fused) continue;  // timed in (1)/(2)
+                        Candidate c = base[i];
+                        c.shape = fused ? SSSP_SHAPE_NARROW : win_shape;
+                        c.fused = fused;
+                        c.local = local;
+                        if ((rc = time_config(g, c, sources, ns2, dist, st, e0, e1, &c.ms)) != SSSP_OK) break;
+                        ++timed;
+                        if (c.ms < best.ms) best = c;
+                    }
             if (rc != SSSP_OK) break;
         }
         // (4) rho-Stepping: how many dense steps use rho/10 (Sec. 6 uses two)
@@ -251,17 +258,7 @@ int sssp_autotune_ex(sssp_graph* g, const uint32_t* sources, uint32_t k, uint32_
             }
             if (rc != SSSP_OK) break;
         }
-        // (5) fused super-sparse steps (narrow shape), for graphs whose solves
-        //     take many small steps
-        if (g->n && (double)g->m / (double)g->n < 20.0) {
-            Candidate c = best;
-            c.shape = SSSP_SHAPE_NARROW;
-            c.fused = 1;
-            if ((rc = time_config(g, c, sources, ns2, dist, st, e0, e1, &c.ms)) != SSSP_OK) break;
-            ++timed;
-            if (c.ms < best.ms) best = c;
-        }
-        // (6) degree-bin cut-offs: the small-degree bound, then the chunk length
+        // (5) degree-bin cut-offs: the small-degree bound, then the chunk length
         {
             Candidate base = best;
             for (uint32_t sd : {16u, 64u}) {
@@ -282,7 +279,7 @@ int sssp_autotune_ex(sssp_graph* g, const uint32_t* sources, uint32_t k, uint32_
             }
             if (rc != SSSP_OK) break;
         }
-        // (7)
+        // (6)
         if ((rc = time_config(g, best, sources, k, dist, st, e0, e1, &best.ms)) != SSSP_OK) break;
     } while (false);
     cudaEventDestroy(e0);
@@ -321,8 +318,8 @@ int sssp_autotune_ex(sssp_graph* g, const uint32_t* sources, uint32_t k, uint32_
 // local budget the batch would use); the two best of each rule re-timed on all
 // k sources (separate instances, SSSP_BATCH_SEPARATE) and, for k <= 64, with
 // one shared edge scan per step (SSSP_BATCH_SHARED); then local budgets 0, 64
-// and 256 for a separate-instance winner on graphs where batched launches use
-// local relaxation, and for a rho-Stepping winner 4, 6, 8 or no dense steps
+// and 256 for every separate-instance finalist on graphs where batched
+// launches use local relaxation, and for a rho-Stepping winner 4, 6, 8 or no dense steps
 // with rho/10 (the paper's 2 is the starting point).  The result is kept as the graph's batch tuning,
 // which the batched and serving calls prefer.
 int sssp_autotune_batch(sssp_graph* g, const uint32_t* sources, uint32_t k, uint32_t rules, sssp_tuning* out,
@@ -436,15 +433,19 @@ int sssp_autotune_batch(sssp_graph* g, const uint32_t* sources, uint32_t k, uint
             if (rc != SSSP_OK) break;
         }
     }
-    if (rc == SSSP_OK && best.batch_mode == SSSP_BATCH_SEPARATE && g->n >= (1u << 20) &&
-        (double)g->m / (double)g->n < 20.0) {
-        for (uint32_t local : {0u, 64u, 256u}) {
-            if (local == best.local_budget) continue;
-            sssp_tuning t = best;
-            t.local_budget = local;
-            if ((rc = time_batch(t, &ms)) != SSSP_OK) break;
-            ++timed;
-            if (ms < best_ms) { best_ms = ms; best = t; }
+    // local budgets for every finalist of the separate-instance kernel (the
+    // budget changes which rule and parameter win, as in single solves)
+    if (rc == SSSP_OK && g->n >= (1u << 20) && (double)g->m / (double)g->n < 20.0) {
+        for (const sssp_tuning& f : finalists) {
+            for (uint32_t local : {0u, 64u, 256u}) {
+                if (local == f.local_budget) continue;
+                sssp_tuning t = f;
+                t.local_budget = local;
+                if ((rc = time_batch(t, &ms)) != SSSP_OK) break;
+                ++timed;
+                if (ms < best_ms) { best_ms = ms; best = t; }
+            }
+            if (rc != SSSP_OK) break;
         }
     }
     if (rc == SSSP_OK && best.algo == SSSP_RHO) {  // dense steps with rho/10 (Sec. 6 uses two)

@@ -494,7 +494,7 @@ typedef struct {
  * < n) and keep the fastest: rho in {n/4, n/8, ..., n/1024} (at least 64) and
  * Delta in mean-weight x {1/8, 1/4, ..., 8} in the wide shape on the first
  * source; the two best in both shapes on two sources; on graphs with mean
- * out-degree < 20 the two best parameters of each rule in the winning shape
+ * out-degree < 20 the three best parameters of each rule in the winning shape
  * with local budgets 64, 256, 1024 and in the narrow shape with
  * SSSP_SOLVE_FUSED and local budgets 0, 64, 256, 1024; for a rho winner the
  * count of dense steps at rho/10 (2, 4, 6, 8, none); the degree-bin cut-offs

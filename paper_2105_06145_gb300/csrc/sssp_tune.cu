@@ -15,7 +15,7 @@
 //      weight x 1/8 ... 8, factors of 2 apart), wide shape, no local
 //      relaxation, on the first sample source;
 //   2. the two fastest of (1) in both shapes, on up to two sources;
-//   3. sparse graphs (mean out-degree < 20): the two fastest of (1) of each
+//   3. sparse graphs (mean out-degree < 20): the three fastest of (1) of each
 //      rule, in the winning shape with local budgets 64, 256 and 1024, and in
 //      the narrow shape with fused super-sparse steps (SSSP_SOLVE_FUSED) with
 //      local budgets 0, 64, 256 and 1024;
@@ -222,11 +222,13 @@ int sssp_autotune_ex(sssp_graph* g, const uint32_t* sources, uint32_t k, uint32_
         //     multi-hop steps), so it is tried on the two best of (1) of each
         //     rule, in the shape that won (2)
         if (g->n && (double)g->m / (double)g->n < 20.0) {
+            // (the ranking of (1) -- wide, unfused, no local relaxation -- is a
+            // rough guide here, so the three best of each rule are taken)
             std::vector<Candidate> base;
             for (sssp_algo a : {SSSP_RHO, SSSP_DELTA_STAR}) {
                 int taken = 0;
                 for (const Candidate& c : sorted)
-                    if (c.algo == a && taken < 2) { base.push_back(c); ++taken; }
+                    if (c.algo == a && taken < 3) { base.push_back(c); ++taken; }
             }
             // ... and, since fused super-sparse steps change the ranking as
             // much, the same in the narrow shape with fused steps (also

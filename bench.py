@@ -475,7 +475,9 @@ def measure_serving(sssp, G, g, torch, sources, rates, window_s=1.0, hard_s=10.0
     algo = sssp.SSSP_RHO if algo is None else algo
     srv = sssp.sssp_server_create(G.handle, slots=slots, algo=algo, param=param, gang=gang, gang_wait_ns=gang_wait_ns)
     S = sssp.sssp_server_slots(srv)
-    nbuf = S + 32
+    # enough client buffers that a full cohort of S queries can wait while S
+    # run (a shared-scan server admits queries in cohorts of S)
+    nbuf = 2 * S + 32
     free_b, _ = torch.cuda.mem_get_info()
     nbuf = int(max(1, min(nbuf, (free_b * 0.8) // (8 * g.n))))
     bufs = [torch.empty(g.n, dtype=torch.int64, device="cuda") for _ in range(nbuf)]

@@ -971,8 +971,8 @@ def main():
         # the server's configuration and slot count from the batch autotuner
         btune = sssp.sssp_autotune_batch(G.handle, gg_sources(g)[:64], 1 << sssp.SSSP_RHO, stream)
         torch.cuda.empty_cache()
-        served = {"rmat22": measure_serving(sssp, G, g, torch, gg_sources(g), [100, 1000], window_s=0.5,
-                                            hard_s=6.0, slots=0, algo=btune["algo"], param=btune["param"],
+        served = {"rmat22": measure_serving(sssp, G, g, torch, gg_sources(g), [100, 1000], window_s=2.0,
+                                            hard_s=10.0, slots=0, algo=btune["algo"], param=btune["param"],
                                             tuned=True)}
         served["rmat22"]["batch_tuning"] = btune
 

@@ -627,11 +627,9 @@ __device__ __forceinline__ void block_reduce_2add_min(uint64_t& a, uint64_t& b, 
     }
 }
 
-// Block-wide reduction of four sums and two minima (s_tmp: 6 * kWarps);
-// results valid in thread 0.
-__device__ __forceinline__ void block_reduce_4add_2min(uint64_t (&a)[4], uint64_t (&mn)[2], uint64_t* s_tmp)
+// Warp-wide reduction of four sums and two minima (every lane gets the results).
+__device__ __forceinline__ void warp_reduce_4add_2min(uint64_t (&a)[4], uint64_t (&mn)[2])
 {
-    const uint32_t lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
 #pragma unroll
@@ -640,30 +638,6 @@ __device__ __forceinline__ void block_reduce_4add_2min(uint64_t (&a)[4], uint64_
         for (int t = 0; t < 2; ++t) {
             const uint64_t y = __shfl_xor_sync(FULL_MASK, mn[t], o);
             mn[t] = y < mn[t] ? y : mn[t];
-        }
-    }
-    __syncthreads();
-    if (lane == 0) {
-#pragma unroll
-        for (int t = 0; t < 4; ++t) s_tmp[t * kWarps + wid] = a[t];
-#pragma unroll
-        for (int t = 0; t < 2; ++t) s_tmp[(4 + t) * kWarps + wid] = mn[t];
-    }
-    __syncthreads();
-    if (wid == 0) {
-#pragma unroll
-        for (int t = 0; t < 4; ++t) a[t] = lane < (uint32_t)kWarps ? s_tmp[t * kWarps + lane] : 0;
-#pragma unroll
-        for (int t = 0; t < 2; ++t) mn[t] = lane < (uint32_t)kWarps ? s_tmp[(4 + t) * kWarps + lane] : kInf;
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) {
-#pragma unroll
-            for (int t = 0; t < 4; ++t) a[t] += __shfl_xor_sync(FULL_MASK, a[t], o);
-#pragma unroll
-            for (int t = 0; t < 2; ++t) {
-                const uint64_t y = __shfl_xor_sync(FULL_MASK, mn[t], o);
-                mn[t] = y < mn[t] ? y : mn[t];
-            }
         }
     }
 }

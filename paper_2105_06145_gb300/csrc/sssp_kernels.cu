@@ -625,54 +625,59 @@ __global__ void __launch_bounds__(kBlock, kMinBlocks) solve_kernel(SolveParams p
                                        &ctrl->qsize[nx], &ctrl->status, Qnext, n, p.lrel);
             }
 
-            // (c) block-aggregated flush of what is left in the warps' staging
-            if (lane == 0) s_wcnt[wid] = stc;
+            // (c) block-aggregated flush of what is left in the warps' staging,
+            //     together with the step's counters (a fused step's Extract
+            //     counters too): warp sums by shuffles, then one block phase
+            //     (warp 0) for the flush reservation and the counters
+            uint64_t sums[4] = {lupd, ledg, f_cnt, f_edg}, mins[2] = {lmin, f_kmin};
+            warp_reduce_4add_2min(sums, mins);
+            if (lane == 0) {
+                s_wcnt[wid] = stc;
+#pragma unroll
+                for (int t = 0; t < 4; ++t) s_tmp[t * kWarps + wid] = sums[t];
+#pragma unroll
+                for (int t = 0; t < 2; ++t) s_tmp[(4 + t) * kWarps + wid] = mins[t];
+            }
             __syncthreads();
             if (wid == 0) {
                 const uint32_t cnt = lane < (uint32_t)kWarps ? s_wcnt[lane] : 0u;
                 const uint32_t incl = (uint32_t)warp_incl_scan64(cnt, lane);
                 uint32_t tot = __shfl_sync(FULL_MASK, incl, 31);
                 if (lane < (uint32_t)kWarps) s_wcnt[lane] = incl - cnt;
+#pragma unroll
+                for (int t = 0; t < 4; ++t) sums[t] = lane < (uint32_t)kWarps ? s_tmp[t * kWarps + lane] : 0ull;
+#pragma unroll
+                for (int t = 0; t < 2; ++t) mins[t] = lane < (uint32_t)kWarps ? s_tmp[(4 + t) * kWarps + lane] : kInf;
+                warp_reduce_4add_2min(sums, mins);
                 if (lane == 0) {
                     const uint32_t base = tot ? atomicAdd(&ctrl->qsize[nx], tot) : 0u;
                     if ((uint64_t)base + tot > (uint64_t)n) { raise_error(&ctrl->bar, &ctrl->status, SSSP_ERR_INTERNAL); tot = 0; }
                     s_base[0] = base;
                     s_base[1] = tot;
+                    const uint64_t bu = sums[0], bl = sums[1], bf = sums[2], be = sums[3], bm = mins[0], bk = mins[1];
+                    if (bf) atomicAdd(&ctrl->fcount[c], (unsigned int)bf);
+                    if (be) atomicAdd(&ctrl->fedges[c], (unsigned long long)be);
+                    if (algo_tracks_qmin(p.algo) && bk != kInf) atomicMin(&ctrl->qmin[nx], (unsigned long long)bk);
+                    if (bu) atomicAdd(&ctrl->updates[c], (unsigned long long)bu);
+                    if (bl) atomicAdd(&ctrl->ledges[c], (unsigned long long)bl);
+                    if (algo_tracks_qmin(p.algo) && bm != kInf) {
+                        atomicMin(&ctrl->qmin[nx], (unsigned long long)bm);
+                        atomicMin(&ctrl->umin[nx], (unsigned long long)bm);
+                    }
+                    if (p.trace && k - 1 < p.trace_cap) {
+                        const unsigned long long now = global_timer_ns() - s_t_start;
+                        atomicMin((unsigned long long*)&p.trace[k - 1].t_relax_end_min, now);
+                        atomicMax((unsigned long long*)&p.trace[k - 1].t_relax_end_max, now);
+                    }
+                    // step k-1 is complete: fold its counters into the totals and
+                    // recycle its slot (reused for Q_{k+2} from the next step on)
+                    if (blockIdx.x == 0) fold_step(p, ctrl, pv, k - 1);
                 }
-                // step k-1 is complete: fold its counters into the totals and
-                // recycle its slot (reused for Q_{k+2} from the next step on)
-                if (blockIdx.x == 0 && lane == 0) fold_step(p, ctrl, pv, k - 1);
             }
             __syncthreads();
             if (s_base[1] != 0) {
                 const uint32_t wb = s_base[0] + s_wcnt[wid];
                 for (uint32_t i = lane; i < stc; i += 32) Qnext[wb + i] = stage[i];
-            }
-            // (with the fused step's Extract counters: one reduction)
-            uint64_t bu = lupd, bl = ledg, bm = lmin;
-            uint64_t bf = 0, be = 0, bk = kInf;
-            if (kFusedSteps && fused) {
-                uint64_t sums[4] = {bu, bl, f_cnt, f_edg}, mins[2] = {bm, f_kmin};
-                block_reduce_4add_2min(sums, mins, s_tmp);
-                bu = sums[0]; bl = sums[1]; bf = sums[2]; be = sums[3]; bm = mins[0]; bk = mins[1];
-            } else {
-                block_reduce_2add_min(bu, bl, bm, s_tmp);
-            }
-            if (tid == 0) {
-                if (bf) atomicAdd(&ctrl->fcount[c], (unsigned int)bf);
-                if (be) atomicAdd(&ctrl->fedges[c], (unsigned long long)be);
-                if (algo_tracks_qmin(p.algo) && bk != kInf) atomicMin(&ctrl->qmin[nx], (unsigned long long)bk);
-                if (bu) atomicAdd(&ctrl->updates[c], (unsigned long long)bu);
-                if (bl) atomicAdd(&ctrl->ledges[c], (unsigned long long)bl);
-                if (algo_tracks_qmin(p.algo) && bm != kInf) {
-                    atomicMin(&ctrl->qmin[nx], (unsigned long long)bm);
-                    atomicMin(&ctrl->umin[nx], (unsigned long long)bm);
-                }
-                if (p.trace && k - 1 < p.trace_cap) {
-                    const unsigned long long now = global_timer_ns() - s_t_start;
-                    atomicMin((unsigned long long*)&p.trace[k - 1].t_relax_end_min, now);
-                    atomicMax((unsigned long long*)&p.trace[k - 1].t_relax_end_max, now);
-                }
             }
         }
         if (!grid_sync_err(&ctrl->bar, &ctrl->status, &s_bar_target, p.timeout_ns)) break;

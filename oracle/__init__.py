@@ -83,7 +83,7 @@ def _L():
         lib.oracle_delta_theta.restype = u64
         lib.oracle_delta_finish.argtypes = [ctypes.POINTER(u64), u64, u64]
         lib.oracle_delta_finish.restype = None
-        lib.oracle_stepping.argtypes = [u32, P, P, P, u32, i32, u64, u64, u32, P, P,
+        lib.oracle_stepping.argtypes = [u32, P, P, P, u32, i32, u64, u64, u32, u32, u64, P, P,
                                         ctypes.POINTER(Stats)]
         lib.oracle_stepping.restype = i32
         lib.oracle_lbpq_extract.argtypes = [u32, P, P, u64, P]
@@ -188,15 +188,19 @@ def delta_finish(i: int, theta: int, min_new: int) -> int:
 
 
 def stepping(g, s: int, algo: int, param: int, seed: int = 0,
-             want_ext: bool = False, reduced: int = 2) -> tuple[np.ndarray, dict, np.ndarray | None]:
+             want_ext: bool = False, reduced: int = 2, warm_steps: int = 0,
+             warm_rho: int = 0) -> tuple[np.ndarray, dict, np.ndarray | None]:
     """Algorithm 1 run sequentially: (dist, stats, per-vertex extraction counts).
-    reduced: rho-Stepping's count of dense steps that use rho/10 (the paper's 2)."""
+    reduced: rho-Stepping's count of dense steps that use rho/10 (the paper's 2).
+    warm_steps, warm_rho: rho-Stepping's first warm_steps steps use rho =
+    warm_rho, without the dense-step reduction and without counting as dense
+    steps (0 = the paper's schedule)."""
     off, tgt, w = _arrs(g)
     dist = np.empty(g.n, dtype=np.uint64)
     ext = np.empty(g.n, dtype=np.uint32) if want_ext else None
     st = Stats()
     rc = _L().oracle_stepping(g.n, off.ctypes.data, tgt.ctypes.data, w.ctypes.data, s, algo,
-                              param, seed, reduced, dist.ctypes.data,
+                              param, seed, reduced, warm_steps, warm_rho, dist.ctypes.data,
                               ext.ctypes.data if want_ext else None, ctypes.byref(st))
     if rc != 0:
         raise ValueError("oracle_stepping failed")

@@ -440,7 +440,10 @@ enum { ORC_RHO = 0, ORC_DELTA_STAR = 1, ORC_BELLMAN_FORD = 2, ORC_DELTA = 3, ORC
  * appends the id, Extract scans the queued ids and packs those with key <=
  * theta).  algo selects the ExtDist (and FinishCheck) of Table 2:
  *   ORC_RHO          theta from oracle_rho_extdist (param = rho >= 1;
- *                    rho_reduced = dense steps that use rho/10, the paper's 2)
+ *                    rho_reduced = dense steps that use rho/10, the paper's 2;
+ *                    the first warm_steps steps use rho = warm_rho instead,
+ *                    without the reduction, and are not counted as dense
+ *                    steps -- warm_steps = 0 is the paper's schedule)
  *   ORC_DELTA_STAR   theta from oracle_delta_extdist (param = Delta >= 1)
  *   ORC_BELLMAN_FORD theta = +infinity (param ignored)
  *   ORC_DELTA        theta = i*Delta with FinishCheck (oracle_delta_theta /
@@ -454,10 +457,11 @@ enum { ORC_RHO = 0, ORC_DELTA_STAR = 1, ORC_BELLMAN_FORD = 2, ORC_DELTA = 3, ORC
  */
 int oracle_stepping(uint32_t n, const uint64_t* off, const uint32_t* tgt,
                     const uint32_t* w, uint32_t s, int algo, uint64_t param,
-                    uint64_t seed, uint32_t rho_reduced, uint64_t* dist, uint32_t* ext_count,
-                    oracle_stats* st)
+                    uint64_t seed, uint32_t rho_reduced, uint32_t warm_steps, uint64_t warm_rho,
+                    uint64_t* dist, uint32_t* ext_count, oracle_stats* st)
 {
     if (s >= n) return -1;
+    if (algo == ORC_RHO && warm_steps > 0 && warm_rho == 0) return -1;
     if (algo != ORC_BELLMAN_FORD && algo != ORC_DIJKSTRA && param == 0) return -1;
     if (algo < 0 || algo > 4) return -1;
     uint8_t* inq = (uint8_t*)calloc(n, 1);
@@ -492,6 +496,10 @@ int oracle_stepping(uint32_t n, const uint64_t* off, const uint32_t* tgt,
             theta = oracle_delta_theta(&delta_i, param, qmin);
         } else if (algo == ORC_DIJKSTRA) {
             theta = qmin;
+        } else if (z.steps <= warm_steps) {
+            /* warm-up step: rho = warm_rho, no dense-step reduction */
+            theta = oracle_rho_extdist(Q, qlen, dist, n, warm_rho, seed, z.steps, 0, 0);
+            if ((uint64_t)qlen <= warm_rho) z.partial_steps++; else z.full_steps++;
         } else {
             int dense = (uint64_t)qlen * 20u > (uint64_t)n;
             uint64_t rho_eff = param;

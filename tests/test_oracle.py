@@ -308,6 +308,51 @@ def test_stepping_with_any_reduced_count(reduced):
             assert st["partial_steps"] <= kn + 1
 
 
+@pytest.mark.parametrize("warm_steps,warm_rho", [(1, 1), (3, 4), (6, 256), (50, 16)])
+def test_stepping_with_a_warm_up(warm_steps, warm_rho):
+    """Warm-up steps (the first warm_steps steps use rho = warm_rho) change
+    thresholds only: distances equal Dijkstra's, and Lemma 5.1's extraction
+    bound and the partial-step bound of Theorem 5.3's proof still hold (every
+    warm-up theta is a sampled queued key, as in any rho-Stepping step)."""
+    for g in _bounded_graphs():
+        s = int(np.flatnonzero(gg.largest_cc(g))[0])
+        d = oracle.dijkstra(g, s)
+        h, kn = oracle.hops(g, s)
+        for rho in (64, 1 << 10):
+            ds, st, ext = oracle.stepping(g, s, oracle.RHO, rho, seed=3, want_ext=True, reduced=6,
+                                          warm_steps=warm_steps, warm_rho=warm_rho)
+            assert np.array_equal(d, ds), (g.name, rho, warm_steps, warm_rho)
+            reach = d != oracle.INF
+            hv = h.astype(np.int64)
+            hv[s] = 1
+            assert np.all(ext[reach].astype(np.int64) <= hv[reach])
+            assert st["partial_steps"] <= kn + 1
+
+
+def test_warm_up_special_cases():
+    """No warm-up steps is the paper's schedule (same thresholds, so the same
+    steps and work); a warm-up covering the whole solve is rho-Stepping with
+    rho = warm_rho and no dense-step reduction; a warm-up with warm_rho = rho
+    is the schedule whose reduced dense steps come only after it (with no
+    reduced steps at all, the same as no warm-up)."""
+    g = gg.rmat(12, 8, gen_seed=31, wseed=32)
+    s = int(np.flatnonzero(gg.largest_cc(g))[0])
+    d = oracle.dijkstra(g, s)
+    for rho in (16, 300):
+        base = oracle.stepping(g, s, oracle.RHO, rho, seed=5, reduced=2)
+        same = oracle.stepping(g, s, oracle.RHO, rho, seed=5, reduced=2, warm_steps=0, warm_rho=7)
+        assert np.array_equal(base[0], same[0]) and base[1] == same[1]
+        for wr in (1, 3, 40):
+            all_warm = oracle.stepping(g, s, oracle.RHO, rho, seed=5, reduced=6, warm_steps=10 ** 6, warm_rho=wr)
+            plain = oracle.stepping(g, s, oracle.RHO, wr, seed=5, reduced=0)
+            assert np.array_equal(all_warm[0], d) and all_warm[1] == plain[1], (rho, wr)
+        w_same = oracle.stepping(g, s, oracle.RHO, rho, seed=5, reduced=0, warm_steps=4, warm_rho=rho)
+        no_red = oracle.stepping(g, s, oracle.RHO, rho, seed=5, reduced=0)
+        assert w_same[1] == no_red[1]
+    with pytest.raises(ValueError):
+        oracle.stepping(g, s, oracle.RHO, 64, warm_steps=2, warm_rho=0)
+
+
 # --------------------------------------------------------------------------
 # Algorithm 1 run sequentially: exact distances and the paper's step bounds
 # --------------------------------------------------------------------------

@@ -680,7 +680,7 @@ def run_trace(args):
     per-step trace on (sssp_options.trace), printed as a per-step phase table
     (device times of Extract, the first grid barrier, the relaxation and the
     end-of-step barrier) and a JSON summary.  The configuration is the bench's
-    (rho-Stepping, --param, --rho-reduced) unless --trace-config gives
+    (rho-Stepping, --param, --rho-reduced, --rho-warmup) unless --trace-config gives
     algo,param,shape,local_budget[,flags] (flags: extra SSSP_SOLVE_* bits, e.g.
     2 = fused super-sparse steps, whose steps have no barrier after Extract:
     there the relaxation column starts when block 0 has extracted)."""
@@ -702,6 +702,9 @@ def run_trace(args):
     cap = 100000
     trb = torch.zeros(cap * sssp.TRACE_RECORD_BYTES // 8, dtype=torch.int64, device="cuda")
     base = dict(flags=sssp.SSSP_SOLVE_BIDIRECTIONAL | xflags, shape=shape, local_budget=local, rho_reduced=red)
+    if a == sssp.SSSP_RHO:
+        ws, wr = (int(x) for x in args.rho_warmup.split(","))
+        base.update(rho_warmup_steps=ws, rho_warmup=wr)
     s0 = srcs[0]
     for _ in range(2):
         G.solve(s0, a, prm, d, stream, sssp.make_options(**base))
@@ -726,7 +729,8 @@ def run_trace(args):
                   f"extract_us={ext[i] / 1e3:7.1f} barrier_us={bar1[i] / 1e3:5.1f} relax_us={rel[i] / 1e3:7.1f} "
                   f"end_us={bar2[i] / 1e3:5.1f}")
     summary = {"workload": label, "source": int(s0), "algo": ALGO_NAMES[a], "param": prm, "shape": shape,
-               "local_budget": local, "flags": int(base["flags"]), "rho_reduced": args.rho_reduced, "ms_untraced": e0.elapsed_time(e1),
+               "local_budget": local, "flags": int(base["flags"]), "rho_reduced": args.rho_reduced,
+               "rho_warmup": args.rho_warmup if a == sssp.SSSP_RHO else None, "ms_untraced": e0.elapsed_time(e1),
                "steps": int(st["steps"]), "edges_per_m": st["edges"] / g.m,
                "phase_us_sum": {"extract": float(ext.sum() / 1e3), "barrier_after_extract": float(bar1.sum() / 1e3),
                                 "relax": float(rel.sum() / 1e3), "end_of_step": float(bar2.sum() / 1e3)},
@@ -786,6 +790,8 @@ def main():
     ap.add_argument("--no-bidir", action="store_true", help="plain push relaxation only")
     ap.add_argument("--rho-reduced", type=int, default=6,
                     help="rho-Stepping: dense steps that use rho/10 (the paper uses 2; 0 = none)")
+    ap.add_argument("--rho-warmup", default="6,256",
+                    help="rho-Stepping: STEPS,RHO -- the first STEPS steps use rho = RHO (0,0 = none)")
     ap.add_argument("--no-batch", action="store_true", help="skip the batched-solve measurements")
     ap.add_argument("--no-serve", action="store_true", help="skip the serving measurement")
     ap.add_argument("--no-other", action="store_true", help="skip the road-like and k-NN workloads")
@@ -849,6 +855,10 @@ def main():
     # estimation"); the count is a tuning knob (the paper's 2 was tuned on its
     # 96-core machine; 6 measured best for this workload on the GB300)
     red_opt = args.rho_reduced if args.rho_reduced > 0 else sssp.SSSP_RHO_REDUCED_NONE
+    # ... and may start with warm-up steps at a small rho (the first, sparse
+    # waves, which hold the high-degree vertices, in small groups)
+    warm_steps, warm_rho = (int(x) for x in args.rho_warmup.split(","))
+    warm = dict(rho_warmup_steps=warm_steps, rho_warmup=warm_rho) if algo == sssp.SSSP_RHO else {}
     stream_obj = torch.cuda.Stream()
     stream = stream_obj.cuda_stream
     dist_out = torch.empty(g.n, dtype=torch.int64, device="cuda")
@@ -858,13 +868,13 @@ def main():
     K, W = args.steps, args.warmup
     stats_buf = torch.zeros((K, sssp.STATS_BYTES // 8), dtype=torch.int64, device="cuda")
     with torch.cuda.stream(stream_obj):
-        wopts = sssp.make_options(flags=solve_flags, rho_reduced=red_opt)
+        wopts = sssp.make_options(flags=solve_flags, rho_reduced=red_opt, **warm)
         for i in range(W):
             G.solve(rank_srcs[i % nsrc], algo, param, dist_out, stream, wopts)
         assert G.status(stream) == sssp.SSSP_OK
         ev = [torch.cuda.Event(enable_timing=True) for _ in range(K + 1)]
-        opts = [sssp.make_options(stats_out_ptr=stats_buf[i].data_ptr(), flags=solve_flags, rho_reduced=red_opt)
-                for i in range(K)]
+        opts = [sssp.make_options(stats_out_ptr=stats_buf[i].data_ptr(), flags=solve_flags, rho_reduced=red_opt,
+                                  **warm) for i in range(K)]
         torch.cuda.synchronize()
         if pg:
             pg.barrier()
@@ -932,7 +942,8 @@ def main():
                        (sssp.SSSP_DELTA_STAR, 1 << 13), (sssp.SSSP_DELTA_STAR, 1 << 15),
                        (sssp.SSSP_DELTA_STAR, 1 << 17), (sssp.SSSP_BELLMAN_FORD, 0)):
             sbuf = torch.zeros((nsrc, sssp.STATS_BYTES // 8), dtype=torch.int64, device="cuda")
-            sopt = [sssp.make_options(stats_out_ptr=sbuf[i].data_ptr(), flags=solve_flags, rho_reduced=red_opt)
+            sw = dict(rho_warmup_steps=warm_steps, rho_warmup=warm_rho) if sa == sssp.SSSP_RHO else {}
+            sopt = [sssp.make_options(stats_out_ptr=sbuf[i].data_ptr(), flags=solve_flags, rho_reduced=red_opt, **sw)
                     for i in range(nsrc)]
             ts = _timed(torch, stream_obj, lambda: [G.solve(srcs[i], sa, sp, dist_out, stream, sopt[i])
                                                     for i in range(nsrc)])
@@ -1009,6 +1020,7 @@ def main():
             "scaling": "weak", "vs_baseline": None, "dtype": "u64", "data": "synthetic",
             "config": {"workload": label, "n": g.n, "m": g.m, "algo": args.algo, "param": param,
                        "rho_reduced_dense_steps": args.rho_reduced if args.algo == "rho" else None,
+                       "rho_warmup": {"steps": warm_steps, "rho": warm_rho} if args.algo == "rho" else None,
                        "bidirectional": bidir, "graph_layout": "relabelled by decreasing degree (SSSP_GRAPH_REORDER)",
                        "sources": nsrc, "parallelism": "replicas" if world > 1 else "single",
                        "l2": "inputs larger than L2 (packed edges %.2f GB > 129 MB L2)" % (8 * g.m / 1e9),

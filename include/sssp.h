@@ -121,6 +121,16 @@ typedef struct {
     uint32_t chunk;          /* edges per chunk record (a chunk never crosses a multiple
                                 of this in the edge array).  0 = 256; else 128, 256, 512
                                 or 1024.  Neither cut-off changes the distances.       */
+    uint32_t rho_warmup_steps; /* rho-Stepping: the first rho_warmup_steps steps use
+                                rho = rho_warmup instead (without the dense-step
+                                reduction, and not counted among the dense steps of
+                                rho_reduced), so that the first, sparse waves -- which
+                                on power-law graphs hold the high-degree vertices --
+                                advance in small, nearly ordered groups.  0 = none (the
+                                paper's schedule); rho_warmup must then be 0 too.  An
+                                extension of Sec. 6's reduced rho for early steps; the
+                                distances are the same.  Other rules ignore both.      */
+    uint32_t rho_warmup;     /* rho of the warm-up steps (>= 1 when rho_warmup_steps > 0) */
 } sssp_options;
 
 #define SSSP_RHO_REDUCED_NONE 0xFFFFFFFFu /* sssp_options.rho_reduced: plain rho on every step */
@@ -487,6 +497,8 @@ typedef struct {
     uint32_t small_deg;      /* sssp_options.small_deg (0 = 32; single solves only)         */
     uint32_t chunk;          /* sssp_options.chunk (0 = 256; single solves only)            */
     uint32_t batch_mode;     /* batch autotuner: SSSP_BATCH_SHARED or SSSP_BATCH_SEPARATE   */
+    uint32_t rho_warmup_steps; /* sssp_options.rho_warmup_steps (single solves only)        */
+    uint32_t rho_warmup;     /* sssp_options.rho_warmup                                     */
 } sssp_tuning;
 
 /*
@@ -497,7 +509,9 @@ typedef struct {
  * out-degree < 20 the three best parameters of each rule in the winning shape
  * with local budgets 64, 256, 1024 and in the narrow shape with
  * SSSP_SOLVE_FUSED and local budgets 0, 64, 256, 1024; for a rho winner the
- * count of dense steps at rho/10 (2, 4, 6, 8, none); the degree-bin cut-offs
+ * count of dense steps at rho/10 (2, 4, 6, 8, none), then 4, 6 or 8 warm-up
+ * steps at rho 256 (rho_warmup_steps; with that count, 2 or 6 reduced dense
+ * steps after them); the degree-bin cut-offs
  * (small_deg 16, 32, 64, then chunk 128, 256, 512); the winner is re-timed on
  * all k sources.
  * Bidirectional relaxation is used when the graph was created

@@ -386,7 +386,16 @@ int sssp_solve_ex(const sssp_graph* gc, uint32_t source, sssp_algo algo, uint64_
         p.iperm = g->d_iperm;
         p.source = g->h_perm[source];
     }
+    if (o.rho_warmup_steps != 0 && o.rho_warmup == 0) return SSSP_ERR_INVALID_ARG;
+    if (o.rho_warmup_steps == 0 && o.rho_warmup != 0) return SSSP_ERR_INVALID_ARG;
     p.sample_cap = (algo == SSSP_RHO) ? rho_sample_bound(g->n, param) : 0;
+    if (algo == SSSP_RHO && o.rho_warmup_steps != 0) {
+        p.warm_steps = o.rho_warmup_steps;
+        p.warm_rho = o.rho_warmup;
+        // warm-up steps sample at rho_warmup itself (the bound assumes rho/10)
+        const uint32_t wcap = rho_sample_bound(g->n, 10ull * o.rho_warmup);
+        if (wcap > p.sample_cap) p.sample_cap = wcap;
+    }
     if (o.shape > SSSP_SHAPE_NARROW) return SSSP_ERR_INVALID_ARG;
     const int shape = o.shape == SSSP_SHAPE_NARROW ? 1 : 0;
     const size_t dyn_smem = kShapes[shape].smem();

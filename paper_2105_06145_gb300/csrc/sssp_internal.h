@@ -122,6 +122,10 @@ struct SolveParams {
     // (vertex, -, distance it was relaxed with) -- the vertices the block
     // extracted in a fused step, re-checked after the step; null = no fused steps
     uint4* fre;
+    // rho-Stepping warm-up: steps 1..warm_steps use rho = warm_rho (no
+    // dense-step reduction, not counted as dense steps); 0 = none
+    uint32_t warm_steps;
+    uint64_t warm_rho;
     // relabelled graph (SSSP_GRAPH_REORDER): the solve runs on the relabelled
     // copy with dist = internal distances in the new ids; at the end
     // dist_out[v] = dist[perm[v]] for every caller id v; ext_count is indexed

@@ -197,8 +197,12 @@ __global__ void __launch_bounds__(kBlock, kMinBlocks) solve_kernel(SolveParams p
             // rho-Stepping: theta is selected from s sampled keys in the first
             // Extract round below, with that round's loads in flight
             theta = kInf;
-            rho_sample = rho_sample_plan(q, n, p.param, dense_seen, p.rho_reduced, &s_cnt, &r_idx);
-            if ((uint64_t)q * 20ull > (uint64_t)n) ++dense_seen;
+            // (warm-up steps: rho = warm_rho, no dense-step reduction, not
+            // counted as dense steps)
+            const bool warm = k <= p.warm_steps;
+            rho_sample = rho_sample_plan(q, n, warm ? p.warm_rho : p.param, warm ? 0xFFFFFFFFu : dense_seen,
+                                         p.rho_reduced, &s_cnt, &r_idx);
+            if ((uint64_t)q * 20ull > (uint64_t)n && !warm) ++dense_seen;
         }
 
         // SSSP_SOLVE_FUSED: a super-sparse step whose theta every block has

@@ -20,7 +20,9 @@
 //      the narrow shape with fused super-sparse steps (SSSP_SOLVE_FUSED) with
 //      local budgets 0, 64, 256 and 1024;
 //   4. rho-Stepping winner: the number of dense steps that use rho/10 (the
-//      paper's 2, then 4, 6, 8 and none);
+//      paper's 2, then 4, 6, 8 and none), then 4, 6 or 8 warm-up steps at
+//      rho = 256 (sssp_options.rho_warmup_steps), each with the count found,
+//      2 or 6 reduced dense steps after it;
 //   5. the degree-bin cut-offs: small-degree bound 16 and 64 (default 32),
 //      then chunk records of 128 and 512 edges (default 256);
 //   6. the winner on every sample source (sssp_tuning.ms).
@@ -62,6 +64,8 @@ struct Candidate {
     uint32_t small_deg;     // 0 = default
     uint32_t chunk;         // 0 = default
     uint32_t fused;         // 1 = SSSP_SOLVE_FUSED
+    uint32_t warm_steps;    // sssp_options.rho_warmup_steps / rho_warmup
+    uint32_t warm_rho;
 };
 
 // Mean time of one solve per source (ms); a failed solve is reported as rc.
@@ -74,6 +78,8 @@ int time_config(const sssp_graph* g, const Candidate& c, const uint32_t* srcs, u
     o.shape = c.shape;
     o.local_budget = c.local;
     o.rho_reduced = c.rho_reduced;
+    o.rho_warmup_steps = c.warm_steps;
+    o.rho_warmup = c.warm_rho;
     o.small_deg = c.small_deg;
     o.chunk = c.chunk;
     double total = 0;
@@ -176,7 +182,7 @@ int sssp_autotune_ex(sssp_graph* g, const uint32_t* sources, uint32_t k, uint32_
     }
     int rc = SSSP_OK;
     uint32_t timed = 0;
-    Candidate best{SSSP_RHO, 0, SSSP_SHAPE_WIDE, 0, 0, 0, 0, 0, 0};
+    Candidate best{SSSP_RHO, 0, SSSP_SHAPE_WIDE, 0, 0, 0, 0, 0, 0, 0, 0};
     do {
         // rule / parameter candidates: rho = n/4 ... n/1024 (>= 64) and Delta =
         // mean weight x {1/8 ... 8}, each a factor of 2 apart
@@ -186,12 +192,12 @@ int sssp_autotune_ex(sssp_graph* g, const uint32_t* sources, uint32_t k, uint32_
             if (rho < 64) rho = 64;
             bool dup = false;
             for (const Candidate& c : cand) dup = dup || (c.algo == SSSP_RHO && c.param == rho);
-            if (!dup) cand.push_back({SSSP_RHO, rho, SSSP_SHAPE_WIDE, 0, 0, 0, 0, 0, 0});
+            if (!dup) cand.push_back({SSSP_RHO, rho, SSSP_SHAPE_WIDE, 0, 0, 0, 0, 0, 0, 0, 0});
         }
         for (double f : {0.125, 0.25, 0.5, 1.0, 2.0, 4.0, 8.0}) {
             if (!(rules & (1u << SSSP_DELTA_STAR))) break;
             const double d = g->mean_w * f;
-            cand.push_back({SSSP_DELTA_STAR, d > 1.0 ? (uint64_t)d : 1ull, SSSP_SHAPE_WIDE, 0, 0, 0, 0, 0, 0});
+            cand.push_back({SSSP_DELTA_STAR, d > 1.0 ? (uint64_t)d : 1ull, SSSP_SHAPE_WIDE, 0, 0, 0, 0, 0, 0, 0, 0});
         }
         // one warm-up solve (first launch of the kernel, lazy allocations)
         double ignore;
@@ -259,6 +265,22 @@ int sssp_autotune_ex(sssp_graph* g, const uint32_t* sources, uint32_t k, uint32_
                 if (c.ms < best.ms) best = c;
             }
             if (rc != SSSP_OK) break;
+            // ... and warm-up steps at a small rho (the first, sparse waves in
+            // small groups); each count of reduced dense steps again after it
+            const Candidate base2 = best;
+            for (uint32_t ws : {4u, 6u, 8u}) {
+                for (uint32_t red : {base2.rho_reduced, 2u, 6u}) {
+                    Candidate c = base2;
+                    c.warm_steps = ws;
+                    c.warm_rho = 256;
+                    c.rho_reduced = red == 2u ? 0u : red;
+                    if ((rc = time_config(g, c, sources, ns2, dist, st, e0, e1, &c.ms)) != SSSP_OK) break;
+                    ++timed;
+                    if (c.ms < best.ms) best = c;
+                }
+                if (rc != SSSP_OK) break;
+            }
+            if (rc != SSSP_OK) break;
         }
         // (5) degree-bin cut-offs: the small-degree bound, then the chunk length
         {
@@ -298,6 +320,8 @@ int sssp_autotune_ex(sssp_graph* g, const uint32_t* sources, uint32_t k, uint32_
     t.ms = best.ms;
     t.candidates = timed;
     t.rho_reduced = best.rho_reduced;
+    t.rho_warmup_steps = best.warm_steps;
+    t.rho_warmup = best.warm_rho;
     t.small_deg = best.small_deg;
     t.chunk = best.chunk;
     {
@@ -512,6 +536,7 @@ int sssp_graph_set_tuning(sssp_graph* g, const sssp_tuning* t)
     if (t->chunk != 0 && t->chunk != 128 && t->chunk != 256 && t->chunk != 512 && t->chunk != 1024)
         return SSSP_ERR_INVALID_ARG;
     if (t->batch_mode > SSSP_BATCH_SEPARATE) return SSSP_ERR_INVALID_ARG;
+    if ((t->rho_warmup_steps == 0) != (t->rho_warmup == 0)) return SSSP_ERR_INVALID_ARG;
     std::lock_guard<std::mutex> lk(g->mu);
     g->tuning = *t;
     g->tuned = true;
@@ -535,6 +560,8 @@ int sssp_solve_tuned(const sssp_graph* g, uint32_t source, uint64_t* dist_out, v
     o.shape = t.shape;
     o.local_budget = t.local_budget;
     o.rho_reduced = t.rho_reduced;
+    o.rho_warmup_steps = t.rho_warmup_steps;
+    o.rho_warmup = t.rho_warmup;
     o.small_deg = t.small_deg;
     o.chunk = t.chunk;
     return sssp_solve_ex(g, source, t.algo, t.param, dist_out, &o, stream);

@@ -70,7 +70,8 @@ class sssp_options(ctypes.Structure):
                 ("stats_out", ctypes.c_void_p), ("solve_timeout_ns", ctypes.c_uint64),
                 ("flags", ctypes.c_uint32), ("local_budget", ctypes.c_uint32),
                 ("shape", ctypes.c_uint32), ("rho_reduced", ctypes.c_uint32),
-                ("small_deg", ctypes.c_uint32), ("chunk", ctypes.c_uint32)]
+                ("small_deg", ctypes.c_uint32), ("chunk", ctypes.c_uint32),
+                ("rho_warmup_steps", ctypes.c_uint32), ("rho_warmup", ctypes.c_uint32)]
 
 
 TRACE_RECORD_BYTES = ctypes.sizeof(sssp_step_trace)
@@ -177,7 +178,8 @@ class sssp_tuning(ctypes.Structure):
                 ("flags", ctypes.c_uint32), ("local_budget", ctypes.c_uint32), ("ms", ctypes.c_double),
                 ("candidates", ctypes.c_uint32), ("slots", ctypes.c_uint32),
                 ("rho_reduced", ctypes.c_uint32), ("small_deg", ctypes.c_uint32), ("chunk", ctypes.c_uint32),
-                ("batch_mode", ctypes.c_uint32)]
+                ("batch_mode", ctypes.c_uint32), ("rho_warmup_steps", ctypes.c_uint32),
+                ("rho_warmup", ctypes.c_uint32)]
 
     def as_dict(self) -> dict:
         return {k: (float(getattr(self, k)) if k == "ms" else int(getattr(self, k))) for k, _ in self._fields_}
@@ -256,7 +258,8 @@ def make_options(seed: int = 0, timeout_ns: int = 0, max_steps: int = 0, ext_cou
                  trace_ptr: int = 0, trace_cap: int = 0, grid_limit: int = 0,
                  test_exit_block: int = 0, stats_out_ptr: int = 0,
                  solve_timeout_ns: int = 0, flags: int = 0, local_budget: int = 0,
-                 shape: int = 0, rho_reduced: int = 0, small_deg: int = 0, chunk: int = 0) -> sssp_options:
+                 shape: int = 0, rho_reduced: int = 0, small_deg: int = 0, chunk: int = 0,
+                 rho_warmup_steps: int = 0, rho_warmup: int = 0) -> sssp_options:
     o = sssp_options()
     o.seed, o.timeout_ns, o.max_steps = seed, timeout_ns, max_steps
     o.ext_count = ext_count_ptr or None
@@ -268,6 +271,7 @@ def make_options(seed: int = 0, timeout_ns: int = 0, max_steps: int = 0, ext_cou
     o.local_budget = local_budget
     o.shape = shape
     o.rho_reduced, o.small_deg, o.chunk = rho_reduced, small_deg, chunk
+    o.rho_warmup_steps, o.rho_warmup = rho_warmup_steps, rho_warmup
     return o
 
 

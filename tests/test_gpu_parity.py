@@ -415,3 +415,37 @@ def test_fused_super_sparse_steps(lib):
                 assert np.all(rec["queued"] >= 1)
         G.close()
     assert ended_with_recheck > 0
+
+
+def test_rho_warmup_steps(lib):
+    """rho-Stepping warm-up steps (the first steps at a small rho, without the
+    dense-step reduction): distances equal the oracle's on power-law, grid and
+    road-like graphs, in both layouts and shapes, with bidirectional, local
+    relaxation and fused steps; a count without a rho (or the reverse) is
+    refused."""
+    sym = lib.SSSP_GRAPH_SYMMETRIC | lib.SSSP_GRAPH_VERIFY
+    graphs = [(gg.rmat(15, 16, gen_seed=51, wseed=52), sym | lib.SSSP_GRAPH_REORDER),
+              (gg.rmat(14, 16, gen_seed=53, wseed=54), 0), (gg.grid(60, 70, wseed=55), sym),
+              (gg.road(120, 0.75, seed=56), sym)]
+    for g, gflags in graphs:
+        G = lib.Graph(g, gflags)
+        for s in gg.pick_sources(g, 2, 57):
+            want = oracle.dijkstra(g, s)
+            for ws, wr, red in ((1, 1, 0), (3, 16, 6), (6, 256, 6), (8, 256, 2), (50, 64, 0)):
+                for kw in (dict(), dict(shape=lib.SSSP_SHAPE_NARROW), dict(local_budget=64),
+                           dict(shape=lib.SSSP_SHAPE_NARROW, flags=lib.SSSP_SOLVE_FUSED, local_budget=256)):
+                    kw = dict(kw)
+                    if gflags & lib.SSSP_GRAPH_SYMMETRIC:
+                        kw["flags"] = kw.get("flags", 0) | lib.SSSP_SOLVE_BIDIRECTIONAL
+                    o = lib.make_options(rho_reduced=red, rho_warmup_steps=ws, rho_warmup=wr, **kw)
+                    for rho in (64, max(64, g.n // 16)):
+                        got, st = solve(lib, g, s, 0, rho, opts=o, G=G)
+                        assert st["status"] == 0 and np.array_equal(got, want), (g.name, s, ws, wr, red, kw, rho)
+        G.close()
+    g = gg.grid(8, 8)
+    G = lib.Graph(g)
+    dist = torch.empty(g.n, dtype=torch.int64, device="cuda")
+    for kw in ({"rho_warmup_steps": 3}, {"rho_warmup": 64}):
+        rc = lib.sssp_solve_ex(G.handle, 0, 0, 64, dist.data_ptr(), lib.make_options(**kw), 0, check=False)
+        assert rc == lib.SSSP_ERR_INVALID_ARG, kw
+    G.close()

@@ -77,6 +77,8 @@ def _L():
         lib.oracle_hops.restype = i64
         lib.oracle_rho_extdist.argtypes = [P, u32, P, u32, u64, u64, u64, u32, u32]
         lib.oracle_rho_extdist.restype = u64
+        lib.oracle_rho_extdist_capped.argtypes = [P, u32, P, u32, u64, u64, u64, u32, u32, u32]
+        lib.oracle_rho_extdist_capped.restype = u64
         lib.oracle_delta_extdist.argtypes = [ctypes.POINTER(u64), u64, u64]
         lib.oracle_delta_extdist.restype = u64
         lib.oracle_delta_theta.argtypes = [ctypes.POINTER(u64), u64, u64]
@@ -157,11 +159,15 @@ def hops(g, s: int) -> tuple[np.ndarray, int]:
 
 
 def rho_extdist(queue: np.ndarray, dist: np.ndarray, n: int, rho: int, seed: int, step: int,
-                dense_before: int, reduced: int = 2) -> int:
-    """reduced: how many dense steps use rho/10 (Sec. 6 uses the first two)."""
+                dense_before: int, reduced: int = 2, max_samples: int = 0) -> int:
+    """reduced: how many dense steps use rho/10 (Sec. 6 uses the first two);
+    max_samples: cap on the sample count (0 = 4096, the default rule)."""
     queue = np.ascontiguousarray(queue, dtype=np.uint32)
     dist = np.ascontiguousarray(dist, dtype=np.uint64)
     qp = queue.ctypes.data if queue.size else np.zeros(1, np.uint32).ctypes.data
+    if max_samples:
+        return int(_L().oracle_rho_extdist_capped(qp, queue.size, dist.ctypes.data, n, rho, seed, step,
+                                                  dense_before, reduced, max_samples))
     return int(_L().oracle_rho_extdist(qp, queue.size, dist.ctypes.data, n, rho, seed, step,
                                        dense_before, reduced))
 

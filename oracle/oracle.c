@@ -313,6 +313,7 @@ int64_t oracle_hops(uint32_t n, const uint64_t* off, const uint32_t* tgt,
 /* Upper bound on the rho-sampler's sample count (a reading: the paper only
  * says s = O(n/rho + log n); the cap bounds the sort). */
 #define ORC_MAX_SAMPLES 4096u
+#define ORC_WARM_SAMPLES 1024u  /* sample cap of the warm-up steps of oracle_stepping */
 
 static uint64_t floor_log2_u64(uint64_t x) /* x >= 1 */
 {
@@ -352,10 +353,29 @@ static int cmp_u64(const void* a, const void* b)
  *   - when q <= rho' every queued vertex is extracted; theta = UINT64_MAX
  *     selects exactly the same set as the largest queued key.
  */
+uint64_t oracle_rho_extdist_capped(const uint32_t* queue, uint32_t q, const uint64_t* dist,
+                                   uint32_t n, uint64_t rho, uint64_t seed, uint64_t step,
+                                   uint32_t dense_before, uint32_t reduced, uint32_t max_samples);
+
 uint64_t oracle_rho_extdist(const uint32_t* queue, uint32_t q, const uint64_t* dist,
                             uint32_t n, uint64_t rho, uint64_t seed, uint64_t step,
                             uint32_t dense_before, uint32_t reduced)
 {
+    return oracle_rho_extdist_capped(queue, q, dist, n, rho, seed, step, dense_before, reduced,
+                                     ORC_MAX_SAMPLES);
+}
+
+/*
+ * The same rule with the sample count capped at max_samples (1 ..
+ * ORC_MAX_SAMPLES) instead of 4096: s = min(max_samples, 10 * (ceil(q/rho')
+ * + 1 + floor(log2(q+1)))), the rank taken from that s.  The warm-up steps of
+ * oracle_stepping use 1024 (a reading of this library, see oracle_stepping).
+ */
+uint64_t oracle_rho_extdist_capped(const uint32_t* queue, uint32_t q, const uint64_t* dist,
+                                   uint32_t n, uint64_t rho, uint64_t seed, uint64_t step,
+                                   uint32_t dense_before, uint32_t reduced, uint32_t max_samples)
+{
+    if (max_samples < 1 || max_samples > ORC_MAX_SAMPLES) max_samples = ORC_MAX_SAMPLES;
     uint64_t rho_eff = rho;
     if ((uint64_t)q * 20u > (uint64_t)n && dense_before < reduced) {
         rho_eff = rho / 10u;
@@ -363,7 +383,7 @@ uint64_t oracle_rho_extdist(const uint32_t* queue, uint32_t q, const uint64_t* d
     }
     if ((uint64_t)q <= rho_eff) return ORC_INF;
     uint64_t s = 10u * ((q + rho_eff - 1) / rho_eff + 1u + floor_log2_u64((uint64_t)q + 1u));
-    if (s > ORC_MAX_SAMPLES) s = ORC_MAX_SAMPLES;
+    if (s > max_samples) s = max_samples;
     uint64_t keys[ORC_MAX_SAMPLES];
     for (uint64_t j = 0; j < s; ++j) {
         uint64_t h = oracle_splitmix64(seed, (step << 32) | j);
@@ -442,8 +462,9 @@ enum { ORC_RHO = 0, ORC_DELTA_STAR = 1, ORC_BELLMAN_FORD = 2, ORC_DELTA = 3, ORC
  *   ORC_RHO          theta from oracle_rho_extdist (param = rho >= 1;
  *                    rho_reduced = dense steps that use rho/10, the paper's 2;
  *                    the first warm_steps steps use rho = warm_rho instead,
- *                    without the reduction, and are not counted as dense
- *                    steps -- warm_steps = 0 is the paper's schedule)
+ *                    without the reduction, from at most 1024 samples, and
+ *                    are not counted as dense steps -- warm_steps = 0 is the
+ *                    paper's schedule)
  *   ORC_DELTA_STAR   theta from oracle_delta_extdist (param = Delta >= 1)
  *   ORC_BELLMAN_FORD theta = +infinity (param ignored)
  *   ORC_DELTA        theta = i*Delta with FinishCheck (oracle_delta_theta /
@@ -498,7 +519,7 @@ int oracle_stepping(uint32_t n, const uint64_t* off, const uint32_t* tgt,
             theta = qmin;
         } else if (z.steps <= warm_steps) {
             /* warm-up step: rho = warm_rho, no dense-step reduction */
-            theta = oracle_rho_extdist(Q, qlen, dist, n, warm_rho, seed, z.steps, 0, 0);
+            theta = oracle_rho_extdist_capped(Q, qlen, dist, n, warm_rho, seed, z.steps, 0, 0, ORC_WARM_SAMPLES);
             if ((uint64_t)qlen <= warm_rho) z.partial_steps++; else z.full_steps++;
         } else {
             int dense = (uint64_t)qlen * 20u > (uint64_t)n;

@@ -329,10 +329,40 @@ def test_stepping_with_a_warm_up(warm_steps, warm_rho):
             assert st["partial_steps"] <= kn + 1
 
 
+def test_rho_extdist_sample_cap():
+    """The capped rule: a cap of 4096 (or one above the formula's count) is
+    the default rule; below it, theta is the rank floor(rho' s / q) of the
+    first s draws with s the cap -- checked against the draws themselves
+    (positions from the published generator), sorted here with a library sort."""
+    rng = np.random.default_rng(41)
+    for trial in range(60):
+        n = int(rng.integers(1000, 400000))
+        q = int(rng.integers(1, n + 1))
+        dist = rng.integers(0, 1 << 40, n, dtype=np.uint64)
+        queue = rng.permutation(n)[:q].astype(np.uint32)
+        rho = int([1, 7, 256, 5000][trial % 4])
+        seed, step = int(rng.integers(0, 1 << 62)), int(rng.integers(1, 100))
+        base = oracle.rho_extdist(queue, dist, n, rho, seed, step, 0, 0)
+        assert oracle.rho_extdist(queue, dist, n, rho, seed, step, 0, 0, max_samples=4096) == base
+        lg = int(math.floor(math.log2(q + 1)))
+        s_formula = min(4096, 10 * (-(-q // rho) + 1 + lg))
+        if q <= rho:
+            assert oracle.rho_extdist(queue, dist, n, rho, seed, step, 0, 0, max_samples=64) == INF
+            continue
+        assert oracle.rho_extdist(queue, dist, n, rho, seed, step, 0, 0, max_samples=s_formula) == base
+        for cap in (1, 100, 1024):
+            s = min(cap, s_formula)
+            pos = [(oracle.splitmix64(seed, (step << 32) | j) * q) >> 64 for j in range(s)]
+            keys = np.sort(dist[queue[pos]])
+            r = min(s - 1, rho * s // q)
+            assert oracle.rho_extdist(queue, dist, n, rho, seed, step, 0, 0, max_samples=cap) == int(keys[r])
+
+
 def test_warm_up_special_cases():
     """No warm-up steps is the paper's schedule (same thresholds, so the same
     steps and work); a warm-up covering the whole solve is rho-Stepping with
-    rho = warm_rho and no dense-step reduction; a warm-up with warm_rho = rho
+    rho = warm_rho and no dense-step reduction (where its sample count stays
+    under the warm-up cap of 1024); a warm-up with warm_rho = rho
     is the schedule whose reduced dense steps come only after it (with no
     reduced steps at all, the same as no warm-up)."""
     g = gg.rmat(12, 8, gen_seed=31, wseed=32)
@@ -342,7 +372,9 @@ def test_warm_up_special_cases():
         base = oracle.stepping(g, s, oracle.RHO, rho, seed=5, reduced=2)
         same = oracle.stepping(g, s, oracle.RHO, rho, seed=5, reduced=2, warm_steps=0, warm_rho=7)
         assert np.array_equal(base[0], same[0]) and base[1] == same[1]
-        for wr in (1, 3, 40):
+        # (warm-up steps draw at most 1024 samples; with rho_w >= 64 on 4,096
+        # vertices the default rule draws no more: 10 (4096/64 + 1 + 12) < 1024)
+        for wr in (64, 100, 300):
             all_warm = oracle.stepping(g, s, oracle.RHO, rho, seed=5, reduced=6, warm_steps=10 ** 6, warm_rho=wr)
             plain = oracle.stepping(g, s, oracle.RHO, wr, seed=5, reduced=0)
             assert np.array_equal(all_warm[0], d) and all_warm[1] == plain[1], (rho, wr)

@@ -265,7 +265,9 @@ int sssp_last_stats(const sssp_graph* g, sssp_stats* out, void* stream);
  * theta to *theta_out (device uint64).  n is the vertex count, step the
  * 1-based step number, dense_before the number of earlier dense steps and
  * reduced the number of dense steps that use rho/10 (the exact count: 2 is
- * the paper's).  The sample count s, its cap of 4096, the sample positions
+ * the paper's); max_samples caps the sample count (0 = 4096, the solve's
+ * rule; its warm-up steps use 1024 with dense_before beyond reduced; at most
+ * 4096, INVALID_ARG above).  The sample count s, its cap, the sample positions
  * (splitmix64 output step*2^32 + j from state `seed`, reduced by
  * multiply-high), the rank floor(rho'*s/q) and the dense-step rule (rho' =
  * max(1, rho/10) when 20*q > n and dense_before < reduced) are those of the
@@ -274,7 +276,7 @@ int sssp_last_stats(const sssp_graph* g, sssp_stats* out, void* stream);
  */
 int sssp_rho_threshold(const uint32_t* queue, uint32_t q, const uint64_t* dist, uint32_t n,
                        uint64_t rho, uint64_t seed, uint64_t step, uint32_t dense_before,
-                       uint32_t reduced, uint64_t* theta_out, void* stream);
+                       uint32_t reduced, uint32_t max_samples, uint64_t* theta_out, void* stream);
 
 /* ------------------------------------------------------------------------ */
 /* Batched solves: many independent instances of the stepping loop (each its */

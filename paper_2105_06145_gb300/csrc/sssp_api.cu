@@ -498,10 +498,12 @@ int sssp_solve_host_ex(const sssp_graph* gc, uint32_t source, sssp_algo algo, ui
 }
 
 int sssp_rho_threshold(const uint32_t* queue, uint32_t q, const uint64_t* dist, uint32_t n, uint64_t rho,
-                       uint64_t seed, uint64_t step, uint32_t dense_before, uint32_t reduced, uint64_t* theta_out,
-                       void* stream)
+                       uint64_t seed, uint64_t step, uint32_t dense_before, uint32_t reduced,
+                       uint32_t max_samples, uint64_t* theta_out, void* stream)
 {
     if ((q > 0 && !queue) || !dist || !theta_out || n == 0 || rho == 0 || q > n) return SSSP_ERR_INVALID_ARG;
+    if (max_samples > kMaxSamples) return SSSP_ERR_INVALID_ARG;
+    if (max_samples == 0) max_samples = kMaxSamples;
     static uint32_t* d_err = nullptr;
     static std::mutex mu;
     {
@@ -511,8 +513,8 @@ int sssp_rho_threshold(const uint32_t* queue, uint32_t q, const uint64_t* dist, 
             if (e != cudaSuccess) { d_err = nullptr; return cuda_fail(e); }
         }
     }
-    cudaError_t e = launch_rho_threshold(queue, q, dist, n, rho, seed, step, dense_before, reduced, theta_out,
-                                         d_err, reinterpret_cast<cudaStream_t>(stream));
+    cudaError_t e = launch_rho_threshold(queue, q, dist, n, rho, seed, step, dense_before, reduced, max_samples,
+                                         theta_out, d_err, reinterpret_cast<cudaStream_t>(stream));
     return e == cudaSuccess ? SSSP_OK : cuda_fail(e);
 }
 

@@ -223,13 +223,15 @@ __device__ __forceinline__ uint64_t block_reduce_min64(uint64_t x, uint64_t* s_t
 //
 // Sample count s, rank r and the effective rho' of a step with q queued ids:
 // rho' = max(1, rho/10) in the first `reduced` dense steps (20 q > n; the
-// paper uses the first two), else rho; s = min(4096, 10 (ceil(q/rho') + 1 +
-// floor(log2(q+1)))); r = min(s-1, floor(rho' s / q)); theta is the r-th
-// smallest (0-based) of the s sampled keys.  Returns false when q <= rho'
-// (theta = +inf: extract every queued id).
+// paper uses the first two), else rho; s = min(max_samples, 10 (ceil(q/rho')
+// + 1 + floor(log2(q+1)))) with max_samples 4096 (1024 in warm-up steps);
+// r = min(s-1, floor(rho' s / q)); theta is the r-th smallest (0-based) of the
+// s sampled keys.  Returns false when q <= rho' (theta = +inf: extract every
+// queued id).
 // ---------------------------------------------------------------------------
 __device__ __forceinline__ bool rho_sample_plan(uint32_t q, uint32_t n, uint64_t rho, uint32_t dense_before,
-                                                uint32_t reduced, uint32_t* s_out, uint32_t* r_out)
+                                                uint32_t reduced, uint32_t* s_out, uint32_t* r_out,
+                                                uint32_t max_samples = kMaxSamples)
 {
     uint64_t rho_eff = rho;
     if ((uint64_t)q * 20ull > (uint64_t)n && dense_before < reduced) {
@@ -239,7 +241,7 @@ __device__ __forceinline__ bool rho_sample_plan(uint32_t q, uint32_t n, uint64_t
     if ((uint64_t)q <= rho_eff) return false;
     const uint64_t lg = 63u - (uint32_t)__clzll((long long)((uint64_t)q + 1ull));
     uint64_t s = 10ull * (((uint64_t)q + rho_eff - 1ull) / rho_eff + 1ull + lg);
-    if (s > kMaxSamples) s = kMaxSamples;
+    if (s > max_samples) s = max_samples;
     uint64_t r = rho_eff * s / (uint64_t)q;
     if (r > s - 1) r = s - 1;
     *s_out = (uint32_t)s;
@@ -317,10 +319,11 @@ __device__ __forceinline__ uint64_t block_select(uint64_t x, uint32_t s, uint32_
 // point; the solve kernel runs the same steps with its Extract loads in flight).
 static __device__ __noinline__ uint64_t rho_extdist_block(const uint32_t* Q, uint32_t q, const uint64_t* dist, uint32_t n,
                                       uint64_t rho, uint64_t seed, uint64_t step, uint32_t dense_before,
-                                      uint32_t reduced, uint64_t* skeys, uint32_t cap, int* err)
+                                      uint32_t reduced, uint64_t* skeys, uint32_t cap, int* err,
+                                      uint32_t max_samples = kMaxSamples)
 {
     uint32_t s, r;
-    if (!rho_sample_plan(q, n, rho, dense_before, reduced, &s, &r)) return kInf;  // extract every queued vertex
+    if (!rho_sample_plan(q, n, rho, dense_before, reduced, &s, &r, max_samples)) return kInf;  // extract every queued vertex
     uint64_t x = kInf;
     if (s <= blockDim.x) {
         if (threadIdx.x < s) x = ldcg64(&dist[ldcg32(&Q[rho_sample_pos(seed, step, threadIdx.x, q)])]);

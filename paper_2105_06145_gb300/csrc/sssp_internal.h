@@ -38,6 +38,7 @@ constexpr uint32_t kRhoReducedDefault = 2;  // dense steps with rho/10 (Sec. 6)
 constexpr int kExtractItems = SSSP_EXTRACT_ITEMS;  // batched kernels: queue entries per thread per extract tile
 constexpr int kStage = 512;                 // per-warp staging slots for re-queued ids
 constexpr uint32_t kMaxSamples = 4096;      // cap on the rho sampler's sample count
+constexpr uint32_t kWarmSamples = 1024;     // ... in rho-Stepping's warm-up steps
 constexpr uint64_t kInf = ~0ull;
 
 // Dynamic shared memory.  Per warp kStage re-queue staging slots (relaxation
@@ -159,7 +160,7 @@ int solve_kernel_threads();             // threads per block of this build of th
 unsigned int solve_kernel_smem();       // its dynamic shared memory per block
 cudaError_t launch_rho_threshold(const uint32_t* queue, uint32_t q, const uint64_t* dist,
                                  uint32_t n, uint64_t rho, uint64_t seed, uint64_t step,
-                                 uint32_t dense_before, uint32_t reduced, uint64_t* theta_out,
+                                 uint32_t dense_before, uint32_t reduced, uint32_t max_samples, uint64_t* theta_out,
                                  uint32_t* err_out, cudaStream_t st);
 uint32_t rho_sample_bound(uint32_t n, uint64_t rho);   // power-of-two smem keys needed
 

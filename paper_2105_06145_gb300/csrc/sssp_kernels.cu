@@ -197,11 +197,11 @@ __global__ void __launch_bounds__(kBlock, kMinBlocks) solve_kernel(SolveParams p
             // rho-Stepping: theta is selected from s sampled keys in the first
             // Extract round below, with that round's loads in flight
             theta = kInf;
-            // (warm-up steps: rho = warm_rho, no dense-step reduction, not
-            // counted as dense steps)
+            // (warm-up steps: rho = warm_rho, at most 1024 samples, no
+            // dense-step reduction, not counted as dense steps)
             const bool warm = k <= p.warm_steps;
             rho_sample = rho_sample_plan(q, n, warm ? p.warm_rho : p.param, warm ? 0xFFFFFFFFu : dense_seen,
-                                         p.rho_reduced, &s_cnt, &r_idx);
+                                         p.rho_reduced, &s_cnt, &r_idx, warm ? kWarmSamples : kMaxSamples);
             if ((uint64_t)q * 20ull > (uint64_t)n && !warm) ++dense_seen;
         }
 
@@ -736,14 +736,15 @@ __global__ void __launch_bounds__(kBlock) rho_threshold_kernel(const uint32_t* q
                                                                const uint64_t* dist, uint32_t n,
                                                                uint64_t rho, uint64_t seed, uint64_t step,
                                                                uint32_t dense_before, uint32_t reduced,
-                                                               uint64_t* theta_out, uint32_t* err_out, uint32_t cap)
+                                                               uint32_t max_samples, uint64_t* theta_out,
+                                                               uint32_t* err_out, uint32_t cap)
 {
     extern __shared__ uint64_t s_keys[];
     __shared__ int s_e;
     if (threadIdx.x == 0) s_e = 0;
     __syncthreads();
     const uint64_t th = rho_extdist_block(queue, q, dist, n, rho, seed, step, dense_before, reduced, s_keys, cap,
-                                          &s_e);
+                                          &s_e, max_samples);
     __syncthreads();
     if (threadIdx.x == 0) {
         *theta_out = th;
@@ -766,7 +767,8 @@ uint32_t rho_sample_bound(uint32_t n, uint64_t rho)
 
 cudaError_t launch_rho_threshold(const uint32_t* queue, uint32_t q, const uint64_t* dist, uint32_t n,
                                  uint64_t rho, uint64_t seed, uint64_t step, uint32_t dense_before,
-                                 uint32_t reduced, uint64_t* theta_out, uint32_t* err_out, cudaStream_t st)
+                                 uint32_t reduced, uint32_t max_samples, uint64_t* theta_out, uint32_t* err_out,
+                                 cudaStream_t st)
 {
     const uint32_t cap = kMaxSamples;
     static bool attr_set = false;
@@ -777,8 +779,8 @@ cudaError_t launch_rho_threshold(const uint32_t* queue, uint32_t q, const uint64
         attr_set = true;
     }
     rho_threshold_kernel<<<1, kBlock, cap * sizeof(uint64_t), st>>>(queue, q, dist, n, rho, seed, step,
-                                                                    dense_before, reduced, theta_out, err_out,
-                                                                    cap);
+                                                                    dense_before, reduced, max_samples, theta_out,
+                                                                    err_out, cap);
     return cudaGetLastError();
 }
 

@@ -98,7 +98,7 @@ _lib.sssp_last_status.argtypes = [_P, _P]
 _lib.sssp_last_status.restype = _i32
 _lib.sssp_last_stats.argtypes = [_P, ctypes.POINTER(sssp_stats), _P]
 _lib.sssp_last_stats.restype = _i32
-_lib.sssp_rho_threshold.argtypes = [_P, _u32, _P, _u32, _u64, _u64, _u64, _u32, _u32, _P, _P]
+_lib.sssp_rho_threshold.argtypes = [_P, _u32, _P, _u32, _u64, _u64, _u64, _u32, _u32, _u32, _P, _P]
 _lib.sssp_rho_threshold.restype = _i32
 _lib.sssp_solve_noalloc.argtypes = [_u32, _u64, _P, _P, _u32, _i32, _u64, _P, _P, _P]
 _lib.sssp_solve_noalloc.restype = _i32
@@ -307,9 +307,10 @@ def sssp_last_stats(g: int, stream: int = 0) -> dict:
 
 
 def sssp_rho_threshold(queue_ptr: int, q: int, dist_ptr: int, n: int, rho: int, seed: int,
-                       step: int, dense_before: int, reduced: int, theta_out_ptr: int, stream: int = 0) -> int:
+                       step: int, dense_before: int, reduced: int, theta_out_ptr: int, stream: int = 0,
+                       max_samples: int = 0) -> int:
     return _check(_lib.sssp_rho_threshold(queue_ptr or None, q, dist_ptr, n, rho, seed, step,
-                                          dense_before, reduced, theta_out_ptr, stream or None),
+                                          dense_before, reduced, max_samples, theta_out_ptr, stream or None),
                   "sssp_rho_threshold")
 
 

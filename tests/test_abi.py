@@ -44,7 +44,7 @@ def test_host_validation_without_gpu():
     with pytest.raises(sssp.SSSPError):
         sssp.sssp_graph_create(0, 0, np.zeros(1, np.uint64), tgt, w)
     assert sssp._lib.sssp_solve(None, 0, 0, 1, None, None) == sssp.SSSP_ERR_INVALID_ARG
-    assert sssp._lib.sssp_rho_threshold(None, 4, None, 8, 1, 0, 1, 0, 2, None, None) == \
+    assert sssp._lib.sssp_rho_threshold(None, 4, None, 8, 1, 0, 1, 0, 2, 0, None, None) == \
         sssp.SSSP_ERR_INVALID_ARG
     assert sssp.sssp_status_string(sssp.SSSP_ERR_TIMEOUT) == "device-wide wait timed out"
 

@@ -211,13 +211,14 @@ def test_rho_threshold_matches_oracle(lib):
         step = int(rng.integers(1, 1000))
         dense_before = int(trial % 4)
         reduced = [2, 0, 6, 3, 1][trial % 5]  # dense steps that use rho/10 (the paper's 2)
-        want = oracle.rho_extdist(queue, dist, n, rho, seed, step, dense_before, reduced)
+        cap = [0, 1024, 0, 100, 4096, 1][trial % 6]  # sample cap (0: 4096; warm-up steps: 1024)
+        want = oracle.rho_extdist(queue, dist, n, rho, seed, step, dense_before, reduced, max_samples=cap)
         dq = torch.from_numpy(queue.view(np.int32).copy()).cuda() if q else torch.zeros(1, dtype=torch.int32, device="cuda")
         dd = torch.from_numpy(dist.view(np.int64).copy()).cuda()
         lib.sssp_rho_threshold(dq.data_ptr(), q, dd.data_ptr(), n, rho, seed, step, dense_before, reduced,
-                               out.data_ptr(), stream)
+                               out.data_ptr(), stream, max_samples=cap)
         got = int(out.cpu().numpy().view(np.uint64)[0])
-        assert got == want, (trial, n, q, rho, reduced)
+        assert got == want, (trial, n, q, rho, reduced, cap)
 
 
 def test_timeout_is_reported_not_hung(lib):

@@ -512,8 +512,8 @@ typedef struct {
  * with local budgets 64, 256, 1024 and in the narrow shape with
  * SSSP_SOLVE_FUSED and local budgets 0, 64, 256, 1024; for a rho winner the
  * count of dense steps at rho/10 (2, 4, 6, 8, none), then 4, 6 or 8 warm-up
- * steps at rho 256 (rho_warmup_steps; with that count, 2 or 6 reduced dense
- * steps after them); the degree-bin cut-offs
+ * steps at rho 256 (rho_warmup_steps; with that count, 2, 4 or 6 reduced
+ * dense steps after them); the degree-bin cut-offs
  * (small_deg 16, 32, 64, then chunk 128, 256, 512); the winner is re-timed on
  * all k sources.
  * Bidirectional relaxation is used when the graph was created

@@ -22,7 +22,7 @@
 //   4. rho-Stepping winner: the number of dense steps that use rho/10 (the
 //      paper's 2, then 4, 6, 8 and none), then 4, 6 or 8 warm-up steps at
 //      rho = 256 (sssp_options.rho_warmup_steps), each with the count found,
-//      2 or 6 reduced dense steps after it;
+//      2, 4 or 6 reduced dense steps after it;
 //   5. the degree-bin cut-offs: small-degree bound 16 and 64 (default 32),
 //      then chunk records of 128 and 512 edges (default 256);
 //   6. the winner on every sample source (sssp_tuning.ms).
@@ -269,7 +269,7 @@ int sssp_autotune_ex(sssp_graph* g, const uint32_t* sources, uint32_t k, uint32_
             // small groups); each count of reduced dense steps again after it
             const Candidate base2 = best;
             for (uint32_t ws : {4u, 6u, 8u}) {
-                for (uint32_t red : {base2.rho_reduced, 2u, 6u}) {
+                for (uint32_t red : {base2.rho_reduced, 2u, 4u, 6u}) {
                     Candidate c = base2;
                     c.warm_steps = ws;
                     c.warm_rho = 256;

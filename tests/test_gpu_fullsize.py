@@ -53,8 +53,9 @@ def test_rmat22_all_rules(lib):
     for red, sd, ch in ((6, 0, 0), (4, 64, 512), (8, 16, 128)):
         o = lib.make_options(flags=lib.SSSP_SOLVE_BIDIRECTIONAL, rho_reduced=red, small_deg=sd, chunk=ch)
         _run(lib, g, [s] + extra, [(0, 1 << 18), (0, 1 << 19)], bench_flags, o)
-    # ... and the benchmark's warm-up steps (6 steps at rho = 256), and others
-    for ws, wr, red in ((6, 256, 6), (8, 256, 2), (4, 1024, 6)):
+    # ... and the benchmark's warm-up steps (8 steps at rho = 256, then 4
+    # dense steps at rho/10), and others
+    for ws, wr, red in ((8, 256, 4), (6, 256, 6), (4, 1024, 2)):
         o = lib.make_options(flags=lib.SSSP_SOLVE_BIDIRECTIONAL, rho_reduced=red, rho_warmup_steps=ws, rho_warmup=wr)
         _run(lib, g, [s] + extra, [(0, 1 << 18)], bench_flags, o)
 

@@ -499,7 +499,8 @@ typedef struct {
     uint32_t small_deg;      /* sssp_options.small_deg (0 = 32; single solves only)         */
     uint32_t chunk;          /* sssp_options.chunk (0 = 256; single solves only)            */
     uint32_t batch_mode;     /* batch autotuner: SSSP_BATCH_SHARED or SSSP_BATCH_SEPARATE   */
-    uint32_t rho_warmup_steps; /* sssp_options.rho_warmup_steps (single solves only)        */
+    uint32_t rho_warmup_steps; /* sssp_options.rho_warmup_steps (single solves and
+                                shared-scan batches; the separate-instance kernel ignores it) */
     uint32_t rho_warmup;     /* sssp_options.rho_warmup                                     */
 } sssp_tuning;
 
@@ -536,7 +537,8 @@ int sssp_autotune_ex(sssp_graph* g, const uint32_t* sources, uint32_t k, uint32_
    sssp_autotune's first stage (rules: as sssp_autotune_ex), each timed as one
    sssp_solve_sources launch over up to 8 of the sources, the two best of each
    rule re-timed on all k (for k <= 64 also with one shared edge scan,
-   SSSP_BATCH_SHARED); on graphs of >= 2^20 vertices and mean degree < 20
+   SSSP_BATCH_SHARED, with 2 or 6 reduced dense steps, or 8 warm-up steps at
+   rho 256 and 4 reduced steps); on graphs of >= 2^20 vertices and mean degree < 20
    local budgets 0, 64, 256 for each of those of the separate-instance
    kernel; for a rho winner the count of dense steps at rho/10 (4, 6, 8,
    none); then the winner's throughput

@@ -1129,7 +1129,9 @@ int sssp_solve_sources_ex(const sssp_graph* g, const uint32_t* sources, uint32_t
         uint32_t red = kRhoReducedDefault;
         if (tuned && t.rho_reduced) red = t.rho_reduced == SSSP_RHO_REDUCED_NONE ? 0u : t.rho_reduced;
         const bool bidir = tuned && (t.flags & SSSP_SOLVE_BIDIRECTIONAL) && (g->flags & SSSP_GRAPH_SYMMETRIC);
-        const int rc = ms_solve_sources(g, sources, k, algo, params, outs.data(), red, bidir, stream);
+        const uint32_t ws = tuned ? t.rho_warmup_steps : 0u;
+        const uint64_t wr = tuned ? t.rho_warmup : 0u;
+        const int rc = ms_solve_sources(g, sources, k, algo, params, outs.data(), red, ws, wr, bidir, stream);
         if (rc == SSSP_OK) set_last_kind(g->device, kLastShared);
         return rc;
     }
@@ -1248,8 +1250,10 @@ int sssp_server_create(const sssp_graph* g, const sssp_server_config* cfg, sssp_
         uint32_t red = kRhoReducedDefault;
         if (btuned && bt.rho_reduced) red = bt.rho_reduced == SSSP_RHO_REDUCED_NONE ? 0u : bt.rho_reduced;
         const bool bidir = btuned && (bt.flags & SSSP_SOLVE_BIDIRECTIONAL);
-        const int rc = ms_server_create(g, s->S, s->algo, s->param, red, bidir, s->d_cmd, s->d_done, s->d_shared,
-                                        s->idle_ns, c.gang, c.gang_wait_ns, &s->ms);
+        const uint32_t ws = btuned ? bt.rho_warmup_steps : 0u;
+        const uint64_t wr = btuned ? bt.rho_warmup : 0u;
+        const int rc = ms_server_create(g, s->S, s->algo, s->param, red, ws, wr, bidir, s->d_cmd, s->d_done,
+                                        s->d_shared, s->idle_ns, c.gang, c.gang_wait_ns, &s->ms);
         if (rc != SSSP_OK) { sssp_server_destroy(s); return rc; }
         s->worker = std::thread(server_loop, s);
         *out = s;

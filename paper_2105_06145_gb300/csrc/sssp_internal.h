@@ -197,7 +197,7 @@ struct ServeShared {              // host-mapped
 struct MsServer;
 size_t ms_server_bytes(const sssp_graph* g, uint32_t S);
 int ms_server_create(const sssp_graph* g, uint32_t S, sssp_algo algo, uint64_t param, uint32_t rho_reduced,
-                     bool bidir, SlotCmd* d_cmd, SlotDone* d_done, ServeShared* d_shared, uint64_t idle_ns,
+                     uint32_t warm_steps, uint64_t warm_rho, bool bidir, SlotCmd* d_cmd, SlotDone* d_done, ServeShared* d_shared, uint64_t idle_ns,
                      uint32_t gang, uint64_t gang_wait_ns, MsServer** out);
 int ms_server_launch(MsServer* s, cudaStream_t st);
 int ms_server_status(MsServer* s);      // device status after the loop returned (synchronous)
@@ -207,8 +207,8 @@ void ms_server_destroy(MsServer* s);
 // per step (sssp_msbatch.cu): outs[i] receives instance i's distances.
 bool ms_batch_supported(sssp_algo algo, uint32_t k);
 int ms_solve_sources(const sssp_graph* g, const uint32_t* sources, uint32_t k, sssp_algo algo,
-                     const uint64_t* params, uint64_t* const* outs, uint32_t rho_reduced, bool bidir,
-                     void* stream);
+                     const uint64_t* params, uint64_t* const* outs, uint32_t rho_reduced, uint32_t warm_steps,
+                     uint64_t warm_rho, bool bidir, void* stream);
 int ms_last_stats(int dev, sssp_stats* out, uint32_t k, cudaStream_t st);
 constexpr uint32_t kMsRecEdges = 32;        // edges per relaxation record of the shared-scan kernel
 

@@ -69,7 +69,7 @@ struct MsInst {                       // per instance; zeroed before the launch
     unsigned long long delta_i;       // Delta*-Stepping bucket index
     unsigned long long queued, extracted, edges, updates;  // totals
     unsigned int last_step;           // steps the instance took
-    unsigned int pad;
+    unsigned int steps_run;           // steps run so far (rho-Stepping warm-up)
 };
 
 struct MsCtrl {
@@ -89,6 +89,8 @@ struct MsParams {
     uint32_t K;                       // instances
     uint32_t R;                       // row stride of D (multiple of 4, >= K)
     uint32_t rho_reduced;
+    uint32_t warm_steps;              // rho-Stepping: each instance's first warm_steps steps use
+    uint64_t warm_rho;                //   rho = warm_rho (at most 1024 samples, no dense reduction)
     uint64_t* D;                      // [n][R]
     uint64_t* QM;                     // [n] queue masks
     uint32_t* qa;                     // union lists [n]
@@ -197,10 +199,16 @@ __device__ void ms_phase_T(const MsParams& p, uint64_t k, uint32_t U, MsSmem& S,
             if (tid == 0) I->delta_i = cur + 1;
         } else if (q != 0 && p.algo == SSSP_RHO) {
             const uint32_t dense = ldcg32(&I->dense_seen);
-            uint64_t rho_eff = p.param[i];
-            if ((uint64_t)q * 20ull > (uint64_t)p.n && dense < p.rho_reduced) rho_eff = rho_eff / 10 ? rho_eff / 10 : 1;
+            // the instance's own step count: its first warm_steps steps use
+            // rho = warm_rho, without the dense-step reduction
+            const bool warm = ldcg32(&I->steps_run) < p.warm_steps;
+            const uint64_t rho_i = warm ? p.warm_rho : p.param[i];
+            uint64_t rho_eff = rho_i;
+            if (!warm && (uint64_t)q * 20ull > (uint64_t)p.n && dense < p.rho_reduced)
+                rho_eff = rho_eff / 10 ? rho_eff / 10 : 1;
             uint32_t s = 0, r = 0;
-            if (rho_sample_plan(q, p.n, p.param[i], dense, p.rho_reduced, &s, &r)) {
+            if (rho_sample_plan(q, p.n, rho_i, warm ? 0xFFFFFFFFu : dense, p.rho_reduced, &s, &r,
+                                warm ? kWarmSamples : kMaxSamples)) {
                 // uniform samples of Q_i: positions of the union list drawn
                 // uniformly (splitmix64, multiply-high), kept where the
                 // vertex carries bit i; at most kMsDraws draws
@@ -230,9 +238,12 @@ __device__ void ms_phase_T(const MsParams& p, uint64_t k, uint32_t U, MsSmem& S,
                 }
                 (void)r;
             }
-            if (tid == 0 && (uint64_t)q * 20ull > (uint64_t)p.n) I->dense_seen = dense + 1;
+            if (tid == 0 && (uint64_t)q * 20ull > (uint64_t)p.n && !warm) I->dense_seen = dense + 1;
         }
-        if (tid == 0) I->theta = theta;
+        if (tid == 0) {
+            I->theta = theta;
+            if (q != 0) I->steps_run += 1;
+        }
         __syncthreads();
     }
 }
@@ -1075,7 +1086,8 @@ bool ms_batch_supported(sssp_algo algo, uint32_t k)
 }
 
 int ms_solve_sources(const sssp_graph* g, const uint32_t* sources, uint32_t k, sssp_algo algo,
-                     const uint64_t* params, uint64_t* const* outs, uint32_t rho_reduced, bool bidir, void* stream)
+                     const uint64_t* params, uint64_t* const* outs, uint32_t rho_reduced, uint32_t warm_steps,
+                     uint64_t warm_rho, bool bidir, void* stream)
 {
     if (!g || !sources || !outs || !ms_batch_supported(algo, k)) return SSSP_ERR_INVALID_ARG;
     for (uint32_t i = 0; i < k; ++i) {
@@ -1139,6 +1151,8 @@ int ms_solve_sources(const sssp_graph* g, const uint32_t* sources, uint32_t k, s
     p.K = k;
     p.R = R;
     p.rho_reduced = rho_reduced;
+    p.warm_steps = warm_rho ? warm_steps : 0u;
+    p.warm_rho = warm_rho;
     p.bidir = (bidir && (g->flags & SSSP_GRAPH_SYMMETRIC)) ? 1u : 0u;
     p.inst = w.d_inst;
     p.ctrl = w.d_ctrl;
@@ -1200,7 +1214,7 @@ size_t ms_server_bytes(const sssp_graph* g, uint32_t S)
 }
 
 int ms_server_create(const sssp_graph* g, uint32_t S, sssp_algo algo, uint64_t param, uint32_t rho_reduced,
-                     bool bidir, SlotCmd* d_cmd, SlotDone* d_done, ServeShared* d_shared, uint64_t idle_ns,
+                     uint32_t warm_steps, uint64_t warm_rho, bool bidir, SlotCmd* d_cmd, SlotDone* d_done, ServeShared* d_shared, uint64_t idle_ns,
                      uint32_t gang, uint64_t gang_wait_ns, MsServer** out)
 {
     if (!g || !out || S == 0 || S > kMsMax || !ms_batch_supported(algo, S)) return SSSP_ERR_INVALID_ARG;
@@ -1235,6 +1249,8 @@ int ms_server_create(const sssp_graph* g, uint32_t S, sssp_algo algo, uint64_t p
     p.K = S;
     p.R = R;
     p.rho_reduced = rho_reduced;
+    p.warm_steps = warm_rho ? warm_steps : 0u;
+    p.warm_rho = warm_rho;
     p.bidir = (bidir && (g->flags & SSSP_GRAPH_SYMMETRIC)) ? 1u : 0u;
     p.src = m->sp.src_w;
     p.param = d_param;

@@ -446,12 +446,16 @@ int sssp_autotune_batch(sssp_graph* g, const uint32_t* sources, uint32_t k, uint
     // dense steps at rho/10
     if (rc == SSSP_OK && sssp::ms_batch_supported(SSSP_RHO, k)) {
         for (const sssp_tuning& f : finalists) {
-            for (uint32_t red : {0u, 6u}) {
-                if (red && f.algo != SSSP_RHO) continue;
+            for (uint32_t variant = 0; variant < 3; ++variant) {
+                // the paper's 2 reduced dense steps, 6, and 8 warm-up steps at
+                // rho 256 followed by 4
+                if (variant && f.algo != SSSP_RHO) continue;
                 sssp_tuning t = f;
                 t.batch_mode = SSSP_BATCH_SHARED;
                 t.local_budget = 0;
-                t.rho_reduced = red;
+                t.rho_reduced = variant == 0 ? 0u : variant == 1 ? 6u : 4u;
+                t.rho_warmup_steps = variant == 2 ? 8u : 0u;
+                t.rho_warmup = variant == 2 ? 256u : 0u;
                 if ((rc = time_batch(t, &ms)) != SSSP_OK) break;
                 ++timed;
                 if (ms < best_ms) { best_ms = ms; best = t; }

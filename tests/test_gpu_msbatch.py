@@ -152,3 +152,34 @@ def test_shared_scan_bidirectional(lib):
                 for i, s in enumerate(srcs):
                     assert np.array_equal(got[i], oracle.dijkstra(g, s)), (g.name, extra, algo, i)
             G.close()
+
+
+def test_shared_scan_warmup_steps(lib):
+    """rho-Stepping warm-up steps in the shared scan (each instance's first
+    steps at a small rho, counted per instance, so that queries admitted to
+    the server at different steps each get their own): every instance of a
+    batch and every served query equals the oracle."""
+    flags = lib.SSSP_GRAPH_SYMMETRIC | lib.SSSP_GRAPH_VERIFY
+    for g, extra in ((gg.rmat(15, 16, gen_seed=61, wseed=62), lib.SSSP_GRAPH_REORDER), (_hub_graph(30000, 9), 0),
+                     (gg.grid(50, 60, wseed=63), 0)):
+        G = lib.Graph(g, flags | extra)
+        srcs = gg.pick_sources(g, 37, 64)
+        for ws, wr, red in ((8, 256, 4), (3, 16, 0), (40, 1, 6)):
+            lib.sssp_graph_set_tuning(G.handle, {"algo": 0, "param": max(64, g.n // 16), "flags": 1,
+                                                 "batch_mode": lib.SSSP_BATCH_SHARED, "rho_reduced": red,
+                                                 "rho_warmup_steps": ws, "rho_warmup": wr})
+            got, _ = _run(lib, G, g, srcs, 0, None, lib.SSSP_BATCH_AUTO)
+            for i, s in enumerate(srcs):
+                assert np.array_equal(got[i], oracle.dijkstra(g, s)), (g.name, ws, wr, red, i)
+        # the server: queries admitted one by one (continuous admission)
+        srv = lib.sssp_server_create(G.handle, slots=8, algo=0, param=max(64, g.n // 16),
+                                     batch_mode=lib.SSSP_BATCH_SHARED, gang=1)
+        outs = [torch.full((g.n,), 3, dtype=torch.int64, device="cuda") for _ in srcs[:16]]
+        torch.cuda.synchronize()
+        tickets = [lib.sssp_server_submit(srv, s, o.data_ptr()) for s, o in zip(srcs[:16], outs)]
+        for t in tickets:
+            assert lib.sssp_server_wait(srv, t, 60_000_000_000)["status"] == 0
+        for s, o in zip(srcs[:16], outs):
+            assert np.array_equal(o.cpu().numpy().view(np.uint64), oracle.dijkstra(g, s)), (g.name, s)
+        lib.sssp_server_destroy(srv)
+        G.close()

@@ -500,7 +500,8 @@ typedef struct {
     uint32_t chunk;          /* sssp_options.chunk (0 = 256; single solves only)            */
     uint32_t batch_mode;     /* batch autotuner: SSSP_BATCH_SHARED or SSSP_BATCH_SEPARATE   */
     uint32_t rho_warmup_steps; /* sssp_options.rho_warmup_steps (single solves and
-                                shared-scan batches; the separate-instance kernel ignores it) */
+                                shared-scan batches; the separate-instance kernel and the
+                                server ignore it)                                          */
     uint32_t rho_warmup;     /* sssp_options.rho_warmup                                     */
 } sssp_tuning;
 
@@ -508,7 +509,8 @@ typedef struct {
  * Time candidate configurations on the k sample sources (HOST uint32[k], each
  * < n) and keep the fastest: rho in {n/4, n/8, ..., n/1024} (at least 64) and
  * Delta in mean-weight x {1/8, 1/4, ..., 8} in the wide shape on the first
- * source; the two best in both shapes on two sources; on graphs with mean
+ * source; the two best in both shapes on up to three sources (as every
+ * later stage); on graphs with mean
  * out-degree < 20 the three best parameters of each rule in the winning shape
  * with local budgets 64, 256, 1024 and in the narrow shape with
  * SSSP_SOLVE_FUSED and local budgets 0, 64, 256, 1024; for a rho winner the

@@ -1250,9 +1250,9 @@ int sssp_server_create(const sssp_graph* g, const sssp_server_config* cfg, sssp_
         uint32_t red = kRhoReducedDefault;
         if (btuned && bt.rho_reduced) red = bt.rho_reduced == SSSP_RHO_REDUCED_NONE ? 0u : bt.rho_reduced;
         const bool bidir = btuned && (bt.flags & SSSP_SOLVE_BIDIRECTIONAL);
-        const uint32_t ws = btuned ? bt.rho_warmup_steps : 0u;
-        const uint64_t wr = btuned ? bt.rho_warmup : 0u;
-        const int rc = ms_server_create(g, s->S, s->algo, s->param, red, ws, wr, bidir, s->d_cmd, s->d_done,
+        // (no warm-up steps in the server: under a stream of queries the
+        // warm-up cohorts served RMAT-22 at 325 queries/s against 507 without)
+        const int rc = ms_server_create(g, s->S, s->algo, s->param, red, 0u, 0u, bidir, s->d_cmd, s->d_done,
                                         s->d_shared, s->idle_ns, c.gang, c.gang_wait_ns, &s->ms);
         if (rc != SSSP_OK) { sssp_server_destroy(s); return rc; }
         s->worker = std::thread(server_loop, s);

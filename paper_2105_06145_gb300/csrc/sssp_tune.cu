@@ -14,7 +14,8 @@
 //   1. every rule/parameter candidate (rho = n/4 ... n/1024 and Delta = mean
 //      weight x 1/8 ... 8, factors of 2 apart), wide shape, no local
 //      relaxation, on the first sample source;
-//   2. the two fastest of (1) in both shapes, on up to two sources;
+//   2. the two fastest of (1) in both shapes, on up to three sources (as
+//      every later stage);
 //   3. sparse graphs (mean out-degree < 20): the three fastest of (1) of each
 //      rule, in the winning shape with local budgets 64, 256 and 1024, and in
 //      the narrow shape with fused super-sparse steps (SSSP_SOLVE_FUSED) with
@@ -212,8 +213,9 @@ int sssp_autotune_ex(sssp_graph* g, const uint32_t* sources, uint32_t k, uint32_
         for (size_t i = 0; i < sorted.size(); ++i)
             for (size_t j = i + 1; j < sorted.size(); ++j)
                 if (sorted[j].ms < sorted[i].ms) std::swap(sorted[i], sorted[j]);
-        // (2)
-        const uint32_t ns2 = k < 2 ? k : 2;
+        // (2) (and the later stages) on up to three sources: one or two sources
+        //     let the source's own cost decide between close candidates
+        const uint32_t ns2 = k < 3 ? k : 3;
         best.ms = INFINITY;
         for (size_t i = 0; i < 2 && i < sorted.size(); ++i)
             for (uint32_t shape : {SSSP_SHAPE_WIDE, SSSP_SHAPE_NARROW}) {

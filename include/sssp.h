@@ -122,9 +122,10 @@ typedef struct {
                                 of this in the edge array).  0 = 256; else 128, 256, 512
                                 or 1024.  Neither cut-off changes the distances.       */
     uint32_t rho_warmup_steps; /* rho-Stepping: the first rho_warmup_steps steps use
-                                rho = rho_warmup instead (without the dense-step
-                                reduction, and not counted among the dense steps of
-                                rho_reduced), so that the first, sparse waves -- which
+                                rho = rho_warmup instead, from at most 1024 samples
+                                (without the dense-step reduction, and not counted among
+                                the dense steps of rho_reduced), so that the first,
+                                sparse waves -- which
                                 on power-law graphs hold the high-degree vertices --
                                 advance in small, nearly ordered groups.  0 = none (the
                                 paper's schedule); rho_warmup must then be 0 too.  An

@@ -358,6 +358,24 @@ def test_rho_extdist_sample_cap():
             assert oracle.rho_extdist(queue, dist, n, rho, seed, step, 0, 0, max_samples=cap) == int(keys[r])
 
 
+def test_rho_extdist_capped_sample_order_statistic():
+    """The capped sample count, against order statistics: with distinct keys
+    0..q-1, rho = 256 and q in [300k, 500k], a cap of 1024 gives rank
+    floor(256 * 1024 / q) = 0, so theta is the smallest of 1024 uniform draws
+    and the extracted count theta + 1 averages (q + 1) / 1025.  (The uncapped
+    rule draws 4096 samples with rank 0-3 here, a wrong count or rank moves the
+    mean by a factor of 1.3 or more.)"""
+    rng = np.random.default_rng(5)
+    ratios = []
+    for _ in range(150):
+        q = int(rng.integers(300000, 500001))
+        dist = rng.permutation(q).astype(np.uint64)
+        queue = np.arange(q, dtype=np.uint32)
+        th = oracle.rho_extdist(queue, dist, 10 ** 7, 256, int(rng.integers(0, 1 << 62)), 1, 0, 0, max_samples=1024)
+        ratios.append((th + 1) / ((q + 1) / 1025))
+    assert 0.8 < float(np.mean(ratios)) < 1.2, np.mean(ratios)
+
+
 def test_warm_up_special_cases():
     """No warm-up steps is the paper's schedule (same thresholds, so the same
     steps and work); a warm-up covering the whole solve is rho-Stepping with
